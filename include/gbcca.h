@@ -1,0 +1,213 @@
+/*
+ * gbcca.h - C ABI of the GB300 (sm_103a) sketch-preconditioned Riemannian
+ * solver for regularized CCA and Fisher LDA on tall data (n >> d).
+ *
+ * Method: Shustin & Avron, "Faster Randomized Methods for Orthogonality
+ * Constrained Problems".  Problem statements: Def. 4.1 (CCA) and Def. 5.1
+ * (FDA).  Algorithm: Alg. 1 (CCA) and Alg. 2 (FDA) - sketch the data,
+ * factor the sketch preconditioner M = Z^T S^T S Z + lambda I as R^T R
+ * (Sec. 3), warm-start from the exact solution of the sketched problem, then
+ * run Riemannian CG on the generalized Stiefel manifold with the metric
+ * g(xi, eta) = tr(xi^T M eta) (Table 1).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  A data matrix of n rows and d columns with
+ *     leading dimension ld (elements, ld >= d) has element (i, j) at
+ *     base[i * ld + j].  Iterates U (dx x k), V (dy x k), W (d x k) are dense
+ *     row-major float64 with leading dimension k.
+ *   - Pointers named "device" must point to memory of the current CUDA device;
+ *     "host" pointers are plain CPU memory.  The library never frees memory
+ *     it did not allocate.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work of a call is ordered on that stream; a call
+ *     returns after its work is enqueued unless it says it synchronizes.
+ *   - Return value: GBCCA_OK (0) or a negative gbcca_status.  No C++
+ *     exception crosses this interface.  gbcca_last_error() gives a one-line
+ *     description of the most recent failure on the calling thread.
+ *   - A plan is not thread-safe: one thread at a time may use it.
+ */
+#ifndef GBCCA_H
+#define GBCCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbcca_plan_s* gbcca_plan_t;
+
+/* Storage type of the data matrices X, Y (the arithmetic type of the data
+ * pass is FP32 accumulate for BF16/FP32 data and FP64 for FP64 data). */
+enum gbcca_dtype { GBCCA_BF16 = 0, GBCCA_FP32 = 1, GBCCA_FP64 = 2 };
+
+/* Preconditioner M of the Riemannian metric.
+ *   COUNTSKETCH  M = (S Z)^T (S Z) + lambda I, S a CountSketch (Sec. 3).
+ *   SRHT         S a subsampled randomized Hadamard transform (App. A).
+ *   IDENTITY     M = I (no preconditioning; the "M = I" ablation of Sec. 6).
+ *   EXACT        M = Z^T Z + lambda I (the "M = Sigma" ablation of Sec. 6;
+ *                S = I, costs O(n d^2)). */
+enum gbcca_sketch {
+  GBCCA_SKETCH_COUNTSKETCH = 0,
+  GBCCA_SKETCH_SRHT = 1,
+  GBCCA_SKETCH_IDENTITY = 2,
+  GBCCA_SKETCH_EXACT = 3
+};
+
+enum gbcca_status {
+  GBCCA_OK = 0,
+  GBCCA_ERR_INVALID_ARG = -1,   /* bad shape, pointer or option           */
+  GBCCA_ERR_UNSUPPORTED = -2,   /* valid but not implemented (size limit) */
+  GBCCA_ERR_OOM = -3,           /* device allocation failed               */
+  GBCCA_ERR_NOT_SPD = -4,       /* a Cholesky pivot was not positive      */
+  GBCCA_ERR_MAXITER = -5,       /* max_iter reached; results are written  */
+  GBCCA_ERR_TIMEOUT = -6,       /* a bounded device wait ran out          */
+  GBCCA_ERR_CUDA = -7,          /* CUDA runtime error                     */
+  GBCCA_ERR_STATE = -8          /* call out of order (e.g. solve before precondition) */
+};
+
+/* Options of a plan.  Fill with gbcca_default_options() and override. */
+typedef struct {
+  int32_t sketch;        /* enum gbcca_sketch                                   */
+  int64_t s;             /* sketch rows; 0 = 4 (dx + dy) for CCA, 3 d for LDA   */
+  uint64_t seed;         /* seed of the library's own sketch draws              */
+  int32_t max_iter;      /* Riemannian CG iteration cap (default 1000)          */
+  double gtol;           /* stop when ||grad||_M <= gtol ||grad_0||_M (1e-8)    */
+  int32_t refine;        /* BF16/FP32 data: FP64 Rayleigh-Ritz refinement at the
+                            end (1, default) or none (0); ignored for FP64 data */
+  int32_t warm_start;    /* 1: start from the exact solution of the sketched
+                            problem (Alg. 1 step 4 / Alg. 2 step 5); 0: start
+                            from the U/V (W) buffers passed to the solve call  */
+  int32_t check_every;   /* iterations between convergence read-backs (8)      */
+} gbcca_options;
+
+/* Per-solve report (host struct filled by the solve calls). */
+typedef struct {
+  int32_t iters;         /* Riemannian CG iterations taken                      */
+  int32_t passes;        /* fused data passes over the n rows                   */
+  int32_t status;        /* gbcca_status of the solve                           */
+  int32_t stalled;       /* 1 if the line search found no decrease (f at its
+                            rounding floor), which also ends the iteration      */
+  double grad_norm;      /* ||grad||_M at the last iterate                      */
+  double grad_norm0;     /* ||grad||_M at the first iterate                     */
+  double objective;      /* f at the returned point (f_CCA or f_FDA)            */
+} gbcca_info;
+
+/* Fills `opt` with defaults (CountSketch, s = 0, seed 0, max_iter 1000,
+ * gtol 1e-8, refine 1, warm_start 1, check_every 8).  Returns GBCCA_OK or
+ * GBCCA_ERR_INVALID_ARG if opt is NULL. */
+int gbcca_default_options(gbcca_options* opt);
+
+/* Regularized CCA plan (Def. 4.1; Alg. 1 inputs: X n x dx, Y n x dy,
+ * s >= max(dx, dy)).  Validates shapes (1 <= k <= min(dx, dy) <= 1024,
+ * k <= 20, n >= max(dx, dy)), copies `opt` (host; NULL = defaults), allocates
+ * all device workspace (sketches, R factors, iterates, pass partials) on the
+ * current device, and writes the handle to *plan (host).  Returns
+ * GBCCA_ERR_OOM if the workspace does not fit. */
+int cca_plan(gbcca_plan_t* plan, int64_t n, int32_t dx, int32_t dy, int32_t k,
+             int32_t dtype, const gbcca_options* opt);
+
+/* Alg. 1 steps 2-5 (Sec. 3 preconditioner, Sec. 4.4): sketch X and Y with the
+ * same S, factor M_xx = R_x^T R_x and M_yy = R_y^T R_y in FP64 (R from the
+ * Cholesky factorization of the sketch Gram, which is the R factor of the QR
+ * of [S Z; sqrt(lambda) I]), and compute the warm start (exact CCA of the
+ * sketched pair, step 4).  X (n x dx, leading dimension ldx) and Y (n x dy,
+ * ldy) are device pointers of the plan's dtype; the caller owns them and must
+ * keep them valid and unchanged until the last cca_solve on this plan.
+ * lambda_x, lambda_y >= 0, and > 0 unless the sketch has full column rank.
+ * Optional explicit sketch randomness (device, may be NULL to let the
+ * library draw from opt.seed): CountSketch: h (int32, n entries in [0, s)),
+ * g (int8, n entries +-1); SRHT: h = sampled row indices (int32, s entries,
+ * distinct, in [0, n_pad)), g = signs (int8, n_pad entries), n_pad the
+ * power of two >= n.  Returns GBCCA_ERR_NOT_SPD if a factor breaks down. */
+int cca_precondition(gbcca_plan_t plan, const void* X, int64_t ldx, const void* Y, int64_t ldy,
+                     double lambda_x, double lambda_y, const int32_t* sketch_h,
+                     const int8_t* sketch_g, void* stream);
+
+/* Alg. 1 step 8: Riemannian CG for max tr(U^T Sxy V N) on
+ * St_Sxx(k, dx) x St_Syy(k, dy) with the metric of M (Sec. 4.2-4.4).
+ * mu (host, k entries, strictly decreasing, > 0; NULL = k, k-1, ..., 1) is
+ * the diagonal of N.  tol overrides opt.gtol when > 0.  U (dx x k), V (dy x k)
+ * and sigma (k) are device buffers (float64, caller-owned); with
+ * opt.warm_start = 0, U and V also provide the starting point.  On return
+ * sigma holds the canonical correlations sigma_1 >= ... >= sigma_k and U, V
+ * the canonical weights (U^T Sxx U = I, V^T Syy V = I, U^T Sxy V = diag(sigma)),
+ * from a final Rayleigh-Ritz step on the computed subspaces.  info (host,
+ * may be NULL) receives the report.  This call synchronizes `stream`
+ * every opt.check_every iterations to read the convergence flag.
+ * Returns GBCCA_OK, GBCCA_ERR_MAXITER (results still written) or an error. */
+int cca_solve(gbcca_plan_t plan, const double* mu, double tol, double* U, double* V,
+              double* sigma, gbcca_info* info, void* stream);
+
+/* Fisher LDA plan (Def. 5.1; Alg. 2 inputs X n x d, labels, s >= d).
+ * 2 <= n_classes <= 64, 1 <= k <= n_classes - 1, k <= 20, d <= 1024. */
+int lda_plan(gbcca_plan_t* plan, int64_t n, int32_t d, int32_t n_classes, int32_t k,
+             int32_t dtype, const gbcca_options* opt);
+
+/* Alg. 2 end to end: class statistics (S_B = Yhat^T Yhat and the class means
+ * that define Xhat, Sec. 5.1), sketch of Xhat, preconditioner, warm start
+ * (exact FDA of the sketch), Riemannian CG for max tr(W^T S_B W N) on
+ * St_{S_w + lambda I}(k, d), and a final Rayleigh-Ritz step.  X (device,
+ * n x d, ld), labels (device int32, n entries in [0, n_classes); every class
+ * must be non-empty), W (device float64, d x k; also the start when
+ * opt.warm_start = 0), rho (device float64, k: the generalized eigenvalues of
+ * (S_B, S_w + lambda I)), mu as for cca_solve, info (host, may be NULL).
+ * X and labels must stay valid until the call returns.  Synchronizes like
+ * cca_solve. */
+int lda_solve(gbcca_plan_t plan, const void* X, int64_t ldx, const int32_t* labels,
+              double lambda, const double* mu, double tol, const int32_t* sketch_h,
+              const int8_t* sketch_g, double* W, double* rho, gbcca_info* info, void* stream);
+
+/* One fused data pass (the per-iteration hot path, Sec. 4.4 / Cor. 4.6):
+ * with Phi_x (dx x 2k) and Phi_y (dy x 2k) device float64 row-major (columns
+ * [U, eta_U] and [V, eta_V]), computes in one sweep over the rows of the
+ * plan's X and Y (set by cca_precondition):
+ *   W = [X Phi_x, Y Phi_y] (n x 4k, kept on chip), Gx = X^T W (dx x 4k),
+ *   Gy = Y^T W (dy x 4k), Gram = W^T W (4k x 4k),
+ * written as float64 row-major device arrays (caller-owned).  Arithmetic is
+ * the plan's: FP64 for FP64 data, FP32 accumulation otherwise.  For an LDA
+ * plan (after lda_solve) the pass is the FDA one: Phi (d x 2k) in Phi_x,
+ * Phi_y ignored, W = Xhat Phi, Gx = Xhat^T W (d x 2k), Gram (2k x 2k), Gy
+ * unused.  Enqueued on `stream`; no synchronization. */
+int gbcca_fused_pass(gbcca_plan_t plan, const double* Phi_x, const double* Phi_y,
+                     double* Gx, double* Gy, double* Gram, void* stream);
+
+/* Copies an internal result of the last precondition / solve to `dst`
+ * (device float64 buffer of at least gbcca_query_size(plan, what) elements).
+ * Used to check each step of the method on its own. */
+enum gbcca_query {
+  GBCCA_Q_SKETCH_X = 0,   /* S X  (s x dx), or S Xhat for LDA              */
+  GBCCA_Q_SKETCH_Y = 1,   /* S Y  (s x dy)                                 */
+  GBCCA_Q_R_X = 2,        /* R_x  (dx x dx, upper triangular)              */
+  GBCCA_Q_R_Y = 3,        /* R_y  (dy x dy)                                */
+  GBCCA_Q_WARM_U = 4,     /* warm start U~ (dx x k) before qf_B            */
+  GBCCA_Q_WARM_V = 5,     /* warm start V~ (dy x k)                        */
+  GBCCA_Q_HISTORY = 6,    /* per iteration (f, ||grad||_M, t): 3 (max_iter+1) */
+  GBCCA_Q_CLASS_MEANS = 7 /* LDA class means (n_classes x d)               */
+};
+int64_t gbcca_query_size(gbcca_plan_t plan, int32_t what);
+int gbcca_query(gbcca_plan_t plan, int32_t what, double* dst, void* stream);
+
+/* Draws the library's own sketch randomness for `seed` (Sec. 3 CountSketch:
+ * h[n] in [0, s), g[n] = +-1; App. A SRHT: rows[s] distinct in [0, n_pad),
+ * signs[n_pad]) into device buffers.  Every value is a function of
+ * (seed, index) through SplitMix64 (Steele, Lea & Flood 2014):
+ * r = mix(seed + (i + 1) 0x9E3779B97F4A7C15); CountSketch h = ((r >> 32) s)
+ * >> 32, g = (r & 1) ? -1 : +1; SRHT signs from bit 0 of the stream at
+ * seed ^ 0xD1B54A32D192ED03, rows = pi(0..s-1) for a 4-round Feistel
+ * permutation pi of [0, n_pad) keyed by seed ^ 0x8CB92BA72F3D8DD7 (odd log2
+ * sizes use cycle walking).  kind = GBCCA_SKETCH_COUNTSKETCH (h: n entries,
+ * g: n entries) or GBCCA_SKETCH_SRHT (h: s rows, g: n signs, n a power of
+ * two). */
+int gbcca_sketch_draws(int32_t kind, int64_t n, int64_t s, uint64_t seed, int32_t* h,
+                       int8_t* g, void* stream);
+
+void gbcca_plan_destroy(gbcca_plan_t plan);
+const char* gbcca_status_string(int status);
+const char* gbcca_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBCCA_H */

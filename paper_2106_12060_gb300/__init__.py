@@ -1,0 +1,199 @@
+"""GB300 (sm_103a) sketch-preconditioned Riemannian CCA / Fisher LDA.
+
+Thin Python binding over libgbcca.so with the names of the C ABI
+(include/gbcca.h).  Device memory and streams come from PyTorch; every step
+of the method runs in the library's CUDA kernels.  Importing works without a
+GPU; calls need CUDA tensors on the current device.
+
+Method: Shustin & Avron, "Faster Randomized Methods for Orthogonality
+Constrained Problems" - Alg. 1 (CCA) and Alg. 2 (FDA).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    BF16, FP32, FP64, COUNTSKETCH, SRHT, IDENTITY, EXACT, Options, Info, GbccaError,
+    Q_SKETCH_X, Q_SKETCH_Y, Q_R_X, Q_R_Y, Q_WARM_U, Q_WARM_V, Q_HISTORY, Q_CLASS_MEANS,
+    OK, ERR_MAXITER, ERR_NOT_SPD, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_STATE,
+)
+
+_DTYPE_NAMES = {"bf16": BF16, "f32": FP32, "fp32": FP32, "f64": FP64, "fp64": FP64}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(dtype) -> int:
+    """Library dtype code of a torch dtype or a name ('bf16', 'f32', 'f64')."""
+    if isinstance(dtype, int):
+        return dtype
+    if isinstance(dtype, str):
+        return _DTYPE_NAMES[dtype]
+    torch = _torch()
+    return {torch.bfloat16: BF16, torch.float32: FP32, torch.float64: FP64}[dtype]
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def default_options(**kw) -> Options:
+    lib = _lib.load()
+    o = Options()
+    _lib.check(lib.gbcca_default_options(C.byref(o)), "gbcca_default_options")
+    for key, val in kw.items():
+        setattr(o, key, val)
+    return o
+
+
+class Plan:
+    """Owns a gbcca_plan_t; frees it on close() / garbage collection."""
+
+    def __init__(self, handle, kind, n, dims, k, dtype, opt, l=0):
+        self.handle = handle
+        self.kind = kind
+        self.n = n
+        self.dims = dims
+        self.k = k
+        self.dtype = dtype
+        self.opt = opt
+        self.l = l
+
+    def close(self):
+        if self.handle is not None:
+            _lib.load().gbcca_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cca_plan(n, dx, dy, k, dtype, opt: Options | None = None) -> Plan:
+    lib = _lib.load()
+    h = C.c_void_p()
+    code = dtype_code(dtype)
+    _lib.check(lib.cca_plan(C.byref(h), n, dx, dy, k, code, C.byref(opt) if opt else None), "cca_plan")
+    return Plan(h, "cca", n, (dx, dy), k, code, opt)
+
+
+def lda_plan(n, d, n_classes, k, dtype, opt: Options | None = None) -> Plan:
+    lib = _lib.load()
+    h = C.c_void_p()
+    code = dtype_code(dtype)
+    _lib.check(lib.lda_plan(C.byref(h), n, d, n_classes, k, code, C.byref(opt) if opt else None), "lda_plan")
+    return Plan(h, "lda", n, (d,), k, code, opt, l=n_classes)
+
+
+def cca_precondition(plan: Plan, X, Y, lambda_x, lambda_y, sketch_h=None, sketch_g=None, stream=None):
+    """X (n x dx), Y (n x dy): CUDA tensors of the plan's dtype, rows contiguous."""
+    lib = _lib.load()
+    assert X.stride(1) == 1 and Y.stride(1) == 1
+    _lib.check(lib.cca_precondition(plan.handle, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), float(lambda_x),
+                                    float(lambda_y), _ptr(sketch_h), _ptr(sketch_g), _stream(stream)),
+               "cca_precondition")
+    plan._data = (X, Y, sketch_h, sketch_g)  # keep the caller's buffers alive with the plan
+
+
+def cca_solve(plan: Plan, mu=None, tol=0.0, U=None, V=None, sigma=None, stream=None, allow_maxiter=True):
+    """Returns (sigma, U, V, info dict).  U/V (float64, dx x k / dy x k) are
+    also the start when the plan was made with warm_start = 0."""
+    torch = _torch()
+    lib = _lib.load()
+    dx, dy = plan.dims
+    dev = torch.device("cuda", torch.cuda.current_device())
+    U = U if U is not None else torch.empty(dx, plan.k, dtype=torch.float64, device=dev)
+    V = V if V is not None else torch.empty(dy, plan.k, dtype=torch.float64, device=dev)
+    sigma = sigma if sigma is not None else torch.empty(plan.k, dtype=torch.float64, device=dev)
+    info = Info()
+    mu_arr = (C.c_double * plan.k)(*mu) if mu is not None else None
+    allow = (OK, ERR_MAXITER) if allow_maxiter else (OK,)
+    _lib.check(lib.cca_solve(plan.handle, mu_arr, float(tol), _ptr(U), _ptr(V), _ptr(sigma), C.byref(info),
+                             _stream(stream)), "cca_solve", allow)
+    return sigma, U, V, info.as_dict()
+
+
+def lda_solve(plan: Plan, X, labels, lam, mu=None, tol=0.0, W=None, rho=None, sketch_h=None, sketch_g=None,
+              stream=None, allow_maxiter=True):
+    """X (n x d) CUDA tensor of the plan's dtype, labels int32 (n).  Returns
+    (rho, W, info dict)."""
+    torch = _torch()
+    lib = _lib.load()
+    (d,) = plan.dims
+    dev = X.device
+    W = W if W is not None else torch.empty(d, plan.k, dtype=torch.float64, device=dev)
+    rho = rho if rho is not None else torch.empty(plan.k, dtype=torch.float64, device=dev)
+    info = Info()
+    mu_arr = (C.c_double * plan.k)(*mu) if mu is not None else None
+    allow = (OK, ERR_MAXITER) if allow_maxiter else (OK,)
+    assert X.stride(1) == 1 and labels.dtype == torch.int32
+    _lib.check(lib.lda_solve(plan.handle, _ptr(X), X.stride(0), _ptr(labels), float(lam), mu_arr, float(tol),
+                             _ptr(sketch_h), _ptr(sketch_g), _ptr(W), _ptr(rho), C.byref(info), _stream(stream)),
+               "lda_solve", allow)
+    plan._data = (X, labels)
+    return rho, W, info.as_dict()
+
+
+def gbcca_fused_pass(plan: Plan, Phi_x, Phi_y=None, stream=None):
+    """One fused data pass at Phi_x (dx x 2k) / Phi_y (dy x 2k).  Returns
+    (Gx, Gy, Gram) as float64 CUDA tensors (Gy None for an FDA plan)."""
+    torch = _torch()
+    lib = _lib.load()
+    dev = Phi_x.device
+    k2 = 2 * plan.k
+    nc = (2 if plan.kind == "cca" else 1) * k2
+    Gx = torch.empty(plan.dims[0], nc, dtype=torch.float64, device=dev)
+    Gy = torch.empty(plan.dims[1], nc, dtype=torch.float64, device=dev) if plan.kind == "cca" else None
+    Gram = torch.empty(nc, nc, dtype=torch.float64, device=dev)
+    _lib.check(lib.gbcca_fused_pass(plan.handle, _ptr(Phi_x.contiguous()),
+                                    _ptr(Phi_y.contiguous() if Phi_y is not None else None), _ptr(Gx), _ptr(Gy),
+                                    _ptr(Gram), _stream(stream)), "gbcca_fused_pass")
+    return Gx, Gy, Gram
+
+
+fused_pass = gbcca_fused_pass
+
+
+def gbcca_query(plan: Plan, what: int, stream=None):
+    torch = _torch()
+    lib = _lib.load()
+    n = lib.gbcca_query_size(plan.handle, what)
+    if n < 0:
+        raise ValueError("query not available for this plan")
+    out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _lib.check(lib.gbcca_query(plan.handle, what, _ptr(out), _stream(stream)), "gbcca_query")
+    return out
+
+
+query = gbcca_query
+
+
+def gbcca_sketch_draws(kind, n, s, seed, stream=None):
+    """Library-drawn sketch randomness: CountSketch -> (h[n], g[n]);
+    SRHT (n a power of two) -> (rows[s], signs[n])."""
+    torch = _torch()
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if kind == COUNTSKETCH:
+        h = torch.empty(n, dtype=torch.int32, device=dev)
+        g = torch.empty(n, dtype=torch.int8, device=dev)
+    else:
+        h = torch.empty(s, dtype=torch.int32, device=dev)
+        g = torch.empty(n, dtype=torch.int8, device=dev)
+    _lib.check(lib.gbcca_sketch_draws(kind, n, s, seed, _ptr(h), _ptr(g), _stream(stream)), "gbcca_sketch_draws")
+    return h, g
+
+
+sketch_draws = gbcca_sketch_draws

@@ -1,0 +1,95 @@
+// Shared device/host helpers of the gbcca library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <type_traits>
+
+#include "../../include/gbcca.h"
+
+namespace gbcca {
+
+// ---------------------------------------------------------------- errors
+void set_last_error(const std::string& msg);
+
+struct Status {
+  int code = GBCCA_OK;
+  bool ok() const { return code == GBCCA_OK; }
+};
+
+#define GB_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      ::gbcca::set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+      return GBCCA_ERR_CUDA;                                                              \
+    }                                                                                     \
+  } while (0)
+
+#define GB_CHECK_LAUNCH()                                                                 \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess) {                                                              \
+      ::gbcca::set_last_error(std::string("kernel launch at ") + __FILE__ + ":" +          \
+                              std::to_string(__LINE__) + ": " + cudaGetErrorString(e_));  \
+      return GBCCA_ERR_CUDA;                                                              \
+    }                                                                                     \
+  } while (0)
+
+#define GB_TRY(expr)           \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != GBCCA_OK) return r_; \
+  } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------- loads
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return (float)v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T cvt(float v);
+template <typename T> __device__ __forceinline__ T cvt(double v);
+template <> __device__ __forceinline__ float cvt<float>(float v) { return v; }
+template <> __device__ __forceinline__ float cvt<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double cvt<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
+
+template <typename Tacc, typename Tin> __device__ __forceinline__ Tacc ld_as(const Tin* p);
+template <> __device__ __forceinline__ float ld_as<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ld_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <> __device__ __forceinline__ float ld_as<float, double>(const double* p) { return (float)__ldg(p); }
+template <> __device__ __forceinline__ double ld_as<double, double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ double ld_as<double, float>(const float* p) { return (double)__ldg(p); }
+template <> __device__ __forceinline__ double ld_as<double, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return (double)__bfloat162float(*p);
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- SplitMix64
+// Counter-based SplitMix64 (Steele, Lea & Flood 2014): the i-th output of the
+// stream seeded with `seed`.
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t kSaltSigns = 0xD1B54A32D192ED03ull;
+constexpr uint64_t kSaltRows = 0x8CB92BA72F3D8DD7ull;
+
+}  // namespace gbcca

@@ -1,0 +1,142 @@
+// Internal plan of the gbcca library: shapes, options and device workspace.
+#pragma once
+#include "common.cuh"
+
+namespace gbcca {
+
+constexpr int kMaxK = 20;       // columns of an iterate (p in the paper)
+constexpr int kMaxD = 1024;     // columns of one data view
+constexpr int kMaxClasses = 64; // LDA classes
+
+enum ProblemKind { kCCA = 0, kLDA = 1 };
+
+// Scalars and k x k matrices of the Riemannian CG state, resident on the
+// device so one iteration runs without host round trips.
+struct DevState {
+  int iter, done, status, stalled, passes, ls_trials, first, force_zero_step;
+  double t, f, df, t_prev, df_prev, gn, gn0, beta, t0, gtol, ftrial_best;
+  double mu[kMaxK];
+  double lam[2];
+  double Linv[2][kMaxK * kMaxK];    // L^{-T} of the accepted retraction, per view
+  double S[2][3][kMaxK * kMaxK];    // Sylvester solutions (grad, eta, old grad)
+  double sigma[kMaxK];              // Rayleigh-Ritz values at the end
+  double rot[2][kMaxK * kMaxK];     // Rayleigh-Ritz rotation per view
+  double YW[kMaxClasses * kMaxK];   // FDA: Yhat times the current W (l x k)
+  double ftrial[64];                // line-search trial values (diagnostics)
+  int max_iter;
+  int ntrials;
+};
+
+// One generalized Stiefel factor: the data view it is built on and the
+// iterate that lives on it.
+struct View {
+  int d = 0;
+  const void* Z = nullptr;  // caller-owned data, row-major n x d, leading dim ld
+  int64_t ld = 0;
+  double lam = 0;
+  int ocol = 0;             // first column of this view's block in the pass W
+  double* SZ = nullptr;     // sketch S Z (s x d)
+  double* R = nullptr;      // d x d upper triangular, R^T R = M
+  double* Rinv = nullptr;   // d x d, R^{-1}
+  float* Rinv32 = nullptr;  // FP32 copy for the low-precision path
+  double* Phi = nullptr;    // d x 2k: [U | eta]
+  float* Phi32 = nullptr;   // FP32 copy of Phi for the low-precision pass
+  double* Meta = nullptr;   // d x k: M eta
+  double* gold = nullptr;   // d x k: previous Riemannian gradient
+  double* Mgold = nullptr;  // d x k: M * previous gradient
+  double* LL = nullptr;     // d x 4k: [M^{-1} B U | M^{-1} egrad | eta | grad]
+  double* RR = nullptr;     // d x 4k: [B U | egrad | M eta | M grad]
+  double* tmp = nullptr;    // d x 2k scratch for M^{-1}
+  double* warm = nullptr;   // d x k warm start
+  double* wsU = nullptr;    // d x 2k warm-start iteration block
+  double* wsT = nullptr;    // d x 2k warm-start scratch
+};
+
+struct Plan {
+  int kind = kCCA;
+  int64_t n = 0;
+  int k = 0;
+  int dtype = GBCCA_FP64;
+  gbcca_options opt{};
+  int nviews = 0;
+  View v[2];
+  int D = 0;    // total data columns (dx + dy, or d)
+  int NC = 0;   // pass columns: 4k (CCA) or 2k (LDA)
+  int64_t s = 0, n_pad = 0;
+  int l = 0;    // LDA classes
+  bool preconditioned = false;
+  int dev = 0;
+  int sm_count = 0;
+
+  // sketch randomness and CountSketch sort buffers
+  int32_t* h = nullptr;     // CountSketch buckets (n) or SRHT rows (s)
+  int8_t* g = nullptr;      // CountSketch signs (n) or SRHT signs (n_pad)
+  int32_t* cs_tab = nullptr;  // per-chunk bucket counters (cs_nch x s)
+  int32_t* cs_off = nullptr;  // bucket offsets (s + 1)
+  int32_t* perm = nullptr;    // rows sorted by bucket (n)
+  int cs_nch = 0;
+  void* srht_T = nullptr;     // SRHT stage-1 scratch (n_pad x dmax)
+
+  // pass buffers
+  double* G = nullptr;        // D x NC
+  double* Gram = nullptr;     // NC x NC
+  void* Wbuf = nullptr;       // n x NC (pass intermediate)
+  void* partG = nullptr;      // chunksB x D x NC
+  void* partGram = nullptr;   // ctasA x NC x NC
+  void* partCls = nullptr;    // ctasA x l x NC (LDA per-class sums)
+  int ctasA = 0, chunksB = 0;
+
+  // LDA
+  const int32_t* labels = nullptr;
+  double* counts = nullptr;   // l
+  double* means = nullptr;    // l x d
+  double* Yhat = nullptr;     // l x d
+  double* Cls = nullptr;      // l x NC: class means times Phi
+  double* YPhi = nullptr;     // l x 2k: Yhat Phi
+  double* clsPart = nullptr;  // class-statistics partials
+
+  // RCG state
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;  // pinned mirror for read-back
+  double* phigram = nullptr;    // per view 2k x 2k Gram of Phi
+  double* phipart = nullptr;    // partials of phigram
+  double* cross = nullptr;      // per view 4k x 4k cross Gram (final)
+  double* crosspart = nullptr;  // partials
+  int thinCtas = 0;
+  double* history = nullptr;    // 3 (max_iter + 1)
+  double* ws = nullptr;         // FP64 scratch for dense routines
+  int64_t ws_len = 0;
+  int* flag = nullptr;          // device error flag (NOT_SPD etc.)
+};
+
+// sketch.cu
+int sketch_draws(int kind, int64_t n, int64_t s, uint64_t seed, int32_t* h, int8_t* g,
+                 cudaStream_t st);
+int countsketch_apply(Plan& p, int view, bool center, cudaStream_t st);
+int countsketch_prepare(Plan& p, cudaStream_t st);
+int srht_apply(Plan& p, int view, cudaStream_t st);
+
+// dense.cu
+int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1,
+            int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st);
+int cholesky_upper(double* A, int d, int* flag, cudaStream_t st);
+int tri_inverse_upper(const double* R, double* Rinv, int d, cudaStream_t st);
+int to_f32(const double* a, float* b, int64_t len, cudaStream_t st);
+// C (m x c, ldc) = op(A) B (rows of B = columns of op(A), ldb); A is
+// ra x ca row-major; tri = 1 skips the zero half of an upper-triangular A.
+template <typename T>
+int mat_thin(const T* A, int ra, int ca, bool transA, bool tri, const double* B, int64_t ldb, double* C,
+             int64_t ldc, int c, cudaStream_t st);
+
+// pass.cu
+int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols = 0,
+               const int* done = nullptr);
+int exact_gram(Plan& p, int view, double* out, cudaStream_t st);
+int lda_class_stats(Plan& p, cudaStream_t st);
+
+// rcg.cu
+int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals,
+            gbcca_info* info, cudaStream_t st);
+int warm_start(Plan& p, cudaStream_t st);
+
+}  // namespace gbcca

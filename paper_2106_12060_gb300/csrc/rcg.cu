@@ -1,0 +1,1350 @@
+// Riemannian CG on products of generalized Stiefel manifolds with the
+// preconditioned metric g(xi, eta) = tr(xi^T M eta), M = R^T R (Sec. 3, Table 1),
+// for the CCA cost (Sec. 4.2) and the FDA cost (Sec. 5.2); warm start from the
+// exact solution of the sketched problem (Alg. 1 step 4, Alg. 2 step 5); final
+// Rayleigh-Ritz step.
+//
+// One iteration = one fused data pass at Phi = [U, eta] plus small kernels:
+//   line search   every Gram the retraction and the cost need along
+//                 t -> R_U(t eta) is a quadratic in t of k x k blocks of the
+//                 pass Gram, so all trial steps are evaluated from the pass
+//                 (35 trials in parallel, then the sequential Armijo rule);
+//   update        U+ = (U + t eta) L^{-T} (QR retraction in Cholesky form,
+//                 Table 1), B U+ and the Euclidean gradient from the linear
+//                 pass outputs Z^T W (Sec. 4.2 gradient), no second pass;
+//   M^{-1}        two products with R^{-1};
+//   direction     one k x k eigendecomposition per factor solves the three
+//                 Sylvester equations of the projection (Table 1) for the
+//                 gradient and the two transported vectors; Hestenes-Stiefel
+//                 beta (clipped at 0) in the metric g; restart if not descent;
+//   new direction eta+ = -grad + beta T(eta), with its M-image carried along
+//                 so no product with M is ever formed.
+// Each kernel returns at once when the device flag `done` is set, so the host
+// enqueues iterations in batches and reads the flag between batches.
+#include "plan.h"
+
+namespace gbcca {
+
+constexpr double kC1 = 1e-4;
+constexpr int kMaxLS = 25;
+constexpr int kMaxExpand = 10;
+constexpr int kNTrials = kMaxLS + kMaxExpand;
+constexpr int kLSWarps = 8;
+
+// ================================================================ helpers
+// Block-wide small dense routines on shared memory (row-major, FP64).
+__device__ void blk_sync() { __syncthreads(); }
+
+// C (m x n) = op(A) op(B), inner dimension q; C must not alias A or B.
+__device__ void blk_mm(const double* A, bool tA, const double* B, bool tB, double* C, int m, int q, int n, int lda,
+                       int ldb) {
+  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+    int i = e / n, j = e % n;
+    double s = 0;
+    for (int l = 0; l < q; ++l) s += (tA ? A[l * lda + i] : A[i * lda + l]) * (tB ? B[j * ldb + l] : B[l * ldb + j]);
+    C[e] = s;
+  }
+  __syncthreads();
+}
+
+// Symmetric eigendecomposition by parallel (round-robin ordered) Jacobi:
+// A (n x n, destroyed) -> eigenvalues in lam (descending), eigenvectors in
+// the columns of Q (n x n).  rot is shared scratch of 3 * 33 doubles/ints.
+__device__ void blk_jacobi(double* A, double* Q, double* lam, int n, double* rot) {
+  double* cs = rot;
+  double* sn = rot + 33;
+  int* pp = reinterpret_cast<int*>(rot + 66);
+  int* qq = pp + 33;
+  __shared__ double offn;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Q[e] = (e / n == e % n) ? 1.0 : 0.0;
+  __syncthreads();
+  const int m = n + (n & 1);
+  for (int sweep = 0; sweep < 30 && n > 1; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0, dg = 0;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          double v = A[i * n + j] * A[i * n + j];
+          if (i == j) dg += v;
+          else off += v;
+        }
+      offn = (off <= 1e-30 * dg || off == 0.0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (offn > 0.5) break;
+    for (int r = 0; r < m - 1; ++r) {
+      if (threadIdx.x < m / 2) {
+        int i = threadIdx.x;
+        int a = (i == 0) ? 0 : 1 + ((i - 1 + r) % (m - 1));
+        int b = 1 + ((m - 2 - i + r) % (m - 1));
+        int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = A[p * n + q];
+          if (apq != 0.0) {
+            double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[i] = c;
+        sn[i] = s;
+        pp[i] = p;
+        qq[i] = q < n ? q : -1;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = threadIdx.x; e < (m / 2) * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        if (qq[i] < 0) continue;
+        int p = pp[i], q = qq[i];
+        double ap = A[p * n + j], aq = A[q * n + j];
+        A[p * n + j] = cs[i] * ap - sn[i] * aq;
+        A[q * n + j] = sn[i] * ap + cs[i] * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, Q <- Q J
+      for (int e = threadIdx.x; e < (m / 2) * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        if (qq[i] < 0) continue;
+        int p = pp[i], q = qq[i];
+        double ap = A[j * n + p], aq = A[j * n + q];
+        A[j * n + p] = cs[i] * ap - sn[i] * aq;
+        A[j * n + q] = sn[i] * ap + cs[i] * aq;
+        double qp = Q[j * n + p], qv = Q[j * n + q];
+        Q[j * n + p] = cs[i] * qp - sn[i] * qv;
+        Q[j * n + q] = sn[i] * qp + cs[i] * qv;
+      }
+      __syncthreads();
+    }
+  }
+  // sort descending (selection sort by one thread, swapping Q columns)
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+    for (int i = 0; i < n; ++i) {
+      int b = i;
+      for (int j = i + 1; j < n; ++j)
+        if (lam[j] > lam[b]) b = j;
+      if (b != i) {
+        double t = lam[i];
+        lam[i] = lam[b];
+        lam[b] = t;
+        for (int r = 0; r < n; ++r) {
+          double u = Q[r * n + i];
+          Q[r * n + i] = Q[r * n + b];
+          Q[r * n + b] = u;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// In-place Cholesky A = L L^T (lower; upper part zeroed).  Returns false
+// (uniformly in the block) if a pivot is not positive.
+__device__ bool blk_chol(double* A, int n) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double dj = A[j * n + j];
+      if (!(dj > 0.0)) {
+        bad = 1;
+        dj = 1.0;
+      }
+      A[j * n + j] = sqrt(dj);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + j] /= A[j * n + j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int i = e / n, c = e % n;
+      if (i > j && c > j && c <= i) A[i * n + c] -= A[i * n + j] * A[c * n + j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+    if (e % n > e / n) A[e] = 0.0;
+  __syncthreads();
+  return bad == 0;
+}
+
+// Li = L^{-1} for lower-triangular L (n x n), column-parallel forward substitution.
+__device__ void blk_lower_inv(const double* L, double* Li, int n) {
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int q = c; q < i; ++q) s -= L[i * n + q] * Li[q * n + c];
+      Li[i * n + c] = (i < c) ? 0.0 : s / L[i * n + i];
+    }
+  }
+  __syncthreads();
+}
+
+// Warp-level versions used by the parallel line-search trials (n <= 32).
+__device__ bool warp_chol(double* A, int n) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    double dj = A[j * n + j];
+    if (!(dj > 0.0)) {
+      ok = false;
+      dj = 1.0;
+    }
+    double ljj = sqrt(dj);
+    __syncwarp();
+    if (lane == j) A[j * n + j] = ljj;
+    if (lane > j && lane < n) A[lane * n + j] /= ljj;
+    __syncwarp();
+    if (lane > j && lane < n)
+      for (int c = j + 1; c <= lane; ++c) A[lane * n + c] -= A[lane * n + j] * A[c * n + j];
+    __syncwarp();
+  }
+  return ok;
+}
+
+// Li = L^{-1} (lane c computes column c)
+__device__ void warp_lower_inv(const double* L, double* Li, int n) {
+  const int c = threadIdx.x & 31;
+  if (c < n) {
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int q = c; q < i; ++q) s -= L[i * n + q] * Li[q * n + c];
+      Li[i * n + c] = (i < c) ? 0.0 : s / L[i * n + i];
+    }
+  }
+  __syncwarp();
+}
+
+// ========================================================= thin Grams
+// part[view][blk] (ca x cb) = A[rows of blk]^T B[rows of blk], A: d x ca
+// (row stride lda), B: d x cb (ldb), 64 rows per block.
+struct ThinArgs {
+  const double* A[2];
+  const double* B[2];
+  int lda[2], ldb[2], d[2];
+  int ca, cb, nblk;
+  double* part;
+  const int* done;
+};
+
+__global__ void thin_gram_kernel(ThinArgs a) {
+  extern __shared__ double tsm[];
+  if (a.done != nullptr && *a.done) return;
+  const int v = blockIdx.y;
+  const int d = a.d[v];
+  const int r0 = blockIdx.x * 64;
+  double* As = tsm;
+  double* Bs = tsm + 64 * a.ca;
+  const int nr = min(64, d - r0);
+  for (int e = threadIdx.x; e < 64 * a.ca; e += blockDim.x) {
+    int r = e / a.ca, c = e % a.ca;
+    As[e] = r < nr ? a.A[v][(int64_t)(r0 + r) * a.lda[v] + c] : 0.0;
+  }
+  for (int e = threadIdx.x; e < 64 * a.cb; e += blockDim.x) {
+    int r = e / a.cb, c = e % a.cb;
+    Bs[e] = r < nr ? a.B[v][(int64_t)(r0 + r) * a.ldb[v] + c] : 0.0;
+  }
+  __syncthreads();
+  double* out = a.part + ((int64_t)v * a.nblk + blockIdx.x) * a.ca * a.cb;
+  for (int e = threadIdx.x; e < a.ca * a.cb; e += blockDim.x) {
+    int i = e / a.cb, j = e % a.cb;
+    double s = 0;
+    for (int r = 0; r < nr; ++r) s += As[r * a.ca + i] * Bs[r * a.cb + j];
+    out[e] = s;
+  }
+}
+
+static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const double* B0, const double* B1,
+                     int ldb, int ca, int cb, double* part, cudaStream_t st, const int* done) {
+  ThinArgs a{};
+  a.A[0] = A0;
+  a.A[1] = A1;
+  a.B[0] = B0;
+  a.B[1] = B1;
+  int dmax = 0;
+  for (int v = 0; v < p.nviews; ++v) {
+    a.lda[v] = lda;
+    a.ldb[v] = ldb;
+    a.d[v] = p.v[v].d;
+    dmax = std::max(dmax, p.v[v].d);
+  }
+  a.ca = ca;
+  a.cb = cb;
+  a.nblk = ceil_div(dmax, 64);
+  a.part = part;
+  a.done = done;
+  size_t smem = sizeof(double) * 64 * (ca + cb);
+  GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // blocks past a view's rows write zeros (nr <= 0 loops are empty)
+  thin_gram_kernel<<<dim3(a.nblk, p.nviews), 256, smem, st>>>(a);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+__device__ void sum_blocks(const double* part, int nblk, int len, double* out) {
+  for (int e = threadIdx.x; e < len; e += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * len + e];
+    out[e] = s;
+  }
+  __syncthreads();
+}
+
+// ============================================================ line search
+struct LSArgs {
+  DevState* st;
+  const double* Gram;     // pass Gram (NC x NC)
+  const double* phipart;  // [view][nblk][2k x 2k]
+  int nblk;
+  int NC, k, nviews, kind;
+  const double* YPhi;     // FDA: Yhat Phi (l x 2k)
+  int l;
+  double* history;
+  int max_iter;
+};
+
+// f(t) for one trial, evaluated by one warp from the coefficient matrices.
+// coef layout per view v (k x k each): A_v, B_v, C_v  (Gram(t) = A + t B + t^2 C)
+// and the cross / S_B terms X0, X1, X2 (Cross(t) = X0 + t X1 + t^2 X2).
+__device__ double ls_eval(const LSArgs& a, const double* coef, double t, double* w, const double* mu) {
+  const int k = a.k, kk = k * k, lane = threadIdx.x & 31;
+  double* Gx = w;
+  double* Gy = w + kk;
+  double* Cx = w + 2 * kk;
+  double* Li = w + 3 * kk;
+  for (int e = lane; e < kk; e += 32) {
+    Gx[e] = coef[e] + t * coef[kk + e] + t * t * coef[2 * kk + e];
+    if (a.kind == kCCA) Gy[e] = coef[3 * kk + e] + t * coef[4 * kk + e] + t * t * coef[5 * kk + e];
+    Cx[e] = coef[6 * kk + e] + t * coef[7 * kk + e] + t * t * coef[8 * kk + e];
+  }
+  __syncwarp();
+  bool ok = warp_chol(Gx, k);
+  if (a.kind == kCCA) ok = warp_chol(Gy, k) && ok;
+  // Y = Lx^{-1} Cross  (lane c solves column c)
+  if (lane < k) {
+    for (int i = 0; i < k; ++i) {
+      double s = Cx[i * k + lane];
+      for (int q = 0; q < i; ++q) s -= Gx[i * k + q] * Cx[q * k + lane];
+      Cx[i * k + lane] = s / Gx[i * k + i];
+    }
+  }
+  __syncwarp();
+  // second factor: Ly (CCA) or Lx again (FDA: L^{-1} S_B L^{-T})
+  warp_lower_inv(a.kind == kCCA ? Gy : Gx, Li, k);
+  double part = 0;
+  if (lane < k) {
+    double z = 0;
+    for (int j = 0; j <= lane; ++j) z += Cx[lane * k + j] * Li[lane * k + j];
+    part = mu[lane] * z;
+  }
+  double f = -warp_sum(part);
+  if (a.kind == kLDA) f *= 0.5;
+  if (!ok || !(f == f)) f = INFINITY;
+  return f;
+}
+
+__global__ void linesearch_kernel(LSArgs a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  extern __shared__ double lsm[];
+  const int k = a.k, kk = k * k, k2 = 2 * k;
+  double* coef = lsm;                       // 9 kk
+  double* phig = coef + 9 * kk;             // 2 views x 4 kk
+  double* work = phig + 8 * kk;             // kLSWarps x 4 kk
+  __shared__ double ft[kNTrials], tt[kNTrials];
+  __shared__ double mu_s[kMaxK];
+  __shared__ int chosen;
+  __shared__ double t_acc;
+  if (threadIdx.x < k) mu_s[threadIdx.x] = st->mu[threadIdx.x];
+  for (int v = 0; v < a.nviews; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * kk, a.nblk, 4 * kk,
+                                                phig + v * 4 * kk);
+  // coefficient matrices
+  const int NC = a.NC;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    // block (bi, bj), entry (i, j) of the pass Gram / of Phi^T Phi
+    auto G = [&](int bi, int bj) { return a.Gram[(bi * k + i) * NC + bj * k + j]; };
+    for (int v = 0; v < a.nviews; ++v) {
+      const double* pg = phig + v * 4 * kk;  // 2k x 2k
+      auto P = [&](int bi, int bj) { return pg[(bi * k + i) * k2 + bj * k + j]; };
+      double lam = st->lam[v];
+      int b0 = 2 * v;  // pass blocks of this view: [P_U, P_eta] or [Q_V, Q_eta]
+      coef[(3 * v + 0) * kk + e] = G(b0, b0) + lam * P(0, 0);
+      coef[(3 * v + 1) * kk + e] = G(b0, b0 + 1) + G(b0 + 1, b0) + lam * (P(0, 1) + P(1, 0));
+      coef[(3 * v + 2) * kk + e] = G(b0 + 1, b0 + 1) + lam * P(1, 1);
+    }
+    if (a.kind == kCCA) {
+      coef[6 * kk + e] = G(0, 2);
+      coef[7 * kk + e] = G(0, 3) + G(1, 2);
+      coef[8 * kk + e] = G(1, 3);
+    } else {
+      // S_B(t) = (Yhat W + t Yhat eta)^T (Yhat W + t Yhat eta)
+      double s0 = 0, s1 = 0, s2 = 0;
+      for (int c = 0; c < a.l; ++c) {
+        double wi = a.YPhi[c * k2 + i], wj = a.YPhi[c * k2 + j];
+        double ei = a.YPhi[c * k2 + k + i], ej = a.YPhi[c * k2 + k + j];
+        s0 += wi * wj;
+        s1 += wi * ej + ei * wj;
+        s2 += ei * ej;
+      }
+      coef[6 * kk + e] = s0;
+      coef[7 * kk + e] = s1;
+      coef[8 * kk + e] = s2;
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* w = work + warp * 4 * kk;
+  const bool zero_step = st->force_zero_step != 0;
+  if (zero_step) {
+    if (warp == 0) {
+      double f0 = ls_eval(a, coef, 0.0, w, mu_s);
+      if (lane == 0) {
+        ft[0] = f0;
+        tt[0] = 0.0;
+        chosen = 0;
+        t_acc = 0.0;
+      }
+    }
+    __syncthreads();
+  } else {
+    const double t0 = st->t0;
+    for (int tr = warp; tr < kNTrials; tr += kLSWarps) {
+      double t = tr < kMaxLS ? ldexp(t0, -tr) : ldexp(t0, tr - kMaxLS + 1);
+      double f = ls_eval(a, coef, t, w, mu_s);
+      if (lane == 0) {
+        ft[tr] = f;
+        tt[tr] = t;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double f0 = st->f, df = st->df;
+      int acc = -1;
+      for (int j = 0; j < kMaxLS; ++j)
+        if (ft[j] <= f0 + kC1 * tt[j] * df) {
+          acc = j;
+          break;
+        }
+      if (acc == 0) {
+        for (int e = 0; e < kMaxExpand; ++e) {
+          int idx = kMaxLS + e;
+          if (ft[idx] < ft[acc] && ft[idx] <= f0 + kC1 * tt[idx] * df) acc = idx;
+          else break;
+        }
+      }
+      chosen = acc;
+      t_acc = acc >= 0 ? tt[acc] : 0.0;
+      st->ls_trials = acc < 0 ? kMaxLS : (acc < kMaxLS ? acc + 1 : kMaxLS + 1);
+      for (int j = 0; j < kNTrials; ++j) st->ftrial[j] = ft[j];
+    }
+    __syncthreads();
+  }
+  if (chosen < 0) {
+    if (threadIdx.x == 0) {
+      st->stalled = 1;
+      st->done = 1;
+    }
+    return;
+  }
+  // factors at the accepted step: Linv_v = L_v(t)^{-T} (upper), stored row-major
+  const double t = t_acc;
+  if (warp == 0) {
+    double* Gx = w;
+    for (int v = 0; v < a.nviews; ++v) {
+      for (int e = lane; e < kk; e += 32)
+        Gx[e] = coef[(3 * v) * kk + e] + t * coef[(3 * v + 1) * kk + e] + t * t * coef[(3 * v + 2) * kk + e];
+      __syncwarp();
+      warp_chol(Gx, k);
+      double* Li = w + 3 * kk;
+      warp_lower_inv(Gx, Li, k);
+      for (int e = lane; e < kk; e += 32) {
+        int i = e / k, j = e % k;
+        st->Linv[v][e] = Li[j * k + i];  // (L^{-1})^T
+      }
+      __syncwarp();
+    }
+    if (a.kind == kLDA) {
+      // YW+ = (Yhat W + t Yhat eta) L^{-T}
+      for (int e = lane; e < a.l * k; e += 32) {
+        int c = e / k, j = e % k;
+        double s = 0;
+        for (int q = 0; q < k; ++q)
+          s += (a.YPhi[c * k2 + q] + t * a.YPhi[c * k2 + k + q]) * st->Linv[0][q * k + j];
+        st->YW[e] = s;
+      }
+    }
+    if (lane == 0) {
+      double fnew = ft[chosen];
+      st->t = t;
+      st->f = fnew;
+      if (!zero_step) {
+        st->t_prev = t;
+        st->df_prev = st->df;
+        st->iter += 1;
+      }
+    }
+  }
+}
+
+// ================================================================ update
+struct UpdArgs {
+  DevState* st;
+  const double* G;      // D x NC pass output
+  int NC, k, nviews, kind, l, D;
+  double* Phi[2];
+  double* LL[2];
+  double* RR[2];
+  const double* Meta[2];
+  const double* gold[2];
+  const double* Mgold[2];
+  int d[2];
+  int dofs[2];
+  const double* Yhat;   // FDA (l x d)
+};
+
+// row j of view v: U+ = (U + t eta) Lv^{-T}; B U+; Euclidean gradient.
+__global__ void update_kernel(UpdArgs a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  const int v = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = a.k, k2 = 2 * k, k4 = 4 * k;
+  if (j >= a.d[v]) return;
+  const double t = st->t, lam = st->lam[v];
+  const double* Li = st->Linv[v];
+  double* Phi = a.Phi[v] + (int64_t)j * k2;
+  const double* Grow = a.G + (int64_t)(a.dofs[v] + j) * a.NC;
+  double ut[kMaxK], bt[kMaxK], ct[kMaxK];
+  for (int q = 0; q < k; ++q) {
+    double e = Phi[k + q];
+    ut[q] = Phi[q] + t * e;
+    // own block: B-image; other block: cross term (CCA) - columns of W are
+    // [P_U, P_eta, Q_V, Q_eta]
+    int own = 2 * v, oth = 2 * (1 - v);
+    bt[q] = Grow[own * k + q] + t * Grow[(own + 1) * k + q] + lam * ut[q];
+    if (a.kind == kCCA) ct[q] = Grow[oth * k + q] + t * Grow[(oth + 1) * k + q];
+  }
+  double* LLr = a.LL[v] + (int64_t)j * k4;
+  double* RRr = a.RR[v] + (int64_t)j * k4;
+  // old direction and gradient (and their M-images) move to the Gram buffers
+  for (int q = 0; q < k; ++q) {
+    LLr[2 * k + q] = Phi[k + q];
+    LLr[3 * k + q] = a.gold[v][(int64_t)j * k + q];
+    RRr[2 * k + q] = a.Meta[v][(int64_t)j * k + q];
+    RRr[3 * k + q] = a.Mgold[v][(int64_t)j * k + q];
+  }
+  for (int c = 0; c < k; ++c) {
+    double u = 0, b = 0, g = 0;
+    for (int q = 0; q < k; ++q) {
+      u += ut[q] * Li[q * k + c];
+      b += bt[q] * Li[q * k + c];
+    }
+    if (a.kind == kCCA) {
+      const double* Lo = st->Linv[1 - v];
+      for (int q = 0; q < k; ++q) g += ct[q] * Lo[q * k + c];
+      g = -g * st->mu[c];
+    } else {
+      // egrad = -S_B W+ N = -Yhat^T (Yhat W+) N
+      for (int cl = 0; cl < a.l; ++cl) g += a.Yhat[(int64_t)cl * a.d[0] + j] * st->YW[cl * k + c];
+      g = -g * st->mu[c];
+    }
+    Phi[c] = u;
+    RRr[c] = b;
+    RRr[k + c] = g;
+  }
+}
+
+// ============================================================= direction
+struct DirArgs {
+  DevState* st;
+  const double* crosspart;  // [view][nblk][4k x 4k]
+  int nblk, k, nviews;
+  double* history;
+  int max_iter;
+};
+
+// <u, M w> for u = L_a - Wn Su, M w = R_b - BU Sw from the cross Gram X
+// (4k x 4k, blocks X[a][b] = L_a^T R_b); Su / Sw may be null (= 0).
+__device__ double cross_ip(const double* X, int k, int a, const double* Su, int b, const double* Sw, double* tmp) {
+  const int k4 = 4 * k, kk = k * k;
+  __shared__ double red[256];
+  double s = 0;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    // tr(X[a][b]) contributes on the diagonal
+    if (i == j) s += X[(a * k + i) * k4 + b * k + i];
+    // - tr(X[a][0] Sw) = - sum_ij X[a][0]_ij Sw_ji
+    if (Sw) s -= X[(a * k + i) * k4 + 0 * k + j] * Sw[j * k + i];
+    // - tr(Su^T X[0][b]) = - sum_ij Su_ij X[0][b]_ij
+    if (Su) s -= Su[i * k + j] * X[(0 * k + i) * k4 + b * k + j];
+  }
+  // + tr(Su^T X00 Sw) = sum_ij Su_ij (X00 Sw)_ij
+  if (Su && Sw) {
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      int i = e / k, j = e % k;
+      double z = 0;
+      for (int q = 0; q < k; ++q) z += X[(0 * k + i) * k4 + 0 * k + q] * Sw[q * k + j];
+      s += Su[e] * z;
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void direction_kernel(DirArgs a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  extern __shared__ double dsm[];
+  const int k = a.k, kk = k * k, k4 = 4 * k;
+  double* X = dsm;                 // 16 kk per view
+  double* A = X + 2 * 16 * kk;     // kk
+  double* Q = A + kk;              // kk
+  double* lam = Q + kk;            // k
+  double* T1 = lam + kMaxK;        // kk
+  double* T2 = T1 + kk;            // kk
+  double* rot = T2 + kk;           // 100
+  for (int v = 0; v < a.nviews; ++v)
+    sum_blocks(a.crosspart + (int64_t)v * a.nblk * 16 * kk, a.nblk, 16 * kk, X + v * 16 * kk);
+  for (int v = 0; v < a.nviews; ++v) {
+    const double* Xv = X + v * 16 * kk;
+    // Sylvester coefficient (U^T B M^{-1} B U) = Wn^T BU, symmetrized
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      int i = e / k, j = e % k;
+      A[e] = 0.5 * (Xv[i * k4 + j] + Xv[j * k4 + i]);
+    }
+    __syncthreads();
+    blk_jacobi(A, Q, lam, k, rot);
+    // three right-hand sides: (BU)^T xi, (BU)^T eta, (BU)^T g = X[a][0]^T
+    for (int r = 0; r < 3; ++r) {
+      const int ablk = r + 1;
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        int i = e / k, j = e % k;
+        T1[e] = Xv[(ablk * k + i) * k4 + j] + Xv[(ablk * k + j) * k4 + i];  // C + C^T
+      }
+      __syncthreads();
+      blk_mm(Q, true, T1, false, T2, k, k, k, k, k);   // Q^T C
+      blk_mm(T2, false, Q, false, T1, k, k, k, k, k);  // Q^T C Q
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        int i = e / k, j = e % k;
+        T1[e] /= (lam[i] + lam[j]);
+      }
+      __syncthreads();
+      blk_mm(Q, false, T1, false, T2, k, k, k, k, k);  // Q S'
+      blk_mm(T2, false, Q, true, st->S[v][r], k, k, k, k, k);  // Q S' Q^T
+    }
+  }
+  // inner products in g, summed over the factors
+  double gg = 0, g_Tg = 0, Te_g = 0, Te_Tg = 0, dfg = 0, dfTe = 0;
+  for (int v = 0; v < a.nviews; ++v) {
+    const double* Xv = X + v * 16 * kk;
+    const double* Sg = st->S[v][0];
+    const double* Se = st->S[v][1];
+    const double* So = st->S[v][2];
+    gg += cross_ip(Xv, k, 1, Sg, 1, Sg, T1);
+    g_Tg += cross_ip(Xv, k, 1, Sg, 3, So, T1);
+    Te_g += cross_ip(Xv, k, 2, Se, 1, Sg, T1);
+    Te_Tg += cross_ip(Xv, k, 2, Se, 3, So, T1);
+    // tr(egrad^T grad) = tr(X[1][1]) - tr(X[0][1]^T Sg); tr(egrad^T T eta) similar
+    dfg += cross_ip(Xv, k, 1, Sg, 1, nullptr, T1);
+    dfTe += cross_ip(Xv, k, 2, Se, 1, nullptr, T1);
+  }
+  if (threadIdx.x == 0) {
+    double beta = 0;
+    if (!st->first) {
+      double num = gg - g_Tg, den = Te_g - Te_Tg;
+      beta = den != 0.0 ? fmax(0.0, num / den) : 0.0;
+    }
+    double df = -dfg + beta * dfTe;
+    if (df >= 0) {
+      beta = 0;
+      df = -gg;
+    }
+    double gn = sqrt(fmax(gg, 0.0));
+    if (st->first) {
+      st->gn0 = gn;
+      st->t0 = 1.0 / gn;
+    } else {
+      st->t0 = st->t_prev * st->df_prev / df;
+    }
+    st->beta = beta;
+    st->df = df;
+    st->gn = gn;
+    const int it = st->iter;
+    if (a.history != nullptr && it <= a.max_iter) {
+      a.history[3 * it + 0] = st->f;
+      a.history[3 * it + 1] = gn;
+      a.history[3 * it + 2] = st->first ? 0.0 : st->t;
+    }
+    st->first = 0;
+    st->force_zero_step = 0;
+    if (!(gn > st->gtol * st->gn0)) {
+      st->done = 1;
+      st->status = GBCCA_OK;
+    } else if (it >= a.max_iter) {
+      st->done = 1;
+      st->status = GBCCA_ERR_MAXITER;
+    }
+  }
+}
+
+// ========================================================== new direction
+struct NewArgs {
+  DevState* st;
+  int k, nviews;
+  double* Phi[2];
+  double* Meta[2];
+  double* gold[2];
+  double* Mgold[2];
+  const double* LL[2];
+  const double* RR[2];
+  int d[2];
+};
+
+__global__ void newdir_kernel(NewArgs a) {
+  DevState* st = a.st;
+  if (st->done) return;
+  const int v = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = a.k, k4 = 4 * k;
+  if (j >= a.d[v]) return;
+  const double* L = a.LL[v] + (int64_t)j * k4;
+  const double* R = a.RR[v] + (int64_t)j * k4;
+  const double* Sg = st->S[v][0];
+  const double* Se = st->S[v][1];
+  const double beta = st->beta;
+  for (int c = 0; c < k; ++c) {
+    double wg = 0, bg = 0, we = 0, be = 0;
+    for (int q = 0; q < k; ++q) {
+      wg += L[q] * Sg[q * k + c];
+      bg += R[q] * Sg[q * k + c];
+      we += L[q] * Se[q * k + c];
+      be += R[q] * Se[q * k + c];
+    }
+    double g = L[k + c] - wg;          // grad = xi - Wn Sg
+    double Mg = R[k + c] - bg;         // M grad = egrad - BU Sg
+    double Te = L[2 * k + c] - we;     // T eta = eta - Wn Se
+    double MTe = R[2 * k + c] - be;    // M T eta = M eta - BU Se
+    a.gold[v][(int64_t)j * k + c] = g;
+    a.Mgold[v][(int64_t)j * k + c] = Mg;
+    a.Phi[v][(int64_t)j * 2 * k + k + c] = -g + beta * Te;
+    a.Meta[v][(int64_t)j * k + c] = -Mg + beta * MTe;
+  }
+}
+
+// ===================================================== Rayleigh-Ritz (end)
+// From the Grams of [X U, Y V] (or [Xhat W]) at the final point: CCA
+// C = Lx^{-1} (U^T Sxy V) Ly^{-T}, SVD via the eigenvectors of C^T C; FDA
+// eigen of L^{-1} (W^T S_B W) L^{-T}.  Rotations rot_v map the point to the
+// canonical weights; a sign convention makes the largest-magnitude entry of
+// each column of U (W) positive.
+struct RRArgs {
+  DevState* st;
+  const double* Gram;     // 2k x 2k (CCA: [P_U | Q_V]) or k x k (FDA)
+  const double* phipart;  // [view][nblk][2k x 2k] Gram of Phi (U^T U in the corner)
+  int nblk, k, kind, l;
+  const double* YPhi;     // FDA (l x 2k)
+};
+
+__global__ void rr_kernel(RRArgs a) {
+  extern __shared__ double rsm[];
+  DevState* st = a.st;
+  const int k = a.k, kk = k * k, k2 = 2 * k;
+  double* Gx = rsm;
+  double* Gy = Gx + kk;
+  double* C = Gy + kk;
+  double* Lxi = C + kk;
+  double* Lyi = Lxi + kk;
+  double* T1 = Lyi + kk;
+  double* T2 = T1 + kk;
+  double* Q = T2 + kk;
+  double* lam = Q + kk;
+  double* rot = lam + kMaxK;
+  double* phig = rot + 100;  // 2 x 4kk
+  const int nv = a.kind == kCCA ? 2 : 1;
+  for (int v = 0; v < nv; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * kk, a.nblk, 4 * kk, phig + v * 4 * kk);
+  const int NC = a.kind == kCCA ? 2 * k : k;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    int i = e / k, j = e % k;
+    Gx[e] = a.Gram[i * NC + j] + st->lam[0] * phig[i * k2 + j];
+    if (a.kind == kCCA) {
+      Gy[e] = a.Gram[(k + i) * NC + k + j] + st->lam[1] * phig[4 * kk + i * k2 + j];
+      C[e] = a.Gram[i * NC + k + j];
+    } else {
+      double s = 0;
+      for (int c = 0; c < a.l; ++c) s += a.YPhi[c * k2 + i] * a.YPhi[c * k2 + j];
+      C[e] = s;
+    }
+  }
+  __syncthreads();
+  bool ok = blk_chol(Gx, k);
+  if (a.kind == kCCA) ok = blk_chol(Gy, k) && ok;
+  if (!ok) {
+    if (threadIdx.x == 0) st->status = GBCCA_ERR_NOT_SPD;
+    return;
+  }
+  blk_lower_inv(Gx, Lxi, k);
+  if (a.kind == kCCA) blk_lower_inv(Gy, Lyi, k);
+  else
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) Lyi[e] = Lxi[e];
+  __syncthreads();
+  blk_mm(Lxi, false, C, false, T1, k, k, k, k, k);   // Lx^{-1} C
+  blk_mm(T1, false, Lyi, true, C, k, k, k, k, k);    // ... Ly^{-T}  => whitened cross (or FDA matrix)
+  if (a.kind == kCCA) {
+    blk_mm(C, true, C, false, T1, k, k, k, k, k);    // C^T C
+  } else {
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      int i = e / k, j = e % k;
+      T1[e] = 0.5 * (C[i * k + j] + C[j * k + i]);
+    }
+    __syncthreads();
+  }
+  blk_jacobi(T1, Q, lam, k, rot);                    // right singular vectors (CCA) / eigvecs (FDA)
+  // CCA: sigma_i = ||C q_i||, left vectors a_i = C q_i / sigma_i
+  if (a.kind == kCCA) {
+    blk_mm(C, false, Q, false, T2, k, k, k, k, k);   // C Q (columns a_i sigma_i)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      double s = 0;
+      for (int r = 0; r < k; ++r) s += T2[r * k + i] * T2[r * k + i];
+      st->sigma[i] = sqrt(s);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      int c = e % k;
+      double sg = st->sigma[c];
+      T2[e] = sg > 0 ? T2[e] / sg : 0.0;
+    }
+    __syncthreads();
+  } else {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) st->sigma[i] = lam[i];
+    __syncthreads();
+  }
+  // rot_x = Lx^{-T} A (A = T2 for CCA, Q for FDA); rot_y = Ly^{-T} Q
+  blk_mm(Lxi, true, a.kind == kCCA ? T2 : Q, false, st->rot[0], k, k, k, k, k);
+  if (a.kind == kCCA) blk_mm(Lyi, true, Q, false, st->rot[1], k, k, k, k, k);
+}
+
+// out_v (d x k) = Phi_v[:, :k] rot_v, then the sign convention.
+__global__ void rr_apply_kernel(DevState* st, const double* Phi, int d, int k, int v, double* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  for (int c = 0; c < k; ++c) {
+    double s = 0;
+    for (int q = 0; q < k; ++q) s += Phi[(int64_t)j * 2 * k + q] * st->rot[v][q * k + c];
+    out[(int64_t)j * k + c] = s;
+  }
+}
+
+// sign[c] from view 0: +1 if the largest-magnitude entry of column c is > 0
+__global__ void sign_fix_kernel(double* U, int dx, double* V, int dy, int k) {
+  const int c = threadIdx.x;
+  if (c >= k) return;
+  double best = 0;
+  for (int j = 0; j < dx; ++j) {
+    double u = U[(int64_t)j * k + c];
+    if (fabs(u) > fabs(best)) best = u;
+  }
+  if (best < 0) {
+    for (int j = 0; j < dx; ++j) U[(int64_t)j * k + c] = -U[(int64_t)j * k + c];
+    if (V != nullptr)
+      for (int j = 0; j < dy; ++j) V[(int64_t)j * k + c] = -V[(int64_t)j * k + c];
+  }
+}
+
+__global__ void copy_sigma_kernel(const DevState* st, double* out, int k) {
+  if (threadIdx.x < k) out[threadIdx.x] = st->sigma[threadIdx.x];
+}
+
+// FDA: Yhat Phi (l x 2k)
+__global__ void yphi_kernel(const DevState* st, const double* Yhat, const double* Phi, int l, int d, int k2,
+                            double* YPhi, int check_done) {
+  if (check_done && st->done) return;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= l * k2) return;
+  int c = e / k2, q = e % k2;
+  double s = 0;
+  for (int j = 0; j < d; ++j) s += Yhat[(int64_t)c * d + j] * Phi[(int64_t)j * k2 + q];
+  YPhi[e] = s;
+}
+
+// ============================================================== driver
+namespace {
+
+int minv(Plan& p, int v, cudaStream_t st) {
+  View& w = p.v[v];
+  const int k = p.k, k2 = 2 * k, k4 = 4 * k;
+  // tmp = R^{-T} RR[:, 0:2k]; LL[:, 0:2k] = R^{-1} tmp
+  if (p.dtype == GBCCA_FP64) {
+    GB_TRY(mat_thin<double>(w.Rinv, w.d, w.d, true, true, w.RR, k4, w.tmp, k2, k2, st));
+    GB_TRY(mat_thin<double>(w.Rinv, w.d, w.d, false, true, w.tmp, k2, w.LL, k4, k2, st));
+  } else {
+    GB_TRY(mat_thin<float>(w.Rinv32, w.d, w.d, true, true, w.RR, k4, w.tmp, k2, k2, st));
+    GB_TRY(mat_thin<float>(w.Rinv32, w.d, w.d, false, true, w.tmp, k2, w.LL, k4, k2, st));
+  }
+  return GBCCA_OK;
+}
+
+int phigram(Plan& p, cudaStream_t st, const int* done) {
+  const int k2 = 2 * p.k;
+  return thin_gram(p, p.v[0].Phi, p.nviews > 1 ? p.v[1].Phi : nullptr, k2, p.v[0].Phi,
+                   p.nviews > 1 ? p.v[1].Phi : nullptr, k2, k2, k2, p.phipart, st, done);
+}
+
+int yphi(Plan& p, cudaStream_t st, int check_done) {
+  if (p.kind != kLDA) return GBCCA_OK;
+  int len = p.l * 2 * p.k;
+  yphi_kernel<<<ceil_div(len, 128), 128, 0, st>>>(p.st, p.Yhat, p.v[0].Phi, p.l, p.D, 2 * p.k, p.YPhi, check_done);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+int thin_blocks(const Plan& p) {
+  int dmax = 0;
+  for (int v = 0; v < p.nviews; ++v) dmax = std::max(dmax, p.v[v].d);
+  return ceil_div(dmax, 64);
+}
+
+// One iteration (or, with force_zero_step set on the device, the qf_B
+// normalization of the starting point).
+int iteration(Plan& p, bool low, cudaStream_t st) {
+  const int k = p.k, kk = k * k;
+  const int* done = &p.st->done;
+  GB_TRY(fused_pass(p, low, false, st, 0, done));
+  GB_TRY(phigram(p, st, done));
+  GB_TRY(yphi(p, st, 1));
+  {
+    LSArgs a{};
+    a.st = p.st;
+    a.Gram = p.Gram;
+    a.phipart = p.phipart;
+    a.nblk = thin_blocks(p);
+    a.NC = p.NC;
+    a.k = k;
+    a.nviews = p.nviews;
+    a.kind = p.kind;
+    a.YPhi = p.YPhi;
+    a.l = p.l;
+    a.history = p.history;
+    a.max_iter = p.opt.max_iter;
+    size_t smem = sizeof(double) * (9 * kk + 8 * kk + kLSWarps * 4 * kk);
+    GB_CUDA(cudaFuncSetAttribute(linesearch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    linesearch_kernel<<<1, 32 * kLSWarps, smem, st>>>(a);
+    GB_CHECK_LAUNCH();
+  }
+  {
+    UpdArgs a{};
+    a.st = p.st;
+    a.G = p.G;
+    a.NC = p.NC;
+    a.k = k;
+    a.nviews = p.nviews;
+    a.kind = p.kind;
+    a.l = p.l;
+    a.D = p.D;
+    a.Yhat = p.Yhat;
+    int dofs = 0, dmax = 0;
+    for (int v = 0; v < p.nviews; ++v) {
+      a.Phi[v] = p.v[v].Phi;
+      a.LL[v] = p.v[v].LL;
+      a.RR[v] = p.v[v].RR;
+      a.Meta[v] = p.v[v].Meta;
+      a.gold[v] = p.v[v].gold;
+      a.Mgold[v] = p.v[v].Mgold;
+      a.d[v] = p.v[v].d;
+      a.dofs[v] = dofs;
+      dofs += p.v[v].d;
+      dmax = std::max(dmax, p.v[v].d);
+    }
+    update_kernel<<<dim3(ceil_div(dmax, 64), p.nviews), 64, 0, st>>>(a);
+    GB_CHECK_LAUNCH();
+  }
+  for (int v = 0; v < p.nviews; ++v) GB_TRY(minv(p, v, st));
+  GB_TRY(thin_gram(p, p.v[0].LL, p.nviews > 1 ? p.v[1].LL : nullptr, 4 * k, p.v[0].RR,
+                   p.nviews > 1 ? p.v[1].RR : nullptr, 4 * k, 4 * k, 4 * k, p.crosspart, st, done));
+  {
+    DirArgs a{};
+    a.st = p.st;
+    a.crosspart = p.crosspart;
+    a.nblk = thin_blocks(p);
+    a.k = k;
+    a.nviews = p.nviews;
+    a.history = p.history;
+    a.max_iter = p.opt.max_iter;
+    size_t smem = sizeof(double) * (2 * 16 * kk + 4 * kk + kMaxK + 100 + 16);
+    GB_CUDA(cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    direction_kernel<<<1, 256, smem, st>>>(a);
+    GB_CHECK_LAUNCH();
+  }
+  {
+    NewArgs a{};
+    a.st = p.st;
+    a.k = k;
+    a.nviews = p.nviews;
+    int dmax = 0;
+    for (int v = 0; v < p.nviews; ++v) {
+      a.Phi[v] = p.v[v].Phi;
+      a.Meta[v] = p.v[v].Meta;
+      a.gold[v] = p.v[v].gold;
+      a.Mgold[v] = p.v[v].Mgold;
+      a.LL[v] = p.v[v].LL;
+      a.RR[v] = p.v[v].RR;
+      a.d[v] = p.v[v].d;
+      dmax = std::max(dmax, p.v[v].d);
+    }
+    newdir_kernel<<<dim3(ceil_div(dmax, 64), p.nviews), 64, 0, st>>>(a);
+    GB_CHECK_LAUNCH();
+  }
+  return GBCCA_OK;
+}
+
+}  // namespace
+
+__global__ void state_init_kernel(DevState* st, double gtol, int max_iter, double lam0, double lam1) {
+  st->iter = 0;
+  st->done = 0;
+  st->status = GBCCA_OK;
+  st->stalled = 0;
+  st->passes = 0;
+  st->ls_trials = 0;
+  st->first = 1;
+  st->force_zero_step = 1;
+  st->t = st->f = st->df = st->t_prev = st->df_prev = st->gn = st->gn0 = st->beta = st->t0 = 0;
+  st->gtol = gtol;
+  st->max_iter = max_iter;
+  st->lam[0] = lam0;
+  st->lam[1] = lam1;
+}
+
+// Starting point in Phi[:, :k] (eta = 0 and all carried vectors zero).
+__global__ void start_kernel(const double* src, double* Phi, double* Meta, double* gold, double* Mgold, int d, int k) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  for (int c = 0; c < k; ++c) {
+    Phi[(int64_t)j * 2 * k + c] = src[(int64_t)j * k + c];
+    Phi[(int64_t)j * 2 * k + k + c] = 0.0;
+    Meta[(int64_t)j * k + c] = 0.0;
+    gold[(int64_t)j * k + c] = 0.0;
+    Mgold[(int64_t)j * k + c] = 0.0;
+  }
+}
+
+int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals, gbcca_info* info,
+            cudaStream_t st) {
+  const int k = p.k;
+  const bool low = p.dtype != GBCCA_FP64;
+  const double gtol = tol > 0 ? tol : p.opt.gtol;
+  state_init_kernel<<<1, 1, 0, st>>>(p.st, gtol, p.opt.max_iter, p.v[0].lam, p.nviews > 1 ? p.v[1].lam : 0.0);
+  GB_CHECK_LAUNCH();
+  double muh[kMaxK];
+  for (int i = 0; i < k; ++i) muh[i] = mu ? mu[i] : (double)(k - i);
+  GB_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(p.st) + offsetof(DevState, mu), muh, sizeof(double) * k,
+                          cudaMemcpyHostToDevice, st));
+  for (int v = 0; v < p.nviews; ++v) {
+    const double* src = p.opt.warm_start ? p.v[v].warm : (v == 0 ? out0 : out1);
+    start_kernel<<<ceil_div(p.v[v].d, 128), 128, 0, st>>>(src, p.v[v].Phi, p.v[v].Meta, p.v[v].gold, p.v[v].Mgold,
+                                                          p.v[v].d, k);
+    GB_CHECK_LAUNCH();
+  }
+  GB_CUDA(cudaMemsetAsync(p.history, 0, sizeof(double) * 3 * (p.opt.max_iter + 1), st));
+  // qf_B of the start (zero step), then iterations in batches
+  GB_TRY(iteration(p, low, st));
+  int launched = 0;
+  int passes = 1;
+  const int batch = std::max(1, p.opt.check_every);
+  while (true) {
+    GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (p.st_host->done || launched >= p.opt.max_iter) break;
+    for (int b = 0; b < batch && launched < p.opt.max_iter; ++b, ++launched) GB_TRY(iteration(p, low, st));
+  }
+  const DevState& hs = *p.st_host;
+  passes += hs.iter;
+  // Rayleigh-Ritz at the final point from an FP64 pass over [X U, Y V]
+  GB_TRY(fused_pass(p, false, true, st, k, nullptr));
+  GB_TRY(phigram(p, st, nullptr));
+  GB_TRY(yphi(p, st, 0));
+  {
+    RRArgs a{};
+    a.st = p.st;
+    a.Gram = p.Gram;
+    a.phipart = p.phipart;
+    a.nblk = thin_blocks(p);
+    a.k = k;
+    a.kind = p.kind;
+    a.l = p.l;
+    a.YPhi = p.YPhi;
+    size_t smem = sizeof(double) * (9 * k * k + kMaxK + 100 + 8 * k * k);
+    GB_CUDA(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rr_kernel<<<1, 256, smem, st>>>(a);
+    GB_CHECK_LAUNCH();
+  }
+  for (int v = 0; v < p.nviews; ++v) {
+    double* out = v == 0 ? out0 : out1;
+    rr_apply_kernel<<<ceil_div(p.v[v].d, 128), 128, 0, st>>>(p.st, p.v[v].Phi, p.v[v].d, k, v, out);
+    GB_CHECK_LAUNCH();
+  }
+  sign_fix_kernel<<<1, 32, 0, st>>>(out0, p.v[0].d, p.nviews > 1 ? out1 : nullptr, p.nviews > 1 ? p.v[1].d : 0, k);
+  GB_CHECK_LAUNCH();
+  copy_sigma_kernel<<<1, 32, 0, st>>>(p.st, vals, k);
+  GB_CHECK_LAUNCH();
+  GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  GB_CUDA(cudaStreamSynchronize(st));
+  int status = p.st_host->status;
+  if (info != nullptr) {
+    info->iters = p.st_host->iter;
+    info->passes = passes + 1;
+    info->status = status;
+    info->stalled = p.st_host->stalled;
+    info->grad_norm = p.st_host->gn;
+    info->grad_norm0 = p.st_host->gn0;
+    info->objective = p.st_host->f;
+  }
+  return status;
+}
+
+// ============================================================ warm start
+// CCA: top-k singular pairs of C = R_x^{-T} (X_S^T Y_S) R_y^{-1} by block
+// power iteration with CholeskyQR re-orthonormalization (2k columns), then a
+// Rayleigh-Ritz step; U~ = R_x^{-1} A_k, V~ = R_y^{-1} B_k (exact CCA of the
+// sketched pair, Alg. 1 step 4).  FDA: eigen of G G^T with G = Yhat R^{-1}
+// (l x l), W~ = R^{-1} G^T Q_k diag(lambda)^{-1/2} (Alg. 2 step 5).
+
+__global__ void rand_block_kernel(double* B, int d, int c, uint64_t seed) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d * c) return;
+  uint64_t r = sm64(seed ^ 0xA5A5A5A5DEADBEEFull, (uint64_t)e);
+  B[e] = (double)(r >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+// small Gram (c x c) of a d x c block: reduce partials, Cholesky (ridge for
+// safety) -> upper R in out (R^T R = G), and its inverse in out + c*c.
+__global__ void small_chol_kernel(const double* part, int nblk, int c, double* out, int* flag) {
+  extern __shared__ double ssm[];
+  double* G = ssm;
+  double* Li = G + c * c;
+  sum_blocks(part, nblk, c * c, G);
+  double tr = 0;
+  for (int i = 0; i < c; ++i) tr += G[i * c + i];
+  __syncthreads();
+  if (threadIdx.x < c) G[threadIdx.x * c + threadIdx.x] += 1e-14 * tr / c;
+  __syncthreads();
+  if (!blk_chol(G, c)) {
+    if (threadIdx.x == 0) atomicExch(flag, 1);
+  }
+  blk_lower_inv(G, Li, c);
+  // R^{-1} = (L^{-1})^T
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    int i = e / c, j = e % c;
+    out[e] = Li[j * c + i];
+  }
+}
+
+// B (d x c) <- B Rinv (c x c upper), rows in parallel
+__global__ void apply_small_kernel(double* B, int d, int c, const double* Rinv) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  double row[2 * kMaxK];
+  for (int q = 0; q < c; ++q) row[q] = B[(int64_t)j * c + q];
+  for (int q = 0; q < c; ++q) {
+    double s = 0;
+    for (int r = 0; r <= q; ++r) s += row[r] * Rinv[r * c + q];
+    B[(int64_t)j * c + q] = s;
+  }
+}
+
+// Rayleigh-Ritz of the power iteration: Bsmall = U^T (C V) (c x c), take the
+// top-k singular pairs: U A_k, V B_k in out (d x k each).
+__global__ void small_svd_kernel(const double* part, int nblk, int c, int k, double* rotU, double* rotV) {
+  extern __shared__ double wsm[];
+  double* Bm = wsm;
+  double* T = Bm + c * c;
+  double* Q = T + c * c;
+  double* lam = Q + c * c;
+  double* rot = lam + 2 * kMaxK;
+  sum_blocks(part, nblk, c * c, Bm);
+  blk_mm(Bm, true, Bm, false, T, c, c, c, c, c);  // B^T B
+  blk_jacobi(T, Q, lam, c, rot);                 // right singular vectors
+  blk_mm(Bm, false, Q, false, T, c, c, c, c, c);  // B Q = A Sigma
+  for (int e = threadIdx.x; e < c * k; e += blockDim.x) {
+    int r = e / k, i = e % k;
+    double s = 0;
+    for (int q = 0; q < c; ++q) s += T[q * c + i] * T[q * c + i];
+    s = sqrt(s);
+    rotU[r * k + i] = s > 0 ? T[r * c + i] / s : 0.0;
+    rotV[r * k + i] = Q[r * c + i];
+  }
+}
+
+__global__ void thin_apply_kernel(const double* B, int d, int c, const double* rot, int k, double* out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d) return;
+  for (int i = 0; i < k; ++i) {
+    double s = 0;
+    for (int q = 0; q < c; ++q) s += B[(int64_t)j * c + q] * rot[q * k + i];
+    out[(int64_t)j * k + i] = s;
+  }
+}
+
+// FDA warm start pieces
+__global__ void transpose_kernel(const double* A, int r, int c, double* At) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * c) return;
+  int i = e / c, j = e % c;
+  At[(int64_t)j * r + i] = A[e];
+}
+
+__global__ void fda_warm_kernel(const double* part, int nblk, int l, int k, double* rot) {
+  extern __shared__ double fsm[];
+  double* K = fsm;
+  double* Q = K + l * l;
+  double* lam = Q + l * l;
+  double* r = lam + kMaxClasses;
+  sum_blocks(part, nblk, l * l, K);
+  blk_jacobi(K, Q, lam, l, r);
+  for (int e = threadIdx.x; e < l * k; e += blockDim.x) {
+    int q = e / k, i = e % k;
+    rot[e] = lam[i] > 0 ? Q[q * l + i] / sqrt(lam[i]) : 0.0;
+  }
+}
+
+namespace {
+
+int orth(Plan& p, double* B, int d, int c, double* part, double* small, cudaStream_t st) {
+  // Gram of B (d x c) via a one-view thin Gram
+  ThinArgs a{};
+  a.A[0] = B;
+  a.B[0] = B;
+  a.lda[0] = c;
+  a.ldb[0] = c;
+  a.d[0] = d;
+  a.ca = c;
+  a.cb = c;
+  a.nblk = ceil_div(d, 64);
+  a.part = part;
+  a.done = nullptr;
+  size_t smem = sizeof(double) * 64 * 2 * c;
+  GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
+  GB_CHECK_LAUNCH();
+  small_chol_kernel<<<1, 256, sizeof(double) * 2 * c * c, st>>>(part, a.nblk, c, small, p.flag);
+  GB_CHECK_LAUNCH();
+  apply_small_kernel<<<ceil_div(d, 128), 128, 0, st>>>(B, d, c, small);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+}  // namespace
+
+int warm_start(Plan& p, cudaStream_t st) {
+  const int k = p.k;
+  if (p.kind == kCCA) {
+    View& x = p.v[0];
+    View& y = p.v[1];
+    const int dx = x.d, dy = y.d;
+    const int c = std::min(2 * k, std::min(dx, dy));
+    // Cxy = X_S^T Y_S (dx x dy), kept in ws after the Gram partials
+    double* Cxy = p.ws + (p.ws_len - (int64_t)dx * dy);
+    GB_TRY(gram_tn(x.SZ, dx, y.SZ, dy, p.s, dx, dy, Cxy, 0.0, p.ws, p.ws_len - (int64_t)dx * dy, st));
+    double* Vb = y.wsU;  // dy x c
+    double* Ub = x.wsU;  // dx x c
+    double* part = p.crosspart;
+    double* small = p.phigram;
+    rand_block_kernel<<<ceil_div(dy * c, 256), 256, 0, st>>>(Vb, dy, c, p.opt.seed);
+    GB_CHECK_LAUNCH();
+    GB_TRY(orth(p, Vb, dy, c, part, small, st));
+    const int iters = 12;
+    for (int it = 0; it <= iters; ++it) {
+      // U = orth(R_x^{-T} Cxy R_y^{-1} V)
+      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, Vb, c, y.wsT, c, c, st));
+      GB_TRY(mat_thin<double>(Cxy, dx, dy, false, false, y.wsT, c, x.wsT, c, c, st));
+      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, true, true, x.wsT, c, Ub, c, c, st));
+      if (it == iters) break;  // Ub = C V (unnormalized) for the Rayleigh-Ritz step
+      GB_TRY(orth(p, Ub, dx, c, part, small, st));
+      // V = orth(R_y^{-T} Cxy^T R_x^{-1} U)
+      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, Ub, c, x.wsT, c, c, st));
+      GB_TRY(mat_thin<double>(Cxy, dx, dy, true, false, x.wsT, c, y.wsT, c, c, st));
+      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, true, true, y.wsT, c, Vb, c, c, st));
+      GB_TRY(orth(p, Vb, dy, c, part, small, st));
+    }
+    // Ub = C V: take U0 = orth(Ub) and Bm = U0^T (C V)
+    GB_CUDA(cudaMemcpyAsync(x.wsT, Ub, sizeof(double) * dx * c, cudaMemcpyDeviceToDevice, st));
+    GB_TRY(orth(p, Ub, dx, c, part, small, st));
+    {
+      ThinArgs a{};
+      a.A[0] = Ub;
+      a.B[0] = x.wsT;
+      a.lda[0] = c;
+      a.ldb[0] = c;
+      a.d[0] = dx;
+      a.ca = c;
+      a.cb = c;
+      a.nblk = ceil_div(dx, 64);
+      a.part = part;
+      size_t smem = sizeof(double) * 64 * 2 * c;
+      GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
+      GB_CHECK_LAUNCH();
+      double* rotU = small;
+      double* rotV = small + c * k;
+      size_t sm2 = sizeof(double) * (3 * c * c + 2 * kMaxK + 100);
+      GB_CUDA(cudaFuncSetAttribute(small_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+      small_svd_kernel<<<1, 256, sm2, st>>>(part, a.nblk, c, k, rotU, rotV);
+      GB_CHECK_LAUNCH();
+      // whitened top-k vectors, then back through R^{-1}
+      thin_apply_kernel<<<ceil_div(dx, 128), 128, 0, st>>>(Ub, dx, c, rotU, k, x.wsT);
+      thin_apply_kernel<<<ceil_div(dy, 128), 128, 0, st>>>(Vb, dy, c, rotV, k, y.wsT);
+      GB_CHECK_LAUNCH();
+      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, x.wsT, k, x.warm, k, k, st));
+      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, y.wsT, k, y.warm, k, k, st));
+    }
+    return GBCCA_OK;
+  }
+  // FDA
+  View& x = p.v[0];
+  const int d = x.d, l = p.l;
+  double* YhT = x.wsT;              // d x l  (wsT has d x 2k >= ... use ws instead when l > 2k)
+  double* Gt = p.ws;                // d x l: R^{-T} Yhat^T
+  double* YT = p.ws + (int64_t)d * l;
+  (void)YhT;
+  transpose_kernel<<<ceil_div(l * d, 256), 256, 0, st>>>(p.Yhat, l, d, YT);
+  GB_CHECK_LAUNCH();
+  GB_TRY(mat_thin<double>(x.Rinv, d, d, true, true, YT, l, Gt, l, l, st));
+  {
+    ThinArgs a{};
+    a.A[0] = Gt;
+    a.B[0] = Gt;
+    a.lda[0] = l;
+    a.ldb[0] = l;
+    a.d[0] = d;
+    a.ca = l;
+    a.cb = l;
+    a.nblk = ceil_div(d, 64);
+    a.part = p.crosspart;
+    size_t smem = sizeof(double) * 64 * 2 * l;
+    GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
+    GB_CHECK_LAUNCH();
+    double* rot = p.phigram;  // l x k
+    size_t sm2 = sizeof(double) * (2 * l * l + kMaxClasses + 100);
+    GB_CUDA(cudaFuncSetAttribute(fda_warm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    fda_warm_kernel<<<1, 256, sm2, st>>>(p.crosspart, a.nblk, l, k, rot);
+    GB_CHECK_LAUNCH();
+    double* Wwh = p.ws + 2 * (int64_t)d * l;  // d x k
+    thin_apply_kernel<<<ceil_div(d, 128), 128, 0, st>>>(Gt, d, l, rot, k, Wwh);
+    GB_CHECK_LAUNCH();
+    GB_TRY(mat_thin<double>(x.Rinv, d, d, false, true, Wwh, k, x.warm, k, k, st));
+  }
+  return GBCCA_OK;
+}
+
+}  // namespace gbcca

@@ -72,12 +72,16 @@ def _colscale(d: int, colscale):
 
 
 def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float = 0.5,
-                       colscale=None, dtype: str = "f64", seed: int = 0, chunk: int = 65536):
+                       colscale=None, dtype: str = "f64", seed: int = 0, chunk: int = 65536,
+                       latent_scale=None):
     """Two views sharing a latent signal: X = (Z Ax + noise Ex) diag(c), same for Y.
 
     Z (n x latent), Ax, Ay, Ex, Ey are i.i.d. N(0, 1).  ``colscale=(1, 1e-4)``
     multiplies column j by 10^(-4 j / (d - 1)), which makes X^T X
     ill-conditioned (kappa ~ 1e8) without mixing the columns.
+    ``latent_scale`` (length latent) multiplies the latent columns, which
+    spreads the canonical correlations apart (equal scales give near-equal
+    correlations).
     Returns dict(X, Y, X64, Y64) where X/Y are in the storage dtype (uint16
     bit patterns for bf16) and X64/Y64 are the stored values in float64.
     """
@@ -93,6 +97,8 @@ def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float 
         r1 = min(n, r0 + chunk)
         m = r1 - r0
         Z = rng.standard_normal((m, latent))
+        if latent_scale is not None:
+            Z = Z * np.asarray(latent_scale, dtype=np.float64)[None, :]
         Ex = rng.standard_normal((m, dx), dtype=wdt)
         Ey = rng.standard_normal((m, dy), dtype=wdt)
         xb = (Z @ Ax).astype(wdt) + wdt(noise) * Ex

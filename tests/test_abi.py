@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/gbcca.h declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "gbcca.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    return ctypes.CDLL(os.path.join(ROOT, "paper_2106_12060_gb300", "libgbcca.so"))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("cca_plan", "cca_precondition", "cca_solve", "lda_plan", "lda_solve", "gbcca_fused_pass"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), f"{name} declared in gbcca.h but not exported"
+
+
+def test_binding_covers_every_symbol():
+    from paper_2106_12060_gb300 import _lib
+    assert set(_declared()) == set(_lib.SIGNATURES)
+
+
+def test_host_only_calls(lib):
+    """Entry points that need no device: defaults, status strings, argument checks."""
+    from paper_2106_12060_gb300 import _lib
+    L = _lib.load()
+    o = _lib.Options()
+    assert L.gbcca_default_options(ctypes.byref(o)) == 0
+    assert o.max_iter == 1000 and o.warm_start == 1 and o.check_every == 8
+    assert L.gbcca_default_options(None) == _lib.ERR_INVALID_ARG
+    assert L.gbcca_status_string(_lib.ERR_NOT_SPD) == b"matrix not positive definite"
+    h = ctypes.c_void_p()
+    # k > min(dx, dy) is rejected before any device work
+    assert L.cca_plan(ctypes.byref(h), 100, 5, 4, 6, 2, None) == _lib.ERR_INVALID_ARG
+    assert L.lda_plan(ctypes.byref(h), 100, 5, 3, 3, 2, None) == _lib.ERR_INVALID_ARG
+    assert b"k" in L.gbcca_last_error()

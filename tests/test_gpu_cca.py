@@ -1,0 +1,181 @@
+"""GPU parity of the CCA hot path (Alg. 1) against the CPU oracle, through the C ABI.
+
+Tolerances: FP64 data -> results within 1e-8 relative of the oracle (sketch,
+R, pass: ~1e-12, set by FP64 rounding of sums of length <= n); BF16/FP32
+data -> pass outputs within the FP32-accumulation bound below, canonical
+correlations within 1e-6 relative after the FP64 Rayleigh-Ritz refinement.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import to_dev, np64, rel, subspace_sin
+from oracle import cca as OC
+from oracle import fused as OF
+from oracle import rcg as ORCG
+from oracle import rng as ORNG
+from oracle.precond import precond_R
+from oracle.sketch import countsketch_apply, srht_apply
+from synth import cca_latent_problem, countsketch_draws, srht_draws
+
+pytestmark = pytest.mark.gpu
+
+SEP = [1.0, 0.6, 0.35, 0.2]
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2106_12060_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _plan(gb, P, n, dx, dy, k, dt, lam, sketch=0, s=0, h=None, g=None, **opt):
+    o = gb.default_options(sketch=sketch, s=s, **opt)
+    plan = gb.cca_plan(n, dx, dy, k, dt, o)
+    X, Y = to_dev(P["X"], dt), to_dev(P["Y"], dt)
+    gb.cca_precondition(plan, X, Y, lam, lam, h, g)
+    return plan, X, Y
+
+
+def test_countsketch_explicit_draws_fp64(gb):
+    import torch
+    n, dx, dy, s = 3001, 37, 29, 200  # ragged sizes: not multiples of any tile
+    P = cca_latent_problem(n, dx, dy, latent=5, dtype="f64", seed=1)
+    h, g = countsketch_draws(n, s, seed=4)
+    plan, _, _ = _plan(gb, P, n, dx, dy, 3, "f64", 1e-2, s=s, h=torch.from_numpy(h).cuda(),
+                       g=torch.from_numpy(g).cuda())
+    SX = np64(gb.query(plan, gb.Q_SKETCH_X)).reshape(s, dx)
+    SY = np64(gb.query(plan, gb.Q_SKETCH_Y)).reshape(s, dy)
+    assert rel(SX, countsketch_apply(P["X64"], h, g, s)) < 1e-13
+    assert rel(SY, countsketch_apply(P["Y64"], h, g, s)) < 1e-13
+    # R factor: R^T R = (SX)^T SX + lambda I and equal to the oracle's QR factor
+    Rx = np64(gb.query(plan, gb.Q_R_X)).reshape(dx, dx)
+    Ro = precond_R(countsketch_apply(P["X64"], h, g, s), 1e-2)
+    assert rel(Rx, Ro) < 1e-10
+    assert np.allclose(np.tril(Rx, -1), 0)
+
+
+def test_countsketch_library_draws_bitexact(gb):
+    n, s, seed = 100003, 977, 12345
+    h, g = gb.sketch_draws(gb.COUNTSKETCH, n, s, seed)
+    ho, go = ORNG.countsketch_hash(n, s, seed)
+    assert np.array_equal(h.cpu().numpy(), ho)
+    assert np.array_equal(g.cpu().numpy(), go)
+
+
+def test_srht_library_draws_bitexact(gb):
+    for m, s in ((12, 300), (13, 1000)):
+        rows, signs = gb.sketch_draws(gb.SRHT, 1 << m, s, 77)
+        assert np.array_equal(rows.cpu().numpy(), ORNG.srht_rows(1 << m, s, 77))
+        assert np.array_equal(signs.cpu().numpy(), ORNG.srht_signs(1 << m, 77))
+
+
+@pytest.mark.parametrize("dt,tol", [("f64", 1e-12), ("f32", 2e-6), ("bf16", 2e-6)])
+def test_srht_sketch(gb, dt, tol):
+    import torch
+    n, dx, dy, s = 5000, 40, 33, 300   # n_pad = 8192 = 2^13 -> two stages
+    P = cca_latent_problem(n, dx, dy, latent=4, dtype=dt, seed=2)
+    D, rows = srht_draws(8192, s, seed=3)
+    plan, _, _ = _plan(gb, P, n, dx, dy, 2, dt, 1e-2, sketch=gb.SRHT, s=s,
+                       h=torch.from_numpy(rows).cuda(), g=torch.from_numpy(D).cuda())
+    SX = np64(gb.query(plan, gb.Q_SKETCH_X)).reshape(s, dx)
+    assert rel(SX, srht_apply(P["X64"], D, rows)) < tol
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+def test_fused_pass(gb, dt):
+    import torch
+    n, dx, dy, k = 4099, 70, 45, 5
+    P = cca_latent_problem(n, dx, dy, latent=6, dtype=dt, seed=5)
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, dt, 1e-2)
+    rng = np.random.default_rng(0)
+    Px, Py = rng.standard_normal((dx, 2 * k)), rng.standard_normal((dy, 2 * k))
+    Gx, Gy, Gram = gb.fused_pass(plan, torch.from_numpy(Px).cuda(), torch.from_numpy(Py).cuda())
+    ox, oy, og = OF.cca_pass(P["X64"], P["Y64"], Px, Py)
+    # FP32 accumulation: each entry errs by <= ~(sum length) * 6e-8 relative to
+    # the sum of |terms|; compare against the magnitude of the result matrix.
+    tol = 1e-12 if dt == "f64" else 5e-5
+    assert rel(np64(Gx), ox) < tol
+    assert rel(np64(Gy), oy) < tol
+    assert rel(np64(Gram), og) < tol
+
+
+def test_solve_separated_fp64(gb):
+    n, dx, dy, k, lam = 1000, 24, 20, 3, 1e-3
+    P = cca_latent_problem(n, dx, dy, latent=4, noise=0.6, dtype="f64", seed=3, latent_scale=SEP)
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, max_iter=2000, gtol=1e-11)
+    sig, U, V, info = gb.cca_solve(plan)
+    ref, Uo, Vo = OC.cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    assert rel(np64(sig), ref) < 1e-9, (np64(sig), ref, info)
+    Sxx, Syy, Sxy = OC.sigmas(P["X64"], P["Y64"], lam, lam)
+    U, V = np64(U), np64(V)
+    assert np.max(np.abs(U.T @ Sxx @ U - np.eye(k))) < 1e-9
+    assert np.max(np.abs(U.T @ Sxy @ V - np.diag(ref))) < 1e-9
+    assert subspace_sin(U, Uo, Sxx) < 1e-6
+
+
+def test_warm_start_is_sketched_cca(gb):
+    import torch
+    n, dx, dy, k, lam, s = 2000, 30, 26, 3, 1e-2, 240
+    P = cca_latent_problem(n, dx, dy, latent=4, noise=0.6, dtype="f64", seed=6, latent_scale=SEP)
+    h, g = countsketch_draws(n, s, seed=7)
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, s=s, h=torch.from_numpy(h).cuda(),
+                       g=torch.from_numpy(g).cuda())
+    SX, SY = countsketch_apply(P["X64"], h, g, s), countsketch_apply(P["Y64"], h, g, s)
+    _, Uw, Vw = OC.cca_whiten(SX, SY, lam, lam, k)
+    Ug = np64(gb.query(plan, gb.Q_WARM_U)).reshape(dx, k)
+    Mx = SX.T @ SX + lam * np.eye(dx)
+    assert subspace_sin(Ug, Uw, Mx) < 1e-6
+
+
+def test_trajectory_matches_reference_rcg(gb):
+    """Same start, same sketch metric: the GPU iterates follow the oracle's
+    Riemannian CG (same line-search decisions) for the first 25 iterations."""
+    import torch
+    n, dx, dy, k, lam, s = 1500, 20, 16, 3, 1e-2, 144
+    P = cca_latent_problem(n, dx, dy, latent=4, noise=0.6, dtype="f64", seed=8, latent_scale=SEP)
+    h, g = countsketch_draws(n, s, seed=9)
+    iters = 25
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, s=s, h=torch.from_numpy(h).cuda(),
+                       g=torch.from_numpy(g).cuda(), warm_start=0, max_iter=iters, gtol=0.0)
+    rng = np.random.default_rng(1)
+    U0, V0 = rng.standard_normal((dx, k)), rng.standard_normal((dy, k))
+    gb.cca_solve(plan, U=torch.from_numpy(U0.copy()).cuda(), V=torch.from_numpy(V0.copy()).cuda())
+    hist = np64(gb.query(plan, gb.Q_HISTORY)).reshape(-1, 3)[: iters + 1]
+    SX, SY = countsketch_apply(P["X64"], h, g, s), countsketch_apply(P["Y64"], h, g, s)
+    Rx, Ry = precond_R(SX, lam), precond_R(SY, lam)
+    Sxx, Syy, Sxy = OC.sigmas(P["X64"], P["Y64"], lam, lam)
+    from oracle.problems import CCAProblem
+    prob = CCAProblem(Sxx, Syy, Sxy, OC.default_mu(k))
+    res = ORCG.rcg(prob, [Rx.T @ Rx, Ry.T @ Ry], [U0, V0], max_iter=iters, gtol=0.0)
+    ho = np.array(res["history"])
+    m = min(len(ho), iters + 1)
+    assert np.max(np.abs(hist[:m, 0] - ho[:m, 0]) / np.abs(ho[:m, 0])) < 1e-10   # f
+    assert np.max(np.abs(hist[1:m, 2] - ho[1:m, 2]) / np.abs(ho[1:m, 2])) < 1e-8  # accepted steps
+    assert np.max(np.abs(hist[:m, 1] - ho[:m, 1]) / np.abs(ho[:m, 1])) < 1e-6    # ||grad||_M
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_solve_low_precision_refined(gb, dt):
+    n, dx, dy, k, lam = 20000, 64, 48, 4, 1e-4
+    P = cca_latent_problem(n, dx, dy, latent=6, noise=0.5, colscale=(1.0, 1e-4), dtype=dt, seed=10,
+                           latent_scale=[1.0, 0.7, 0.5, 0.35, 0.25, 0.18])
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, dt, lam, sketch=gb.SRHT, max_iter=1000, gtol=1e-7)
+    sig, U, V, info = gb.cca_solve(plan)
+    ref, _, _ = OC.cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    assert rel(np64(sig), ref) < 1e-6, (np64(sig), ref, info)
+
+
+def test_solve_small_fp64_workload(gb):
+    """The plain FP64 workload (n=2000, dx=50, dy=40, k=5, lambda=1e-3, CountSketch
+    s=360).  Its five leading correlations lie within 3e-3 of each other, so CG
+    needs a few thousand iterations; parity is on the canonical correlations."""
+    n, dx, dy, k, lam = 2000, 50, 40, 5, 1e-3
+    P = cca_latent_problem(n, dx, dy, latent=10, noise=0.5, dtype="f64", seed=0)
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, s=360, max_iter=6000, gtol=1e-10, check_every=64)
+    sig, U, V, info = gb.cca_solve(plan)
+    ref, _, _ = OC.cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    assert rel(np64(sig), ref) < 1e-8, (np64(sig), ref, info)
