@@ -80,6 +80,8 @@ typedef struct {
                             problem (Alg. 1 step 4 / Alg. 2 step 5); 0: start
                             from the U/V (W) buffers passed to the solve call  */
   int32_t check_every;   /* iterations between convergence read-backs (8)      */
+  int32_t time_passes;   /* 1: time every fused data pass with CUDA events on
+                            the solve's stream (reported in gbcca_info)         */
 } gbcca_options;
 
 /* Per-solve report (host struct filled by the solve calls). */
@@ -91,11 +93,15 @@ typedef struct {
                             rounding floor), which also ends the iteration      */
   double grad_norm;      /* ||grad||_M at the last iterate                      */
   double grad_norm0;     /* ||grad||_M at the first iterate                     */
-  double objective;      /* f at the returned point (f_CCA or f_FDA)            */
+  double objective;      /* f at the iterate before the final Rayleigh-Ritz step */
+  double pass_ms;        /* with opt.time_passes: mean device time of one fused
+                            pass (ms, CUDA events), else 0                      */
+  int32_t pass_count;    /* passes included in pass_ms                          */
 } gbcca_info;
 
 /* Fills `opt` with defaults (CountSketch, s = 0, seed 0, max_iter 1000,
- * gtol 1e-8, refine 1, warm_start 1, check_every 8).  Returns GBCCA_OK or
+ * gtol 1e-8, refine 1, warm_start 1, check_every 8, time_passes 0).
+ * Returns GBCCA_OK or
  * GBCCA_ERR_INVALID_ARG if opt is NULL. */
 int gbcca_default_options(gbcca_options* opt);
 
@@ -120,7 +126,8 @@ int cca_plan(gbcca_plan_t* plan, int64_t n, int32_t dx, int32_t dy, int32_t k,
  * library draw from opt.seed): CountSketch: h (int32, n entries in [0, s)),
  * g (int8, n entries +-1); SRHT: h = sampled row indices (int32, s entries,
  * distinct, in [0, n_pad)), g = signs (int8, n_pad entries), n_pad the
- * power of two >= n.  Returns GBCCA_ERR_NOT_SPD if a factor breaks down. */
+ * power of two >= n.  Synchronizes `stream` to check the factorizations;
+ * returns GBCCA_ERR_NOT_SPD if a factor breaks down. */
 int cca_precondition(gbcca_plan_t plan, const void* X, int64_t ldx, const void* Y, int64_t ldy,
                      double lambda_x, double lambda_y, const int32_t* sketch_h,
                      const int8_t* sketch_g, void* stream);
@@ -202,6 +209,10 @@ int gbcca_query(gbcca_plan_t plan, int32_t what, double* dst, void* stream);
  * two). */
 int gbcca_sketch_draws(int32_t kind, int64_t n, int64_t s, uint64_t seed, int32_t* h,
                        int8_t* g, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * plans and threads); a host-side counter for profiling. */
+int64_t gbcca_launch_count(void);
 
 void gbcca_plan_destroy(gbcca_plan_t plan);
 const char* gbcca_status_string(int status);

@@ -197,3 +197,11 @@ def gbcca_sketch_draws(kind, n, s, seed, stream=None):
 
 
 sketch_draws = gbcca_sketch_draws
+
+
+def gbcca_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(_lib.load().gbcca_launch_count())
+
+
+launch_count = gbcca_launch_count

@@ -26,6 +26,7 @@ class Options(C.Structure):
         ("refine", C.c_int32),
         ("warm_start", C.c_int32),
         ("check_every", C.c_int32),
+        ("time_passes", C.c_int32),
     ]
 
 
@@ -38,6 +39,8 @@ class Info(C.Structure):
         ("grad_norm", C.c_double),
         ("grad_norm0", C.c_double),
         ("objective", C.c_double),
+        ("pass_ms", C.c_double),
+        ("pass_count", C.c_int32),
     ]
 
     def as_dict(self):
@@ -63,6 +66,7 @@ SIGNATURES = {
     "gbcca_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "gbcca_sketch_draws": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "gbcca_launch_count": (C.c_int64, []),
     "gbcca_plan_destroy": (None, [C.c_void_p]),
     "gbcca_status_string": (C.c_char_p, [C.c_int]),
     "gbcca_last_error": (C.c_char_p, []),

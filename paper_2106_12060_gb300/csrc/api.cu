@@ -10,6 +10,7 @@ namespace gbcca {
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+std::atomic<long long> g_launches{0};
 
 namespace {
 
@@ -53,6 +54,7 @@ void free_plan(Plan* p) {
                   (void*)p->ws, (void*)p->flag})
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
+  for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
   delete p;
 }
 
@@ -148,6 +150,12 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->ws, p->ws_len));
   GB_TRY(dalloc(&p->flag, 1));
   GB_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
+  if (p->opt.time_passes) {
+    for (int i = 0; i < 2 * kMaxTimedBatch; ++i) {
+      GB_CUDA(cudaEventCreate(&p->ev[i]));
+      p->nev = i + 1;
+    }
+  }
   return GBCCA_OK;
 }
 
@@ -280,6 +288,7 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
     for (int v = 0; v < p.nviews; ++v) {
       int d = p.v[v].d;
       identity_kernel<<<ceil_div(d * d, 256), 256, 0, st>>>(p.v[v].R, d);
+      GB_CHECK_LAUNCH();
       identity_kernel<<<ceil_div(d * d, 256), 256, 0, st>>>(p.v[v].Rinv, d);
       GB_CHECK_LAUNCH();
     }
@@ -441,9 +450,11 @@ int gbcca_fused_pass(gbcca_plan_t plan, const double* Phi_x, const double* Phi_y
     GB_CUDA(cudaMemcpyAsync(p->v[1].Phi, Phi_y, sizeof(double) * p->v[1].d * k2, cudaMemcpyDeviceToDevice, st));
   GB_TRY(fused_pass(*p, p->dtype != GBCCA_FP64, false, st, 0, nullptr));
   scatter_rows_kernel<<<ceil_div(p->v[0].d * p->NC, 256), 256, 0, st>>>(p->G, p->NC, 0, p->v[0].d, Gx);
-  if (p->kind == kCCA)
-    scatter_rows_kernel<<<ceil_div(p->v[1].d * p->NC, 256), 256, 0, st>>>(p->G, p->NC, p->v[0].d, p->v[1].d, Gy);
   GB_CHECK_LAUNCH();
+  if (p->kind == kCCA) {
+    scatter_rows_kernel<<<ceil_div(p->v[1].d * p->NC, 256), 256, 0, st>>>(p->G, p->NC, p->v[0].d, p->v[1].d, Gy);
+    GB_CHECK_LAUNCH();
+  }
   GB_CUDA(cudaMemcpyAsync(Gram, p->Gram, sizeof(double) * p->NC * p->NC, cudaMemcpyDeviceToDevice, st));
   return GBCCA_OK;
 }
@@ -494,6 +505,8 @@ int gbcca_sketch_draws(int32_t kind, int64_t n, int64_t s, uint64_t seed, int32_
   }
   return sketch_draws(kind, n, s, seed, h, g, reinterpret_cast<cudaStream_t>(stream));
 }
+
+int64_t gbcca_launch_count(void) { return (int64_t)g_launches.load(); }
 
 void gbcca_plan_destroy(gbcca_plan_t plan) { free_plan(as_plan(plan)); }
 

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <atomic>
 #include <string>
 #include <type_traits>
 
@@ -13,6 +14,7 @@ namespace gbcca {
 
 // ---------------------------------------------------------------- errors
 void set_last_error(const std::string& msg);
+extern std::atomic<long long> g_launches;  // kernels launched by this library
 
 struct Status {
   int code = GBCCA_OK;
@@ -30,6 +32,7 @@ struct Status {
 
 #define GB_CHECK_LAUNCH()                                                                 \
   do {                                                                                    \
+    ::gbcca::g_launches.fetch_add(1, std::memory_order_relaxed);                          \
     cudaError_t e_ = cudaGetLastError();                                                  \
     if (e_ != cudaSuccess) {                                                              \
       ::gbcca::set_last_error(std::string("kernel launch at ") + __FILE__ + ":" +          \

@@ -35,9 +35,9 @@ constexpr int kCI = 10;   // class-sum entries per thread (l * NC <= 2560)
 
 template <typename Tin, typename Tacc, int RN>
 __global__ void __launch_bounds__(256)
-pass_w_kernel(PassViews pv, int64_t n, int NC, Tacc* __restrict__ W, Tacc* __restrict__ partGram,
+pass_w_kernel(PassViews pv, int64_t n, int NC, Tacc* __restrict__ W, double* __restrict__ partGram,
               const int32_t* __restrict__ labels, const Tacc* __restrict__ Cls, int l,
-              Tacc* __restrict__ partCls) {
+              double* __restrict__ partCls) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Tacc* Zs = reinterpret_cast<Tacc*>(smem_raw);              // [32][kTM + 1]
   Tacc* Ps = Zs + 32 * (kTM + 1);                             // [32][8 * RN]
@@ -48,10 +48,12 @@ pass_w_kernel(PassViews pv, int64_t n, int NC, Tacc* __restrict__ W, Tacc* __res
   const int tr = tid & 31, tc = tid >> 5;
   const int PW = 8 * RN;
 
-  Tacc g_acc[kGI];
+  // per-tile sums are formed in Tacc and added into FP64 accumulators, so
+  // FP32 rounding only ever acts on sums of kTM = 64 terms
+  double g_acc[kGI];
 #pragma unroll
   for (int i = 0; i < kGI; ++i) g_acc[i] = 0;
-  Tacc c_acc[kCI];
+  double c_acc[kCI];
 #pragma unroll
   for (int i = 0; i < kCI; ++i) c_acc[i] = 0;
 
@@ -127,7 +129,7 @@ pass_w_kernel(PassViews pv, int64_t n, int NC, Tacc* __restrict__ W, Tacc* __res
         int a = e / NC, b = e % NC;
         Tacc s = 0;
         for (int r = 0; r < kTM; ++r) s += Wt[r * NC + a] * Wt[r * NC + b];
-        g_acc[i] += s;
+        g_acc[i] += (double)s;
       }
     }
     if (labels != nullptr) {
@@ -139,7 +141,7 @@ pass_w_kernel(PassViews pv, int64_t n, int NC, Tacc* __restrict__ W, Tacc* __res
           Tacc s = 0;
           for (int r = 0; r < kTM; ++r)
             if (ys[r] == cls) s += Wt[r * NC + c];
-          c_acc[i] += s;
+          c_acc[i] += (double)s;
         }
       }
     }
@@ -162,7 +164,7 @@ pass_w_kernel(PassViews pv, int64_t n, int NC, Tacc* __restrict__ W, Tacc* __res
 template <typename Tin, typename Tacc, int RQ>
 __global__ void __launch_bounds__(256)
 pass_g_kernel(PassViews pv, int64_t n, int NC, int D, const Tacc* __restrict__ W,
-              int64_t rows_per_chunk, int nb0, Tacc* __restrict__ partG) {
+              int64_t rows_per_chunk, int nb0, double* __restrict__ partG) {
   __shared__ Tacc Zs[kTB][64];
   __shared__ Tacc Ws[kTB][8 * RQ];
   if (pv.done != nullptr && *pv.done) return;
@@ -176,12 +178,21 @@ pass_g_kernel(PassViews pv, int64_t n, int NC, int D, const Tacc* __restrict__ W
   const Tin* Z = reinterpret_cast<const Tin*>(pv.Z[v]);
   const int64_t r0 = blockIdx.x * rows_per_chunk;
   const int64_t r1 = min(n, r0 + rows_per_chunk);
+  // Tacc partial sums over at most kFlush rows, then FP64 accumulation
+  constexpr int kFlush = 4 * kTB;
   Tacc acc[2][RQ];
+  double acc64[2][RQ];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int q = 0; q < RQ; ++q) acc[a][q] = 0;
+    for (int q = 0; q < RQ; ++q) acc[a][q] = 0, acc64[a][q] = 0;
   for (int64_t i0 = r0; i0 < r1; i0 += kTB) {
+    if (((i0 - r0) % kFlush) == 0 && i0 != r0) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) acc64[a][q] += (double)acc[a][q], acc[a][q] = 0;
+    }
 #pragma unroll
     for (int i = 0; i < (kTB * 64) / 256; ++i) {
       int e = tid + 256 * i;
@@ -217,14 +228,13 @@ pass_g_kernel(PassViews pv, int64_t n, int NC, int D, const Tacc* __restrict__ W
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
       int c = tc + 8 * q;
-      if (c < NC) partG[((int64_t)blockIdx.x * D + grow) * NC + c] = acc[a][q];
+      if (c < NC) partG[((int64_t)blockIdx.x * D + grow) * NC + c] = acc64[a][q] + (double)acc[a][q];
     }
   }
 }
 
-template <typename Tacc>
-__global__ void pass_reduce_kernel(const Tacc* __restrict__ partG, int chunks, int64_t nG,
-                                   const Tacc* __restrict__ partGram, int ctas, int64_t nGram,
+__global__ void pass_reduce_kernel(const double* __restrict__ partG, int chunks, int64_t nG,
+                                   const double* __restrict__ partGram, int ctas, int64_t nGram,
                                    double* __restrict__ G, double* __restrict__ Gram, const int* done) {
   if (done != nullptr && *done) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nG + nGram;
@@ -244,8 +254,7 @@ __global__ void pass_reduce_kernel(const Tacc* __restrict__ partG, int chunks, i
 }
 
 // FDA: Xhat^T P = X^T P - sum_k m_k (sum_{i in k} P_i)^T.
-template <typename Tacc>
-__global__ void lda_correct_kernel(const Tacc* __restrict__ partCls, int ctas, int l, int NC, int d,
+__global__ void lda_correct_kernel(const double* __restrict__ partCls, int ctas, int l, int NC, int d,
                                    const double* __restrict__ means, double* __restrict__ G, const int* done) {
   __shared__ double sP[kMaxClasses * 48];
   if (done != nullptr && *done) return;
@@ -294,9 +303,9 @@ int launch_w(Plan& p, const PassViews& pv, int NC, Tacc* W, cudaStream_t st, con
   size_t smem = sizeof(Tacc) * (32 * (kTM + 1) + 32 * 8 * RN + kTM * NC) + sizeof(int) * kTM;
   auto kern = pass_w_kernel<Tin, Tacc, RN>;
   GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<p.ctasA, 256, smem, st>>>(pv, p.n, NC, W, reinterpret_cast<Tacc*>(p.partGram),
+  kern<<<p.ctasA, 256, smem, st>>>(pv, p.n, NC, W, reinterpret_cast<double*>(p.partGram),
                                     p.kind == kLDA ? p.labels : nullptr, cls, p.l,
-                                    reinterpret_cast<Tacc*>(p.partCls));
+                                    reinterpret_cast<double*>(p.partCls));
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }
@@ -320,7 +329,7 @@ int launch_g(Plan& p, const PassViews& pv, const Tacc* W, cudaStream_t st) {
   int64_t rpc = (p.n + p.chunksB - 1) / p.chunksB;
   dim3 grid(p.chunksB, nb);
   pass_g_kernel<Tin, Tacc, RQ><<<grid, 256, 0, st>>>(pv, p.n, p.NC, p.D, W, rpc, nb0,
-                                                      reinterpret_cast<Tacc*>(p.partG));
+                                                      reinterpret_cast<double*>(p.partG));
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }
@@ -386,13 +395,13 @@ int run_pass(Plan& p, bool gram_only, cudaStream_t st, int phi_cols, const int* 
   if (!gram_only) GB_TRY((dispatch_g<Tin, Tacc>(p, pv, W, st)));
   int64_t nG = gram_only ? 0 : (int64_t)p.D * NC;
   int64_t nGram = (int64_t)NC * NC;
-  pass_reduce_kernel<Tacc><<<ceil_div(nG + nGram, 256), 256, 0, st>>>(
-      gram_only ? nullptr : reinterpret_cast<const Tacc*>(p.partG), p.chunksB, nG,
-      reinterpret_cast<const Tacc*>(p.partGram), p.ctasA, nGram, p.G, p.Gram, done);
+  pass_reduce_kernel<<<ceil_div(nG + nGram, 256), 256, 0, st>>>(
+      gram_only ? nullptr : reinterpret_cast<const double*>(p.partG), p.chunksB, nG,
+      reinterpret_cast<const double*>(p.partGram), p.ctasA, nGram, p.G, p.Gram, done);
   GB_CHECK_LAUNCH();
   if (p.kind == kLDA && !gram_only) {
-    lda_correct_kernel<Tacc><<<ceil_div((int64_t)p.D * NC, 256), 256, 0, st>>>(
-        reinterpret_cast<const Tacc*>(p.partCls), p.ctasA, p.l, NC, p.D, p.means, p.G, done);
+    lda_correct_kernel<<<ceil_div((int64_t)p.D * NC, 256), 256, 0, st>>>(
+        reinterpret_cast<const double*>(p.partCls), p.ctasA, p.l, NC, p.D, p.means, p.G, done);
     GB_CHECK_LAUNCH();
   }
   return GBCCA_OK;

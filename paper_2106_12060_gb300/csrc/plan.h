@@ -7,6 +7,7 @@ namespace gbcca {
 constexpr int kMaxK = 20;       // columns of an iterate (p in the paper)
 constexpr int kMaxD = 1024;     // columns of one data view
 constexpr int kMaxClasses = 64; // LDA classes
+constexpr int kMaxTimedBatch = 256;  // iterations per batch when passes are timed
 
 enum ProblemKind { kCCA = 0, kLDA = 1 };
 
@@ -107,6 +108,8 @@ struct Plan {
   double* ws = nullptr;         // FP64 scratch for dense routines
   int64_t ws_len = 0;
   int* flag = nullptr;          // device error flag (NOT_SPD etc.)
+  cudaEvent_t ev[2 * kMaxTimedBatch];  // pass timing (opt.time_passes)
+  int nev = 0;
 };
 
 // sketch.cu

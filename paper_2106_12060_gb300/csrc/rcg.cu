@@ -916,10 +916,12 @@ int thin_blocks(const Plan& p) {
 
 // One iteration (or, with force_zero_step set on the device, the qf_B
 // normalization of the starting point).
-int iteration(Plan& p, bool low, cudaStream_t st) {
+int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   const int k = p.k, kk = k * k;
   const int* done = &p.st->done;
+  if (e0 != nullptr) GB_CUDA(cudaEventRecord(e0, st));
   GB_TRY(fused_pass(p, low, false, st, 0, done));
+  if (e1 != nullptr) GB_CUDA(cudaEventRecord(e1, st));
   GB_TRY(phigram(p, st, done));
   GB_TRY(yphi(p, st, 1));
   {
@@ -1056,16 +1058,40 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     GB_CHECK_LAUNCH();
   }
   GB_CUDA(cudaMemsetAsync(p.history, 0, sizeof(double) * 3 * (p.opt.max_iter + 1), st));
-  // qf_B of the start (zero step), then iterations in batches
-  GB_TRY(iteration(p, low, st));
+  // qf_B of the start (zero step), then iterations in batches.  With pass
+  // timing, event pair b brackets the pass of global iteration index
+  // first_index + b (index 0 = the qf_B pass); only passes whose iteration
+  // really ran (index <= iterations done) are counted.
+  const bool timed = p.nev > 0;
+  double pass_ms = 0;
+  int pass_count = 0;
+  auto harvest = [&](int first_index, int nb, int iters_done) -> int {
+    for (int b = 0; b < nb; ++b) {
+      if (first_index + b > iters_done) break;
+      float ms = 0;
+      GB_CUDA(cudaEventElapsedTime(&ms, p.ev[2 * b], p.ev[2 * b + 1]));
+      pass_ms += ms;
+      ++pass_count;
+    }
+    return GBCCA_OK;
+  };
+  GB_TRY(iteration(p, low, st, timed ? p.ev[0] : nullptr, timed ? p.ev[1] : nullptr));
   int launched = 0;
   int passes = 1;
-  const int batch = std::max(1, p.opt.check_every);
+  int batch = std::max(1, p.opt.check_every);
+  if (timed) batch = std::min(batch, kMaxTimedBatch);
+  int pending_first = 0, pending_n = timed ? 1 : 0;
   while (true) {
     GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
+    if (timed) GB_TRY(harvest(pending_first, pending_n, p.st_host->iter));
     if (p.st_host->done || launched >= p.opt.max_iter) break;
-    for (int b = 0; b < batch && launched < p.opt.max_iter; ++b, ++launched) GB_TRY(iteration(p, low, st));
+    pending_first = launched + 1;
+    pending_n = 0;
+    for (int b = 0; b < batch && launched < p.opt.max_iter; ++b, ++launched) {
+      GB_TRY(iteration(p, low, st, timed ? p.ev[2 * b] : nullptr, timed ? p.ev[2 * b + 1] : nullptr));
+      pending_n += timed ? 1 : 0;
+    }
   }
   const DevState& hs = *p.st_host;
   passes += hs.iter;
@@ -1108,6 +1134,8 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     info->grad_norm = p.st_host->gn;
     info->grad_norm0 = p.st_host->gn0;
     info->objective = p.st_host->f;
+    info->pass_ms = pass_count > 0 ? pass_ms / pass_count : 0.0;
+    info->pass_count = pass_count;
   }
   return status;
 }
@@ -1302,6 +1330,7 @@ int warm_start(Plan& p, cudaStream_t st) {
       GB_CHECK_LAUNCH();
       // whitened top-k vectors, then back through R^{-1}
       thin_apply_kernel<<<ceil_div(dx, 128), 128, 0, st>>>(Ub, dx, c, rotU, k, x.wsT);
+      GB_CHECK_LAUNCH();
       thin_apply_kernel<<<ceil_div(dy, 128), 128, 0, st>>>(Vb, dy, c, rotV, k, y.wsT);
       GB_CHECK_LAUNCH();
       GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, x.wsT, k, x.warm, k, k, st));

@@ -349,7 +349,9 @@ int srht_run(Plan& p, View& v, cudaStream_t st) {
   int32_t* list = p.perm;
   GB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * N1, st));
   srht_group_kernel<<<ceil_div(p.s, 256), 256, 0, st>>>(p.h, p.s, N1, cnt, off1, list, 0);
+  GB_CHECK_LAUNCH();
   srht_group_kernel<<<1, 32, 0, st>>>(p.h, p.s, N1, cnt, off1, list, 1);
+  GB_CHECK_LAUNCH();
   srht_group_kernel<<<ceil_div(p.s, 256), 256, 0, st>>>(p.h, p.s, N1, cnt, off1, list, 2);
   GB_CHECK_LAUNCH();
   size_t sm2 = sizeof(T) * N2 * CB;

@@ -13,5 +13,7 @@ from .inputs import (  # noqa: F401
     countsketch_draws,
     srht_draws,
     random_tall,
+    latent_scales,
+    make_workload,
     CONFIGS,
 )

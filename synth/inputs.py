@@ -20,13 +20,16 @@ CONFIGS = {
     "cca_small_fp64": dict(kind="cca", n=2000, dx=50, dy=40, k=5, latent=10,
                            noise=0.5, colscale=None, lam=1e-3, dtype="f64",
                            sketch="countsketch", s=4 * (50 + 40), seed=0),
-    # Tall ill-conditioned CCA: columns scaled geometrically 1 -> 1e-4.
+    # Tall ill-conditioned CCA: columns scaled geometrically 1 -> 1e-4; the
+    # 20 latent factors have strengths 10^(-2 j / 19), j = 0..19, so the
+    # canonical correlations decay (0.9995 ... 0.79) and the top 10 are
+    # separated from the rest (sigma_10 - sigma_11 ~ 0.02).
     "cca_tall_bf16": dict(kind="cca", n=262144, dx=512, dy=512, k=10, latent=20,
                           noise=0.5, colscale=(1.0, 1e-4), lam=1e-4, dtype="bf16",
-                          sketch="srht", s=4 * (512 + 512), seed=0),
+                          sketch="srht", s=4 * (512 + 512), seed=0, latent_decay=2.0),
     "cca_tall_f32": dict(kind="cca", n=262144, dx=512, dy=512, k=10, latent=20,
                          noise=0.5, colscale=(1.0, 1e-4), lam=1e-4, dtype="f32",
-                         sketch="srht", s=4 * (512 + 512), seed=0),
+                         sketch="srht", s=4 * (512 + 512), seed=0, latent_decay=2.0),
     # Fisher LDA: 10 classes, 784 features, means N(0, 4I), within-class
     # variances log-uniform in [1e-4, 1].
     "lda_f32": dict(kind="lda", n=100000, d=784, l=10, k=9, dtype="f32",
@@ -69,6 +72,28 @@ def _colscale(d: int, colscale):
         return np.array([hi], dtype=np.float64)
     j = np.arange(d, dtype=np.float64)
     return hi * (lo / hi) ** (j / (d - 1))
+
+
+def latent_scales(latent: int, decay: float):
+    """Strengths 10^(-decay j / (latent - 1)) of the latent factors."""
+    if latent == 1:
+        return np.ones(1)
+    return 10.0 ** (-decay * np.arange(latent) / (latent - 1))
+
+
+def make_workload(name: str, n: int | None = None):
+    """Build the named workload (optionally with fewer rows n)."""
+    c = dict(CONFIGS[name])
+    if n is not None:
+        c["n"] = n
+    if c["kind"] == "cca":
+        ls = latent_scales(c["latent"], c["latent_decay"]) if c.get("latent_decay") else None
+        P = cca_latent_problem(c["n"], c["dx"], c["dy"], latent=c["latent"], noise=c["noise"],
+                               colscale=c["colscale"], dtype=c["dtype"], seed=c["seed"], latent_scale=ls)
+    else:
+        P = lda_problem(c["n"], c["d"], c["l"], dtype=c["dtype"], seed=c["seed"])
+    P["config"] = c
+    return P
 
 
 def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float = 0.5,
