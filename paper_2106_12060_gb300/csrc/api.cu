@@ -51,7 +51,7 @@ void free_plan(Plan* p) {
                   (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
                   (void*)p->phigram, (void*)p->phipart, (void*)p->cross, (void*)p->crosspart, (void*)p->history,
-                  (void*)p->ws, (void*)p->flag})
+                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part})
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
@@ -150,6 +150,11 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->ws, p->ws_len));
   GB_TRY(dalloc(&p->flag, 1));
   GB_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
+  if (p->kind == kCCA && p->dtype == GBCCA_BF16 && 4 * k <= 48 && p->v[0].d <= 512 && p->v[1].d <= 512) {
+    GB_TRY(dalloc(&p->tc_img, 2 * 49152));
+    GB_CUDA(cudaMemset(p->tc_img, 0, 2 * 49152));
+    GB_TRY(dalloc(&p->tc_part, (int64_t)p->sm_count * p->D * k4));
+  }
   if (p->opt.time_passes) {
     for (int i = 0; i < 2 * kMaxTimedBatch; ++i) {
       GB_CUDA(cudaEventCreate(&p->ev[i]));

@@ -415,6 +415,8 @@ int run_pass(Plan& p, bool gram_only, cudaStream_t st, int phi_cols, const int* 
 // turns the launches into no-ops once the solver has stopped.
 int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols, const int* done) {
   if (phi_cols <= 0) phi_cols = 2 * p.k;
+  if (low && !gram_only && phi_cols == 2 * p.k && p.tc_img != nullptr && tc_pass_eligible(p))
+    return tc_pass(p, st, done);
   if (p.kind == kLDA && p.l * phi_cols > 256 * kCI) {
     set_last_error("too many classes x columns for the FDA pass");
     return GBCCA_ERR_UNSUPPORTED;

@@ -1,0 +1,550 @@
+// Tensor-core (tcgen05 + TMA) fused CCA data pass for BF16 data on sm_103a.
+//
+// One Riemannian-CG iteration of the CCA solver needs, for the block-diagonal
+// Phi = blkdiag([U, eta_U], [V, eta_V]) (Sec. 4.2 gradient, Table 1
+// retraction, Cor. 4.6 per-iteration cost O(p (nnz X + nnz Y))):
+//     W = Z Phi  (Z = [X | Y], n x 4k, never leaves the chip)
+//     G = Z^T W  (D x 4k)
+// and W^T W, which equals Phi^T G and is formed afterwards in FP64 from G.
+//
+// Persistent kernel, one CTA per SM, 128-row tiles.  Per tile and per pair of
+// 64-column boxes (128 columns of one view):
+//   phase 1: TMA loads the 128 x 128 BF16 block (two 128B-swizzled boxes) and
+//            tcgen05.mma accumulates W_view (128 x 48 in TMEM; K-major A = the
+//            block, B = Phi split into bf16 hi|lo columns);
+//   epilogue warps read W from TMEM, add the hi and lo halves, split W into
+//            bf16 hi/lo and write it to shared memory as the B operand of
+//   phase 2: the same blocks (re-read through L2) serve as the MN-major A
+//            operand Z^T of G_pair += Z^T (W_hi + W_lo), accumulated in TMEM
+//            (8 pairs x 48 columns) over all tiles of the CTA.
+// At the end the epilogue warps drain G to a per-CTA FP32 partial; a second
+// kernel sums the partials in fixed order in FP64.
+//
+// Roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer, warp 2 =
+// TMEM allocator, warps 4-7 = epilogue (TMEM lane quarters 0-3).  Every
+// mbarrier wait is bounded in time; on expiry the CTA records an error code,
+// waits (bounded) for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+
+#include "plan.h"
+
+namespace gbcca {
+
+namespace tc {
+
+constexpr int kRows = 128;            // rows per tile (MMA M for phase 1)
+constexpr int kNW = 48;               // N of both GEMMs (4k <= 48 real columns)
+constexpr int kHalf = 24;             // B rows of Phi: [hi of 2k cols | lo of 2k cols], 24 each
+constexpr int kStages = 3;            // ring of 32 KB pair slots
+constexpr int kSlot = 32768;          // two 128 x 64 BF16 boxes
+constexpr int kBox = 16384;
+constexpr int kPhiView = 49152;       // per view: 8 K-boxes x 48 rows x 128 B
+constexpr int kKBox = 6144;           // 48 rows x 128 B
+constexpr int kWs = 12288;            // W operand: 2 K-boxes x 48 rows x 128 B
+constexpr int kPhiBytes = 2 * kPhiView;
+constexpr int kRingOff = kPhiBytes;
+constexpr int kWsOff = kRingOff + kStages * kSlot;
+constexpr int kBarOff = kWsOff + 2 * kWs;
+constexpr int kSmemBytes = kBarOff + 256 + 1024;  // + alignment slack
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kTimeout = 2000000000ll;      // cycles (~1 s)
+
+enum Bar { kFull = 0, kEmpty = kStages, kD1Full = 2 * kStages, kD1Free, kWReady, kWFree, kGDone, kFinal, kNumBars };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the time limit passes or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kTimeout) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, 128-byte swizzle (start, leading and
+// stride byte offsets in 16-byte units; version 1; layout SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of element (row, e) inside a K-major 128B-swizzled K-box of
+// 64 bf16 elements per row (8-row groups of 1024 bytes)
+__host__ __device__ __forceinline__ uint32_t swz(int row, int e) {
+  const int chunk = (e >> 3) ^ (row & 7);
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (e & 7) * 2);
+}
+
+struct Args {
+  int64_t n;
+  int d[2];
+  int pairs[2];
+  int k2;        // columns of Phi per view (2k)
+  int ntiles;
+  const uint8_t* phi_img;  // [view][K-box][48][128 B], pre-swizzled
+  float* partG;            // [cta][D][4k]
+  int* err;
+  const int* done;
+};
+
+__global__ void __launch_bounds__(256, 1)
+tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, Args a) {
+  if (a.done != nullptr && *a.done) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* phi_s = smem;
+  uint8_t* ring = smem + kRingOff;
+  uint8_t* ws = smem + kWsOff;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int npairs = a.pairs[0] + a.pairs[1];
+  const int k4 = 2 * a.k2;
+
+  // Phi image -> shared memory (generic proxy), then make it visible to the
+  // tensor core (async proxy).
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.phi_img);
+    uint4* dst = reinterpret_cast<uint4*>(phi_s);
+    for (int i = threadIdx.x; i < kPhiBytes / 16; i += blockDim.x) dst[i] = src[i];
+    uint4* wz = reinterpret_cast<uint4*>(ws);
+    for (int i = threadIdx.x; i < 2 * kWs / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bars[kFull + s]), 1);
+      mbar_init(smem_u32(&bars[kEmpty + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[kD1Full]), 1);
+    mbar_init(smem_u32(&bars[kD1Free]), 128);
+    mbar_init(smem_u32(&bars[kWReady]), 128);
+    mbar_init(smem_u32(&bars[kWFree]), 1);
+    mbar_init(smem_u32(&bars[kGDone]), 1);
+    mbar_init(smem_u32(&bars[kFinal]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    int it = 0;
+    bool ok = true;
+    int last_use[kStages];
+    for (int s = 0; s < kStages; ++s) last_use[s] = -1;
+    for (int j = 0; j < my_tiles && ok; ++j) {
+      const int row0 = (blockIdx.x + j * gridDim.x) * kRows;
+      for (int phase = 0; phase < 2 && ok; ++phase) {
+        for (int p = 0; p < npairs && ok; ++p, ++it) {
+          const int slot = it % kStages, use = it / kStages;
+          if (!mbar_wait(smem_u32(&bars[kEmpty + slot]), (use & 1) ^ 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&bars[kFull + slot]);
+          mbar_expect_tx(fb, kSlot);
+          const int view = p < a.pairs[0] ? 0 : 1;
+          const int col = 128 * (view == 0 ? p : p - a.pairs[0]);
+          const CUtensorMap* map = view == 0 ? &tmx : &tmy;
+          const uint32_t dst = smem_u32(ring + slot * kSlot);
+          tma_load_2d(dst, map, col, row0, fb);
+          tma_load_2d(dst + kBox, map, col + 64, row0, fb);
+          last_use[slot] = use;
+        }
+      }
+    }
+    if (!ok) {
+      // wait (bounded) for the copies this thread issued before leaving
+      for (int s = 0; s < kStages; ++s) {
+        if (last_use[s] < 0) continue;
+        const long long t0 = clock64();
+        while (!mbar_try(smem_u32(&bars[kFull + s]), last_use[s] & 1) && clock64() - t0 < kTimeout) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t id1 = idesc_bf16(128, kNW, 0, 0);
+    constexpr uint32_t id2 = idesc_bf16(128, kNW, 1, 0);
+    int it = 0;
+    bool ok = true;
+    for (int j = 0; j < my_tiles && ok; ++j) {
+      if (j > 0 && !(ok = mbar_wait(smem_u32(&bars[kD1Free]), (j - 1) & 1, abort_flag))) break;
+      tc_fence_after();
+      for (int p = 0; p < npairs; ++p, ++it) {
+        const int slot = it % kStages, use = it / kStages;
+        if (!(ok = mbar_wait(smem_u32(&bars[kFull + slot]), use & 1, abort_flag))) break;
+        tc_fence_after();
+        const int view = p < a.pairs[0] ? 0 : 1;
+        const int pp = view == 0 ? p : p - a.pairs[0];
+        const uint32_t d1 = tmem + (uint32_t)(view * kNW);
+        const uint32_t abase = smem_u32(ring + slot * kSlot);
+        const uint32_t bbase = smem_u32(phi_s + view * kPhiView);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const int box = s >> 2, kin = s & 3;
+          const uint64_t ad = sdesc(abase + box * kBox + kin * 32, 16, 1024);
+          const uint64_t bd = sdesc(bbase + (2 * pp + box) * kKBox + kin * 32, 16, 1024);
+          mma_bf16(d1, ad, bd, id1, (pp > 0 || s > 0) ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&bars[kEmpty + slot]));
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&bars[kD1Full]));
+      if (!(ok = mbar_wait(smem_u32(&bars[kWReady]), j & 1, abort_flag))) break;
+      tc_fence_after();
+      const uint32_t wbase = smem_u32(ws);
+      for (int p = 0; p < npairs; ++p, ++it) {
+        const int slot = it % kStages, use = it / kStages;
+        if (!(ok = mbar_wait(smem_u32(&bars[kFull + slot]), use & 1, abort_flag))) break;
+        tc_fence_after();
+        const uint32_t g = tmem + (uint32_t)(2 * kNW + p * kNW);
+        const uint32_t abase = smem_u32(ring + slot * kSlot);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const uint64_t ad = sdesc(abase + s * 2048, kBox, 1024);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint64_t bd = sdesc(wbase + h * kWs + (s >> 2) * kKBox + (s & 3) * 32, 16, 1024);
+            mma_bf16(g, ad, bd, id2, (j > 0 || s > 0 || h > 0) ? 1u : 0u);
+          }
+        }
+        mma_commit(smem_u32(&bars[kEmpty + slot]));
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&bars[kWFree]));
+    }
+    if (ok) {
+      mma_commit(smem_u32(&bars[kGDone]));
+    } else {
+      // let the MMAs already issued finish before the CTA frees its memory
+      mma_commit(smem_u32(&bars[kFinal]));
+      const long long t0 = clock64();
+      while (!mbar_try(smem_u32(&bars[kFinal]), 0) && clock64() - t0 < kTimeout) {
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp - 4;             // TMEM lane quarter
+    const int r = 32 * q + lane;        // row of the tile / of a G pair block
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    bool ok = true;
+    for (int j = 0; j < my_tiles && ok; ++j) {
+      if (!(ok = mbar_wait(smem_u32(&bars[kD1Full]), j & 1, abort_flag))) break;
+      tc_fence_after();
+      float d1[2][kNW];
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(v * kNW + c), &d1[v][c]);
+      tmem_ld_wait();
+      tc_fence_before();
+      mbar_arrive(smem_u32(&bars[kD1Free]));
+      if (j > 0 && !(ok = mbar_wait(smem_u32(&bars[kWFree]), (j - 1) & 1, abort_flag))) break;
+      // W row r: columns [P_U, P_eta, Q_V, Q_eta]; view v's column c is the
+      // sum of its hi part (TMEM column c) and lo part (column kHalf + c)
+#pragma unroll
+      for (int v = 0; v < 2; ++v)
+#pragma unroll
+        for (int c = 0; c < kHalf; ++c) {
+          if (c < a.k2) {
+            const float w = d1[v][c] + d1[v][kHalf + c];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
+            const uint32_t off = (uint32_t)((r >> 6) * kKBox) + swz(v * a.k2 + c, r & 63);
+            *reinterpret_cast<__nv_bfloat16*>(ws + off) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(ws + kWs + off) = lo;
+          }
+        }
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&bars[kWReady]));
+    }
+    if (ok && my_tiles > 0 && mbar_wait(smem_u32(&bars[kGDone]), 0, abort_flag)) {
+      tc_fence_after();
+      const int D0 = a.d[0];
+      const int D = a.d[0] + a.d[1];
+      float* out = a.partG + (int64_t)blockIdx.x * D * k4;
+      for (int p = 0; p < npairs; ++p) {
+        float g[kNW];
+#pragma unroll
+        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(2 * kNW + p * kNW + c), &g[c]);
+        tmem_ld_wait();
+        const int view = p < a.pairs[0] ? 0 : 1;
+        const int pp = view == 0 ? p : p - a.pairs[0];
+        const int col = 128 * pp + r;
+        if (col < a.d[view]) {
+          float* o = out + (int64_t)(view * D0 + col) * k4;
+#pragma unroll
+          for (int c = 0; c < kNW; ++c)
+            if (c < k4) o[c] = g[c];
+        }
+      }
+    } else if (my_tiles > 0) {
+      // rows of a CTA that stopped early are not trustworthy: zero them so the
+      // reduction stays finite; the error flag reports the failure
+      const int D = a.d[0] + a.d[1];
+      float* out = a.partG + (int64_t)blockIdx.x * D * k4;
+      for (int e = threadIdx.x - 128; e < D * k4; e += 128) out[e] = 0.f;
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 4);
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Phi image: per view, K-boxes of 64 columns; B rows 0..23 hold the bf16 hi
+// parts of the 2k columns [U | eta], rows 24..47 their lo parts (x - hi);
+// 128B-swizzled.  Phi is then rounded in place to hi + lo so that the point
+// the pass evaluates is exactly the point the solver holds.
+__global__ void phi_image_kernel(double* __restrict__ Phi, int d, int k2, int kboxes, uint8_t* __restrict__ img) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (kbox, row, elem)
+  if (e >= kboxes * kNW * 64) return;
+  const int kb = e / (kNW * 64);
+  const int rem = e % (kNW * 64);
+  const int row = rem / 64, el = rem % 64;
+  const int j = kb * 64 + el;  // data column
+  const int c = row < kHalf ? row : row - kHalf;
+  __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+  if (j < d && c < k2) {
+    const double x = Phi[(int64_t)j * k2 + c];
+    const __nv_bfloat16 hi = __double2bfloat16(x);
+    const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+    v = row < kHalf ? hi : lo;
+  }
+  *reinterpret_cast<__nv_bfloat16*>(img + (int64_t)kb * kKBox + swz(row, el)) = v;
+}
+
+__global__ void phi_round_kernel(double* __restrict__ Phi, int64_t len) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  const double x = Phi[i];
+  const __nv_bfloat16 hi = __double2bfloat16(x);
+  const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+  Phi[i] = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
+}
+
+// G (D x 4k, FP64) = sum over CTAs of the FP32 partials, fixed order.
+__global__ void tc_reduce_kernel(const float* __restrict__ part, int ctas, int64_t len, double* __restrict__ G,
+                                 const int* done) {
+  if (done != nullptr && *done) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int c = 0; c < ctas; ++c) s += (double)part[(int64_t)c * len + e];
+    G[e] = s;
+  }
+}
+
+// W^T W = Phi_bd^T G (4k x 4k), Phi_bd = blkdiag(Phi_x, Phi_y), in FP64.
+__global__ void tc_gram_kernel(const double* __restrict__ Phix, const double* __restrict__ Phiy, int dx, int dy,
+                               int k2, const double* __restrict__ G, double* __restrict__ Gram, const int* done) {
+  if (done != nullptr && *done) return;
+  const int k4 = 2 * k2;
+  const int e = blockIdx.x;  // one output per CTA, threads split the sum
+  const int a = e / k4, b = e % k4;
+  const int v = a < k2 ? 0 : 1;
+  const int ca = a - v * k2;
+  const double* Phi = v == 0 ? Phix : Phiy;
+  const int d = v == 0 ? dx : dy;
+  const int off = v == 0 ? 0 : dx;
+  double s = 0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s += Phi[(int64_t)j * k2 + ca] * G[(int64_t)(off + j) * k4 + b];
+  __shared__ double red[128];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Gram[e] = red[0];
+}
+
+}  // namespace tc
+
+// ----------------------------------------------------------------- host side
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (fn == nullptr) {
+    set_last_error("cuTensorMapEncodeTiled is not available from the driver");
+    return GBCCA_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)tc::kRows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return GBCCA_ERR_CUDA;
+  }
+  return GBCCA_OK;
+}
+
+}  // namespace
+
+// The tensor-core pass serves CCA plans with BF16 data, k <= 12 (4k <= 48
+// MMA columns), dx, dy <= 512 (TMEM and shared-memory budget), 16-byte
+// aligned rows (ld a multiple of 8) and 16-byte aligned bases.
+bool tc_pass_eligible(const Plan& p) {
+  if (p.kind != kCCA || p.dtype != GBCCA_BF16 || 2 * p.k > tc::kHalf || p.v[0].d > 512 || p.v[1].d > 512)
+    return false;
+  for (int v = 0; v < 2; ++v) {
+    if (p.v[v].ld % 8 != 0 || (reinterpret_cast<uintptr_t>(p.v[v].Z) & 15) != 0) return false;
+  }
+  return true;
+}
+
+int tc_pass(Plan& p, cudaStream_t st, const int* done) {
+  if (p.tc_map_for[0] != p.v[0].Z || p.tc_map_for[1] != p.v[1].Z) {
+    for (int v = 0; v < 2; ++v)
+      GB_TRY(make_map(reinterpret_cast<CUtensorMap*>(p.tc_map[v]), p.v[v].Z, p.n, p.v[v].d, p.v[v].ld));
+    p.tc_map_for[0] = p.v[0].Z;
+    p.tc_map_for[1] = p.v[1].Z;
+  }
+  const int k2 = 2 * p.k, k4 = 4 * p.k;
+  tc::Args a{};
+  a.n = p.n;
+  int kb_total = 0;
+  for (int v = 0; v < 2; ++v) {
+    a.d[v] = p.v[v].d;
+    a.pairs[v] = ceil_div(p.v[v].d, 128);
+    const int kboxes = 2 * a.pairs[v];
+    // view v's image starts at v * kPhiView (K-boxes of 64 columns)
+    tc::phi_image_kernel<<<ceil_div(kboxes * tc::kNW * 64, 256), 256, 0, st>>>(
+        p.v[v].Phi, p.v[v].d, k2, kboxes, p.tc_img + v * tc::kPhiView);
+    GB_CHECK_LAUNCH();
+    tc::phi_round_kernel<<<ceil_div((int64_t)p.v[v].d * k2, 256), 256, 0, st>>>(p.v[v].Phi, (int64_t)p.v[v].d * k2);
+    GB_CHECK_LAUNCH();
+    kb_total += kboxes;
+  }
+  (void)kb_total;
+  a.k2 = k2;
+  a.ntiles = ceil_div(p.n, tc::kRows);
+  a.phi_img = p.tc_img;
+  a.partG = p.tc_part;
+  a.err = p.flag;
+  a.done = done;
+  const int grid = std::min(p.sm_count, a.ntiles);
+  GB_CUDA(cudaFuncSetAttribute(tc::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+  tc::tc_pass_kernel<<<grid, 256, tc::kSmemBytes, st>>>(*reinterpret_cast<const CUtensorMap*>(p.tc_map[0]),
+                                                        *reinterpret_cast<const CUtensorMap*>(p.tc_map[1]), a);
+  GB_CHECK_LAUNCH();
+  const int64_t len = (int64_t)p.D * k4;
+  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, p.G, done);
+  GB_CHECK_LAUNCH();
+  tc::tc_gram_kernel<<<k4 * k4, 128, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2, p.G, p.Gram, done);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+}  // namespace gbcca

@@ -110,6 +110,14 @@ struct Plan {
   int* flag = nullptr;          // device error flag (NOT_SPD etc.)
   cudaEvent_t ev[2 * kMaxTimedBatch];  // pass timing (opt.time_passes)
   int nev = 0;
+
+  // tensor-core pass (BF16 CCA): TMA descriptors of X and Y (CUtensorMap,
+  // 128 bytes each, rebuilt when the data pointers change), the swizzled Phi
+  // image and the per-CTA FP32 partials of G
+  alignas(64) unsigned char tc_map[2][128];
+  const void* tc_map_for[2] = {nullptr, nullptr};
+  uint8_t* tc_img = nullptr;
+  float* tc_part = nullptr;
 };
 
 // sketch.cu
@@ -136,6 +144,10 @@ int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols 
                const int* done = nullptr);
 int exact_gram(Plan& p, int view, double* out, cudaStream_t st);
 int lda_class_stats(Plan& p, cudaStream_t st);
+
+// pass_tc.cu
+bool tc_pass_eligible(const Plan& p);
+int tc_pass(Plan& p, cudaStream_t st, const int* done);
 
 // rcg.cu
 int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals,

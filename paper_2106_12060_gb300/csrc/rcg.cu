@@ -28,7 +28,7 @@ namespace gbcca {
 constexpr double kC1 = 1e-4;
 constexpr int kMaxLS = 25;
 constexpr int kMaxExpand = 10;
-constexpr int kNTrials = kMaxLS + kMaxExpand;
+constexpr int kNTrials = kMaxLS + kMaxExpand + 1;  // last one: t = 0 (Armijo reference)
 constexpr int kLSWarps = 8;
 
 // ================================================================ helpers
@@ -413,7 +413,7 @@ __global__ void linesearch_kernel(LSArgs a) {
   } else {
     const double t0 = st->t0;
     for (int tr = warp; tr < kNTrials; tr += kLSWarps) {
-      double t = tr < kMaxLS ? ldexp(t0, -tr) : ldexp(t0, tr - kMaxLS + 1);
+      double t = tr < kMaxLS ? ldexp(t0, -tr) : (tr < kNTrials - 1 ? ldexp(t0, tr - kMaxLS + 1) : 0.0);
       double f = ls_eval(a, coef, t, w, mu_s);
       if (lane == 0) {
         ft[tr] = f;
@@ -422,7 +422,8 @@ __global__ void linesearch_kernel(LSArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double f0 = st->f, df = st->df;
+      // f at the current point, from this pass (the point the pass evaluated)
+      const double f0 = ft[kNTrials - 1], df = st->df;
       int acc = -1;
       for (int j = 0; j < kMaxLS; ++j)
         if (ft[j] <= f0 + kC1 * tt[j] * df) {
@@ -750,7 +751,8 @@ __global__ void newdir_kernel(NewArgs a) {
 // each column of U (W) positive.
 struct RRArgs {
   DevState* st;
-  const double* Gram;     // 2k x 2k (CCA: [P_U | Q_V]) or k x k (FDA)
+  const double* Gram;     // pass Gram: P_U block at column offx, Q_V block at offy
+  int gnc, offx, offy;    // row stride and block offsets of Gram
   const double* phipart;  // [view][nblk][2k x 2k] Gram of Phi (U^T U in the corner)
   int nblk, k, kind, l;
   const double* YPhi;     // FDA (l x 2k)
@@ -773,13 +775,13 @@ __global__ void rr_kernel(RRArgs a) {
   double* phig = rot + 100;  // 2 x 4kk
   const int nv = a.kind == kCCA ? 2 : 1;
   for (int v = 0; v < nv; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * kk, a.nblk, 4 * kk, phig + v * 4 * kk);
-  const int NC = a.kind == kCCA ? 2 * k : k;
+  const int NC = a.gnc, ox = a.offx, oy = a.offy;
   for (int e = threadIdx.x; e < kk; e += blockDim.x) {
     int i = e / k, j = e % k;
-    Gx[e] = a.Gram[i * NC + j] + st->lam[0] * phig[i * k2 + j];
+    Gx[e] = a.Gram[(ox + i) * NC + ox + j] + st->lam[0] * phig[i * k2 + j];
     if (a.kind == kCCA) {
-      Gy[e] = a.Gram[(k + i) * NC + k + j] + st->lam[1] * phig[4 * kk + i * k2 + j];
-      C[e] = a.Gram[i * NC + k + j];
+      Gy[e] = a.Gram[(oy + i) * NC + oy + j] + st->lam[1] * phig[4 * kk + i * k2 + j];
+      C[e] = a.Gram[(ox + i) * NC + oy + j];
     } else {
       double s = 0;
       for (int c = 0; c < a.l; ++c) s += a.YPhi[c * k2 + i] * a.YPhi[c * k2 + j];
@@ -1095,14 +1097,30 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   }
   const DevState& hs = *p.st_host;
   passes += hs.iter;
-  // Rayleigh-Ritz at the final point from an FP64 pass over [X U, Y V]
-  GB_TRY(fused_pass(p, false, true, st, k, nullptr));
+  // Rayleigh-Ritz at the final point.  refine = 1: Grams of [X U, Y V] from
+  // an FP64 pass (exact products of the stored data); refine = 2: Grams from
+  // the plan's own pass (FP32 accumulation for BF16/FP32 data).
+  const bool exact_refine = p.opt.refine != 2 || !low;
+  if (exact_refine) {
+    GB_TRY(fused_pass(p, false, true, st, k, nullptr));
+  } else {
+    GB_TRY(fused_pass(p, true, false, st, 0, nullptr));
+  }
   GB_TRY(phigram(p, st, nullptr));
   GB_TRY(yphi(p, st, 0));
   {
     RRArgs a{};
     a.st = p.st;
     a.Gram = p.Gram;
+    if (exact_refine) {
+      a.gnc = p.nviews * k;
+      a.offx = 0;
+      a.offy = k;
+    } else {
+      a.gnc = p.NC;
+      a.offx = 0;
+      a.offy = 2 * k;
+    }
     a.phipart = p.phipart;
     a.nblk = thin_blocks(p);
     a.k = k;
