@@ -51,7 +51,7 @@ void free_plan(Plan* p) {
                   (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
                   (void*)p->phigram, (void*)p->phipart, (void*)p->cross, (void*)p->crosspart, (void*)p->history,
-                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part})
+                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part})
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
@@ -140,7 +140,7 @@ int alloc_plan(Plan* p) {
   }
   GB_TRY(dalloc(&p->st, 1));
   GB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(DevState)));
-  const int nblk = ceil_div(dmax, 64);
+  const int nblk = ceil_div(dmax, 16);  // thin-Gram row blocks
   GB_TRY(dalloc(&p->phigram, 4096));
   GB_TRY(dalloc(&p->phipart, (int64_t)p->nviews * nblk * 4 * k * k));
   GB_TRY(dalloc(&p->cross, (int64_t)p->nviews * 16 * k * k));
@@ -148,6 +148,7 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->history, 3 * (int64_t)(p->opt.max_iter + 1)));
   p->ws_len = 8 * (int64_t)dmax * dmax + 3 * (int64_t)dmax * std::max(std::max(p->l, k2), 1) + 4096;
   GB_TRY(dalloc(&p->ws, p->ws_len));
+  GB_TRY(dalloc(&p->mt_part, (int64_t)ceil_div(dmax, 64) * dmax * 40));
   GB_TRY(dalloc(&p->flag, 1));
   GB_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
   if (p->kind == kCCA && p->dtype == GBCCA_BF16 && 4 * k <= 48 && p->v[0].d <= 512 && p->v[1].d <= 512) {

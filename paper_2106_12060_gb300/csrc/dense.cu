@@ -244,54 +244,86 @@ int to_f32(const double* a, float* b, int64_t len, cudaStream_t st) {
 // B (rows = columns of op(A)) and C FP64 with row strides ldb, ldc.  T = double
 // (FP64 path) or float (the FP32 copy of R^{-1} used with BF16/FP32 data).
 // With tri set, A is upper triangular and its zero tiles are skipped.
+// Grid = (16-row blocks) x (64-wide slices of the inner dimension); each CTA
+// writes a partial product and a second kernel adds the slices in order.
+constexpr int kMR = 16, kMK = 64, kMC = 40;
+
 template <typename T>
 __global__ void __launch_bounds__(128)
 mat_thin_kernel(const T* __restrict__ A, int ra, int ca, int transA, int tri, const double* __restrict__ B,
-                int64_t ldb, double* __restrict__ C, int64_t ldc, int c) {
-  __shared__ T As[16][33];
-  __shared__ T Bs[32][8];
-  const int tr = threadIdx.x >> 3, tc = threadIdx.x & 7;
+                int64_t ldb, double* __restrict__ part, int c) {
+  __shared__ T As[kMK][kMR + 1];   // As[l][r] = op(A)[i0 + r][l0 + l]
+  __shared__ T Bs[kMK][kMC];
+  const int tr = threadIdx.x & 15, tg = threadIdx.x >> 4;  // row, column group (8 groups)
   const int m = transA ? ca : ra;   // rows of op(A)
   const int K = transA ? ra : ca;   // columns of op(A)
-  const int i0 = blockIdx.x * 16, c0 = blockIdx.y * 8;
-  T acc = 0;
-  for (int l0 = 0; l0 < K; l0 += 32) {
-    // op(A)[i][l] is nonzero only for l >= i (A upper) or l <= i (A^T lower)
-    if (tri && !transA && l0 + 31 < i0) continue;
-    if (tri && transA && l0 > i0 + 15) break;
-    for (int e = threadIdx.x; e < 16 * 32; e += 128) {
-      int r = e >> 5, q = e & 31;
-      int i = i0 + r, l = l0 + q;
-      T v = 0;
-      if (i < m && l < K) v = transA ? A[(int64_t)l * ca + i] : A[(int64_t)i * ca + l];
-      As[r][q] = v;
+  const int i0 = blockIdx.x * kMR, l0 = blockIdx.y * kMK;
+  double* out = part + ((int64_t)blockIdx.y * m) * c;
+  // op(A)[i][l] is nonzero only for l >= i (A upper) or l <= i (A^T lower)
+  const bool zero = (tri && !transA && l0 + kMK - 1 < i0) || (tri && transA && l0 > i0 + kMR - 1);
+  T acc[kMC / 8] = {};
+  if (!zero) {
+    if (transA) {
+      for (int e = threadIdx.x; e < kMK * kMR; e += 128) {
+        int l = e / kMR, r = e % kMR;
+        As[l][r] = (l0 + l < K && i0 + r < m) ? A[(int64_t)(l0 + l) * ca + i0 + r] : T(0);
+      }
+    } else {
+      for (int e = threadIdx.x; e < kMK * kMR; e += 128) {
+        int r = e / kMK, l = e % kMK;
+        As[l][r] = (l0 + l < K && i0 + r < m) ? A[(int64_t)(i0 + r) * ca + l0 + l] : T(0);
+      }
     }
-    for (int e = threadIdx.x; e < 32 * 8; e += 128) {
-      int q = e >> 3, cc = e & 7;
-      int l = l0 + q;
-      Bs[q][cc] = (l < K && c0 + cc < c) ? (T)B[(int64_t)l * ldb + c0 + cc] : T(0);
+    for (int e = threadIdx.x; e < kMK * kMC; e += 128) {
+      int l = e / kMC, cc = e % kMC;
+      Bs[l][cc] = (l0 + l < K && cc < c) ? (T)B[(int64_t)(l0 + l) * ldb + cc] : T(0);
     }
     __syncthreads();
+#pragma unroll 16
+    for (int l = 0; l < kMK; ++l) {
+      const T a = As[l][tr];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc += As[tr][q] * Bs[q][tc];
-    __syncthreads();
+      for (int q = 0; q < kMC / 8; ++q) acc[q] += a * Bs[l][tg + 8 * q];
+    }
   }
-  int i = i0 + tr, cc = c0 + tc;
-  if (i < m && cc < c) C[(int64_t)i * ldc + cc] = (double)acc;
+  const int i = i0 + tr;
+  if (i < m) {
+#pragma unroll
+    for (int q = 0; q < kMC / 8; ++q) {
+      const int cc = tg + 8 * q;
+      if (cc < c) out[(int64_t)i * c + cc] = (double)acc[q];
+    }
+  }
+}
+
+__global__ void mat_thin_sum_kernel(const double* __restrict__ part, int nslices, int m, int c,
+                                    double* __restrict__ C, int64_t ldc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * c) return;
+  double s = 0;
+  for (int q = 0; q < nslices; ++q) s += part[(int64_t)q * m * c + e];
+  C[(int64_t)(e / c) * ldc + e % c] = s;
 }
 
 template <typename T>
 int mat_thin(const T* A, int ra, int ca, bool transA, bool tri, const double* B, int64_t ldb, double* C,
-             int64_t ldc, int c, cudaStream_t st) {
-  int m = transA ? ca : ra;
-  dim3 grid(ceil_div(m, 16), ceil_div(c, 8));
-  mat_thin_kernel<T><<<grid, 128, 0, st>>>(A, ra, ca, transA ? 1 : 0, tri ? 1 : 0, B, ldb, C, ldc, c);
-  GB_CHECK_LAUNCH();
+             int64_t ldc, int c, double* part, cudaStream_t st) {
+  const int m = transA ? ca : ra;
+  const int K = transA ? ra : ca;
+  const int ns = ceil_div(K, kMK);
+  for (int c0 = 0; c0 < c; c0 += kMC) {
+    const int cw = std::min(kMC, c - c0);
+    mat_thin_kernel<T><<<dim3(ceil_div(m, kMR), ns), 128, 0, st>>>(A, ra, ca, transA ? 1 : 0, tri ? 1 : 0, B + c0,
+                                                                   ldb, part, cw);
+    GB_CHECK_LAUNCH();
+    mat_thin_sum_kernel<<<ceil_div(m * cw, 256), 256, 0, st>>>(part, ns, m, cw, C + c0, ldc);
+    GB_CHECK_LAUNCH();
+  }
   return GBCCA_OK;
 }
 template int mat_thin<double>(const double*, int, int, bool, bool, const double*, int64_t, double*, int64_t, int,
-                              cudaStream_t);
+                              double*, cudaStream_t);
 template int mat_thin<float>(const float*, int, int, bool, bool, const double*, int64_t, double*, int64_t, int,
-                             cudaStream_t);
+                             double*, cudaStream_t);
 
 }  // namespace gbcca

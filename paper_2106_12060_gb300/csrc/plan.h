@@ -24,8 +24,10 @@ struct DevState {
   double rot[2][kMaxK * kMaxK];     // Rayleigh-Ritz rotation per view
   double YW[kMaxClasses * kMaxK];   // FDA: Yhat times the current W (l x k)
   double ftrial[64];                // line-search trial values (diagnostics)
+  double Qsyl[2][kMaxK * kMaxK];    // eigenvectors of the last Sylvester coefficient
   int max_iter;
   int ntrials;
+  int qsyl_valid;
 };
 
 // One generalized Stiefel factor: the data view it is built on and the
@@ -105,6 +107,7 @@ struct Plan {
   double* crosspart = nullptr;  // partials
   int thinCtas = 0;
   double* history = nullptr;    // 3 (max_iter + 1)
+  double* mt_part = nullptr;    // slice partials of mat_thin
   double* ws = nullptr;         // FP64 scratch for dense routines
   int64_t ws_len = 0;
   int* flag = nullptr;          // device error flag (NOT_SPD etc.)
@@ -135,9 +138,10 @@ int tri_inverse_upper(const double* R, double* Rinv, int d, cudaStream_t st);
 int to_f32(const double* a, float* b, int64_t len, cudaStream_t st);
 // C (m x c, ldc) = op(A) B (rows of B = columns of op(A), ldb); A is
 // ra x ca row-major; tri = 1 skips the zero half of an upper-triangular A.
+// `part` is scratch of ceil(K / 64) * m * min(c, 40) doubles.
 template <typename T>
 int mat_thin(const T* A, int ra, int ca, bool transA, bool tri, const double* B, int64_t ldb, double* C,
-             int64_t ldc, int c, cudaStream_t st);
+             int64_t ldc, int c, double* part, cudaStream_t st);
 
 // pass.cu
 int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols = 0,

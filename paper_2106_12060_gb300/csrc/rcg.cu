@@ -50,27 +50,44 @@ __device__ void blk_mm(const double* A, bool tA, const double* B, bool tB, doubl
 // Symmetric eigendecomposition by parallel (round-robin ordered) Jacobi:
 // A (n x n, destroyed) -> eigenvalues in lam (descending), eigenvectors in
 // the columns of Q (n x n).  rot is shared scratch of 3 * 33 doubles/ints.
-__device__ void blk_jacobi(double* A, double* Q, double* lam, int n, double* rot) {
-  double* cs = rot;
-  double* sn = rot + 33;
+template <typename R>
+__device__ void blk_jacobi(R* A, R* Q, R* lam, int n, double* rot) {
+  R* cs = reinterpret_cast<R*>(rot);
+  R* sn = cs + 33;
   int* pp = reinterpret_cast<int*>(rot + 66);
   int* qq = pp + 33;
   __shared__ double offn;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) Q[e] = (e / n == e % n) ? 1.0 : 0.0;
   __syncthreads();
   const int m = n + (n & 1);
-  for (int sweep = 0; sweep < 30 && n > 1; ++sweep) {
-    if (threadIdx.x == 0) {
-      double off = 0, dg = 0;
-      for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-          double v = A[i * n + j] * A[i * n + j];
-          if (i == j) dg += v;
-          else off += v;
+  __shared__ double s_off[32], s_dg[32];
+  for (int sweep = 0; sweep < 20 && n > 1; ++sweep) {
+    {
+      R off = 0, dg = 0;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        R v = A[e] * A[e];
+        if (e / n == e % n) dg += v;
+        else off += v;
+      }
+      off = warp_sum(off);
+      dg = warp_sum(dg);
+      if ((threadIdx.x & 31) == 0) {
+        s_off[threadIdx.x >> 5] = off;
+        s_dg[threadIdx.x >> 5] = dg;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double o = 0, d = 0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+          o += s_off[w];
+          d += s_dg[w];
         }
-      offn = (off <= 1e-30 * dg || off == 0.0) ? 1.0 : 0.0;
+        // off-diagonal norm below 1e-13 of the diagonal: the next sweep would
+        // only move entries at the rounding level
+        offn = (o <= (sizeof(R) == 8 ? 1e-26 : 1e-12) * d || o == 0.0) ? 1.0 : 0.0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (offn > 0.5) break;
     for (int r = 0; r < m - 1; ++r) {
       if (threadIdx.x < m / 2) {
@@ -78,13 +95,15 @@ __device__ void blk_jacobi(double* A, double* Q, double* lam, int n, double* rot
         int a = (i == 0) ? 0 : 1 + ((i - 1 + r) % (m - 1));
         int b = 1 + ((m - 2 - i + r) % (m - 1));
         int p = min(a, b), q = max(a, b);
-        double c = 1.0, s = 0.0;
+        R c = 1, s = 0;
         if (q < n) {
-          double apq = A[p * n + q];
-          if (apq != 0.0) {
-            double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+          R apq = A[p * n + q];
+          // rotations of entries far below the rounding level of the pivots are skipped
+          const R eps = R(sizeof(R) == 8 ? 1e-17 : 1e-8);
+          if (apq * apq > eps * eps * fabs(A[p * n + p] * A[q * n + q])) {
+            R tau = (A[q * n + q] - A[p * n + p]) / (R(2) * apq);
+            R t = (tau >= 0 ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+            c = R(1) / sqrt(R(1) + t * t);
             s = t * c;
           }
         }
@@ -99,7 +118,7 @@ __device__ void blk_jacobi(double* A, double* Q, double* lam, int n, double* rot
         int i = e / n, j = e % n;
         if (qq[i] < 0) continue;
         int p = pp[i], q = qq[i];
-        double ap = A[p * n + j], aq = A[q * n + j];
+        R ap = A[p * n + j], aq = A[q * n + j];
         A[p * n + j] = cs[i] * ap - sn[i] * aq;
         A[q * n + j] = sn[i] * ap + cs[i] * aq;
       }
@@ -109,10 +128,10 @@ __device__ void blk_jacobi(double* A, double* Q, double* lam, int n, double* rot
         int i = e / n, j = e % n;
         if (qq[i] < 0) continue;
         int p = pp[i], q = qq[i];
-        double ap = A[j * n + p], aq = A[j * n + q];
+        R ap = A[j * n + p], aq = A[j * n + q];
         A[j * n + p] = cs[i] * ap - sn[i] * aq;
         A[j * n + q] = sn[i] * ap + cs[i] * aq;
-        double qp = Q[j * n + p], qv = Q[j * n + q];
+        R qp = Q[j * n + p], qv = Q[j * n + q];
         Q[j * n + p] = cs[i] * qp - sn[i] * qv;
         Q[j * n + q] = sn[i] * qp + cs[i] * qv;
       }
@@ -127,11 +146,11 @@ __device__ void blk_jacobi(double* A, double* Q, double* lam, int n, double* rot
       for (int j = i + 1; j < n; ++j)
         if (lam[j] > lam[b]) b = j;
       if (b != i) {
-        double t = lam[i];
+        R t = lam[i];
         lam[i] = lam[b];
         lam[b] = t;
         for (int r = 0; r < n; ++r) {
-          double u = Q[r * n + i];
+          R u = Q[r * n + i];
           Q[r * n + i] = Q[r * n + b];
           Q[r * n + b] = u;
         }
@@ -184,7 +203,9 @@ __device__ void blk_lower_inv(const double* L, double* Li, int n) {
 }
 
 // Warp-level versions used by the parallel line-search trials (n <= 32).
-__device__ bool warp_chol(double* A, int n) {
+// The reciprocal of each pivot is kept on the diagonal's mirror (invd) so the
+// triangular solves multiply instead of divide.
+__device__ bool warp_chol(double* A, int n, double* invd) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
   for (int j = 0; j < n; ++j) {
@@ -193,26 +214,32 @@ __device__ bool warp_chol(double* A, int n) {
       ok = false;
       dj = 1.0;
     }
-    double ljj = sqrt(dj);
+    const double ljj = sqrt(dj);
+    const double rj = 1.0 / ljj;
     __syncwarp();
-    if (lane == j) A[j * n + j] = ljj;
-    if (lane > j && lane < n) A[lane * n + j] /= ljj;
+    if (lane == j) {
+      A[j * n + j] = ljj;
+      invd[j] = rj;
+    }
+    if (lane > j && lane < n) A[lane * n + j] *= rj;
     __syncwarp();
-    if (lane > j && lane < n)
-      for (int c = j + 1; c <= lane; ++c) A[lane * n + c] -= A[lane * n + j] * A[c * n + j];
+    if (lane > j && lane < n) {
+      const double lij = A[lane * n + j];
+      for (int c = j + 1; c <= lane; ++c) A[lane * n + c] -= lij * A[c * n + j];
+    }
     __syncwarp();
   }
   return ok;
 }
 
 // Li = L^{-1} (lane c computes column c)
-__device__ void warp_lower_inv(const double* L, double* Li, int n) {
+__device__ void warp_lower_inv(const double* L, const double* invd, double* Li, int n) {
   const int c = threadIdx.x & 31;
   if (c < n) {
     for (int i = 0; i < n; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
       for (int q = c; q < i; ++q) s -= L[i * n + q] * Li[q * n + c];
-      Li[i * n + c] = (i < c) ? 0.0 : s / L[i * n + i];
+      Li[i * n + c] = (i < c) ? 0.0 : s * invd[i];
     }
   }
   __syncwarp();
@@ -220,7 +247,8 @@ __device__ void warp_lower_inv(const double* L, double* Li, int n) {
 
 // ========================================================= thin Grams
 // part[view][blk] (ca x cb) = A[rows of blk]^T B[rows of blk], A: d x ca
-// (row stride lda), B: d x cb (ldb), 64 rows per block.
+// (row stride lda), B: d x cb (ldb), kThinRows rows per block.
+constexpr int kThinRows = 16;
 struct ThinArgs {
   const double* A[2];
   const double* B[2];
@@ -235,15 +263,15 @@ __global__ void thin_gram_kernel(ThinArgs a) {
   if (a.done != nullptr && *a.done) return;
   const int v = blockIdx.y;
   const int d = a.d[v];
-  const int r0 = blockIdx.x * 64;
+  const int r0 = blockIdx.x * kThinRows;
   double* As = tsm;
-  double* Bs = tsm + 64 * a.ca;
-  const int nr = min(64, d - r0);
-  for (int e = threadIdx.x; e < 64 * a.ca; e += blockDim.x) {
+  double* Bs = tsm + kThinRows * a.ca;
+  const int nr = min(kThinRows, d - r0);
+  for (int e = threadIdx.x; e < kThinRows * a.ca; e += blockDim.x) {
     int r = e / a.ca, c = e % a.ca;
     As[e] = r < nr ? a.A[v][(int64_t)(r0 + r) * a.lda[v] + c] : 0.0;
   }
-  for (int e = threadIdx.x; e < 64 * a.cb; e += blockDim.x) {
+  for (int e = threadIdx.x; e < kThinRows * a.cb; e += blockDim.x) {
     int r = e / a.cb, c = e % a.cb;
     Bs[e] = r < nr ? a.B[v][(int64_t)(r0 + r) * a.ldb[v] + c] : 0.0;
   }
@@ -273,10 +301,10 @@ static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const
   }
   a.ca = ca;
   a.cb = cb;
-  a.nblk = ceil_div(dmax, 64);
+  a.nblk = ceil_div(dmax, kThinRows);
   a.part = part;
   a.done = done;
-  size_t smem = sizeof(double) * 64 * (ca + cb);
+  size_t smem = sizeof(double) * kThinRows * (ca + cb);
   GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // blocks past a view's rows write zeros (nr <= 0 loops are empty)
   thin_gram_kernel<<<dim3(a.nblk, p.nviews), 256, smem, st>>>(a);
@@ -285,9 +313,16 @@ static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const
 }
 
 __device__ void sum_blocks(const double* part, int nblk, int len, double* out) {
+  // loads are issued 8 at a time (independent), then added in block order
   for (int e = threadIdx.x; e < len; e += blockDim.x) {
     double s = 0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * len + e];
+    for (int b0 = 0; b0 < nblk; b0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (b0 + u < nblk) ? part[(int64_t)(b0 + u) * len + e] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
     out[e] = s;
   }
   __syncthreads();
@@ -315,25 +350,28 @@ __device__ double ls_eval(const LSArgs& a, const double* coef, double t, double*
   double* Gy = w + kk;
   double* Cx = w + 2 * kk;
   double* Li = w + 3 * kk;
+  double* ix = w + 4 * kk;
+  double* iy = ix + kMaxK;
   for (int e = lane; e < kk; e += 32) {
     Gx[e] = coef[e] + t * coef[kk + e] + t * t * coef[2 * kk + e];
     if (a.kind == kCCA) Gy[e] = coef[3 * kk + e] + t * coef[4 * kk + e] + t * t * coef[5 * kk + e];
     Cx[e] = coef[6 * kk + e] + t * coef[7 * kk + e] + t * t * coef[8 * kk + e];
   }
   __syncwarp();
-  bool ok = warp_chol(Gx, k);
-  if (a.kind == kCCA) ok = warp_chol(Gy, k) && ok;
+  bool ok = warp_chol(Gx, k, ix);
+  if (a.kind == kCCA) ok = warp_chol(Gy, k, iy) && ok;
   // Y = Lx^{-1} Cross  (lane c solves column c)
   if (lane < k) {
     for (int i = 0; i < k; ++i) {
       double s = Cx[i * k + lane];
       for (int q = 0; q < i; ++q) s -= Gx[i * k + q] * Cx[q * k + lane];
-      Cx[i * k + lane] = s / Gx[i * k + i];
+      Cx[i * k + lane] = s * ix[i];
     }
   }
   __syncwarp();
   // second factor: Ly (CCA) or Lx again (FDA: L^{-1} S_B L^{-T})
-  warp_lower_inv(a.kind == kCCA ? Gy : Gx, Li, k);
+  if (a.kind == kCCA) warp_lower_inv(Gy, iy, Li, k);
+  else warp_lower_inv(Gx, ix, Li, k);
   double part = 0;
   if (lane < k) {
     double z = 0;
@@ -346,6 +384,13 @@ __device__ double ls_eval(const LSArgs& a, const double* coef, double t, double*
   return f;
 }
 
+// Trials are evaluated in groups of kLSWarps (one per warp).  Group 0 holds
+// t = 0 (the Armijo reference, evaluated at the point of this pass), t0 and
+// the first expansions 2 t0 .. 2^6 t0; later groups hold the remaining
+// expansions or the backtracking steps t0 2^-j.  The decision follows the
+// sequential rule exactly: the first j in 0..24 with Armijo at t0 2^-j is
+// accepted; only if j = 0, t doubles while f keeps decreasing and Armijo
+// holds (at most 10 doublings).
 __global__ void linesearch_kernel(LSArgs a) {
   DevState* st = a.st;
   if (st->done) return;
@@ -353,15 +398,16 @@ __global__ void linesearch_kernel(LSArgs a) {
   const int k = a.k, kk = k * k, k2 = 2 * k;
   double* coef = lsm;                       // 9 kk
   double* phig = coef + 9 * kk;             // 2 views x 4 kk
-  double* work = phig + 8 * kk;             // kLSWarps x 4 kk
-  __shared__ double ft[kNTrials], tt[kNTrials];
+  double* work = phig + 8 * kk;             // kLSWarps x (4 kk + 2 kMaxK)
+  __shared__ double gt[kLSWarps], gf[kLSWarps];
   __shared__ double mu_s[kMaxK];
-  __shared__ int chosen;
-  __shared__ double t_acc;
+  __shared__ int ctl[5];                    // 0: phase, 1: next index, 2: accepted (-1 none), 3: finished,
+                                            // 4: warp whose buffers hold the accepted trial (-1: none)
+  __shared__ double sh_f0, sh_tacc, sh_facc;
   if (threadIdx.x < k) mu_s[threadIdx.x] = st->mu[threadIdx.x];
   for (int v = 0; v < a.nviews; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * kk, a.nblk, 4 * kk,
                                                 phig + v * 4 * kk);
-  // coefficient matrices
+  // coefficient matrices: Gram_v(t) = A + t B + t^2 C, Cross(t) = X0 + t X1 + t^2 X2
   const int NC = a.NC;
   for (int e = threadIdx.x; e < kk; e += blockDim.x) {
     int i = e / k, j = e % k;
@@ -397,77 +443,155 @@ __global__ void linesearch_kernel(LSArgs a) {
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* w = work + warp * 4 * kk;
+  double* w = work + warp * (4 * kk + 2 * kMaxK);
   const bool zero_step = st->force_zero_step != 0;
-  if (zero_step) {
-    if (warp == 0) {
-      double f0 = ls_eval(a, coef, 0.0, w, mu_s);
-      if (lane == 0) {
-        ft[0] = f0;
-        tt[0] = 0.0;
-        chosen = 0;
-        t_acc = 0.0;
-      }
-    }
-    __syncthreads();
-  } else {
-    const double t0 = st->t0;
-    for (int tr = warp; tr < kNTrials; tr += kLSWarps) {
-      double t = tr < kMaxLS ? ldexp(t0, -tr) : (tr < kNTrials - 1 ? ldexp(t0, tr - kMaxLS + 1) : 0.0);
-      double f = ls_eval(a, coef, t, w, mu_s);
-      if (lane == 0) {
-        ft[tr] = f;
-        tt[tr] = t;
-      }
+  const double t0 = st->t0, df = st->df;
+  if (threadIdx.x == 0) {
+    ctl[0] = zero_step ? 3 : 0;  // phases: 0 first group, 1 more expansions, 2 backtracking, 3 zero step
+    ctl[1] = 1;
+    ctl[2] = -1;
+    ctl[3] = 0;
+    ctl[4] = -1;
+    sh_tacc = 0.0;
+  }
+  __syncthreads();
+  int trials = 0;
+  while (true) {
+    const int phase = ctl[0], next = ctl[1];
+    // trial t of this warp in this group (NaN marks an unused slot)
+    double t = NAN;
+    if (phase == 0) t = warp == 0 ? 0.0 : (warp <= 2 ? ldexp(t0, warp - 1) : NAN);  // 0, t0, 2 t0
+    else if (phase == 1) t = (next + warp <= kMaxExpand) ? ldexp(t0, next + warp) : NAN;
+    else if (phase == 2) t = (next + warp < kMaxLS) ? ldexp(t0, -(next + warp)) : NAN;
+    else t = warp == 0 ? 0.0 : NAN;
+    double f = INFINITY;
+    if (t == t) f = ls_eval(a, coef, t, w, mu_s);
+    if (lane == 0) {
+      gt[warp] = t;
+      gf[warp] = f;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      // f at the current point, from this pass (the point the pass evaluated)
-      const double f0 = ft[kNTrials - 1], df = st->df;
-      int acc = -1;
-      for (int j = 0; j < kMaxLS; ++j)
-        if (ft[j] <= f0 + kC1 * tt[j] * df) {
-          acc = j;
-          break;
+      trials += 1;
+      if (phase == 3) {
+        sh_f0 = gf[0];
+        sh_tacc = 0.0;
+        sh_facc = gf[0];
+        ctl[2] = 0;
+        ctl[3] = 1;
+        ctl[4] = 0;
+      } else if (phase == 0) {
+        sh_f0 = gf[0];
+        const double f0 = gf[0];
+        if (gf[1] <= f0 + kC1 * gt[1] * df) {
+          // t0 accepted; expand while f decreases and Armijo holds
+          sh_tacc = gt[1];
+          sh_facc = gf[1];
+          ctl[2] = 1;
+          ctl[4] = 1;
+          if (gf[2] < gf[1] && gf[2] <= f0 + kC1 * gt[2] * df) {
+            sh_tacc = gt[2];
+            sh_facc = gf[2];
+            ctl[4] = 2;
+            ctl[0] = 1;  // keep doubling from 4 t0
+            ctl[1] = 2;
+          } else {
+            ctl[3] = 1;
+          }
+        } else {
+          ctl[0] = 2;  // backtrack from t0 / 2
+          ctl[1] = 1;
         }
-      if (acc == 0) {
-        for (int e = 0; e < kMaxExpand; ++e) {
-          int idx = kMaxLS + e;
-          if (ft[idx] < ft[acc] && ft[idx] <= f0 + kC1 * tt[idx] * df) acc = idx;
-          else break;
+      } else if (phase == 1) {
+        const double f0 = sh_f0;
+        bool stop = false;
+        int e = 0;
+        for (; e < kLSWarps; ++e) {
+          if (!(gt[e] == gt[e])) {
+            stop = true;
+            break;
+          }
+          if (gf[e] < sh_facc && gf[e] <= f0 + kC1 * gt[e] * df) {
+            sh_tacc = gt[e];
+            sh_facc = gf[e];
+          } else {
+            stop = true;
+            break;
+          }
         }
+        ctl[4] = e > 0 ? e - 1 : -1;  // accepted trial of this group, or of an earlier one
+        ctl[1] = next + kLSWarps;
+        if (stop || next + kLSWarps > kMaxExpand) ctl[3] = 1;
+      } else {
+        const double f0 = sh_f0;
+        for (int e = 0; e < kLSWarps; ++e) {
+          if (!(gt[e] == gt[e])) break;
+          if (gf[e] <= f0 + kC1 * gt[e] * df) {
+            sh_tacc = gt[e];
+            sh_facc = gf[e];
+            ctl[2] = 1;
+            ctl[4] = e;
+            break;
+          }
+        }
+        ctl[1] = next + kLSWarps;
+        if (ctl[2] >= 0 || next + kLSWarps >= kMaxLS) ctl[3] = 1;
       }
-      chosen = acc;
-      t_acc = acc >= 0 ? tt[acc] : 0.0;
-      st->ls_trials = acc < 0 ? kMaxLS : (acc < kMaxLS ? acc + 1 : kMaxLS + 1);
-      for (int j = 0; j < kNTrials; ++j) st->ftrial[j] = ft[j];
     }
     __syncthreads();
+    if (ctl[3]) break;
   }
-  if (chosen < 0) {
+  if (ctl[2] < 0) {
     if (threadIdx.x == 0) {
       st->stalled = 1;
       st->done = 1;
+      st->ls_trials = trials;
     }
     return;
   }
-  // factors at the accepted step: Linv_v = L_v(t)^{-T} (upper), stored row-major
-  const double t = t_acc;
-  if (warp == 0) {
+  // factors at the accepted step: Linv_v = L_v(t)^{-T} (upper), stored row-major.
+  // The warp that evaluated the accepted trial still holds L_x, L_y and the
+  // inverse of the second factor; otherwise warp 0 recomputes them.
+  const double t = sh_tacc;
+  const int wacc = ctl[4];
+  if ((wacc >= 0 && warp == wacc) || (wacc < 0 && warp == 0)) {
     double* Gx = w;
-    for (int v = 0; v < a.nviews; ++v) {
-      for (int e = lane; e < kk; e += 32)
-        Gx[e] = coef[(3 * v) * kk + e] + t * coef[(3 * v + 1) * kk + e] + t * t * coef[(3 * v + 2) * kk + e];
-      __syncwarp();
-      warp_chol(Gx, k);
-      double* Li = w + 3 * kk;
-      warp_lower_inv(Gx, Li, k);
-      for (int e = lane; e < kk; e += 32) {
-        int i = e / k, j = e % k;
-        st->Linv[v][e] = Li[j * k + i];  // (L^{-1})^T
+    double* Gy = w + kk;
+    double* Lt = w + 2 * kk;
+    double* Li = w + 3 * kk;
+    double* ix = w + 4 * kk;
+    double* iy = ix + kMaxK;
+    if (wacc >= 0) {
+      if (a.kind == kCCA) {
+        warp_lower_inv(Gx, ix, Lt, k);
+        for (int e = lane; e < kk; e += 32) {
+          int i = e / k, j = e % k;
+          st->Linv[0][e] = Lt[j * k + i];
+          st->Linv[1][e] = Li[j * k + i];
+        }
+      } else {
+        for (int e = lane; e < kk; e += 32) {
+          int i = e / k, j = e % k;
+          st->Linv[0][e] = Li[j * k + i];
+        }
       }
       __syncwarp();
+    } else {
+      for (int v = 0; v < a.nviews; ++v) {
+        for (int e = lane; e < kk; e += 32)
+          Gx[e] = coef[(3 * v) * kk + e] + t * coef[(3 * v + 1) * kk + e] + t * t * coef[(3 * v + 2) * kk + e];
+        __syncwarp();
+        warp_chol(Gx, k, ix);
+        warp_lower_inv(Gx, ix, Li, k);
+        for (int e = lane; e < kk; e += 32) {
+          int i = e / k, j = e % k;
+          st->Linv[v][e] = Li[j * k + i];  // (L^{-1})^T
+        }
+        __syncwarp();
+      }
     }
+    (void)Gy;
+    (void)iy;
     if (a.kind == kLDA) {
       // YW+ = (Yhat W + t Yhat eta) L^{-T}
       for (int e = lane; e < a.l * k; e += 32) {
@@ -479,9 +603,9 @@ __global__ void linesearch_kernel(LSArgs a) {
       }
     }
     if (lane == 0) {
-      double fnew = ft[chosen];
       st->t = t;
-      st->f = fnew;
+      st->f = sh_facc;
+      st->ls_trials = trials;
       if (!zero_step) {
         st->t_prev = t;
         st->df_prev = st->df;
@@ -568,98 +692,186 @@ struct DirArgs {
   int max_iter;
 };
 
-// <u, M w> for u = L_a - Wn Su, M w = R_b - BU Sw from the cross Gram X
-// (4k x 4k, blocks X[a][b] = L_a^T R_b); Su / Sw may be null (= 0).
-__device__ double cross_ip(const double* X, int k, int a, const double* Su, int b, const double* Sw, double* tmp) {
-  const int k4 = 4 * k, kk = k * k;
-  __shared__ double red[256];
-  double s = 0;
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    int i = e / k, j = e % k;
-    // tr(X[a][b]) contributes on the diagonal
-    if (i == j) s += X[(a * k + i) * k4 + b * k + i];
-    // - tr(X[a][0] Sw) = - sum_ij X[a][0]_ij Sw_ji
-    if (Sw) s -= X[(a * k + i) * k4 + 0 * k + j] * Sw[j * k + i];
-    // - tr(Su^T X[0][b]) = - sum_ij Su_ij X[0][b]_ij
-    if (Su) s -= Su[i * k + j] * X[(0 * k + i) * k4 + b * k + j];
-  }
-  // + tr(Su^T X00 Sw) = sum_ij Su_ij (X00 Sw)_ij
-  if (Su && Sw) {
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-      int i = e / k, j = e % k;
-      double z = 0;
-      for (int q = 0; q < k; ++q) z += X[(0 * k + i) * k4 + 0 * k + q] * Sw[q * k + j];
-      s += Su[e] * z;
-    }
-  }
-  red[threadIdx.x] = s;
+// Block-wide sum of NV per-thread values (blockDim <= 256).
+template <int NV>
+__device__ void blk_sum(double (&v)[NV], double* red) {
+  for (int q = 0; q < NV; ++q) red[q * 256 + threadIdx.x] = v[q];
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o)
+      for (int q = 0; q < NV; ++q) red[q * 256 + threadIdx.x] += red[q * 256 + threadIdx.x + o];
     __syncthreads();
   }
-  double r = red[0];
+  for (int q = 0; q < NV; ++q) v[q] = red[q * 256];
   __syncthreads();
-  return r;
 }
 
+// Per factor: X = [Wn, xi, eta, g]^T [BU, egrad, M eta, M g] (4k x 4k blocks
+// X[a][b]).  The projection of Table 1 needs S with A S + S A = C + C^T for
+// A = sym(X[0][0]) = U^T B M^{-1} B U and C = X[a][0]^T (a = 1: gradient,
+// 2: old direction, 3: old gradient); A = Q diag(lam) Q^T gives
+// S = Q ((Q^T (C + C^T) Q) ./ (lam_i + lam_j)) Q^T.  Inner products in g of
+// u = L_a - Wn Su with M w = R_b - BU Sw expand into
+//   tr X[a][b] - tr(X[a][0] Sw) - tr(Su^T X[0][b]) + tr(Su^T X[0][0] Sw).
+template <typename R>
 __global__ void direction_kernel(DirArgs a) {
   DevState* st = a.st;
   if (st->done) return;
   extern __shared__ double dsm[];
   const int k = a.k, kk = k * k, k4 = 4 * k;
-  double* X = dsm;                 // 16 kk per view
-  double* A = X + 2 * 16 * kk;     // kk
-  double* Q = A + kk;              // kk
-  double* lam = Q + kk;            // k
-  double* T1 = lam + kMaxK;        // kk
-  double* T2 = T1 + kk;            // kk
-  double* rot = T2 + kk;           // 100
+  double* X = dsm;                 // 16 kk per view (FP64 cross Gram)
+  double* Y = X + 2 * 16 * kk;     // 2 kk: X00 Sg, X00 So (FP64), then 3 kk: S (FP64)
+  double* rot = Y + 5 * kk;        // 100
+  double* red = rot + 100;         // 6 x 256
+  R* A = reinterpret_cast<R*>(red + 6 * 256);  // kk
+  R* Q = A + kk;                   // kk
+  R* lam = Q + kk;                 // kMaxK
+  R* T = lam + kMaxK;              // 3 kk
+  R* T2 = T + 3 * kk;              // 3 kk
+  R* S = T2 + 3 * kk;              // 3 kk (this view's S_g, S_e, S_o)
   for (int v = 0; v < a.nviews; ++v)
     sum_blocks(a.crosspart + (int64_t)v * a.nblk * 16 * kk, a.nblk, 16 * kk, X + v * 16 * kk);
+  double acc[6] = {0, 0, 0, 0, 0, 0};  // gg, g_Tg, Te_g, Te_Tg, dfg, dfTe
   for (int v = 0; v < a.nviews; ++v) {
     const double* Xv = X + v * 16 * kk;
-    // Sylvester coefficient (U^T B M^{-1} B U) = Wn^T BU, symmetrized
+    auto XB = [&](int ab, int bb, int i, int j) { return Xv[(ab * k + i) * k4 + bb * k + j]; };
+    // warm start: rotate A into the previous iteration's eigenbasis Q0 (A
+    // changes little between iterations, so few Jacobi sweeps remain)
+    double* Q0g = st->Qsyl[v];
+    R* Q0 = S;  // shared copy (S is free until the Sylvester solves)
+    const bool warm = st->qsyl_valid != 0;
     for (int e = threadIdx.x; e < kk; e += blockDim.x) {
       int i = e / k, j = e % k;
-      A[e] = 0.5 * (Xv[i * k4 + j] + Xv[j * k4 + i]);
+      T2[e] = R(0.5 * (XB(0, 0, i, j) + XB(0, 0, j, i)));
+      Q0[e] = warm ? R(Q0g[e]) : R(0);
     }
     __syncthreads();
-    blk_jacobi(A, Q, lam, k, rot);
-    // three right-hand sides: (BU)^T xi, (BU)^T eta, (BU)^T g = X[a][0]^T
-    for (int r = 0; r < 3; ++r) {
-      const int ablk = r + 1;
-      for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    if (warm) {
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // T = A Q0
         int i = e / k, j = e % k;
-        T1[e] = Xv[(ablk * k + i) * k4 + j] + Xv[(ablk * k + j) * k4 + i];  // C + C^T
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += T2[i * k + q] * Q0[q * k + j];
+        T[e] = sum;
       }
       __syncthreads();
-      blk_mm(Q, true, T1, false, T2, k, k, k, k, k);   // Q^T C
-      blk_mm(T2, false, Q, false, T1, k, k, k, k, k);  // Q^T C Q
-      for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // A' = Q0^T T
         int i = e / k, j = e % k;
-        T1[e] /= (lam[i] + lam[j]);
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += Q0[q * k + i] * T[q * k + j];
+        A[e] = sum;
       }
-      __syncthreads();
-      blk_mm(Q, false, T1, false, T2, k, k, k, k, k);  // Q S'
-      blk_mm(T2, false, Q, true, st->S[v][r], k, k, k, k, k);  // Q S' Q^T
+    } else {
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) A[e] = T2[e];
     }
+    __syncthreads();
+    blk_jacobi<R>(A, T2, lam, k, rot);  // A' = J diag(lam) J^T, J in T2
+    if (warm) {
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // Q = Q0 J
+        int i = e / k, j = e % k;
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += Q0[i * k + q] * T2[q * k + j];
+        Q[e] = sum;
+      }
+    } else {
+      for (int e = threadIdx.x; e < kk; e += blockDim.x) Q[e] = T2[e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) Q0g[e] = (double)Q[e];
+    __syncthreads();
+    // Sylvester solves for the three right-hand sides (C_r + C_r^T,
+    // C_r = X[r+1][0]^T) with A = Q diag(lam) Q^T: S_r = Q ((Q^T RHS Q) ./
+    // (lam_i + lam_j)) Q^T in R arithmetic.  With R = float one FP64
+    // residual correction follows: E = RHS - (A S + S A) in FP64, S += the
+    // R-arithmetic solve of A dS + dS A = E.
+    double* Sd = Y + 2 * kk;  // 3 kk doubles
+    for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+      int r = e / kk, f = e % kk, i = f / k, j = f % k;
+      T2[e] = R(XB(r + 1, 0, i, j) + XB(r + 1, 0, j, i));
+    }
+    __syncthreads();
+    for (int pass = 0; pass < (sizeof(R) == 8 ? 1 : 2); ++pass) {
+      // T = Q^T RHS ; T2 = (T Q) ./ (lam_i + lam_j) ; T = Q T2 ; S = T Q^T
+      for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        int r = e / kk, f = e % kk, i = f / k, j = f % k;
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += Q[q * k + i] * T2[r * kk + q * k + j];
+        T[e] = sum;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        int r = e / kk, f = e % kk, i = f / k, j = f % k;
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += T[r * kk + i * k + q] * Q[q * k + j];
+        T2[e] = sum / (lam[i] + lam[j]);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        int r = e / kk, f = e % kk, i = f / k, j = f % k;
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += Q[i * k + q] * T2[r * kk + q * k + j];
+        T[e] = sum;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        int r = e / kk, f = e % kk, i = f / k, j = f % k;
+        R sum = 0;
+        for (int q = 0; q < k; ++q) sum += T[r * kk + i * k + q] * Q[j * k + q];
+        Sd[e] = (pass == 0 ? 0.0 : Sd[e]) + (double)sum;
+      }
+      __syncthreads();
+      if (sizeof(R) == 8) break;
+      if (pass == 0) {
+        // residual in FP64: E = RHS - (A S + S A), A = sym(X00)
+        for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+          int r = e / kk, f = e % kk, i = f / k, j = f % k;
+          const double* Sr = Sd + r * kk;
+          double sum = XB(r + 1, 0, i, j) + XB(r + 1, 0, j, i);
+          for (int q = 0; q < k; ++q) {
+            const double aiq = 0.5 * (XB(0, 0, i, q) + XB(0, 0, q, i));
+            const double aqj = 0.5 * (XB(0, 0, q, j) + XB(0, 0, j, q));
+            sum -= aiq * Sr[q * k + j] + Sr[i * k + q] * aqj;
+          }
+          T2[e] = R(sum);
+        }
+        __syncthreads();
+      }
+    }
+    for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+      S[e] = R(Sd[e]);
+      st->S[v][e / kk][e % kk] = Sd[e];
+    }
+    __syncthreads();
+    const double* Sg = Sd;
+    const double* Se = Sd + kk;
+    const double* So = Sd + 2 * kk;
+    // Y0 = X00 Sg, Y1 = X00 So (FP64)
+    for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
+      int r = e / kk, f = e % kk, i = f / k, j = f % k;
+      const double* Sw = r == 0 ? Sg : So;
+      double sum = 0;
+      for (int q = 0; q < k; ++q) sum += XB(0, 0, i, q) * Sw[q * k + j];
+      Y[e] = sum;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+      int i = e / k, j = e % k;
+      const double dg = (i == j) ? 1.0 : 0.0;
+      const double sg = Sg[e], se = Se[e];
+      const double sgt = Sg[j * k + i], sot = So[j * k + i];
+      // terms: tr X[a][b]; tr(X[a][0] Sw) = sum X[a][0]_ij Sw_ji; tr(Su^T X[0][b]); tr(Su^T Y)
+      const double x11 = dg * XB(1, 1, i, i), x13 = dg * XB(1, 3, i, i);
+      const double x21 = dg * XB(2, 1, i, i), x23 = dg * XB(2, 3, i, i);
+      acc[0] += x11 - XB(1, 0, i, j) * sgt - sg * XB(0, 1, i, j) + sg * Y[e];
+      acc[1] += x13 - XB(1, 0, i, j) * sot - sg * XB(0, 3, i, j) + sg * Y[kk + e];
+      acc[2] += x21 - XB(2, 0, i, j) * sgt - se * XB(0, 1, i, j) + se * Y[e];
+      acc[3] += x23 - XB(2, 0, i, j) * sot - se * XB(0, 3, i, j) + se * Y[kk + e];
+      acc[4] += x11 - sg * XB(0, 1, i, j);
+      acc[5] += x21 - se * XB(0, 1, i, j);
+    }
+    __syncthreads();
   }
-  // inner products in g, summed over the factors
-  double gg = 0, g_Tg = 0, Te_g = 0, Te_Tg = 0, dfg = 0, dfTe = 0;
-  for (int v = 0; v < a.nviews; ++v) {
-    const double* Xv = X + v * 16 * kk;
-    const double* Sg = st->S[v][0];
-    const double* Se = st->S[v][1];
-    const double* So = st->S[v][2];
-    gg += cross_ip(Xv, k, 1, Sg, 1, Sg, T1);
-    g_Tg += cross_ip(Xv, k, 1, Sg, 3, So, T1);
-    Te_g += cross_ip(Xv, k, 2, Se, 1, Sg, T1);
-    Te_Tg += cross_ip(Xv, k, 2, Se, 3, So, T1);
-    // tr(egrad^T grad) = tr(X[1][1]) - tr(X[0][1]^T Sg); tr(egrad^T T eta) similar
-    dfg += cross_ip(Xv, k, 1, Sg, 1, nullptr, T1);
-    dfTe += cross_ip(Xv, k, 2, Se, 1, nullptr, T1);
-  }
+  blk_sum<6>(acc, red);
+  const double gg = acc[0], g_Tg = acc[1], Te_g = acc[2], Te_Tg = acc[3], dfg = acc[4], dfTe = acc[5];
   if (threadIdx.x == 0) {
     double beta = 0;
     if (!st->first) {
@@ -689,6 +901,7 @@ __global__ void direction_kernel(DirArgs a) {
     }
     st->first = 0;
     st->force_zero_step = 0;
+    st->qsyl_valid = 1;
     if (!(gn > st->gtol * st->gn0)) {
       st->done = 1;
       st->status = GBCCA_OK;
@@ -887,11 +1100,11 @@ int minv(Plan& p, int v, cudaStream_t st) {
   const int k = p.k, k2 = 2 * k, k4 = 4 * k;
   // tmp = R^{-T} RR[:, 0:2k]; LL[:, 0:2k] = R^{-1} tmp
   if (p.dtype == GBCCA_FP64) {
-    GB_TRY(mat_thin<double>(w.Rinv, w.d, w.d, true, true, w.RR, k4, w.tmp, k2, k2, st));
-    GB_TRY(mat_thin<double>(w.Rinv, w.d, w.d, false, true, w.tmp, k2, w.LL, k4, k2, st));
+    GB_TRY(mat_thin<double>(w.Rinv, w.d, w.d, true, true, w.RR, k4, w.tmp, k2, k2, p.mt_part, st));
+    GB_TRY(mat_thin<double>(w.Rinv, w.d, w.d, false, true, w.tmp, k2, w.LL, k4, k2, p.mt_part, st));
   } else {
-    GB_TRY(mat_thin<float>(w.Rinv32, w.d, w.d, true, true, w.RR, k4, w.tmp, k2, k2, st));
-    GB_TRY(mat_thin<float>(w.Rinv32, w.d, w.d, false, true, w.tmp, k2, w.LL, k4, k2, st));
+    GB_TRY(mat_thin<float>(w.Rinv32, w.d, w.d, true, true, w.RR, k4, w.tmp, k2, k2, p.mt_part, st));
+    GB_TRY(mat_thin<float>(w.Rinv32, w.d, w.d, false, true, w.tmp, k2, w.LL, k4, k2, p.mt_part, st));
   }
   return GBCCA_OK;
 }
@@ -913,7 +1126,7 @@ int yphi(Plan& p, cudaStream_t st, int check_done) {
 int thin_blocks(const Plan& p) {
   int dmax = 0;
   for (int v = 0; v < p.nviews; ++v) dmax = std::max(dmax, p.v[v].d);
-  return ceil_div(dmax, 64);
+  return ceil_div(dmax, kThinRows);
 }
 
 // One iteration (or, with force_zero_step set on the device, the qf_B
@@ -940,7 +1153,7 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
     a.l = p.l;
     a.history = p.history;
     a.max_iter = p.opt.max_iter;
-    size_t smem = sizeof(double) * (9 * kk + 8 * kk + kLSWarps * 4 * kk);
+    size_t smem = sizeof(double) * (9 * kk + 8 * kk + kLSWarps * (4 * kk + 2 * kMaxK));
     GB_CUDA(cudaFuncSetAttribute(linesearch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     linesearch_kernel<<<1, 32 * kLSWarps, smem, st>>>(a);
     GB_CHECK_LAUNCH();
@@ -984,9 +1197,15 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
     a.nviews = p.nviews;
     a.history = p.history;
     a.max_iter = p.opt.max_iter;
-    size_t smem = sizeof(double) * (2 * 16 * kk + 4 * kk + kMaxK + 100 + 16);
-    GB_CUDA(cudaFuncSetAttribute(direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    direction_kernel<<<1, 256, smem, st>>>(a);
+    size_t smem = sizeof(double) * (2 * 16 * kk + 5 * kk + 100 + 6 * 256 + 11 * kk + kMaxK);
+    if (low) {
+      GB_CUDA(cudaFuncSetAttribute(direction_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      direction_kernel<float><<<1, 256, smem, st>>>(a);
+    } else {
+      GB_CUDA(cudaFuncSetAttribute(direction_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      direction_kernel<double><<<1, 256, smem, st>>>(a);
+    }
     GB_CHECK_LAUNCH();
   }
   {
@@ -1025,6 +1244,7 @@ __global__ void state_init_kernel(DevState* st, double gtol, int max_iter, doubl
   st->t = st->f = st->df = st->t_prev = st->df_prev = st->gn = st->gn0 = st->beta = st->t0 = 0;
   st->gtol = gtol;
   st->max_iter = max_iter;
+  st->qsyl_valid = 0;
   st->lam[0] = lam0;
   st->lam[1] = lam1;
 }
@@ -1275,10 +1495,10 @@ int orth(Plan& p, double* B, int d, int c, double* part, double* small, cudaStre
   a.d[0] = d;
   a.ca = c;
   a.cb = c;
-  a.nblk = ceil_div(d, 64);
+  a.nblk = ceil_div(d, kThinRows);
   a.part = part;
   a.done = nullptr;
-  size_t smem = sizeof(double) * 64 * 2 * c;
+  size_t smem = sizeof(double) * kThinRows * 2 * c;
   GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
   GB_CHECK_LAUNCH();
@@ -1311,15 +1531,15 @@ int warm_start(Plan& p, cudaStream_t st) {
     const int iters = 12;
     for (int it = 0; it <= iters; ++it) {
       // U = orth(R_x^{-T} Cxy R_y^{-1} V)
-      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, Vb, c, y.wsT, c, c, st));
-      GB_TRY(mat_thin<double>(Cxy, dx, dy, false, false, y.wsT, c, x.wsT, c, c, st));
-      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, true, true, x.wsT, c, Ub, c, c, st));
+      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, Vb, c, y.wsT, c, c, p.mt_part, st));
+      GB_TRY(mat_thin<double>(Cxy, dx, dy, false, false, y.wsT, c, x.wsT, c, c, p.mt_part, st));
+      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, true, true, x.wsT, c, Ub, c, c, p.mt_part, st));
       if (it == iters) break;  // Ub = C V (unnormalized) for the Rayleigh-Ritz step
       GB_TRY(orth(p, Ub, dx, c, part, small, st));
       // V = orth(R_y^{-T} Cxy^T R_x^{-1} U)
-      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, Ub, c, x.wsT, c, c, st));
-      GB_TRY(mat_thin<double>(Cxy, dx, dy, true, false, x.wsT, c, y.wsT, c, c, st));
-      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, true, true, y.wsT, c, Vb, c, c, st));
+      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, Ub, c, x.wsT, c, c, p.mt_part, st));
+      GB_TRY(mat_thin<double>(Cxy, dx, dy, true, false, x.wsT, c, y.wsT, c, c, p.mt_part, st));
+      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, true, true, y.wsT, c, Vb, c, c, p.mt_part, st));
       GB_TRY(orth(p, Vb, dy, c, part, small, st));
     }
     // Ub = C V: take U0 = orth(Ub) and Bm = U0^T (C V)
@@ -1334,9 +1554,9 @@ int warm_start(Plan& p, cudaStream_t st) {
       a.d[0] = dx;
       a.ca = c;
       a.cb = c;
-      a.nblk = ceil_div(dx, 64);
+      a.nblk = ceil_div(dx, kThinRows);
       a.part = part;
-      size_t smem = sizeof(double) * 64 * 2 * c;
+      size_t smem = sizeof(double) * kThinRows * 2 * c;
       GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
       GB_CHECK_LAUNCH();
@@ -1351,8 +1571,8 @@ int warm_start(Plan& p, cudaStream_t st) {
       GB_CHECK_LAUNCH();
       thin_apply_kernel<<<ceil_div(dy, 128), 128, 0, st>>>(Vb, dy, c, rotV, k, y.wsT);
       GB_CHECK_LAUNCH();
-      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, x.wsT, k, x.warm, k, k, st));
-      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, y.wsT, k, y.warm, k, k, st));
+      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, x.wsT, k, x.warm, k, k, p.mt_part, st));
+      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, y.wsT, k, y.warm, k, k, p.mt_part, st));
     }
     return GBCCA_OK;
   }
@@ -1365,7 +1585,7 @@ int warm_start(Plan& p, cudaStream_t st) {
   (void)YhT;
   transpose_kernel<<<ceil_div(l * d, 256), 256, 0, st>>>(p.Yhat, l, d, YT);
   GB_CHECK_LAUNCH();
-  GB_TRY(mat_thin<double>(x.Rinv, d, d, true, true, YT, l, Gt, l, l, st));
+  GB_TRY(mat_thin<double>(x.Rinv, d, d, true, true, YT, l, Gt, l, l, p.mt_part, st));
   {
     ThinArgs a{};
     a.A[0] = Gt;
@@ -1375,9 +1595,9 @@ int warm_start(Plan& p, cudaStream_t st) {
     a.d[0] = d;
     a.ca = l;
     a.cb = l;
-    a.nblk = ceil_div(d, 64);
+    a.nblk = ceil_div(d, kThinRows);
     a.part = p.crosspart;
-    size_t smem = sizeof(double) * 64 * 2 * l;
+    size_t smem = sizeof(double) * kThinRows * 2 * l;
     GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
     GB_CHECK_LAUNCH();
@@ -1389,7 +1609,7 @@ int warm_start(Plan& p, cudaStream_t st) {
     double* Wwh = p.ws + 2 * (int64_t)d * l;  // d x k
     thin_apply_kernel<<<ceil_div(d, 128), 128, 0, st>>>(Gt, d, l, rot, k, Wwh);
     GB_CHECK_LAUNCH();
-    GB_TRY(mat_thin<double>(x.Rinv, d, d, false, true, Wwh, k, x.warm, k, k, st));
+    GB_TRY(mat_thin<double>(x.Rinv, d, d, false, true, Wwh, k, x.warm, k, k, p.mt_part, st));
   }
   return GBCCA_OK;
 }

@@ -1,0 +1,68 @@
+"""Full-size workloads through the C ABI, checked against the FP64 oracle.
+
+The tall CCA workload runs with the benchmark's exact settings (SRHT s=4096,
+gtol from bench.py): canonical correlations within 1e-6 relative and the
+relative objective suboptimality below 1e-6.  The LDA workload (n=100000,
+d=784, 10 classes, FP32): generalized eigenvalues within 1e-6.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import to_dev, np64, rel
+from oracle.cca import cca_qr, default_mu
+from oracle import lda as OL
+from synth import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2106_12060_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+@pytest.fixture(scope="module")
+def tall():
+    P = make_workload("cca_tall_bf16")
+    c = P["config"]
+    ref, _, _ = cca_qr(P["X64"], P["Y64"], c["lam"], c["lam"], c["k"])
+    return P, ref
+
+
+@pytest.mark.parametrize("refine", [1, 2])
+def test_tall_cca_bench_settings(gb, tall, refine):
+    """refine = 1: FP64 Rayleigh-Ritz Grams; refine = 2 (bench.REFINE): from
+    the tensor-core pass."""
+    import bench
+    P, ref = tall
+    c = P["config"]
+    o = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=bench.GTOL,
+                           refine=refine)
+    plan = gb.cca_plan(c["n"], c["dx"], c["dy"], c["k"], c["dtype"], o)
+    X, Y = to_dev(P["X"], c["dtype"]), to_dev(P["Y"], c["dtype"])
+    gb.cca_precondition(plan, X, Y, c["lam"], c["lam"])
+    sig, U, V, info = gb.cca_solve(plan)
+    s = np64(sig)
+    mu = default_mu(c["k"])
+    subopt = abs(np.dot(ref, mu) - np.dot(s, mu)) / np.dot(ref, mu)
+    assert subopt < 1e-6, (subopt, info)
+    assert rel(s, ref) < 1e-6, (s, ref, info)
+
+
+def test_lda_workload(gb):
+    import torch
+    P = make_workload("lda_f32")
+    c = P["config"]
+    lam = 1e-6 * float(np.trace(OL.scatters(P["X64"], P["y"], c["l"])[1])) / c["d"]
+    o = gb.default_options(s=c["s"], max_iter=1000, gtol=1e-6)
+    plan = gb.lda_plan(c["n"], c["d"], c["l"], c["k"], c["dtype"], o)
+    X = to_dev(P["X"], c["dtype"])
+    y = torch.from_numpy(P["y"]).cuda()
+    rho, W, info = gb.lda_solve(plan, X, y, lam)
+    ref, _ = OL.lda_geneig(P["X64"], P["y"], c["l"], lam, c["k"])
+    assert rel(np64(rho), ref) < 1e-6, (np64(rho), ref, info)
