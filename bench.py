@@ -318,6 +318,33 @@ def run_pass_only(args):
     plan.close()
 
 
+def run_solve_only(args):
+    """Full solves (bench settings) on the first `--solve-rows ROWS` rows of
+    the workload, for profiler captures of the per-iteration kernels (prints
+    nothing that counts as a bench value)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2106_12060_gb300 as gb
+    from synth import make_workload
+    torch.cuda.set_device(0)
+    P = make_workload(WORKLOAD, n=args.solve_rows)
+    c = P["config"]
+    n, dx, dy, k, dt = c["n"], c["dx"], c["dy"], c["k"], c["dtype"]
+    to = (lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).view(torch.bfloat16).cuda()) \
+        if dt == "bf16" else (lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda())
+    X, Y = to(P["X"]), to(P["Y"])
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
+                             check_every=8, refine=REFINE)
+    plan = gb.cca_plan(n, dx, dy, k, dt, opt)
+    for _ in range(args.steps):
+        gb.cca_precondition(plan, X, Y, LAM, LAM)
+        info = gb.cca_solve(plan)[3]
+    torch.cuda.synchronize()
+    print(f"solve-only: {args.steps} solves over {n} rows, {info['iters']} iterations")
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,9 +353,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pass-only", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--solve-rows", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.pass_only:
         run_pass_only(args)
+        return
+    if args.solve_rows:
+        run_solve_only(args)
         return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":

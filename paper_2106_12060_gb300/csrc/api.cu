@@ -281,11 +281,13 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
   }
   for (int v = 0; v < p.nviews; ++v) {
     View& w = p.v[v];
-    GB_TRY(gram_tn(w.SZ, w.d, w.SZ, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st));
+    GB_TRY(gram_tn(w.SZ, w.d, w.SZ, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st,
+                   p.dtype != GBCCA_FP64));
     GB_TRY(cholesky_upper(w.R, w.d, p.flag, st));
-    GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, st));
+    GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, p.ws, p.ws_len, st));
   }
   GB_TRY(read_flag(p, st));
+  for (int v = 0; v < p.nviews; ++v) GB_TRY(to_f32(p.v[v].Rinv, p.v[v].Rinv32, (int64_t)p.v[v].d * p.v[v].d, st));
   if (p.opt.warm_start) {
     GB_TRY(warm_start(p, st));
     GB_TRY(read_flag(p, st));
@@ -297,6 +299,7 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
       GB_CHECK_LAUNCH();
       identity_kernel<<<ceil_div(d * d, 256), 256, 0, st>>>(p.v[v].Rinv, d);
       GB_CHECK_LAUNCH();
+      GB_TRY(to_f32(p.v[v].Rinv, p.v[v].Rinv32, (int64_t)d * d, st));
     }
   } else if (p.opt.sketch == GBCCA_SKETCH_EXACT) {
     if (p.dtype != GBCCA_FP64 || p.kind != kCCA) {
@@ -308,11 +311,11 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
       GB_TRY(gram_tn((const double*)w.Z, w.ld, (const double*)w.Z, w.ld, p.n, w.d, w.d, w.R, w.lam, p.ws,
                      p.ws_len, st));
       GB_TRY(cholesky_upper(w.R, w.d, p.flag, st));
-      GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, st));
+      GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, p.ws, p.ws_len, st));
+      GB_TRY(to_f32(w.Rinv, w.Rinv32, (int64_t)w.d * w.d, st));
     }
     GB_TRY(read_flag(p, st));
   }
-  for (int v = 0; v < p.nviews; ++v) GB_TRY(to_f32(p.v[v].Rinv, p.v[v].Rinv32, (int64_t)p.v[v].d * p.v[v].d, st));
   p.preconditioned = true;
   return GBCCA_OK;
 }

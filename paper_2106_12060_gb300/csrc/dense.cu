@@ -67,8 +67,71 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int nparts, in
   }
 }
 
+// Gram in double-float arithmetic (each FP64 input split into an FP32 pair
+// hi + lo; products hi*hi formed exactly as an FP32 pair with fma, the cross
+// terms hi*lo + lo*hi added to the compensation; sums kept as FP32 pairs with
+// TwoSum).  About 2^-44 relative accuracy per term at FP32 instruction rates:
+// GB300 executes FP64 at ~1/60 of its FP32 rate.
+__device__ __forceinline__ void df_acc(float& S, float& Cc, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  const float t = S + p;
+  const float bp = t - S;
+  const float err = (S - (t - bp)) + (p - bp);
+  S = t;
+  Cc += err + e + fmaf(ah, bl, al * bh);
+}
+
+template <typename Tout>
+__global__ void __launch_bounds__(256)
+gram_df_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t m,
+               int d1, int d2, int64_t kchunk, Tout* __restrict__ part) {
+  __shared__ float Ah[kGK][kGT], Al[kGK][kGT], Bh[kGK][kGT], Bl[kGK][kGT];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  const int64_t k0 = blockIdx.z * kchunk, k1 = min(m, k0 + kchunk);
+  float S[4][4] = {}, Cc[4][4] = {};
+  for (int64_t kk = k0; kk < k1; kk += kGK) {
+    for (int e = tid; e < kGK * kGT; e += 256) {
+      int r = e / kGT, c = e % kGT;
+      int64_t row = kk + r;
+      double a = (row < k1 && i0 + c < d1) ? A[row * lda + i0 + c] : 0.0;
+      double b = (row < k1 && j0 + c < d2) ? B[row * ldb + j0 + c] : 0.0;
+      float ah = (float)a, bh = (float)b;
+      Ah[r][c] = ah;
+      Al[r][c] = (float)(a - (double)ah);
+      Bh[r][c] = bh;
+      Bl[r][c] = (float)(b - (double)bh);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kGK; ++r) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ah[u] = Ah[r][ty + 16 * u];
+        al[u] = Al[r][ty + 16 * u];
+        bh[u] = Bh[r][tx + 16 * u];
+        bl[u] = Bl[r][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) df_acc(S[u][w], Cc[u][w], ah[u], al[u], bh[w], bl[w]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      int i = i0 + ty + 16 * u, j = j0 + tx + 16 * w;
+      if (i < d1 && j < d2) part[((int64_t)blockIdx.z * d1 + i) * d2 + j] = (Tout)((double)S[u][w] + (double)Cc[u][w]);
+    }
+}
+
 int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1, int d2, double* C,
-            double diag_add, double* ws, int64_t ws_len, cudaStream_t st) {
+            double diag_add, double* ws, int64_t ws_len, cudaStream_t st, bool df) {
   int tiles = ceil_div(d1, kGT) * ceil_div(d2, kGT);
   int ks = std::max(1, std::min<int>(ceil_div(304, tiles), ceil_div(m, 64)));
   int64_t len = (int64_t)d1 * d2;
@@ -79,7 +142,10 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
   }
   int64_t kchunk = (m + ks - 1) / ks;
   dim3 grid(ceil_div(d2, kGT), ceil_div(d1, kGT), ks);
-  gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
+  if (df)
+    gram_df_kernel<double><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
+  else
+    gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
   GB_CHECK_LAUNCH();
   sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
   GB_CHECK_LAUNCH();
@@ -95,39 +161,53 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
 constexpr int kNB = 32;
 
 __global__ void chol_diag_kernel(double* A, int d, int p, int* flag) {
-  __shared__ double a[kNB][kNB + 1];
+  // lane i holds row i of the 32 x 32 diagonal block in registers; the
+  // column j multipliers come from lane j by shuffles
   const int lane = threadIdx.x;
   const int o = p * kNB, nb = min(kNB, d - o);
-  for (int c = 0; c < nb; ++c) a[lane][c] = lane < nb ? A[(int64_t)(o + lane) * d + o + c] : 0.0;
-  __syncwarp();
-  for (int j = 0; j < nb; ++j) {
-    double piv = a[j][j];
-    if (piv <= 0.0 || !(piv == piv)) {
-      if (lane == 0) atomicExch(flag, 1);
-      piv = 1.0;  // keep going with a harmless value; the result is discarded
+  double row[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) row[c] = (lane < nb && c < nb) ? A[(int64_t)(o + lane) * d + o + c] : 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < kNB; ++j) {
+    if (j < nb) {
+      double piv = __shfl_sync(0xffffffffu, row[j], j);
+      if (!(piv > 0.0)) {
+        bad = true;
+        piv = 1.0;  // keep going with a harmless value; the result is discarded
+      }
+      const double ljj = sqrt(piv);
+      const double rj = 1.0 / ljj;
+      if (lane == j) row[j] = ljj;
+      if (lane > j) row[j] *= rj;
+      const double lij = row[j];
+#pragma unroll
+      for (int c = j + 1; c < kNB; ++c) {
+        const double lcj = __shfl_sync(0xffffffffu, row[j], c);  // L[c][j] from lane c
+        if (lane >= c) row[c] -= lij * lcj;
+      }
     }
-    double ljj = sqrt(piv);
-    __syncwarp();
-    if (lane == j) a[j][j] = ljj;
-    if (lane > j && lane < nb) a[lane][j] /= ljj;
-    __syncwarp();
-    if (lane > j && lane < nb)
-      for (int c = j + 1; c <= lane; ++c) a[lane][c] -= a[lane][j] * a[c][j];
-    __syncwarp();
   }
+  if (bad && lane == 0) atomicExch(flag, 1);
   if (lane < nb)
-    for (int c = 0; c <= lane; ++c) A[(int64_t)(o + lane) * d + o + c] = a[lane][c];
+#pragma unroll
+    for (int c = 0; c < kNB; ++c)
+      if (c <= lane && c < nb) A[(int64_t)(o + lane) * d + o + c] = row[c];
 }
 
 // A[i-block, p] <- A[i-block, p] L_pp^{-T}: each thread solves one row by
 // forward substitution with L_pp.
 __global__ void chol_trsm_kernel(double* A, int d, int p) {
   __shared__ double L[kNB][kNB + 1];
+  __shared__ double rinv[kNB];
   const int o = p * kNB, nb = min(kNB, d - o);
   for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
     int r = e / kNB, c = e % kNB;
     L[r][c] = (r < nb && c <= r) ? A[(int64_t)(o + r) * d + o + c] : 0.0;
   }
+  __syncthreads();
+  if (threadIdx.x < kNB) rinv[threadIdx.x] = threadIdx.x < nb ? 1.0 / L[threadIdx.x][threadIdx.x] : 1.0;
   __syncthreads();
   const int row = o + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= d) return;
@@ -140,7 +220,7 @@ __global__ void chol_trsm_kernel(double* A, int d, int p) {
       double s = x[c];
 #pragma unroll
       for (int q = 0; q < c; ++q) s -= L[c][q] * x[q];
-      x[c] = s / L[c][c];
+      x[c] = s * rinv[c];
     }
   }
 #pragma unroll
@@ -200,31 +280,117 @@ int cholesky_upper(double* A, int d, int* flag, cudaStream_t st) {
 }
 
 // ------------------------------------------------------- triangular inverse
-// Rinv = R^{-1} for upper-triangular R: column j solves R x = e_j by back
-// substitution; one warp per column, the inner products split over lanes.
-__global__ void tri_inv_kernel(const double* __restrict__ R, double* __restrict__ Rinv, int d) {
-  extern __shared__ double xs[];  // [8][d]
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 8 + w;
-  if (j >= d) return;
-  double* x = xs + (int64_t)w * d;
-  for (int i = lane; i < d; i += 32) x[i] = 0.0;
-  __syncwarp();
-  for (int i = j; i >= 0; --i) {
-    double s = 0;
-    for (int q = i + 1 + lane; q <= j; q += 32) s += R[(int64_t)i * d + q] * x[q];
-    s = warp_sum(s);
-    if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) / R[(int64_t)i * d + i];
-    __syncwarp();
+// Rinv = R^{-1} for upper-triangular R by recursive doubling over aligned
+// diagonal blocks: the 32 x 32 diagonal blocks are inverted by back
+// substitution, then at each level h = 32, 64, ... the inverted neighbours
+// A = [r0, r0+h) and C = [c0, c1) (c0 = r0 + h) are joined through
+//   Rinv[A, C] = -Rinv[A, A] (R[A, C] Rinv[C, C]),
+// two FP64 products per level.  Every level is one parallel launch pair, so
+// the d^3/3 multiply-adds spread over all SMs.
+constexpr int kTB = 32;
+
+__global__ void tri_diag_inv_kernel(const double* __restrict__ R, double* __restrict__ Rinv, int d) {
+  __shared__ double L[kTB][kTB + 1];
+  __shared__ double X[kTB][kTB + 1];
+  __shared__ double rinv[kTB];
+  const int o = blockIdx.x * kTB, nb = min(kTB, d - o), j = threadIdx.x;
+  for (int r = 0; r < kTB; ++r) L[r][j] = (r < nb && j < nb && j >= r) ? R[(int64_t)(o + r) * d + o + j] : 0.0;
+  __syncthreads();
+  rinv[j] = j < nb ? 1.0 / L[j][j] : 0.0;
+  __syncthreads();
+  for (int i = kTB - 1; i >= 0; --i) {
+    double x = 0.0;
+    if (i <= j && j < nb) {
+      double s = 0.0;
+      for (int q = i + 1; q <= j; ++q) s += L[i][q] * X[q][j];
+      x = ((i == j) ? 1.0 : 0.0) - s;
+      x *= rinv[i];
+    }
+    X[i][j] = x;  // each thread owns column j: no barrier needed
   }
-  for (int i = lane; i < d; i += 32) Rinv[(int64_t)i * d + j] = x[i];
+  for (int r = 0; r < nb; ++r)
+    if (j < nb) Rinv[(int64_t)(o + r) * d + o + j] = X[r][j];
 }
 
-int tri_inverse_upper(const double* R, double* Rinv, int d, cudaStream_t st) {
-  size_t smem = sizeof(double) * 8 * d;
-  GB_CUDA(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  tri_inv_kernel<<<ceil_div(d, 8), 256, smem, st>>>(R, Rinv, d);
+// stage 0: T_p = R[A, C] Rinv[C, C]  (h x w, row stride h)
+// stage 1: Rinv[A, C] = -Rinv[A, A] T_p
+// Grid (ceil(h/32), ceil(h/32), pairs); each CTA one 32 x 32 output tile,
+// K in chunks of 32 restricted to where the triangular factor is non-zero.
+template <int kStage>
+__global__ void __launch_bounds__(256) tri_level_kernel(const double* __restrict__ R, double* __restrict__ Rinv,
+                                                        double* __restrict__ T, int d, int h) {
+  __shared__ double As[kTB][kTB + 1], Bs[kTB][kTB + 1];
+  const int p = blockIdx.z;
+  const int r0 = 2 * p * h, c0 = r0 + h;
+  if (c0 >= d) return;
+  const int w = min(d, c0 + h) - c0;
+  const int i0 = blockIdx.y * kTB, j0 = blockIdx.x * kTB;
+  if (i0 >= h || j0 >= w) return;
+  double* Tp = T + (int64_t)p * h * h;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // K range: stage 0 runs q in [0, w) with Rinv[C,C][q][j] = 0 for q > j;
+  // stage 1 runs q in [0, h) with Rinv[A,A][i][q] = 0 for q < i
+  const int klo = kStage == 0 ? 0 : i0;
+  const int khi = kStage == 0 ? min(w, j0 + kTB) : h;
+  double acc[2][2] = {};
+  for (int k0 = klo; k0 < khi; k0 += kTB) {
+    for (int e = threadIdx.x; e < kTB * kTB; e += 256) {
+      const int r = e / kTB, c = e % kTB;
+      const int ia = i0 + r, qa = k0 + c;  // A tile element (i, q)
+      const int qb = k0 + r, jb = j0 + c;  // B tile element (q, j)
+      double av = 0.0, bv = 0.0;
+      if (kStage == 0) {
+        if (ia < h && qa < khi) av = R[(int64_t)(r0 + ia) * d + c0 + qa];
+        if (qb < khi && jb < w) bv = Rinv[(int64_t)(c0 + qb) * d + c0 + jb];
+      } else {
+        if (ia < h && qa < khi) av = Rinv[(int64_t)(r0 + ia) * d + r0 + qa];
+        if (qb < khi && jb < w) bv = Tp[(int64_t)qb * h + jb];
+      }
+      As[r][c] = av;
+      Bs[r][c] = bv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < kTB; ++q) {
+      const double a0 = As[ty][q], a1 = As[ty + 16][q];
+      const double b0 = Bs[q][tx], b1 = Bs[q][tx + 16];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < h && j < w) {
+        if (kStage == 0)
+          Tp[(int64_t)i * h + j] = acc[u][v];
+        else
+          Rinv[(int64_t)(r0 + i) * d + c0 + j] = -acc[u][v];
+      }
+    }
+}
+
+int tri_inverse_upper(const double* R, double* Rinv, int d, double* ws, int64_t ws_len, cudaStream_t st) {
+  if (ws_len < (int64_t)d * d) {
+    set_last_error("tri_inverse_upper: workspace too small");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  GB_CUDA(cudaMemsetAsync(Rinv, 0, sizeof(double) * d * d, st));
+  tri_diag_inv_kernel<<<ceil_div(d, kTB), kTB, 0, st>>>(R, Rinv, d);
   GB_CHECK_LAUNCH();
+  for (int h = kTB; h < d; h *= 2) {
+    const int pairs = ceil_div(d - h, 2 * h);
+    dim3 grid(ceil_div(h, kTB), ceil_div(h, kTB), pairs);
+    tri_level_kernel<0><<<grid, 256, 0, st>>>(R, Rinv, ws, d, h);
+    GB_CHECK_LAUNCH();
+    tri_level_kernel<1><<<grid, 256, 0, st>>>(R, Rinv, ws, d, h);
+    GB_CHECK_LAUNCH();
+  }
   return GBCCA_OK;
 }
 

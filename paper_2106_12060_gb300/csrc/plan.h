@@ -131,10 +131,15 @@ int countsketch_prepare(Plan& p, cudaStream_t st);
 int srht_apply(Plan& p, int view, cudaStream_t st);
 
 // dense.cu
+// C = A^T B + diag_add I over m rows.  df = true: double-float arithmetic
+// (~2^-44 relative per product instead of FP64's 2^-53) at FP32 rates, used
+// where the data itself is FP32/BF16 and C only shapes a preconditioner.
 int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1,
-            int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st);
+            int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
+            bool df = false);
 int cholesky_upper(double* A, int d, int* flag, cudaStream_t st);
-int tri_inverse_upper(const double* R, double* Rinv, int d, cudaStream_t st);
+// Rinv = R^{-1} (upper triangular, d x d); ws holds at least d * d doubles.
+int tri_inverse_upper(const double* R, double* Rinv, int d, double* ws, int64_t ws_len, cudaStream_t st);
 int to_f32(const double* a, float* b, int64_t len, cudaStream_t st);
 // C (m x c, ldc) = op(A) B (rows of B = columns of op(A), ldb); A is
 // ra x ca row-major; tri = 1 skips the zero half of an upper-triangular A.

@@ -1404,10 +1404,21 @@ __global__ void small_chol_kernel(const double* part, int nblk, int c, double* o
   __syncthreads();
   if (threadIdx.x < c) G[threadIdx.x * c + threadIdx.x] += 1e-14 * tr / c;
   __syncthreads();
-  if (!blk_chol(G, c)) {
-    if (threadIdx.x == 0) atomicExch(flag, 1);
+  if (c <= 32) {
+    // c <= 32: one warp factors G, pivots used through their reciprocals
+    if (threadIdx.x < 32) {
+      double* invd = Li + c * c;
+      const bool ok = warp_chol(G, c, invd);
+      if (!ok && threadIdx.x == 0) atomicExch(flag, 1);
+      warp_lower_inv(G, invd, Li, c);
+    }
+    __syncthreads();
+  } else {
+    if (!blk_chol(G, c)) {
+      if (threadIdx.x == 0) atomicExch(flag, 1);
+    }
+    blk_lower_inv(G, Li, c);
   }
-  blk_lower_inv(G, Li, c);
   // R^{-1} = (L^{-1})^T
   for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
     int i = e / c, j = e % c;
@@ -1502,7 +1513,7 @@ int orth(Plan& p, double* B, int d, int c, double* part, double* small, cudaStre
   GB_CUDA(cudaFuncSetAttribute(thin_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   thin_gram_kernel<<<dim3(a.nblk, 1), 256, smem, st>>>(a);
   GB_CHECK_LAUNCH();
-  small_chol_kernel<<<1, 256, sizeof(double) * 2 * c * c, st>>>(part, a.nblk, c, small, p.flag);
+  small_chol_kernel<<<1, 256, sizeof(double) * (2 * c * c + c), st>>>(part, a.nblk, c, small, p.flag);
   GB_CHECK_LAUNCH();
   apply_small_kernel<<<ceil_div(d, 128), 128, 0, st>>>(B, d, c, small);
   GB_CHECK_LAUNCH();
@@ -1520,26 +1531,39 @@ int warm_start(Plan& p, cudaStream_t st) {
     const int c = std::min(2 * k, std::min(dx, dy));
     // Cxy = X_S^T Y_S (dx x dy), kept in ws after the Gram partials
     double* Cxy = p.ws + (p.ws_len - (int64_t)dx * dy);
-    GB_TRY(gram_tn(x.SZ, dx, y.SZ, dy, p.s, dx, dy, Cxy, 0.0, p.ws, p.ws_len - (int64_t)dx * dy, st));
+    GB_TRY(gram_tn(x.SZ, dx, y.SZ, dy, p.s, dx, dy, Cxy, 0.0, p.ws, p.ws_len - (int64_t)dx * dy, st,
+                   p.dtype != GBCCA_FP64));
     double* Vb = y.wsU;  // dy x c
     double* Ub = x.wsU;  // dx x c
     double* part = p.crosspart;
     double* small = p.phigram;
+    // the power iterations stay in FP64 for every storage type: with FP32
+    // copies of R^{-1} (kappa ~ 1e4) the start point is visibly worse and
+    // the solve needs more iterations than the FP64 products cost
+    auto rx = [&](bool tr, const double* B, double* C, int cc) {
+      return mat_thin<double>(x.Rinv, dx, dx, tr, true, B, cc, C, cc, cc, p.mt_part, st);
+    };
+    auto ry = [&](bool tr, const double* B, double* C, int cc) {
+      return mat_thin<double>(y.Rinv, dy, dy, tr, true, B, cc, C, cc, cc, p.mt_part, st);
+    };
+    auto cxy = [&](bool tr, const double* B, double* C) {
+      return mat_thin<double>(Cxy, dx, dy, tr, false, B, c, C, c, c, p.mt_part, st);
+    };
     rand_block_kernel<<<ceil_div(dy * c, 256), 256, 0, st>>>(Vb, dy, c, p.opt.seed);
     GB_CHECK_LAUNCH();
     GB_TRY(orth(p, Vb, dy, c, part, small, st));
     const int iters = 12;
     for (int it = 0; it <= iters; ++it) {
       // U = orth(R_x^{-T} Cxy R_y^{-1} V)
-      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, Vb, c, y.wsT, c, c, p.mt_part, st));
-      GB_TRY(mat_thin<double>(Cxy, dx, dy, false, false, y.wsT, c, x.wsT, c, c, p.mt_part, st));
-      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, true, true, x.wsT, c, Ub, c, c, p.mt_part, st));
+      GB_TRY(ry(false, Vb, y.wsT, c));
+      GB_TRY(cxy(false, y.wsT, x.wsT));
+      GB_TRY(rx(true, x.wsT, Ub, c));
       if (it == iters) break;  // Ub = C V (unnormalized) for the Rayleigh-Ritz step
       GB_TRY(orth(p, Ub, dx, c, part, small, st));
       // V = orth(R_y^{-T} Cxy^T R_x^{-1} U)
-      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, Ub, c, x.wsT, c, c, p.mt_part, st));
-      GB_TRY(mat_thin<double>(Cxy, dx, dy, true, false, x.wsT, c, y.wsT, c, c, p.mt_part, st));
-      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, true, true, y.wsT, c, Vb, c, c, p.mt_part, st));
+      GB_TRY(rx(false, Ub, x.wsT, c));
+      GB_TRY(cxy(true, x.wsT, y.wsT));
+      GB_TRY(ry(true, y.wsT, Vb, c));
       GB_TRY(orth(p, Vb, dy, c, part, small, st));
     }
     // Ub = C V: take U0 = orth(Ub) and Bm = U0^T (C V)
@@ -1571,8 +1595,8 @@ int warm_start(Plan& p, cudaStream_t st) {
       GB_CHECK_LAUNCH();
       thin_apply_kernel<<<ceil_div(dy, 128), 128, 0, st>>>(Vb, dy, c, rotV, k, y.wsT);
       GB_CHECK_LAUNCH();
-      GB_TRY(mat_thin<double>(x.Rinv, dx, dx, false, true, x.wsT, k, x.warm, k, k, p.mt_part, st));
-      GB_TRY(mat_thin<double>(y.Rinv, dy, dy, false, true, y.wsT, k, y.warm, k, k, p.mt_part, st));
+      GB_TRY(rx(false, x.wsT, x.warm, k));
+      GB_TRY(ry(false, y.wsT, y.warm, k));
     }
     return GBCCA_OK;
   }
