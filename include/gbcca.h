@@ -210,6 +210,30 @@ int gbcca_query(gbcca_plan_t plan, int32_t what, double* dst, void* stream);
 int gbcca_sketch_draws(int32_t kind, int64_t n, int64_t s, uint64_t seed, int32_t* h,
                        int8_t* g, void* stream);
 
+/* Allocation-free Gram of a sketch: C = A^T A + lambda I, the matrix whose
+ * Cholesky factor is the preconditioner R of Sec. 3 (A = S Z, e.g. read back
+ * with GBCCA_Q_SKETCH_X).  The paper has no counterpart for the
+ * allocation-free form; it exists for callers that may not allocate device
+ * memory during a call: processes that reserve HBM in their own pool up front,
+ * and callers that cannot accept the device-wide synchronization cudaMalloc /
+ * cudaFree may cause.
+ *   A       device, row-major m x d FP64, row stride lda >= d (elements)
+ *   C       device, d x d FP64 row-major output (caller-owned)
+ *   lambda  >= 0, added to the diagonal
+ * Arithmetic: FP64 split-K partial sums over row chunks, added in a fixed
+ * order (deterministic).  Memory: the partials live in a static 8 MiB device
+ * array of the library (no allocation, nothing needs zeroing), so
+ * d <= gbcca_sketch_gram_noalloc_max_d() (724); larger d returns
+ * GBCCA_ERR_INVALID_ARG without device work.  The first call on a device
+ * looks up the array's address; make it before recording a stream capture.
+ * The array is shared by all callers on a device: calls that may run at the
+ * same time (different streams, unordered threads) race and must be
+ * ordered by the caller.  Work is ordered on `stream`; returns GBCCA_OK,
+ * GBCCA_ERR_INVALID_ARG or GBCCA_ERR_CUDA. */
+int gbcca_sketch_gram_noalloc(const double* A, int64_t lda, int64_t m, int32_t d, double lambda, double* C,
+                              void* stream);
+int32_t gbcca_sketch_gram_noalloc_max_d(void);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * plans and threads); a host-side counter for profiling. */
 int64_t gbcca_launch_count(void);

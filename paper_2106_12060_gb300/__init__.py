@@ -199,6 +199,32 @@ def gbcca_sketch_draws(kind, n, s, seed, stream=None):
 sketch_draws = gbcca_sketch_draws
 
 
+def gbcca_sketch_gram_noalloc(A, lam, C, stream=None):
+    """C = A^T A + lam I without any device allocation by the library (the
+    split-K partials use its static scratch).  A: CUDA float64 (m, d) with
+    unit column stride; C: caller-provided CUDA float64 (d, d), contiguous."""
+    lib = _lib.load()
+    if A.dim() != 2 or A.stride(1) != 1 or C.dim() != 2 or not C.is_contiguous():
+        raise ValueError("A must be (m, d) with unit column stride and C a contiguous (d, d) tensor")
+    m, d = A.shape
+    if tuple(C.shape) != (d, d):
+        raise ValueError("C must be (d, d)")
+    _lib.check(lib.gbcca_sketch_gram_noalloc(_ptr(A), A.stride(0), m, d, float(lam), _ptr(C), _stream(stream)),
+               "gbcca_sketch_gram_noalloc")
+    return C
+
+
+sketch_gram_noalloc = gbcca_sketch_gram_noalloc
+
+
+def gbcca_sketch_gram_noalloc_max_d() -> int:
+    """Largest d the allocation-free Gram accepts."""
+    return int(_lib.load().gbcca_sketch_gram_noalloc_max_d())
+
+
+sketch_gram_noalloc_max_d = gbcca_sketch_gram_noalloc_max_d
+
+
 def gbcca_launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(_lib.load().gbcca_launch_count())

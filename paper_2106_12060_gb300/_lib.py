@@ -66,6 +66,9 @@ SIGNATURES = {
     "gbcca_query": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "gbcca_sketch_draws": (C.c_int, [C.c_int32, C.c_int64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p,
                                      C.c_void_p]),
+    "gbcca_sketch_gram_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
+                                            C.c_void_p]),
+    "gbcca_sketch_gram_noalloc_max_d": (C.c_int32, []),
     "gbcca_launch_count": (C.c_int64, []),
     "gbcca_plan_destroy": (None, [C.c_void_p]),
     "gbcca_status_string": (C.c_char_p, [C.c_int]),

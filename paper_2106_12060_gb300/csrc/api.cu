@@ -515,6 +515,17 @@ int gbcca_sketch_draws(int32_t kind, int64_t n, int64_t s, uint64_t seed, int32_
   return sketch_draws(kind, n, s, seed, h, g, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int gbcca_sketch_gram_noalloc(const double* A, int64_t lda, int64_t m, int32_t d, double lambda, double* C,
+                              void* stream) {
+  if (A == nullptr || C == nullptr || m < 1 || d < 1 || lda < d || !(lambda >= 0.0)) {
+    set_last_error("gbcca_sketch_gram_noalloc: bad pointer, size or lambda");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  return gram_noalloc(A, lda, m, d, lambda, C, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int32_t gbcca_sketch_gram_noalloc_max_d(void) { return noalloc_max_d(); }
+
 int64_t gbcca_launch_count(void) { return (int64_t)g_launches.load(); }
 
 void gbcca_plan_destroy(gbcca_plan_t plan) { free_plan(as_plan(plan)); }

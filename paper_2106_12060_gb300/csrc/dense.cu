@@ -6,6 +6,9 @@
 // GB300 executes FP64 at ~1/60 of its FP32 rate, so these kernels spread the
 // O(s d^2) and O(d^3) work over many CTAs (split-K Gram, blocked right-looking
 // Cholesky, one warp per column of R^{-1}).
+#include <mutex>
+#include <string>
+
 #include "plan.h"
 
 namespace gbcca {
@@ -148,6 +151,82 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
     gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
   GB_CHECK_LAUNCH();
   sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+// ------------------------------------------------- allocation-free Gram
+// The same split-K Gram as gram_tn (FP64 gram_tn_kernel + sum_parts_kernel),
+// with its partial slabs in a fixed static device array instead of plan
+// memory.  It serves callers that may not allocate device memory at all: a
+// process that has reserved HBM up front in its own pool and budgets every
+// byte, or one that cannot accept the device-wide synchronization that
+// cudaMalloc / cudaFree may impose on all of its streams.
+//
+// Limit: the scratch holds kNoAllocScratch doubles (8 MiB).  A call needs at
+// least two d x d partial slabs, so d <= 724; larger d is rejected with
+// GBCCA_ERR_INVALID_ARG before any device work.  Nothing in the scratch has
+// to start at zero: every element of a slab that the second kernel reads is
+// written by the first.  The scratch is one buffer per device shared by all
+// callers, so two calls whose kernels may overlap in time (different streams,
+// or threads without ordering) race on it; callers order them.
+constexpr int64_t kNoAllocScratch = int64_t(1) << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch for the current device, looked up once per
+// device.  The first call on a device resolves the symbol (which can load the
+// module), so a caller that records work into a stream capture makes one
+// call on that device before capturing.
+int noalloc_scratch(double** out) {
+  int dev = -1;
+  GB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_last_error("allocation-free Gram: device ordinal out of range");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_last_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+      return GBCCA_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return GBCCA_OK;
+}
+}  // namespace
+
+int noalloc_max_d() {
+  int d = 1;
+  while (2 * (int64_t)(d + 1) * (d + 1) <= kNoAllocScratch) ++d;
+  return d;
+}
+
+int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, double* C, cudaStream_t st) {
+  const int64_t len = (int64_t)d * d;
+  if (2 * len > kNoAllocScratch) {
+    set_last_error("allocation-free Gram: d = " + std::to_string(d) + " exceeds the " +
+                   std::to_string(noalloc_max_d()) + " columns its 8 MiB static scratch holds");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  double* ws = nullptr;
+  GB_TRY(noalloc_scratch(&ws));
+  const int tiles = ceil_div(d, kGT) * ceil_div(d, kGT);
+  int ks = std::max(2, std::min<int>(ceil_div(304, tiles), ceil_div(m, 64)));
+  while (ks > 2 && (int64_t)ks * len > kNoAllocScratch) --ks;
+  const int64_t kchunk = (m + ks - 1) / ks;
+  dim3 grid(ceil_div(d, kGT), ceil_div(d, kGT), ks);
+  gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, A, lda, m, d, d, kchunk, ws);
+  GB_CHECK_LAUNCH();
+  sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d, d, lambda, C);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -138,6 +138,10 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
             int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
             bool df = false);
 int cholesky_upper(double* A, int d, int* flag, cudaStream_t st);
+// C = A^T A + lambda I (A: m x d FP64, row stride lda) with the split-K
+// partials in a static device scratch instead of plan memory; d <= noalloc_max_d().
+int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, double* C, cudaStream_t st);
+int noalloc_max_d();
 // Rinv = R^{-1} (upper triangular, d x d); ws holds at least d * d doubles.
 int tri_inverse_upper(const double* R, double* Rinv, int d, double* ws, int64_t ws_len, cudaStream_t st);
 int to_f32(const double* a, float* b, int64_t len, cudaStream_t st);
