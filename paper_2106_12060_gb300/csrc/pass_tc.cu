@@ -7,23 +7,29 @@
 //     G = Z^T W  (D x 4k)
 // and W^T W, which equals Phi^T G and is formed afterwards in FP64 from G.
 //
-// Persistent kernel, one CTA per SM, 128-row tiles.  Per tile and per pair of
-// 64-column boxes (128 columns of one view):
-//   phase 1: TMA loads the 128 x 128 BF16 block (two 128B-swizzled boxes) and
-//            tcgen05.mma accumulates W_view (128 x 48 in TMEM; K-major A = the
-//            block, B = Phi split into bf16 hi|lo columns);
-//   epilogue warps read W from TMEM, add the hi and lo halves, split W into
-//            bf16 hi/lo and write it to shared memory as the B operand of
-//   phase 2: the same blocks (re-read through L2) serve as the MN-major A
-//            operand Z^T of G_pair += Z^T (W_hi + W_lo), accumulated in TMEM
-//            (8 pairs x 48 columns) over all tiles of the CTA.
-// At the end the epilogue warps drain G to a per-CTA FP32 partial; a second
-// kernel sums the partials in fixed order in FP64.
+// Persistent kernel of 2-CTA clusters; both CTAs of a cluster work on the
+// same 128-row tile, CTA v on view v (X or Y), so that each CTA holds its
+// whole 128 x d_v BF16 block (<= 128 KB) in shared memory and every byte of
+// the data is read from HBM exactly once.  Per tile:
+//   GEMM 1  (tcgen05, per CTA): W_v = Z_v Phi_v, 128 x 48 FP32 in TMEM (B =
+//           Phi_v split into bf16 hi|lo columns, 24 each);
+//   epilogue warps read W_v from TMEM, add the hi and lo halves, split W_v
+//           into bf16 hi/lo and write it into the K-major B operand of GEMM 2
+//           (N rows 24 v .. 24 v + 23) of their own CTA, then push that half
+//           into the peer CTA's operand with a bulk shared::cluster copy;
+//   GEMM 2  (tcgen05, per CTA): G_v += Z_v^T [W_x | W_y] over the same shared
+//           memory blocks read as MN-major A (128 columns of Z_v per MMA),
+//           accumulated in TMEM over all tiles of the cluster.
+// The end of GEMM 2 is signalled to both CTAs (multicast commit), which
+// frees both W operands for the next tile.  At the end the epilogue warps
+// drain G to a per-cluster FP32 partial; a second kernel sums the partials in
+// fixed order.
 //
-// Roles: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer, warp 2 =
-// TMEM allocator, warps 4-7 = epilogue (TMEM lane quarters 0-3).  Every
-// mbarrier wait is bounded in time; on expiry the CTA records an error code,
-// waits (bounded) for its own copies and MMAs, frees TMEM and returns.
+// Roles per CTA: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
+// warp 2 = TMEM allocator, warps 4-7 = epilogue (TMEM lane quarters 0-3).
+// Every mbarrier wait is bounded in time; on expiry the CTA records an error
+// code, waits (bounded) for its own copies and MMAs, frees TMEM and leaves
+// after a cluster barrier (no remote access can target an exited CTA).
 #include <cuda.h>
 
 #include "plan.h"
@@ -32,24 +38,36 @@ namespace gbcca {
 
 namespace tc {
 
-constexpr int kRows = 128;            // rows per tile (MMA M for phase 1)
-constexpr int kNW = 48;               // N of both GEMMs (4k <= 48 real columns)
-constexpr int kHalf = 24;             // B rows of Phi: [hi of 2k cols | lo of 2k cols], 24 each
-constexpr int kStages = 3;            // ring of 32 KB pair slots
+constexpr int kRows = 128;            // rows per tile (MMA M of GEMM 1)
+constexpr int kNW = 48;               // N of both GEMMs
+constexpr int kHalf = 24;             // per view: B rows of Phi hi (0..23) / lo (24..47); W rows of a view
+constexpr int kStages = 4;            // ring of 32 KB pair slots (one 512-column view block)
 constexpr int kSlot = 32768;          // two 128 x 64 BF16 boxes
 constexpr int kBox = 16384;
 constexpr int kPhiView = 49152;       // per view: 8 K-boxes x 48 rows x 128 B
 constexpr int kKBox = 6144;           // 48 rows x 128 B
-constexpr int kWs = 12288;            // W operand: 2 K-boxes x 48 rows x 128 B
-constexpr int kPhiBytes = 2 * kPhiView;
-constexpr int kRingOff = kPhiBytes;
+constexpr int kWs = 12288;            // W operand (hi or lo): 2 K-boxes x 48 rows x 128 B
+constexpr int kWHalf = kHalf * 128;   // one view's rows of one K-box of the W operand
+constexpr int kRingOff = kPhiView;
 constexpr int kWsOff = kRingOff + kStages * kSlot;
 constexpr int kBarOff = kWsOff + 2 * kWs;
 constexpr int kSmemBytes = kBarOff + 256 + 1024;  // + alignment slack
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemCols = 256;   // W: 0..47, G: 48 + 48 p (p < 4 pairs)
 constexpr long long kTimeout = 2000000000ll;      // cycles (~1 s)
 
-enum Bar { kFull = 0, kEmpty = kStages, kD1Full = 2 * kStages, kD1Free, kWReady, kWFree, kGDone, kFinal, kNumBars };
+enum Bar {
+  kFull = 0,
+  kEmpty = kStages,
+  kD1Full = 2 * kStages,
+  kD1Free,
+  kEpiSync,
+  kWReady,
+  kWPeer,
+  kWFree,
+  kGDone,
+  kFinal,
+  kNumBars
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -130,6 +148,48 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// Commit that arrives on the barrier at the same shared-memory offset in every
+// CTA of `mask` (this cluster).
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(bar),
+               "h"(mask)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared-memory location in CTA `rank`
+__device__ __forceinline__ uint32_t map_peer(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Bulk copy of `bytes` from this CTA's shared memory to a shared::cluster
+// address; completion is counted on the destination CTA's barrier.
+__device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst),
+               "r"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -157,14 +217,14 @@ struct Args {
   int k2;        // columns of Phi per view (2k)
   int ntiles;
   const uint8_t* phi_img;  // [view][K-box][48][128 B], pre-swizzled
-  float* partG;            // [cta][D][4k]
+  float* partG;            // [cluster][D][4k]
   int* err;
   const int* done;
 };
 
 __global__ void __launch_bounds__(256, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, Args a) {
-  if (a.done != nullptr && *a.done) return;
+  if (a.done != nullptr && *a.done) return;  // uniform over the cluster: no remote access yet
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* phi_s = smem;
@@ -174,15 +234,17 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int npairs = a.pairs[0] + a.pairs[1];
+  const int view = (int)cluster_ctarank();   // 0: X, 1: Y
+  const uint32_t peer = 1u - (uint32_t)view;
+  const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
+  const int npairs = a.pairs[view];
   const int k4 = 2 * a.k2;
 
-  // Phi image -> shared memory (generic proxy), then make it visible to the
-  // tensor core (async proxy).
+  // own view's Phi image -> shared memory (generic proxy); zero W operand
   {
-    const uint4* src = reinterpret_cast<const uint4*>(a.phi_img);
+    const uint4* src = reinterpret_cast<const uint4*>(a.phi_img + view * kPhiView);
     uint4* dst = reinterpret_cast<uint4*>(phi_s);
-    for (int i = threadIdx.x; i < kPhiBytes / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < kPhiView / 16; i += blockDim.x) dst[i] = src[i];
     uint4* wz = reinterpret_cast<uint4*>(ws);
     for (int i = threadIdx.x; i < 2 * kWs / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
   }
@@ -193,8 +255,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     }
     mbar_init(smem_u32(&bars[kD1Full]), 1);
     mbar_init(smem_u32(&bars[kD1Free]), 128);
-    mbar_init(smem_u32(&bars[kWReady]), 128);
-    mbar_init(smem_u32(&bars[kWFree]), 1);
+    mbar_init(smem_u32(&bars[kEpiSync]), 128);
+    mbar_init(smem_u32(&bars[kWReady]), 1);
+    mbar_init(smem_u32(&bars[kWPeer]), 1);   // + the peer's bytes
+    mbar_init(smem_u32(&bars[kWFree]), 2);   // own and peer's end of GEMM 2
     mbar_init(smem_u32(&bars[kGDone]), 1);
     mbar_init(smem_u32(&bars[kFinal]), 1);
     *abort_flag = 0;
@@ -209,36 +273,32 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // both CTAs' barriers and W operands are initialised
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int my_tiles = (a.ntiles - cid + ncl - 1) / ncl;
+  const int nitems = my_tiles * npairs;
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
-    int it = 0;
     bool ok = true;
     int last_use[kStages];
     for (int s = 0; s < kStages; ++s) last_use[s] = -1;
-    for (int j = 0; j < my_tiles && ok; ++j) {
-      const int row0 = (blockIdx.x + j * gridDim.x) * kRows;
-      for (int phase = 0; phase < 2 && ok; ++phase) {
-        for (int p = 0; p < npairs && ok; ++p, ++it) {
-          const int slot = it % kStages, use = it / kStages;
-          if (!mbar_wait(smem_u32(&bars[kEmpty + slot]), (use & 1) ^ 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          const uint32_t fb = smem_u32(&bars[kFull + slot]);
-          mbar_expect_tx(fb, kSlot);
-          const int view = p < a.pairs[0] ? 0 : 1;
-          const int col = 128 * (view == 0 ? p : p - a.pairs[0]);
-          const CUtensorMap* map = view == 0 ? &tmx : &tmy;
-          const uint32_t dst = smem_u32(ring + slot * kSlot);
-          tma_load_2d(dst, map, col, row0, fb);
-          tma_load_2d(dst + kBox, map, col + 64, row0, fb);
-          last_use[slot] = use;
-        }
+    const CUtensorMap* map = view == 0 ? &tmx : &tmy;
+    for (int it = 0; it < nitems; ++it) {
+      const int j = it / npairs, p = it - j * npairs;
+      const int row0 = (cid + j * ncl) * kRows;
+      const int slot = it % kStages, use = it / kStages;
+      if (!mbar_wait(smem_u32(&bars[kEmpty + slot]), (use & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
       }
+      const uint32_t fb = smem_u32(&bars[kFull + slot]);
+      mbar_expect_tx(fb, kSlot);
+      const uint32_t dst = smem_u32(ring + slot * kSlot);
+      tma_load_2d(dst, map, 128 * p, row0, fb);
+      tma_load_2d(dst + kBox, map, 128 * p + 64, row0, fb);
+      last_use[slot] = use;
     }
     if (!ok) {
       // wait (bounded) for the copies this thread issued before leaving
@@ -253,39 +313,39 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t id1 = idesc_bf16(128, kNW, 0, 0);
     constexpr uint32_t id2 = idesc_bf16(128, kNW, 1, 0);
-    int it = 0;
     bool ok = true;
+    const uint32_t wbase = smem_u32(ws);
+    const uint32_t bbase = smem_u32(phi_s);
     for (int j = 0; j < my_tiles && ok; ++j) {
+      // GEMM 1: W (TMEM columns 0..47) = Z_v Phi_v; the epilogue must have read
+      // the previous tile's W
       if (j > 0 && !(ok = mbar_wait(smem_u32(&bars[kD1Free]), (j - 1) & 1, abort_flag))) break;
       tc_fence_after();
-      for (int p = 0; p < npairs; ++p, ++it) {
+      for (int p = 0; p < npairs; ++p) {
+        const int it = j * npairs + p;
         const int slot = it % kStages, use = it / kStages;
         if (!(ok = mbar_wait(smem_u32(&bars[kFull + slot]), use & 1, abort_flag))) break;
         tc_fence_after();
-        const int view = p < a.pairs[0] ? 0 : 1;
-        const int pp = view == 0 ? p : p - a.pairs[0];
-        const uint32_t d1 = tmem + (uint32_t)(view * kNW);
         const uint32_t abase = smem_u32(ring + slot * kSlot);
-        const uint32_t bbase = smem_u32(phi_s + view * kPhiView);
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
           const int box = s >> 2, kin = s & 3;
           const uint64_t ad = sdesc(abase + box * kBox + kin * 32, 16, 1024);
-          const uint64_t bd = sdesc(bbase + (2 * pp + box) * kKBox + kin * 32, 16, 1024);
-          mma_bf16(d1, ad, bd, id1, (pp > 0 || s > 0) ? 1u : 0u);
+          const uint64_t bd = sdesc(bbase + (2 * p + box) * kKBox + kin * 32, 16, 1024);
+          mma_bf16(tmem, ad, bd, id1, (p > 0 || s > 0) ? 1u : 0u);
         }
-        mma_commit(smem_u32(&bars[kEmpty + slot]));
       }
       if (!ok) break;
       mma_commit(smem_u32(&bars[kD1Full]));
+      // GEMM 2 needs both halves of this tile's W operand: ours and the peer's
+      mbar_expect_tx(smem_u32(&bars[kWPeer]), 4 * kWHalf);
       if (!(ok = mbar_wait(smem_u32(&bars[kWReady]), j & 1, abort_flag))) break;
+      if (!(ok = mbar_wait(smem_u32(&bars[kWPeer]), j & 1, abort_flag))) break;
       tc_fence_after();
-      const uint32_t wbase = smem_u32(ws);
-      for (int p = 0; p < npairs; ++p, ++it) {
-        const int slot = it % kStages, use = it / kStages;
-        if (!(ok = mbar_wait(smem_u32(&bars[kFull + slot]), use & 1, abort_flag))) break;
-        tc_fence_after();
-        const uint32_t g = tmem + (uint32_t)(2 * kNW + p * kNW);
+      for (int p = 0; p < npairs; ++p) {
+        const int it = j * npairs + p;
+        const int slot = it % kStages;
+        const uint32_t g = tmem + (uint32_t)(kNW + p * kNW);
         const uint32_t abase = smem_u32(ring + slot * kSlot);
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
@@ -298,8 +358,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         }
         mma_commit(smem_u32(&bars[kEmpty + slot]));
       }
-      if (!ok) break;
-      mma_commit(smem_u32(&bars[kWFree]));
+      // both CTAs learn that this CTA's GEMM 2 has consumed both W halves
+      mma_commit_mc(smem_u32(&bars[kWFree]), (uint16_t)0x3);
     }
     if (ok) {
       mma_commit(smem_u32(&bars[kGDone]));
@@ -313,70 +373,84 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
     const int q = warp - 4;             // TMEM lane quarter
-    const int r = 32 * q + lane;        // row of the tile / of a G pair block
+    const int r = 32 * q + lane;        // row of the tile / Z column of a G pair block
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     bool ok = true;
     for (int j = 0; j < my_tiles && ok; ++j) {
       if (!(ok = mbar_wait(smem_u32(&bars[kD1Full]), j & 1, abort_flag))) break;
       tc_fence_after();
-      float d1[2][kNW];
+      float d1[kNW];
 #pragma unroll
-      for (int v = 0; v < 2; ++v)
-#pragma unroll
-        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(v * kNW + c), &d1[v][c]);
+      for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)c, &d1[c]);
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(smem_u32(&bars[kD1Free]));
+      // both CTAs' GEMM 2 of the previous tile must be done with both W halves
       if (j > 0 && !(ok = mbar_wait(smem_u32(&bars[kWFree]), (j - 1) & 1, abort_flag))) break;
-      // W row r: columns [P_U, P_eta, Q_V, Q_eta]; view v's column c is the
-      // sum of its hi part (TMEM column c) and lo part (column kHalf + c)
+      // W_v row r = hi part (TMEM column c) + lo part (column kHalf + c), c < 2k
 #pragma unroll
-      for (int v = 0; v < 2; ++v)
-#pragma unroll
-        for (int c = 0; c < kHalf; ++c) {
-          if (c < a.k2) {
-            const float w = d1[v][c] + d1[v][kHalf + c];
-            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
-            const uint32_t off = (uint32_t)((r >> 6) * kKBox) + swz(v * a.k2 + c, r & 63);
-            *reinterpret_cast<__nv_bfloat16*>(ws + off) = hi;
-            *reinterpret_cast<__nv_bfloat16*>(ws + kWs + off) = lo;
-          }
+      for (int c = 0; c < kHalf; ++c) {
+        if (c < a.k2) {
+          const float w = d1[c] + d1[kHalf + c];
+          const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
+          const uint32_t off = (uint32_t)((r >> 6) * kKBox) + swz(view * kHalf + c, r & 63);
+          *reinterpret_cast<__nv_bfloat16*>(ws + off) = hi;
+          *reinterpret_cast<__nv_bfloat16*>(ws + kWs + off) = lo;
         }
+      }
       fence_proxy_async();
-      mbar_arrive(smem_u32(&bars[kWReady]));
+      mbar_arrive(smem_u32(&bars[kEpiSync]));
+      if (threadIdx.x == 128) {
+        // all 128 rows written: push this view's rows of both K-boxes (hi and
+        // lo) into the peer's operand, then release our own GEMM 2
+        if (!(ok = mbar_wait(smem_u32(&bars[kEpiSync]), j & 1, abort_flag))) break;
+        const uint32_t pbar = map_peer(smem_u32(&bars[kWPeer]), peer);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int kb = 0; kb < 2; ++kb) {
+            const uint32_t src = smem_u32(ws + h * kWs + kb * kKBox + view * kWHalf);
+            bulk_to_peer(map_peer(src, peer), src, kWHalf, pbar);
+          }
+        mbar_arrive(smem_u32(&bars[kWReady]));
+      }
     }
     if (ok && my_tiles > 0 && mbar_wait(smem_u32(&bars[kGDone]), 0, abort_flag)) {
       tc_fence_after();
       const int D0 = a.d[0];
       const int D = a.d[0] + a.d[1];
-      float* out = a.partG + (int64_t)blockIdx.x * D * k4;
+      float* out = a.partG + (int64_t)cid * D * k4;
       for (int p = 0; p < npairs; ++p) {
         float g[kNW];
 #pragma unroll
-        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(2 * kNW + p * kNW + c), &g[c]);
+        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(kNW + p * kNW + c), &g[c]);
         tmem_ld_wait();
-        const int view = p < a.pairs[0] ? 0 : 1;
-        const int pp = view == 0 ? p : p - a.pairs[0];
-        const int col = 128 * pp + r;
+        const int col = 128 * p + r;
         if (col < a.d[view]) {
           float* o = out + (int64_t)(view * D0 + col) * k4;
 #pragma unroll
-          for (int c = 0; c < kNW; ++c)
-            if (c < k4) o[c] = g[c];
+          for (int c = 0; c < kNW; ++c) {
+            const int vv = c / kHalf, cc = c - vv * kHalf;
+            if (cc < a.k2) o[vv * a.k2 + cc] = g[c];
+          }
         }
       }
+      // the peer's last end-of-GEMM-2 signal must have reached us before we leave
+      mbar_wait(smem_u32(&bars[kWFree]), (my_tiles - 1) & 1, abort_flag);
     } else if (my_tiles > 0) {
       // rows of a CTA that stopped early are not trustworthy: zero them so the
       // reduction stays finite; the error flag reports the failure
+      const int D0 = a.d[0];
       const int D = a.d[0] + a.d[1];
-      float* out = a.partG + (int64_t)blockIdx.x * D * k4;
-      for (int e = threadIdx.x - 128; e < D * k4; e += 128) out[e] = 0.f;
+      float* out = a.partG + (int64_t)cid * D * k4 + (int64_t)view * D0 * k4;
+      for (int e = threadIdx.x - 128; e < a.d[view] * k4; e += 128) out[e] = 0.f;
     }
     tc_fence_before();
   }
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 4);
+  cluster_sync();  // no bulk copy or remote arrive targets a CTA that has left
   if (warp == 2) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -546,11 +620,32 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   a.partG = p.tc_part;
   a.err = p.flag;
   a.done = done;
-  const int grid = std::min(p.sm_count, a.ntiles);
   GB_CUDA(cudaFuncSetAttribute(tc::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
-  tc::tc_pass_kernel<<<grid, 256, tc::kSmemBytes, st>>>(*reinterpret_cast<const CUtensorMap*>(p.tc_map[0]),
-                                                        *reinterpret_cast<const CUtensorMap*>(p.tc_map[1]), a);
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = tc::kSmemBytes;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (p.tc_clusters <= 0) {
+    // persistent grid: as many 2-CTA clusters as can be resident at once
+    cfg.gridDim = dim3(2 * (p.sm_count / 2), 1, 1);
+    int ncl = 0;
+    GB_CUDA(cudaOccupancyMaxActiveClusters(&ncl, tc::tc_pass_kernel, &cfg));
+    p.tc_clusters = std::max(1, std::min(ncl, p.sm_count / 2));
+  }
+  const int ncl = std::min(p.tc_clusters, a.ntiles);
+  cfg.gridDim = dim3(2 * ncl, 1, 1);
+  const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(p.tc_map[0]);
+  const CUtensorMap* my = reinterpret_cast<const CUtensorMap*>(p.tc_map[1]);
+  GB_CUDA(cudaLaunchKernelEx(&cfg, tc::tc_pass_kernel, *mx, *my, a));
   GB_CHECK_LAUNCH();
+  const int grid = ncl;  // partial slabs, one per cluster
   const int64_t len = (int64_t)p.D * k4;
   tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, p.G, done);
   GB_CHECK_LAUNCH();

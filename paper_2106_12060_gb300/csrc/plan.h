@@ -42,6 +42,8 @@ struct View {
   double* R = nullptr;      // d x d upper triangular, R^T R = M
   double* Rinv = nullptr;   // d x d, R^{-1}
   float* Rinv32 = nullptr;  // FP32 copy for the low-precision path
+  float* Minv_hi = nullptr; // M^{-1} = R^{-1} R^{-T} as a float pair (low-precision plans)
+  float* Minv_lo = nullptr;
   double* Phi = nullptr;    // d x 2k: [U | eta]
   float* Phi32 = nullptr;   // FP32 copy of Phi for the low-precision pass
   double* Meta = nullptr;   // d x k: M eta
@@ -121,6 +123,7 @@ struct Plan {
   const void* tc_map_for[2] = {nullptr, nullptr};
   uint8_t* tc_img = nullptr;
   float* tc_part = nullptr;
+  int tc_clusters = 0;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
 };
 
 // sketch.cu
@@ -142,6 +145,19 @@ int cholesky_upper(double* A, int d, int* flag, cudaStream_t st);
 // partials in a static device scratch instead of plan memory; d <= noalloc_max_d().
 int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, double* C, cudaStream_t st);
 int noalloc_max_d();
+// Double-float M^{-1} = R^{-1} R^{-T} (hi + lo float pairs, d x d) and its
+// application Y_v[:, 0:c] = M^{-1} X_v[:, 0:c] for all views in one launch.
+struct MinvDfArgs {
+  const float* hi[2];
+  const float* lo[2];
+  const double* X[2];
+  double* Y[2];
+  int d[2];
+  int ldx, ldy, c;
+  const int* done;
+};
+int minv_df_build(const double* Rinv, int d, float* hi, float* lo, double* ws, int64_t ws_len, cudaStream_t st);
+int minv_df(const MinvDfArgs& a, int nviews, cudaStream_t st);
 // Rinv = R^{-1} (upper triangular, d x d); ws holds at least d * d doubles.
 int tri_inverse_upper(const double* R, double* Rinv, int d, double* ws, int64_t ws_len, cudaStream_t st);
 int to_f32(const double* a, float* b, int64_t len, cudaStream_t st);
