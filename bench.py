@@ -276,7 +276,7 @@ def run_ours(args, ws, rank, local):
         "fused_pass": {"ms": pass_ms, "GBps": achieved, "frac_of_hbm": achieved / hbm},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
-                     "kernel": "fused CCA data pass (X^T W, Y^T W, W^T W with W = [X Phi_x, Y Phi_y])",
+                     "kernel": "tc_pass_kernel: fused CCA data pass (X^T W, Y^T W with W = [X Phi_x, Y Phi_y])",
                      "algorithmic_bytes": pass_bytes},
         "e2e": {"value": e2e_ms / (args.steps * ws), "unit": "ms",
                 "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size()),

@@ -80,7 +80,8 @@ typedef struct {
                             problem (Alg. 1 step 4 / Alg. 2 step 5); 0: start
                             from the U/V (W) buffers passed to the solve call  */
   int32_t check_every;   /* iterations between convergence read-backs (8)      */
-  int32_t time_passes;   /* 1: time every fused data pass with CUDA events on
+  int32_t time_passes;   /* 1: time the data kernel of every fused pass (the
+                            kernel that streams X and Y) with CUDA events on
                             the solve's stream (reported in gbcca_info)         */
 } gbcca_options;
 
@@ -94,8 +95,8 @@ typedef struct {
   double grad_norm;      /* ||grad||_M at the last iterate                      */
   double grad_norm0;     /* ||grad||_M at the first iterate                     */
   double objective;      /* f at the iterate before the final Rayleigh-Ritz step */
-  double pass_ms;        /* with opt.time_passes: mean device time of one fused
-                            pass (ms, CUDA events), else 0                      */
+  double pass_ms;        /* with opt.time_passes: mean device time of the data
+                            kernel of one fused pass (ms, CUDA events), else 0  */
   int32_t pass_count;    /* passes included in pass_ms                          */
 } gbcca_info;
 

@@ -42,7 +42,7 @@ void free_plan(Plan* p) {
   if (p == nullptr) return;
   for (int v = 0; v < 2; ++v) {
     View& w = p->v[v];
-    for (void* q : {(void*)w.SZ, (void*)w.R, (void*)w.Rinv, (void*)w.Rinv32, (void*)w.Phi, (void*)w.Phi32,
+    for (void* q : {(void*)w.SZ, (void*)w.R, (void*)w.Rinv, (void*)w.Rinv32, (void*)w.Minv_hi, (void*)w.Minv_lo, (void*)w.RRh, (void*)w.RRl, (void*)w.Phi, (void*)w.Phi32,
                     (void*)w.Meta, (void*)w.gold, (void*)w.Mgold, (void*)w.LL, (void*)w.RR, (void*)w.tmp,
                     (void*)w.warm, (void*)w.wsU, (void*)w.wsT})
       dfree(q);
@@ -50,8 +50,8 @@ void free_plan(Plan* p) {
   for (void* q : {(void*)p->h, (void*)p->g, (void*)p->cs_tab, (void*)p->cs_off, (void*)p->perm, p->srht_T,
                   (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
-                  (void*)p->phigram, (void*)p->phipart, (void*)p->cross, (void*)p->crosspart, (void*)p->history,
-                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part})
+                  (void*)p->phigram, (void*)p->phipart, (void*)p->phired, (void*)p->cross, (void*)p->crosspart, (void*)p->history,
+                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->ls_f, (void*)p->ls_L})
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
@@ -69,6 +69,12 @@ int alloc_plan(Plan* p) {
     GB_TRY(dalloc(&w.R, (int64_t)d * d));
     GB_TRY(dalloc(&w.Rinv, (int64_t)d * d));
     GB_TRY(dalloc(&w.Rinv32, (int64_t)d * d));
+    if (p->dtype != GBCCA_FP64) {
+      GB_TRY(dalloc(&w.Minv_hi, (int64_t)d * d));
+      GB_TRY(dalloc(&w.Minv_lo, (int64_t)d * d));
+      GB_TRY(dalloc(&w.RRh, (int64_t)d * k2));
+      GB_TRY(dalloc(&w.RRl, (int64_t)d * k2));
+    }
     GB_TRY(dalloc(&w.Phi, (int64_t)d * k2));
     GB_TRY(dalloc(&w.Phi32, (int64_t)d * k2));
     GB_TRY(dalloc(&w.Meta, (int64_t)d * k));
@@ -143,12 +149,16 @@ int alloc_plan(Plan* p) {
   const int nblk = ceil_div(dmax, 16);  // thin-Gram row blocks
   GB_TRY(dalloc(&p->phigram, 4096));
   GB_TRY(dalloc(&p->phipart, (int64_t)p->nviews * nblk * 4 * k * k));
+  GB_TRY(dalloc(&p->phired, (int64_t)p->nviews * 4 * k * k));
   GB_TRY(dalloc(&p->cross, (int64_t)p->nviews * 16 * k * k));
   GB_TRY(dalloc(&p->crosspart, (int64_t)p->nviews * nblk * std::max(16 * k * k, p->l * p->l)));
   GB_TRY(dalloc(&p->history, 3 * (int64_t)(p->opt.max_iter + 1)));
   p->ws_len = 8 * (int64_t)dmax * dmax + 3 * (int64_t)dmax * std::max(std::max(p->l, k2), 1) + 4096;
   GB_TRY(dalloc(&p->ws, p->ws_len));
   GB_TRY(dalloc(&p->mt_part, (int64_t)ceil_div(dmax, 64) * dmax * 40));
+  GB_TRY(dalloc(&p->dfx, 2 * (int64_t)dmax * k2));
+  GB_TRY(dalloc(&p->ls_f, 64));
+  GB_TRY(dalloc(&p->ls_L, 64 * 2 * (int64_t)kMaxK * kMaxK));
   GB_TRY(dalloc(&p->flag, 1));
   GB_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
   if (p->kind == kCCA && p->dtype == GBCCA_BF16 && 4 * k <= 48 && p->v[0].d <= 512 && p->v[1].d <= 512) {
@@ -258,6 +268,15 @@ int read_flag(Plan& p, cudaStream_t st) {
 
 // Sketch every view, factor the sketch preconditioner and compute the warm
 // start; then install the metric factor the options ask for.
+// Derived forms of R^{-1} used by the iterations: the FP32 copy and, for
+// FP32/BF16 plans, the double-float M^{-1}.
+int finish_factor(Plan& p, int v, cudaStream_t st) {
+  View& w = p.v[v];
+  GB_TRY(to_f32(w.Rinv, w.Rinv32, (int64_t)w.d * w.d, st));
+  if (w.Minv_hi != nullptr) GB_TRY(minv_df_build(w.Rinv, w.d, w.Minv_hi, w.Minv_lo, p.ws, p.ws_len, st));
+  return GBCCA_OK;
+}
+
 int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream_t st) {
   const bool center = p.kind == kLDA;
   const bool srht = p.opt.sketch == GBCCA_SKETCH_SRHT;
@@ -287,7 +306,7 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
     GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, p.ws, p.ws_len, st));
   }
   GB_TRY(read_flag(p, st));
-  for (int v = 0; v < p.nviews; ++v) GB_TRY(to_f32(p.v[v].Rinv, p.v[v].Rinv32, (int64_t)p.v[v].d * p.v[v].d, st));
+  for (int v = 0; v < p.nviews; ++v) GB_TRY(finish_factor(p, v, st));
   if (p.opt.warm_start) {
     GB_TRY(warm_start(p, st));
     GB_TRY(read_flag(p, st));
@@ -299,7 +318,7 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
       GB_CHECK_LAUNCH();
       identity_kernel<<<ceil_div(d * d, 256), 256, 0, st>>>(p.v[v].Rinv, d);
       GB_CHECK_LAUNCH();
-      GB_TRY(to_f32(p.v[v].Rinv, p.v[v].Rinv32, (int64_t)d * d, st));
+      GB_TRY(finish_factor(p, v, st));
     }
   } else if (p.opt.sketch == GBCCA_SKETCH_EXACT) {
     if (p.dtype != GBCCA_FP64 || p.kind != kCCA) {
@@ -312,7 +331,7 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
                      p.ws_len, st));
       GB_TRY(cholesky_upper(w.R, w.d, p.flag, st));
       GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, p.ws, p.ws_len, st));
-      GB_TRY(to_f32(w.Rinv, w.Rinv32, (int64_t)w.d * w.d, st));
+      GB_TRY(finish_factor(p, v, st));
     }
     GB_TRY(read_flag(p, st));
   }

@@ -88,11 +88,14 @@ __device__ __forceinline__ void df_acc(float& S, float& Cc, float ah, float al, 
 template <typename Tout>
 __global__ void __launch_bounds__(256)
 gram_df_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t m,
-               int d1, int d2, int64_t kchunk, Tout* __restrict__ part) {
+               int d1, int d2, int64_t kchunk, Tout* __restrict__ part, int tri) {
   __shared__ float Ah[kGK][kGT], Al[kGK][kGT], Bh[kGK][kGT], Bl[kGK][kGT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
-  const int64_t k0 = blockIdx.z * kchunk, k1 = min(m, k0 + kchunk);
+  // tri: A and B lower triangular (A[q][i] = 0 for i > q), so rows
+  // q < max(i0, j0) contribute nothing to this tile
+  const int64_t k1 = min(m, (int64_t)blockIdx.z * kchunk + kchunk);
+  const int64_t k0 = tri ? max((int64_t)blockIdx.z * kchunk, (int64_t)max(i0, j0)) : (int64_t)blockIdx.z * kchunk;
   float S[4][4] = {}, Cc[4][4] = {};
   for (int64_t kk = k0; kk < k1; kk += kGK) {
     for (int e = tid; e < kGK * kGT; e += 256) {
@@ -134,7 +137,7 @@ gram_df_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
 }
 
 int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1, int d2, double* C,
-            double diag_add, double* ws, int64_t ws_len, cudaStream_t st, bool df) {
+            double diag_add, double* ws, int64_t ws_len, cudaStream_t st, bool df, bool tri) {
   int tiles = ceil_div(d1, kGT) * ceil_div(d2, kGT);
   int ks = std::max(1, std::min<int>(ceil_div(304, tiles), ceil_div(m, 64)));
   int64_t len = (int64_t)d1 * d2;
@@ -146,11 +149,229 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
   int64_t kchunk = (m + ks - 1) / ks;
   dim3 grid(ceil_div(d2, kGT), ceil_div(d1, kGT), ks);
   if (df)
-    gram_df_kernel<double><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
+    gram_df_kernel<double><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws, tri ? 1 : 0);
   else
     gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
   GB_CHECK_LAUNCH();
   sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+// ------------------------------------------- M^{-1} in double-float form
+// For FP32/BF16 plans the solver applies M^{-1} = R^{-1} R^{-T} (Table 1's
+// preconditioned gradient) through an explicit symmetric matrix held as a
+// float pair hi + lo (~2^-44 relative), formed once per preconditioner, and
+// multiplied with double-float arithmetic.  One launch covers both views and
+// replaces two dependent triangular products per view; its rounding error is
+// ~2^-44 sqrt(d) kappa(M), below that of FP32 triangular products
+// (~2^-24 kappa(R) each).
+__global__ void transpose_sq_kernel(const double* __restrict__ A, int d, double* __restrict__ At) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * d) return;
+  const int i = (int)(e / d), j = (int)(e % d);
+  At[(int64_t)j * d + i] = A[e];
+}
+
+__global__ void split_df_kernel(const double* __restrict__ A, int64_t len, float* __restrict__ hi,
+                                float* __restrict__ lo) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  const double x = A[e];
+  const float h = (float)x;
+  hi[e] = h;
+  lo[e] = (float)(x - (double)h);
+}
+
+int minv_df_build(const double* Rinv, int d, float* hi, float* lo, double* ws, int64_t ws_len, cudaStream_t st) {
+  const int64_t dd = (int64_t)d * d;
+  if (ws_len < 5 * dd) {
+    set_last_error("minv_df_build: workspace too small");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  double* T = ws;
+  double* C = ws + dd;
+  transpose_sq_kernel<<<ceil_div(dd, 256), 256, 0, st>>>(Rinv, d, T);
+  GB_CHECK_LAUNCH();
+  // C = T^T T = R^{-1} R^{-T}
+  GB_TRY(gram_tn(T, d, T, d, d, d, d, C, 0.0, ws + 2 * dd, ws_len - 2 * dd, st, true, true));
+  split_df_kernel<<<ceil_div(dd, 256), 256, 0, st>>>(C, dd, hi, lo);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+__device__ __forceinline__ void df_add(float& S, float& Cc, float s2, float c2) {
+  const float t = S + s2;
+  const float bp = t - S;
+  const float err = (S - (t - bp)) + (s2 - bp);
+  S = t;
+  Cc += err + c2;
+}
+
+constexpr int kMvRows = 8, kMvChunk = 256, kMvCols = 10;  // c <= 4 * kMvCols
+constexpr int kMvBatch = 8;                                  // loads in flight per thread while staging
+
+// Y_b (rows r0..r0+7, c columns) = A_b X_b for problem b = blockIdx.y, A_b
+// (m x K, row-major) and X_b (K x c) as double-float pairs hi + lo.  Per
+// 256-wide K chunk: X and the 8 rows of A are staged in shared memory (loads
+// batched, several in flight per thread); warp w takes the K
+// slice [32 w, 32 w + 32) of the chunk; lane = (row r = lane & 7, column
+// group cg = lane >> 3: columns cg, cg + 4, ...).  The 8 warps' double-float
+// partials are added in fixed order.
+__global__ void __launch_bounds__(256) dfmv_kernel(DfmvArgs a) {
+  const int b = blockIdx.y;
+  const DfmvProblem& P = a.p[b];
+  if (a.done != nullptr && *a.done) return;
+  const int m = P.m, K = P.K, c = a.c;
+  const int r0 = blockIdx.x * kMvRows;
+  if (r0 >= m) return;
+  extern __shared__ float msm[];
+  float* Xh = msm;                              // [kMvChunk][c]
+  float* Xl = Xh + kMvChunk * c;
+  float* Ah = Xl + kMvChunk * c;                // [kMvRows][kMvChunk + 1]
+  float* Al = Ah + kMvRows * (kMvChunk + 1);
+  float* red = Al + kMvRows * (kMvChunk + 1);   // [8 warps][kMvRows][c][2]
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, r = lane & 7, cg = lane >> 3;
+  float S[kMvCols], Cc[kMvCols];
+#pragma unroll
+  for (int u = 0; u < kMvCols; ++u) S[u] = Cc[u] = 0.f;
+  const int c2 = c >> 1;  // c is even: X rows are read as float2
+  for (int k0 = 0; k0 < K; k0 += kMvChunk) {
+    const int kn = min(kMvChunk, K - k0);
+    const int nx = kn * c2;
+    for (int base = 0; base < nx; base += 256 * kMvBatch) {
+      float2 vh[kMvBatch], vl[kMvBatch];
+#pragma unroll
+      for (int u = 0; u < kMvBatch; ++u) {
+        const int e = base + tid + 256 * u;
+        if (e < nx) {
+          const int q = e / c2, cp = e - q * c2;
+          const int64_t o = (int64_t)(k0 + q) * P.ldx + 2 * cp;
+          vh[u] = *reinterpret_cast<const float2*>(P.Xh + o);
+          vl[u] = *reinterpret_cast<const float2*>(P.Xl + o);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kMvBatch; ++u) {
+        const int e = base + tid + 256 * u;
+        if (e < nx) {
+          reinterpret_cast<float2*>(Xh)[e] = vh[u];
+          reinterpret_cast<float2*>(Xl)[e] = vl[u];
+        }
+      }
+    }
+    const int na = kMvRows * kn;
+    for (int base = 0; base < na; base += 256 * kMvBatch) {
+      float vh[kMvBatch], vl[kMvBatch];
+#pragma unroll
+      for (int u = 0; u < kMvBatch; ++u) {
+        const int e = base + tid + 256 * u;
+        vh[u] = vl[u] = 0.f;
+        if (e < na) {
+          const int rr = e / kn, q = e - rr * kn;
+          if (r0 + rr < m) {
+            vh[u] = P.hi[(int64_t)(r0 + rr) * K + k0 + q];
+            vl[u] = P.lo[(int64_t)(r0 + rr) * K + k0 + q];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kMvBatch; ++u) {
+        const int e = base + tid + 256 * u;
+        if (e < na) {
+          const int rr = e / kn, q = e - rr * kn;
+          Ah[rr * (kMvChunk + 1) + q] = vh[u];
+          Al[rr * (kMvChunk + 1) + q] = vl[u];
+        }
+      }
+    }
+    __syncthreads();
+    const int qe = min(32 * w + 32, kn);
+    for (int q = 32 * w; q < qe; ++q) {
+      const float ah = Ah[r * (kMvChunk + 1) + q], al = Al[r * (kMvChunk + 1) + q];
+#pragma unroll
+      for (int u = 0; u < kMvCols; ++u) {
+        const int col = cg + 4 * u;
+        if (col < c) df_acc(S[u], Cc[u], ah, al, Xh[q * c + col], Xl[q * c + col]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < kMvCols; ++u) {
+    const int col = cg + 4 * u;
+    if (col < c) {
+      red[((w * kMvRows + r) * c + col) * 2 + 0] = S[u];
+      red[((w * kMvRows + r) * c + col) * 2 + 1] = Cc[u];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kMvRows * c; e += 256) {
+    const int rr = e / c, col = e - rr * c;
+    const int row = r0 + rr;
+    if (row >= m) continue;
+    float s = 0.f, cc = 0.f;
+    for (int w2 = 0; w2 < 8; ++w2)
+      df_add(s, cc, red[((w2 * kMvRows + rr) * c + col) * 2], red[((w2 * kMvRows + rr) * c + col) * 2 + 1]);
+    P.Y[(int64_t)row * P.ldy + col] = (double)s + (double)cc;
+  }
+}
+
+int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st) {
+  if (a.c < 2 || a.c > 4 * kMvCols || (a.c & 1)) {
+    set_last_error("dfmv: unsupported column count");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  int mmax = 0;
+  for (int b = 0; b < nprob; ++b) {
+    if ((a.p[b].ldx & 1) || (reinterpret_cast<uintptr_t>(a.p[b].Xh) & 7) ||
+        (reinterpret_cast<uintptr_t>(a.p[b].Xl) & 7)) {
+      set_last_error("dfmv: X rows must be 8-byte aligned");
+      return GBCCA_ERR_INVALID_ARG;
+    }
+    mmax = std::max(mmax, a.p[b].m);
+  }
+  const size_t smem = sizeof(float) * (2 * kMvChunk * a.c + 2 * kMvRows * (kMvChunk + 1) + 8 * kMvRows * a.c * 2);
+  GB_CUDA(cudaFuncSetAttribute(dfmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dfmv_kernel<<<dim3(ceil_div(mmax, kMvRows), nprob), 256, smem, st>>>(a);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+// hi/lo split of the first c columns of X (rows x ldx doubles) into two
+// rows x c float arrays
+__global__ void split_rows_kernel(const double* __restrict__ X, int rows, int c, int ldx, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * c) return;
+  const int i = e / c, j = e - i * c;
+  const double x = X[(int64_t)i * ldx + j];
+  const float h = (float)x;
+  hi[e] = h;
+  lo[e] = (float)(x - (double)h);
+}
+
+int split_rows(const double* X, int rows, int c, int ldx, float* hi, float* lo, cudaStream_t st) {
+  split_rows_kernel<<<ceil_div(rows * c, 256), 256, 0, st>>>(X, rows, c, ldx, hi, lo);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+// hi/lo split of A (r x c) or of A^T
+__global__ void split_df_t_kernel(const double* __restrict__ A, int r, int c, int trans, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)r * c) return;
+  const int i = (int)(e / c), j = (int)(e % c);
+  const double x = A[e];
+  const float h = (float)x;
+  const int64_t o = trans ? (int64_t)j * r + i : e;
+  hi[o] = h;
+  lo[o] = (float)(x - (double)h);
+}
+
+int split_df(const double* A, int r, int c, bool trans, float* hi, float* lo, cudaStream_t st) {
+  split_df_t_kernel<<<ceil_div((int64_t)r * c, 256), 256, 0, st>>>(A, r, c, trans ? 1 : 0, hi, lo);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -417,6 +417,15 @@ int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols,
   if (phi_cols <= 0) phi_cols = 2 * p.k;
   if (low && !gram_only && phi_cols == 2 * p.k && p.tc_img != nullptr && tc_pass_eligible(p))
     return tc_pass(p, st, done);
+  if (p.kev0 != nullptr) GB_CUDA(cudaEventRecord(p.kev0, st));
+  const int rc = fused_pass_cores(p, low, gram_only, st, phi_cols, done);
+  if (rc == GBCCA_OK && p.kev1 != nullptr) GB_CUDA(cudaEventRecord(p.kev1, st));
+  return rc;
+}
+
+// CUDA-core passes (FP64 / FP32 data, LDA, and the BF16 plans the
+// tensor-core pass does not serve)
+int fused_pass_cores(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols, const int* done) {
   if (p.kind == kLDA && p.l * phi_cols > 256 * kCI) {
     set_last_error("too many classes x columns for the FDA pass");
     return GBCCA_ERR_UNSUPPORTED;

@@ -8,25 +8,29 @@
 // and W^T W, which equals Phi^T G and is formed afterwards in FP64 from G.
 //
 // Persistent kernel of 2-CTA clusters; both CTAs of a cluster work on the
-// same 128-row tile, CTA v on view v (X or Y), so that each CTA holds its
-// whole 128 x d_v BF16 block (<= 128 KB) in shared memory and every byte of
-// the data is read from HBM exactly once.  Per tile:
-//   GEMM 1  (tcgen05, per CTA): W_v = Z_v Phi_v, 128 x 48 FP32 in TMEM (B =
-//           Phi_v split into bf16 hi|lo columns, 24 each);
+// same 64-row tile, CTA v on view v (X or Y), so that each CTA keeps its
+// 64 x d_v BF16 block (<= 64 KB) in shared memory for both GEMMs and every
+// byte of the data is read from HBM exactly once.  Two tiles are resident per
+// CTA (double buffering): the next tile streams in while the current one is
+// in its epilogue and second GEMM.  Per tile:
+//   GEMM 1  (tcgen05, M = 64, per CTA): W_v = Z_v Phi_v, 64 x 48 FP32 in TMEM
+//           (B = Phi_v split into bf16 hi|lo columns, 24 each; rows 16 q ..
+//           16 q + 15 of the M = 64 result sit in lanes 32 q .. 32 q + 15);
 //   epilogue warps read W_v from TMEM, add the hi and lo halves, split W_v
 //           into bf16 hi/lo and write it into the K-major B operand of GEMM 2
 //           (N rows 24 v .. 24 v + 23) of their own CTA, then push that half
 //           into the peer CTA's operand with a bulk shared::cluster copy;
-//   GEMM 2  (tcgen05, per CTA): G_v += Z_v^T [W_x | W_y] over the same shared
-//           memory blocks read as MN-major A (128 columns of Z_v per MMA),
-//           accumulated in TMEM over all tiles of the cluster.
+//   GEMM 2  (tcgen05, M = 128, per CTA): G_v += Z_v^T [W_x | W_y] over the
+//           same shared-memory blocks read as MN-major A (128 columns of Z_v
+//           per MMA), accumulated in TMEM over all tiles of the cluster.
 // The end of GEMM 2 is signalled to both CTAs (multicast commit), which
-// frees both W operands for the next tile.  At the end the epilogue warps
-// drain G to a per-cluster FP32 partial; a second kernel sums the partials in
-// fixed order.
+// frees both CTAs' W operand buffer of that tile.  At the end the epilogue
+// warps drain G to a per-cluster FP32 partial; a second kernel sums the
+// partials in fixed order.
 //
-// Roles per CTA: warp 0 lane 0 = TMA producer, warp 1 lane 0 = MMA issuer,
-// warp 2 = TMEM allocator, warps 4-7 = epilogue (TMEM lane quarters 0-3).
+// Roles per CTA: warp 0 lane 0 = TMA producer, warp 1 lane 0 = GEMM 1
+// issuer, warp 3 lane 0 = GEMM 2 issuer, warp 2 = TMEM allocator, warps 4-7 =
+// epilogue (TMEM lane quarters 0-3).
 // Every mbarrier wait is bounded in time; on expiry the CTA records an error
 // code, waits (bounded) for its own copies and MMAs, frees TMEM and leaves
 // after a cluster barrier (no remote access can target an exited CTA).
@@ -38,35 +42,37 @@ namespace gbcca {
 
 namespace tc {
 
-constexpr int kRows = 128;            // rows per tile (MMA M of GEMM 1)
+constexpr int kRows = 64;             // rows per tile (MMA M of GEMM 1, K of GEMM 2)
 constexpr int kNW = 48;               // N of both GEMMs
 constexpr int kHalf = 24;             // per view: B rows of Phi hi (0..23) / lo (24..47); W rows of a view
-constexpr int kStages = 4;            // ring of 32 KB pair slots (one 512-column view block)
-constexpr int kSlot = 32768;          // two 128 x 64 BF16 boxes
-constexpr int kBox = 16384;
+constexpr int kTileSlots = 4;         // pair slots of one tile (512 columns)
+constexpr int kStages = 2 * kTileSlots;  // two resident tiles
+constexpr int kSlot = 16384;          // two 64 x 64 BF16 boxes
+constexpr int kBox = 8192;
 constexpr int kPhiView = 49152;       // per view: 8 K-boxes x 48 rows x 128 B
 constexpr int kKBox = 6144;           // 48 rows x 128 B
-constexpr int kWs = 12288;            // W operand (hi or lo): 2 K-boxes x 48 rows x 128 B
-constexpr int kWHalf = kHalf * 128;   // one view's rows of one K-box of the W operand
+constexpr int kWs = kKBox;            // W operand (hi or lo) of one tile: 1 K-box (64 rows)
+constexpr int kWBuf = 2 * kWs;        // hi + lo
+constexpr int kWHalf = kHalf * 128;   // one view's rows of the W operand
 constexpr int kRingOff = kPhiView;
 constexpr int kWsOff = kRingOff + kStages * kSlot;
-constexpr int kBarOff = kWsOff + 2 * kWs;
+constexpr int kBarOff = kWsOff + 2 * kWBuf;
 constexpr int kSmemBytes = kBarOff + 256 + 1024;  // + alignment slack
-constexpr uint32_t kTmemCols = 256;   // W: 0..47, G: 48 + 48 p (p < 4 pairs)
+constexpr uint32_t kTmemCols = 512;   // W: 48 b (b = 0, 1), G: 2 kNW + kNW p (p < 4 pairs)
 constexpr long long kTimeout = 2000000000ll;      // cycles (~1 s)
 
 enum Bar {
   kFull = 0,
   kEmpty = kStages,
-  kD1Full = 2 * kStages,
-  kD1Free,
-  kEpiSync,
-  kWReady,
-  kWPeer,
-  kWFree,
-  kGDone,
-  kFinal,
-  kNumBars
+  kD1Full = 2 * kStages,   // [2]
+  kD1Free = kD1Full + 2,   // [2]
+  kEpiSync = kD1Free + 2,
+  kWReady,                 // [2]
+  kWPeer = kWReady + 2,    // [2]
+  kWFree = kWPeer + 2,     // [2]
+  kGDone = kWFree + 2,
+  kFinal,                  // [2]: one per MMA-issuing thread
+  kNumBars = kFinal + 2
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -229,7 +235,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* phi_s = smem;
   uint8_t* ring = smem + kRingOff;
-  uint8_t* ws = smem + kWsOff;
+  uint8_t* ws = smem + kWsOff;  // [buffer][hi | lo][48 rows][128 B]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -239,28 +245,32 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
   const int npairs = a.pairs[view];
   const int k4 = 2 * a.k2;
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
-  // own view's Phi image -> shared memory (generic proxy); zero W operand
+  // own view's Phi image -> shared memory (generic proxy); zero W operands
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.phi_img + view * kPhiView);
     uint4* dst = reinterpret_cast<uint4*>(phi_s);
     for (int i = threadIdx.x; i < kPhiView / 16; i += blockDim.x) dst[i] = src[i];
     uint4* wz = reinterpret_cast<uint4*>(ws);
-    for (int i = threadIdx.x; i < 2 * kWs / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < 2 * kWBuf / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&bars[kFull + s]), 1);
-      mbar_init(smem_u32(&bars[kEmpty + s]), 1);
+      mbar_init(bar(kFull + s), 1);
+      mbar_init(bar(kEmpty + s), 1);
     }
-    mbar_init(smem_u32(&bars[kD1Full]), 1);
-    mbar_init(smem_u32(&bars[kD1Free]), 128);
-    mbar_init(smem_u32(&bars[kEpiSync]), 128);
-    mbar_init(smem_u32(&bars[kWReady]), 1);
-    mbar_init(smem_u32(&bars[kWPeer]), 1);   // + the peer's bytes
-    mbar_init(smem_u32(&bars[kWFree]), 2);   // own and peer's end of GEMM 2
-    mbar_init(smem_u32(&bars[kGDone]), 1);
-    mbar_init(smem_u32(&bars[kFinal]), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(kD1Full + b), 1);
+      mbar_init(bar(kD1Free + b), 128);
+      mbar_init(bar(kWReady + b), 1);
+      mbar_init(bar(kWPeer + b), 1);   // + the peer's bytes
+      mbar_init(bar(kWFree + b), 2);   // own and peer's end of GEMM 2
+    }
+    mbar_init(bar(kEpiSync), 128);
+    mbar_init(bar(kGDone), 1);
+    mbar_init(bar(kFinal), 1);
+    mbar_init(bar(kFinal + 1), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -289,11 +299,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       const int j = it / npairs, p = it - j * npairs;
       const int row0 = (cid + j * ncl) * kRows;
       const int slot = it % kStages, use = it / kStages;
-      if (!mbar_wait(smem_u32(&bars[kEmpty + slot]), (use & 1) ^ 1, abort_flag)) {
+      if (!mbar_wait(bar(kEmpty + slot), (use & 1) ^ 1, abort_flag)) {
         ok = false;
         break;
       }
-      const uint32_t fb = smem_u32(&bars[kFull + slot]);
+      const uint32_t fb = bar(kFull + slot);
       mbar_expect_tx(fb, kSlot);
       const uint32_t dst = smem_u32(ring + slot * kSlot);
       tma_load_2d(dst, map, 128 * p, row0, fb);
@@ -305,118 +315,132 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       for (int s = 0; s < kStages; ++s) {
         if (last_use[s] < 0) continue;
         const long long t0 = clock64();
-        while (!mbar_try(smem_u32(&bars[kFull + s]), last_use[s] & 1) && clock64() - t0 < kTimeout) {
+        while (!mbar_try(bar(kFull + s), last_use[s] & 1) && clock64() - t0 < kTimeout) {
         }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t id1 = idesc_bf16(128, kNW, 0, 0);
+  } else if ((warp == 1 || warp == 3) && lane == 0) {
+    // ------------------------------------------------------------ MMA issuers
+    // warp 1: GEMM 1 of every tile; warp 3: GEMM 2 of every tile.  Separate
+    // issuers keep GEMM 2 of tile j (which frees its ring slots) from waiting
+    // behind the arrival of tile j + 1's data.
+    constexpr uint32_t id1 = idesc_bf16(64, kNW, 0, 0);
     constexpr uint32_t id2 = idesc_bf16(128, kNW, 1, 0);
     bool ok = true;
-    const uint32_t wbase = smem_u32(ws);
-    const uint32_t bbase = smem_u32(phi_s);
-    for (int j = 0; j < my_tiles && ok; ++j) {
-      // GEMM 1: W (TMEM columns 0..47) = Z_v Phi_v; the epilogue must have read
-      // the previous tile's W
-      if (j > 0 && !(ok = mbar_wait(smem_u32(&bars[kD1Free]), (j - 1) & 1, abort_flag))) break;
-      tc_fence_after();
-      for (int p = 0; p < npairs; ++p) {
-        const int it = j * npairs + p;
-        const int slot = it % kStages, use = it / kStages;
-        if (!(ok = mbar_wait(smem_u32(&bars[kFull + slot]), use & 1, abort_flag))) break;
+    if (warp == 1) {
+      const uint32_t bbase = smem_u32(phi_s);
+      for (int j = 0; j < my_tiles && ok; ++j) {
+        const int b = j & 1;
+        // W buffer b was last read by the epilogue of tile j - 2
+        if (j >= 2 && !(ok = mbar_wait(bar(kD1Free + b), ((j - 2) >> 1) & 1, abort_flag))) break;
         tc_fence_after();
-        const uint32_t abase = smem_u32(ring + slot * kSlot);
+        const uint32_t d1 = tmem + (uint32_t)(b * kNW);
+        for (int p = 0; p < npairs; ++p) {
+          const int it = j * npairs + p;
+          const int slot = it % kStages, use = it / kStages;
+          if (!(ok = mbar_wait(bar(kFull + slot), use & 1, abort_flag))) break;
+          tc_fence_after();
+          const uint32_t abase = smem_u32(ring + slot * kSlot);
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const int box = s >> 2, kin = s & 3;
-          const uint64_t ad = sdesc(abase + box * kBox + kin * 32, 16, 1024);
-          const uint64_t bd = sdesc(bbase + (2 * p + box) * kKBox + kin * 32, 16, 1024);
-          mma_bf16(tmem, ad, bd, id1, (p > 0 || s > 0) ? 1u : 0u);
-        }
-      }
-      if (!ok) break;
-      mma_commit(smem_u32(&bars[kD1Full]));
-      // GEMM 2 needs both halves of this tile's W operand: ours and the peer's
-      mbar_expect_tx(smem_u32(&bars[kWPeer]), 4 * kWHalf);
-      if (!(ok = mbar_wait(smem_u32(&bars[kWReady]), j & 1, abort_flag))) break;
-      if (!(ok = mbar_wait(smem_u32(&bars[kWPeer]), j & 1, abort_flag))) break;
-      tc_fence_after();
-      for (int p = 0; p < npairs; ++p) {
-        const int it = j * npairs + p;
-        const int slot = it % kStages;
-        const uint32_t g = tmem + (uint32_t)(kNW + p * kNW);
-        const uint32_t abase = smem_u32(ring + slot * kSlot);
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const uint64_t ad = sdesc(abase + s * 2048, kBox, 1024);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint64_t bd = sdesc(wbase + h * kWs + (s >> 2) * kKBox + (s & 3) * 32, 16, 1024);
-            mma_bf16(g, ad, bd, id2, (j > 0 || s > 0 || h > 0) ? 1u : 0u);
+          for (int s = 0; s < 8; ++s) {
+            const int box = s >> 2, kin = s & 3;
+            const uint64_t ad = sdesc(abase + box * kBox + kin * 32, 16, 1024);
+            const uint64_t bd = sdesc(bbase + (2 * p + box) * kKBox + kin * 32, 16, 1024);
+            mma_bf16(d1, ad, bd, id1, (p > 0 || s > 0) ? 1u : 0u);
           }
         }
-        mma_commit(smem_u32(&bars[kEmpty + slot]));
+        if (!ok) break;
+        mma_commit(bar(kD1Full + b));
       }
-      // both CTAs learn that this CTA's GEMM 2 has consumed both W halves
-      mma_commit_mc(smem_u32(&bars[kWFree]), (uint16_t)0x3);
-    }
-    if (ok) {
-      mma_commit(smem_u32(&bars[kGDone]));
     } else {
-      // let the MMAs already issued finish before the CTA frees its memory
-      mma_commit(smem_u32(&bars[kFinal]));
+      for (int j = 0; j < my_tiles && ok; ++j) {
+        const int b = j & 1;
+        // both halves of this tile's W operand: ours and the peer's
+        mbar_expect_tx(bar(kWPeer + b), 2 * kWHalf);
+        if (!(ok = mbar_wait(bar(kWReady + b), (j >> 1) & 1, abort_flag))) break;
+        if (!(ok = mbar_wait(bar(kWPeer + b), (j >> 1) & 1, abort_flag))) break;
+        tc_fence_after();
+        const uint32_t wbase = smem_u32(ws + b * kWBuf);
+        for (int p = 0; p < npairs; ++p) {
+          const int it = j * npairs + p;
+          const int slot = it % kStages;
+          const uint32_t g = tmem + (uint32_t)(2 * kNW + p * kNW);
+          const uint32_t abase = smem_u32(ring + slot * kSlot);
+#pragma unroll
+          for (int s = 0; s < kRows / 16; ++s) {
+            const uint64_t ad = sdesc(abase + s * 2048, kBox, 1024);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t bd = sdesc(wbase + h * kWs + s * 32, 16, 1024);
+              mma_bf16(g, ad, bd, id2, (j > 0 || s > 0 || h > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(bar(kEmpty + slot));
+        }
+        // both CTAs learn that this CTA's GEMM 2 has consumed buffer b
+        mma_commit_mc(bar(kWFree + b), (uint16_t)0x3);
+      }
+      if (ok) mma_commit(bar(kGDone));
+    }
+    if (!ok) {
+      // let the MMAs this thread issued finish before the CTA frees its memory
+      const int f = kFinal + (warp == 3 ? 1 : 0);
+      mma_commit(bar(f));
       const long long t0 = clock64();
-      while (!mbar_try(smem_u32(&bars[kFinal]), 0) && clock64() - t0 < kTimeout) {
+      while (!mbar_try(bar(f), 0) && clock64() - t0 < kTimeout) {
       }
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
     const int q = warp - 4;             // TMEM lane quarter
-    const int r = 32 * q + lane;        // row of the tile / Z column of a G pair block
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    const int r = 16 * q + lane;        // tile row held by this lane of the M = 64 result (lane < 16)
     bool ok = true;
     for (int j = 0; j < my_tiles && ok; ++j) {
-      if (!(ok = mbar_wait(smem_u32(&bars[kD1Full]), j & 1, abort_flag))) break;
+      const int b = j & 1;
+      if (!(ok = mbar_wait(bar(kD1Full + b), (j >> 1) & 1, abort_flag))) break;
       tc_fence_after();
       float d1[kNW];
 #pragma unroll
-      for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)c, &d1[c]);
+      for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(b * kNW + c), &d1[c]);
       tmem_ld_wait();
       tc_fence_before();
-      mbar_arrive(smem_u32(&bars[kD1Free]));
-      // both CTAs' GEMM 2 of the previous tile must be done with both W halves
-      if (j > 0 && !(ok = mbar_wait(smem_u32(&bars[kWFree]), (j - 1) & 1, abort_flag))) break;
-      // W_v row r = hi part (TMEM column c) + lo part (column kHalf + c), c < 2k
+      mbar_arrive(bar(kD1Free + b));
+      // both CTAs' GEMM 2 of tile j - 2 must be done with both halves of buffer b
+      if (j >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((j - 2) >> 1) & 1, abort_flag))) break;
+      uint8_t* wb = ws + b * kWBuf;
+      if (lane < 16) {
+        // W_v row r = hi part (TMEM column c) + lo part (column kHalf + c), c < 2k
 #pragma unroll
-      for (int c = 0; c < kHalf; ++c) {
-        if (c < a.k2) {
-          const float w = d1[c] + d1[kHalf + c];
-          const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
-          const uint32_t off = (uint32_t)((r >> 6) * kKBox) + swz(view * kHalf + c, r & 63);
-          *reinterpret_cast<__nv_bfloat16*>(ws + off) = hi;
-          *reinterpret_cast<__nv_bfloat16*>(ws + kWs + off) = lo;
+        for (int c = 0; c < kHalf; ++c) {
+          if (c < a.k2) {
+            const float w = d1[c] + d1[kHalf + c];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
+            const uint32_t off = swz(view * kHalf + c, r);
+            *reinterpret_cast<__nv_bfloat16*>(wb + off) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(wb + kWs + off) = lo;
+          }
         }
       }
       fence_proxy_async();
-      mbar_arrive(smem_u32(&bars[kEpiSync]));
+      mbar_arrive(bar(kEpiSync));
       if (threadIdx.x == 128) {
-        // all 128 rows written: push this view's rows of both K-boxes (hi and
-        // lo) into the peer's operand, then release our own GEMM 2
-        if (!(ok = mbar_wait(smem_u32(&bars[kEpiSync]), j & 1, abort_flag))) break;
-        const uint32_t pbar = map_peer(smem_u32(&bars[kWPeer]), peer);
+        // all rows written: push this view's rows (hi and lo) into the peer's
+        // buffer b, then release our own GEMM 2
+        if (!(ok = mbar_wait(bar(kEpiSync), j & 1, abort_flag))) break;
+        const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int kb = 0; kb < 2; ++kb) {
-            const uint32_t src = smem_u32(ws + h * kWs + kb * kKBox + view * kWHalf);
-            bulk_to_peer(map_peer(src, peer), src, kWHalf, pbar);
-          }
-        mbar_arrive(smem_u32(&bars[kWReady]));
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t src = smem_u32(wb + h * kWs + view * kWHalf);
+          bulk_to_peer(map_peer(src, peer), src, kWHalf, pbar);
+        }
+        mbar_arrive(bar(kWReady + b));
       }
     }
-    if (ok && my_tiles > 0 && mbar_wait(smem_u32(&bars[kGDone]), 0, abort_flag)) {
+    const uint32_t g_lane_off = lane_off;
+    const int rg = 32 * q + lane;       // Z column of a G pair block (M = 128 layout)
+    if (ok && my_tiles > 0 && mbar_wait(bar(kGDone), 0, abort_flag)) {
       tc_fence_after();
       const int D0 = a.d[0];
       const int D = a.d[0] + a.d[1];
@@ -424,9 +448,9 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       for (int p = 0; p < npairs; ++p) {
         float g[kNW];
 #pragma unroll
-        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(kNW + p * kNW + c), &g[c]);
+        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + g_lane_off + (uint32_t)(2 * kNW + p * kNW + c), &g[c]);
         tmem_ld_wait();
-        const int col = 128 * p + r;
+        const int col = 128 * p + rg;
         if (col < a.d[view]) {
           float* o = out + (int64_t)(view * D0 + col) * k4;
 #pragma unroll
@@ -436,8 +460,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           }
         }
       }
-      // the peer's last end-of-GEMM-2 signal must have reached us before we leave
-      mbar_wait(smem_u32(&bars[kWFree]), (my_tiles - 1) & 1, abort_flag);
+      // the peer's last end-of-GEMM-2 signals (tiles T - 2 and T - 1, not
+      // waited in the loop) must have reached us before we leave
+      for (int j = std::max(0, my_tiles - 2); j < my_tiles; ++j)
+        mbar_wait(bar(kWFree + (j & 1)), (j >> 1) & 1, abort_flag);
     } else if (my_tiles > 0) {
       // rows of a CTA that stopped early are not trustworthy: zero them so the
       // reduction stays finite; the error flag reports the failure
@@ -460,79 +486,98 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
 // Phi image: per view, K-boxes of 64 columns; B rows 0..23 hold the bf16 hi
 // parts of the 2k columns [U | eta], rows 24..47 their lo parts (x - hi);
 // 128B-swizzled.  Phi is then rounded in place to hi + lo so that the point
-// the pass evaluates is exactly the point the solver holds.
-__global__ void phi_image_kernel(double* __restrict__ Phi, int d, int k2, int kboxes, uint8_t* __restrict__ img) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (kbox, row, elem)
-  if (e >= kboxes * kNW * 64) return;
-  const int kb = e / (kNW * 64);
-  const int rem = e % (kNW * 64);
-  const int row = rem / 64, el = rem % 64;
-  const int j = kb * 64 + el;  // data column
-  const int c = row < kHalf ? row : row - kHalf;
-  __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-  if (j < d && c < k2) {
-    const double x = Phi[(int64_t)j * k2 + c];
-    const __nv_bfloat16 hi = __double2bfloat16(x);
-    const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
-    v = row < kHalf ? hi : lo;
-  }
-  *reinterpret_cast<__nv_bfloat16*>(img + (int64_t)kb * kKBox + swz(row, el)) = v;
-}
-
-__global__ void phi_round_kernel(double* __restrict__ Phi, int64_t len) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= len) return;
-  const double x = Phi[i];
+// the pass evaluates is exactly the point the solver holds.  One thread per
+// element of Phi (both views in one launch); the padding of the image is
+// zero from its allocation and never written.
+__global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__ Phiy, int dx, int dy, int k2,
+                                 uint8_t* __restrict__ img) {
+  const int v = blockIdx.y;
+  const int d = v == 0 ? dx : dy;
+  double* Phi = v == 0 ? Phix : Phiy;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (data column j, Phi column c)
+  if (e >= d * k2) return;
+  const int j = e / k2, c = e - j * k2;
+  const double x = Phi[e];
   const __nv_bfloat16 hi = __double2bfloat16(x);
   const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
-  Phi[i] = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
+  uint8_t* base = img + (int64_t)v * kPhiView + (int64_t)(j >> 6) * kKBox;
+  *reinterpret_cast<__nv_bfloat16*>(base + swz(c, j & 63)) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(base + swz(kHalf + c, j & 63)) = lo;
+  Phi[e] = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
 }
 
-// G (D x 4k, FP64) = sum over CTAs of the FP32 partials, in CTA order, with
-// Neumaier-compensated FP32 arithmetic (error ~2 ulp of the sum, far below
-// the partials' own rounding) and 8 independent loads in flight per thread.
-__global__ void tc_reduce_kernel(const float* __restrict__ part, int ctas, int64_t len, double* __restrict__ G,
-                                 const int* done) {
+// G (D x 4k, FP64) = sum over clusters of the FP32 partials, in cluster
+// order.  A CTA covers 256 consecutive entries: 64 float4 groups x 4 quarters
+// of the partials; each quarter is summed with Neumaier-compensated FP32
+// arithmetic (8 loads in flight), then the four (sum, compensation) pairs are
+// combined in fixed order.  Error ~2 ulp of the sum, far below the partials'
+// own rounding.
+__global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
+                                                        double* __restrict__ G, const int* done) {
   if (done != nullptr && *done) return;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f, comp = 0.f;
-    for (int c0 = 0; c0 < ctas; c0 += 8) {
-      float v[8];
+  __shared__ float4 red_s[4][64], red_c[4][64];
+  const int g = threadIdx.x & 63, qtr = threadIdx.x >> 6;
+  const int64_t e4 = (int64_t)blockIdx.x * 64 + g;  // float4 group
+  const bool in = 4 * e4 < len;
+  const int per = (nparts + 3) / 4;
+  const int p0 = qtr * per, p1 = min(nparts, p0 + per);
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f};
+  if (in) {
+    const float4* src = reinterpret_cast<const float4*>(part) + e4;
+    const int64_t stride4 = len / 4;
+    for (int b0 = p0; b0 < p1; b0 += 8) {
+      float4 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = (c0 + u < ctas) ? part[(int64_t)(c0 + u) * len + e] : 0.f;
+      for (int u = 0; u < 8; ++u) v[u] = (b0 + u < p1) ? src[(int64_t)(b0 + u) * stride4] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const float t = s + v[u];
-        comp += (fabsf(s) >= fabsf(v[u])) ? ((s - t) + v[u]) : ((v[u] - t) + s);
-        s = t;
+        const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float t = s[i] + x[i];
+          cp[i] += (fabsf(s[i]) >= fabsf(x[i])) ? ((s[i] - t) + x[i]) : ((x[i] - t) + s[i]);
+          s[i] = t;
+        }
       }
     }
-    G[e] = (double)s + (double)comp;
+  }
+  red_s[qtr][g] = make_float4(s[0], s[1], s[2], s[3]);
+  red_c[qtr][g] = make_float4(cp[0], cp[1], cp[2], cp[3]);
+  __syncthreads();
+  if (qtr == 0 && in) {
+    double out[4];
+    for (int i = 0; i < 4; ++i) out[i] = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      const float4 a = red_s[q][g], c = red_c[q][g];
+      out[0] += (double)a.x + (double)c.x;
+      out[1] += (double)a.y + (double)c.y;
+      out[2] += (double)a.z + (double)c.z;
+      out[3] += (double)a.w + (double)c.w;
+    }
+    for (int i = 0; i < 4; ++i)
+      if (4 * e4 + i < len) G[4 * e4 + i] = out[i];
   }
 }
 
-// W^T W = Phi_bd^T G (4k x 4k), Phi_bd = blkdiag(Phi_x, Phi_y), in FP64.
+// W^T W = Phi_bd^T G (4k x 4k), Phi_bd = blkdiag(Phi_x, Phi_y), in FP64: one
+// warp per entry, lanes over rows, fixed shuffle tree.
 __global__ void tc_gram_kernel(const double* __restrict__ Phix, const double* __restrict__ Phiy, int dx, int dy,
                                int k2, const double* __restrict__ G, double* __restrict__ Gram, const int* done) {
   if (done != nullptr && *done) return;
   const int k4 = 2 * k2;
-  const int e = blockIdx.x;  // one output per CTA, threads split the sum
-  const int a = e / k4, b = e % k4;
+  const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (e >= k4 * k4) return;
+  const int a = e / k4, b = e - a * k4;
   const int v = a < k2 ? 0 : 1;
   const int ca = a - v * k2;
   const double* Phi = v == 0 ? Phix : Phiy;
   const int d = v == 0 ? dx : dy;
   const int off = v == 0 ? 0 : dx;
   double s = 0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) s += Phi[(int64_t)j * k2 + ca] * G[(int64_t)(off + j) * k4 + b];
-  __shared__ double red[128];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) Gram[e] = red[0];
+  for (int j = lane; j < d; j += 32) s += Phi[(int64_t)j * k2 + ca] * G[(int64_t)(off + j) * k4 + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) Gram[e] = s;
 }
 
 }  // namespace tc
@@ -600,20 +645,16 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   const int k2 = 2 * p.k, k4 = 4 * p.k;
   tc::Args a{};
   a.n = p.n;
-  int kb_total = 0;
   for (int v = 0; v < 2; ++v) {
     a.d[v] = p.v[v].d;
     a.pairs[v] = ceil_div(p.v[v].d, 128);
-    const int kboxes = 2 * a.pairs[v];
-    // view v's image starts at v * kPhiView (K-boxes of 64 columns)
-    tc::phi_image_kernel<<<ceil_div(kboxes * tc::kNW * 64, 256), 256, 0, st>>>(
-        p.v[v].Phi, p.v[v].d, k2, kboxes, p.tc_img + v * tc::kPhiView);
-    GB_CHECK_LAUNCH();
-    tc::phi_round_kernel<<<ceil_div((int64_t)p.v[v].d * k2, 256), 256, 0, st>>>(p.v[v].Phi, (int64_t)p.v[v].d * k2);
-    GB_CHECK_LAUNCH();
-    kb_total += kboxes;
   }
-  (void)kb_total;
+  {
+    const int dmax = std::max(p.v[0].d, p.v[1].d);
+    tc::phi_image_kernel<<<dim3(ceil_div(dmax * k2, 256), 2), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d,
+                                                                           p.v[1].d, k2, p.tc_img);
+    GB_CHECK_LAUNCH();
+  }
   a.k2 = k2;
   a.ntiles = ceil_div(p.n, tc::kRows);
   a.phi_img = p.tc_img;
@@ -643,13 +684,16 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   cfg.gridDim = dim3(2 * ncl, 1, 1);
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(p.tc_map[0]);
   const CUtensorMap* my = reinterpret_cast<const CUtensorMap*>(p.tc_map[1]);
+  if (p.kev0 != nullptr) GB_CUDA(cudaEventRecord(p.kev0, st));
   GB_CUDA(cudaLaunchKernelEx(&cfg, tc::tc_pass_kernel, *mx, *my, a));
   GB_CHECK_LAUNCH();
+  if (p.kev1 != nullptr) GB_CUDA(cudaEventRecord(p.kev1, st));
   const int grid = ncl;  // partial slabs, one per cluster
   const int64_t len = (int64_t)p.D * k4;
   tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, p.G, done);
   GB_CHECK_LAUNCH();
-  tc::tc_gram_kernel<<<k4 * k4, 128, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2, p.G, p.Gram, done);
+  tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
+                                                                  p.G, p.Gram, done);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -28,6 +28,9 @@ struct DevState {
   int max_iter;
   int ntrials;
   int qsyl_valid;
+  double dacc[2][6];                // direction: per-view inner products
+  int dcount;                       // direction: views finished this iteration
+  int ls_count;                     // line search: trials finished this iteration
 };
 
 // One generalized Stiefel factor: the data view it is built on and the
@@ -44,6 +47,8 @@ struct View {
   float* Rinv32 = nullptr;  // FP32 copy for the low-precision path
   float* Minv_hi = nullptr; // M^{-1} = R^{-1} R^{-T} as a float pair (low-precision plans)
   float* Minv_lo = nullptr;
+  float* RRh = nullptr;     // d x 2k: RR[:, 0:2k] as a float pair (input of the M^{-1} product)
+  float* RRl = nullptr;
   double* Phi = nullptr;    // d x 2k: [U | eta]
   float* Phi32 = nullptr;   // FP32 copy of Phi for the low-precision pass
   double* Meta = nullptr;   // d x k: M eta
@@ -105,11 +110,15 @@ struct Plan {
   DevState* st_host = nullptr;  // pinned mirror for read-back
   double* phigram = nullptr;    // per view 2k x 2k Gram of Phi
   double* phipart = nullptr;    // partials of phigram
+  double* phired = nullptr;     // per view 2k x 2k Gram of Phi (summed partials)
   double* cross = nullptr;      // per view 4k x 4k cross Gram (final)
   double* crosspart = nullptr;  // partials
   int thinCtas = 0;
   double* history = nullptr;    // 3 (max_iter + 1)
   double* mt_part = nullptr;    // slice partials of mat_thin
+  float* dfx = nullptr;         // 2 x dmax x 2k floats: split blocks for double-float products
+  double* ls_f = nullptr;       // line-search trial values (kNTrials)
+  double* ls_L = nullptr;       // line-search trial factors (kNTrials x 2 x kMaxK^2)
   double* ws = nullptr;         // FP64 scratch for dense routines
   int64_t ws_len = 0;
   int* flag = nullptr;          // device error flag (NOT_SPD etc.)
@@ -123,7 +132,9 @@ struct Plan {
   const void* tc_map_for[2] = {nullptr, nullptr};
   uint8_t* tc_img = nullptr;
   float* tc_part = nullptr;
-  int tc_clusters = 0;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
+  int tc_clusters = 0;
+  cudaEvent_t kev0 = nullptr;  // when set: recorded around the data kernel of the next pass
+  cudaEvent_t kev1 = nullptr;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
 };
 
 // sketch.cu
@@ -137,27 +148,39 @@ int srht_apply(Plan& p, int view, cudaStream_t st);
 // C = A^T B + diag_add I over m rows.  df = true: double-float arithmetic
 // (~2^-44 relative per product instead of FP64's 2^-53) at FP32 rates, used
 // where the data itself is FP32/BF16 and C only shapes a preconditioner.
+// tri = true (double-float only): A and B lower triangular, zero rows skipped.
 int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1,
             int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
-            bool df = false);
+            bool df = false, bool tri = false);
 int cholesky_upper(double* A, int d, int* flag, cudaStream_t st);
 // C = A^T A + lambda I (A: m x d FP64, row stride lda) with the split-K
 // partials in a static device scratch instead of plan memory; d <= noalloc_max_d().
 int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, double* C, cudaStream_t st);
 int noalloc_max_d();
-// Double-float M^{-1} = R^{-1} R^{-T} (hi + lo float pairs, d x d) and its
-// application Y_v[:, 0:c] = M^{-1} X_v[:, 0:c] for all views in one launch.
-struct MinvDfArgs {
-  const float* hi[2];
-  const float* lo[2];
-  const double* X[2];
-  double* Y[2];
-  int d[2];
-  int ldx, ldy, c;
+// Double-float matrices (hi + lo float pairs) times FP64 thin blocks:
+// Y_b[:, 0:c] = A_b X_b[:, 0:c] for up to two problems in one launch
+// (A_b m x K row-major; c even, <= 40; X rows 16-byte aligned).
+struct DfmvProblem {
+  const float* hi;   // A, m x K
+  const float* lo;
+  const float* Xh;   // X, K x c (row stride ldx floats)
+  const float* Xl;
+  double* Y;         // m x c (row stride ldy doubles)
+  int m, K;
+  int ldx, ldy;
+};
+struct DfmvArgs {
+  DfmvProblem p[2];
+  int c;
   const int* done;
 };
+int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st);
+// hi/lo split of the first c columns of X (rows x ldx) into rows x c floats
+int split_rows(const double* X, int rows, int c, int ldx, float* hi, float* lo, cudaStream_t st);
+// hi/lo split of A (r x c, row-major) or of its transpose (c x r)
+int split_df(const double* A, int r, int c, bool trans, float* hi, float* lo, cudaStream_t st);
+// M^{-1} = R^{-1} R^{-T} as a double-float pair (d x d)
 int minv_df_build(const double* Rinv, int d, float* hi, float* lo, double* ws, int64_t ws_len, cudaStream_t st);
-int minv_df(const MinvDfArgs& a, int nviews, cudaStream_t st);
 // Rinv = R^{-1} (upper triangular, d x d); ws holds at least d * d doubles.
 int tri_inverse_upper(const double* R, double* Rinv, int d, double* ws, int64_t ws_len, cudaStream_t st);
 int to_f32(const double* a, float* b, int64_t len, cudaStream_t st);
@@ -171,6 +194,8 @@ int mat_thin(const T* A, int ra, int ca, bool transA, bool tri, const double* B,
 // pass.cu
 int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols = 0,
                const int* done = nullptr);
+int fused_pass_cores(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols,
+               const int* done);
 int exact_gram(Plan& p, int view, double* out, cudaStream_t st);
 int lda_class_stats(Plan& p, cudaStream_t st);
 

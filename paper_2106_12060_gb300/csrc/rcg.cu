@@ -285,8 +285,25 @@ __global__ void thin_gram_kernel(ThinArgs a) {
   }
 }
 
+// out[v][e] = sum over row blocks b of part[v][b][e]: one warp per output,
+// lanes over blocks, a fixed shuffle tree (deterministic), FP64.
+__global__ void reduce_blocks_kernel(const double* __restrict__ part, int nblk, int len, int nviews,
+                                     double* __restrict__ out, const int* done) {
+  if (done != nullptr && *done) return;
+  const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (gw >= nviews * len) return;
+  const int v = gw / len, e = gw - v * len;
+  const double* pv = part + (int64_t)v * nblk * len + e;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += pv[(int64_t)b * len];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[gw] = s;
+}
+
 static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const double* B0, const double* B1,
-                     int ldb, int ca, int cb, double* part, cudaStream_t st, const int* done) {
+                     int ldb, int ca, int cb, double* part, cudaStream_t st, const int* done,
+                     double* out = nullptr) {
   ThinArgs a{};
   a.A[0] = A0;
   a.A[1] = A1;
@@ -309,6 +326,12 @@ static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const
   // blocks past a view's rows write zeros (nr <= 0 loops are empty)
   thin_gram_kernel<<<dim3(a.nblk, p.nviews), 256, smem, st>>>(a);
   GB_CHECK_LAUNCH();
+  if (out != nullptr) {
+    // partials summed by many CTAs, so the single-CTA consumers read one block
+    const int64_t warps = (int64_t)p.nviews * ca * cb;
+    reduce_blocks_kernel<<<ceil_div(warps * 32, 256), 256, 0, st>>>(part, a.nblk, ca * cb, p.nviews, out, done);
+    GB_CHECK_LAUNCH();
+  }
   return GBCCA_OK;
 }
 
@@ -339,6 +362,8 @@ struct LSArgs {
   int l;
   double* history;
   int max_iter;
+  double* ls_f;           // kNTrials trial values
+  double* ls_L;           // kNTrials x 2 x kMaxK^2 trial factors
 };
 
 // f(t) for one trial, evaluated by one warp from the coefficient matrices.
@@ -384,233 +409,162 @@ __device__ double ls_eval(const LSArgs& a, const double* coef, double t, double*
   return f;
 }
 
-// Trials are evaluated in groups of kLSWarps (one per warp).  Group 0 holds
-// t = 0 (the Armijo reference, evaluated at the point of this pass), t0 and
-// the first expansions 2 t0 .. 2^6 t0; later groups hold the remaining
-// expansions or the backtracking steps t0 2^-j.  The decision follows the
-// sequential rule exactly: the first j in 0..24 with Armijo at t0 2^-j is
-// accepted; only if j = 0, t doubles while f keeps decreasing and Armijo
-// holds (at most 10 doublings).
+// Every trial step of the sequential Armijo rule is evaluated at once, one
+// CTA (one warp) per trial, so the FP64 work of the k x k Cholesky factors
+// is spread over kNTrials SMs instead of queueing on one SM's FP64 pipe:
+//   trial 0: t = 0 (the Armijo reference, at the point of this pass),
+//   trials 1 .. kMaxExpand + 1: t0 2^0 .. t0 2^kMaxExpand (t0 and its expansions),
+//   trials kMaxExpand + 2 ..: t0 2^-1 .. t0 2^-(kMaxLS - 1) (backtracking).
+// Each CTA stores f(t) and the factors L_v(t)^{-T} of its trial; the last CTA
+// to finish applies the sequential rule (first accepted backtracking step; or
+// t0 and then doublings while f decreases and Armijo holds) to the stored
+// values, so the accepted step is exactly the one of the sequential search.
+__device__ __forceinline__ double ls_trial_t(int i, double t0) {
+  if (i == 0) return 0.0;
+  if (i <= kMaxExpand + 1) return ldexp(t0, i - 1);
+  return ldexp(t0, -(i - kMaxExpand - 1));
+}
+
 __global__ void linesearch_kernel(LSArgs a) {
   DevState* st = a.st;
   if (st->done) return;
   extern __shared__ double lsm[];
   const int k = a.k, kk = k * k, k2 = 2 * k;
+  const int i = blockIdx.x, lane = threadIdx.x;
+  const bool zero_step = st->force_zero_step != 0;
   double* coef = lsm;                       // 9 kk
   double* phig = coef + 9 * kk;             // 2 views x 4 kk
-  double* work = phig + 8 * kk;             // kLSWarps x (4 kk + 2 kMaxK)
-  __shared__ double gt[kLSWarps], gf[kLSWarps];
+  double* w = phig + 8 * kk;                // 4 kk + 2 kMaxK
   __shared__ double mu_s[kMaxK];
-  __shared__ int ctl[5];                    // 0: phase, 1: next index, 2: accepted (-1 none), 3: finished,
-                                            // 4: warp whose buffers hold the accepted trial (-1: none)
-  __shared__ double sh_f0, sh_tacc, sh_facc;
-  if (threadIdx.x < k) mu_s[threadIdx.x] = st->mu[threadIdx.x];
-  for (int v = 0; v < a.nviews; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * kk, a.nblk, 4 * kk,
-                                                phig + v * 4 * kk);
-  // coefficient matrices: Gram_v(t) = A + t B + t^2 C, Cross(t) = X0 + t X1 + t^2 X2
-  const int NC = a.NC;
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    int i = e / k, j = e % k;
-    // block (bi, bj), entry (i, j) of the pass Gram / of Phi^T Phi
-    auto G = [&](int bi, int bj) { return a.Gram[(bi * k + i) * NC + bj * k + j]; };
-    for (int v = 0; v < a.nviews; ++v) {
-      const double* pg = phig + v * 4 * kk;  // 2k x 2k
-      auto P = [&](int bi, int bj) { return pg[(bi * k + i) * k2 + bj * k + j]; };
-      double lam = st->lam[v];
-      int b0 = 2 * v;  // pass blocks of this view: [P_U, P_eta] or [Q_V, Q_eta]
-      coef[(3 * v + 0) * kk + e] = G(b0, b0) + lam * P(0, 0);
-      coef[(3 * v + 1) * kk + e] = G(b0, b0 + 1) + G(b0 + 1, b0) + lam * (P(0, 1) + P(1, 0));
-      coef[(3 * v + 2) * kk + e] = G(b0 + 1, b0 + 1) + lam * P(1, 1);
-    }
-    if (a.kind == kCCA) {
-      coef[6 * kk + e] = G(0, 2);
-      coef[7 * kk + e] = G(0, 3) + G(1, 2);
-      coef[8 * kk + e] = G(1, 3);
-    } else {
-      // S_B(t) = (Yhat W + t Yhat eta)^T (Yhat W + t Yhat eta)
-      double s0 = 0, s1 = 0, s2 = 0;
-      for (int c = 0; c < a.l; ++c) {
-        double wi = a.YPhi[c * k2 + i], wj = a.YPhi[c * k2 + j];
-        double ei = a.YPhi[c * k2 + k + i], ej = a.YPhi[c * k2 + k + j];
-        s0 += wi * wj;
-        s1 += wi * ej + ei * wj;
-        s2 += ei * ej;
+  __shared__ int last;
+  if (!zero_step || i == 0) {
+    if (lane < k) mu_s[lane] = st->mu[lane];
+    for (int e = lane; e < a.nviews * 4 * kk; e += blockDim.x) phig[e] = a.phipart[e];
+    __syncwarp();
+    // coefficient matrices: Gram_v(t) = A + t B + t^2 C, Cross(t) = X0 + t X1 + t^2 X2
+    const int NC = a.NC;
+    for (int e = lane; e < kk; e += blockDim.x) {
+      const int r = e / k, c = e % k;
+      auto G = [&](int bi, int bj) { return a.Gram[(bi * k + r) * NC + bj * k + c]; };
+      for (int v = 0; v < a.nviews; ++v) {
+        const double* pg = phig + v * 4 * kk;  // 2k x 2k
+        auto P = [&](int bi, int bj) { return pg[(bi * k + r) * k2 + bj * k + c]; };
+        const double lam = st->lam[v];
+        const int b0 = 2 * v;  // pass blocks of this view: [P_U, P_eta] or [Q_V, Q_eta]
+        coef[(3 * v + 0) * kk + e] = G(b0, b0) + lam * P(0, 0);
+        coef[(3 * v + 1) * kk + e] = G(b0, b0 + 1) + G(b0 + 1, b0) + lam * (P(0, 1) + P(1, 0));
+        coef[(3 * v + 2) * kk + e] = G(b0 + 1, b0 + 1) + lam * P(1, 1);
       }
-      coef[6 * kk + e] = s0;
-      coef[7 * kk + e] = s1;
-      coef[8 * kk + e] = s2;
-    }
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* w = work + warp * (4 * kk + 2 * kMaxK);
-  const bool zero_step = st->force_zero_step != 0;
-  const double t0 = st->t0, df = st->df;
-  if (threadIdx.x == 0) {
-    ctl[0] = zero_step ? 3 : 0;  // phases: 0 first group, 1 more expansions, 2 backtracking, 3 zero step
-    ctl[1] = 1;
-    ctl[2] = -1;
-    ctl[3] = 0;
-    ctl[4] = -1;
-    sh_tacc = 0.0;
-  }
-  __syncthreads();
-  int trials = 0;
-  while (true) {
-    const int phase = ctl[0], next = ctl[1];
-    // trial t of this warp in this group (NaN marks an unused slot)
-    double t = NAN;
-    if (phase == 0) t = warp == 0 ? 0.0 : (warp <= 2 ? ldexp(t0, warp - 1) : NAN);  // 0, t0, 2 t0
-    else if (phase == 1) t = (next + warp <= kMaxExpand) ? ldexp(t0, next + warp) : NAN;
-    else if (phase == 2) t = (next + warp < kMaxLS) ? ldexp(t0, -(next + warp)) : NAN;
-    else t = warp == 0 ? 0.0 : NAN;
-    double f = INFINITY;
-    if (t == t) f = ls_eval(a, coef, t, w, mu_s);
-    if (lane == 0) {
-      gt[warp] = t;
-      gf[warp] = f;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      trials += 1;
-      if (phase == 3) {
-        sh_f0 = gf[0];
-        sh_tacc = 0.0;
-        sh_facc = gf[0];
-        ctl[2] = 0;
-        ctl[3] = 1;
-        ctl[4] = 0;
-      } else if (phase == 0) {
-        sh_f0 = gf[0];
-        const double f0 = gf[0];
-        if (gf[1] <= f0 + kC1 * gt[1] * df) {
-          // t0 accepted; expand while f decreases and Armijo holds
-          sh_tacc = gt[1];
-          sh_facc = gf[1];
-          ctl[2] = 1;
-          ctl[4] = 1;
-          if (gf[2] < gf[1] && gf[2] <= f0 + kC1 * gt[2] * df) {
-            sh_tacc = gt[2];
-            sh_facc = gf[2];
-            ctl[4] = 2;
-            ctl[0] = 1;  // keep doubling from 4 t0
-            ctl[1] = 2;
-          } else {
-            ctl[3] = 1;
-          }
-        } else {
-          ctl[0] = 2;  // backtrack from t0 / 2
-          ctl[1] = 1;
-        }
-      } else if (phase == 1) {
-        const double f0 = sh_f0;
-        bool stop = false;
-        int e = 0;
-        for (; e < kLSWarps; ++e) {
-          if (!(gt[e] == gt[e])) {
-            stop = true;
-            break;
-          }
-          if (gf[e] < sh_facc && gf[e] <= f0 + kC1 * gt[e] * df) {
-            sh_tacc = gt[e];
-            sh_facc = gf[e];
-          } else {
-            stop = true;
-            break;
-          }
-        }
-        ctl[4] = e > 0 ? e - 1 : -1;  // accepted trial of this group, or of an earlier one
-        ctl[1] = next + kLSWarps;
-        if (stop || next + kLSWarps > kMaxExpand) ctl[3] = 1;
+      if (a.kind == kCCA) {
+        coef[6 * kk + e] = G(0, 2);
+        coef[7 * kk + e] = G(0, 3) + G(1, 2);
+        coef[8 * kk + e] = G(1, 3);
       } else {
-        const double f0 = sh_f0;
-        for (int e = 0; e < kLSWarps; ++e) {
-          if (!(gt[e] == gt[e])) break;
-          if (gf[e] <= f0 + kC1 * gt[e] * df) {
-            sh_tacc = gt[e];
-            sh_facc = gf[e];
-            ctl[2] = 1;
-            ctl[4] = e;
-            break;
-          }
+        // S_B(t) = (Yhat W + t Yhat eta)^T (Yhat W + t Yhat eta)
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int cl = 0; cl < a.l; ++cl) {
+          const double wi = a.YPhi[cl * k2 + r], wj = a.YPhi[cl * k2 + c];
+          const double ei = a.YPhi[cl * k2 + k + r], ej = a.YPhi[cl * k2 + k + c];
+          s0 += wi * wj;
+          s1 += wi * ej + ei * wj;
+          s2 += ei * ej;
         }
-        ctl[1] = next + kLSWarps;
-        if (ctl[2] >= 0 || next + kLSWarps >= kMaxLS) ctl[3] = 1;
+        coef[6 * kk + e] = s0;
+        coef[7 * kk + e] = s1;
+        coef[8 * kk + e] = s2;
       }
     }
-    __syncthreads();
-    if (ctl[3]) break;
+    __syncwarp();
+    const double t = ls_trial_t(i, st->t0);
+    const double f = ls_eval(a, coef, t, w, mu_s);
+    // factors L_v(t)^{-T} of this trial (row-major), kept for the decision
+    double* Lout = a.ls_L + (int64_t)i * 2 * kMaxK * kMaxK;
+    double* Gx = w;
+    double* Lt = w + 2 * kk;
+    double* Li = w + 3 * kk;
+    double* ix = w + 4 * kk;
+    if (a.kind == kCCA) {
+      warp_lower_inv(Gx, ix, Lt, k);
+      for (int e = lane; e < kk; e += 32) {
+        const int r = e / k, c = e % k;
+        Lout[e] = Lt[c * k + r];
+        Lout[kMaxK * kMaxK + e] = Li[c * k + r];
+      }
+    } else {
+      for (int e = lane; e < kk; e += 32) {
+        const int r = e / k, c = e % k;
+        Lout[e] = Li[c * k + r];
+      }
+    }
+    if (lane == 0) a.ls_f[i] = f;
   }
-  if (ctl[2] < 0) {
-    if (threadIdx.x == 0) {
+  // the last CTA to finish decides
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) last = atomicAdd(&st->ls_count, 1) == (int)gridDim.x - 1;
+  __syncwarp();
+  if (!last) return;
+  __threadfence();
+  if (lane == 0) st->ls_count = 0;
+  volatile const double* fv = a.ls_f;
+  const double t0 = st->t0, df = st->df;
+  const double f0 = fv[0];
+  int acc = -1, trials = 1;
+  if (zero_step) {
+    acc = 0;
+  } else if (fv[1] <= f0 + kC1 * t0 * df) {
+    acc = 1;
+    trials = 2;
+    for (int e = 2; e <= kMaxExpand + 1; ++e) {
+      const double te = ls_trial_t(e, t0);
+      ++trials;
+      if (fv[e] < fv[acc] && fv[e] <= f0 + kC1 * te * df)
+        acc = e;
+      else
+        break;
+    }
+  } else {
+    trials = 2;
+    for (int e = kMaxExpand + 2; e < (int)gridDim.x; ++e) {
+      ++trials;
+      if (fv[e] <= f0 + kC1 * ls_trial_t(e, t0) * df) {
+        acc = e;
+        break;
+      }
+    }
+  }
+  if (acc < 0) {
+    if (lane == 0) {
       st->stalled = 1;
       st->done = 1;
       st->ls_trials = trials;
     }
     return;
   }
-  // factors at the accepted step: Linv_v = L_v(t)^{-T} (upper), stored row-major.
-  // The warp that evaluated the accepted trial still holds L_x, L_y and the
-  // inverse of the second factor; otherwise warp 0 recomputes them.
-  const double t = sh_tacc;
-  const int wacc = ctl[4];
-  if ((wacc >= 0 && warp == wacc) || (wacc < 0 && warp == 0)) {
-    double* Gx = w;
-    double* Gy = w + kk;
-    double* Lt = w + 2 * kk;
-    double* Li = w + 3 * kk;
-    double* ix = w + 4 * kk;
-    double* iy = ix + kMaxK;
-    if (wacc >= 0) {
-      if (a.kind == kCCA) {
-        warp_lower_inv(Gx, ix, Lt, k);
-        for (int e = lane; e < kk; e += 32) {
-          int i = e / k, j = e % k;
-          st->Linv[0][e] = Lt[j * k + i];
-          st->Linv[1][e] = Li[j * k + i];
-        }
-      } else {
-        for (int e = lane; e < kk; e += 32) {
-          int i = e / k, j = e % k;
-          st->Linv[0][e] = Li[j * k + i];
-        }
-      }
-      __syncwarp();
-    } else {
-      for (int v = 0; v < a.nviews; ++v) {
-        for (int e = lane; e < kk; e += 32)
-          Gx[e] = coef[(3 * v) * kk + e] + t * coef[(3 * v + 1) * kk + e] + t * t * coef[(3 * v + 2) * kk + e];
-        __syncwarp();
-        warp_chol(Gx, k, ix);
-        warp_lower_inv(Gx, ix, Li, k);
-        for (int e = lane; e < kk; e += 32) {
-          int i = e / k, j = e % k;
-          st->Linv[v][e] = Li[j * k + i];  // (L^{-1})^T
-        }
-        __syncwarp();
-      }
+  const double t = ls_trial_t(acc, t0);
+  const volatile double* L = a.ls_L + (int64_t)acc * 2 * kMaxK * kMaxK;
+  for (int e = lane; e < kk; e += 32) {
+    st->Linv[0][e] = L[e];
+    if (a.kind == kCCA) st->Linv[1][e] = L[kMaxK * kMaxK + e];
+  }
+  __syncwarp();
+  if (a.kind == kLDA) {
+    // YW+ = (Yhat W + t Yhat eta) L^{-T}
+    for (int e = lane; e < a.l * k; e += 32) {
+      const int cl = e / k, c = e % k;
+      double s = 0;
+      for (int q = 0; q < k; ++q) s += (a.YPhi[cl * k2 + q] + t * a.YPhi[cl * k2 + k + q]) * st->Linv[0][q * k + c];
+      st->YW[e] = s;
     }
-    (void)Gy;
-    (void)iy;
-    if (a.kind == kLDA) {
-      // YW+ = (Yhat W + t Yhat eta) L^{-T}
-      for (int e = lane; e < a.l * k; e += 32) {
-        int c = e / k, j = e % k;
-        double s = 0;
-        for (int q = 0; q < k; ++q)
-          s += (a.YPhi[c * k2 + q] + t * a.YPhi[c * k2 + k + q]) * st->Linv[0][q * k + j];
-        st->YW[e] = s;
-      }
-    }
-    if (lane == 0) {
-      st->t = t;
-      st->f = sh_facc;
-      st->ls_trials = trials;
-      if (!zero_step) {
-        st->t_prev = t;
-        st->df_prev = st->df;
-        st->iter += 1;
-      }
+  }
+  if (lane == 0) {
+    st->t = t;
+    st->f = fv[acc];
+    st->ls_trials = trials;
+    if (!zero_step) {
+      st->t_prev = t;
+      st->df_prev = st->df;
+      st->iter += 1;
     }
   }
 }
@@ -623,6 +577,8 @@ struct UpdArgs {
   double* Phi[2];
   double* LL[2];
   double* RR[2];
+  float* RRh[2];        // optional float-pair copy of RR[:, 0:2k]
+  float* RRl[2];
   const double* Meta[2];
   const double* gold[2];
   const double* Mgold[2];
@@ -631,55 +587,68 @@ struct UpdArgs {
   const double* Yhat;   // FDA (l x d)
 };
 
-// row j of view v: U+ = (U + t eta) Lv^{-T}; B U+; Euclidean gradient.
+// View v, rows of this CTA: U+ = (U + t eta) Lv^{-T}; B U+; Euclidean
+// gradient.  k threads per row (thread c of a row owns column c): the row
+// vectors u_t = U + t eta, B-image and cross term are formed once per row in
+// shared memory, then each thread forms its column of the three products.
+// The CTA covers whole rows, so U can be overwritten after a barrier.
 __global__ void update_kernel(UpdArgs a) {
   DevState* st = a.st;
   if (st->done) return;
-  const int v = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ double usm[];  // rows x 3k
   const int k = a.k, k2 = 2 * k, k4 = 4 * k;
-  if (j >= a.d[v]) return;
+  const int rows = blockDim.x / k;
+  const int v = blockIdx.y;
+  const int lr = threadIdx.x / k, c = threadIdx.x - lr * k;
+  const int j = blockIdx.x * rows + lr;
+  const bool act = lr < rows && j < a.d[v];
   const double t = st->t, lam = st->lam[v];
-  const double* Li = st->Linv[v];
   double* Phi = a.Phi[v] + (int64_t)j * k2;
-  const double* Grow = a.G + (int64_t)(a.dofs[v] + j) * a.NC;
-  double ut[kMaxK], bt[kMaxK], ct[kMaxK];
-  for (int q = 0; q < k; ++q) {
-    double e = Phi[k + q];
-    ut[q] = Phi[q] + t * e;
-    // own block: B-image; other block: cross term (CCA) - columns of W are
-    // [P_U, P_eta, Q_V, Q_eta]
-    int own = 2 * v, oth = 2 * (1 - v);
-    bt[q] = Grow[own * k + q] + t * Grow[(own + 1) * k + q] + lam * ut[q];
-    if (a.kind == kCCA) ct[q] = Grow[oth * k + q] + t * Grow[(oth + 1) * k + q];
+  double* ut = usm + lr * 3 * k;
+  double* bt = ut + k;
+  double* ct = bt + k;
+  if (act) {
+    // columns of W are [P_U, P_eta, Q_V, Q_eta]: own block gives the
+    // B-image, the other block (CCA) the cross term
+    const double* Grow = a.G + (int64_t)(a.dofs[v] + j) * a.NC;
+    const int own = 2 * v, oth = 2 * (1 - v);
+    const double u = Phi[c] + t * Phi[k + c];
+    ut[c] = u;
+    bt[c] = Grow[own * k + c] + t * Grow[(own + 1) * k + c] + lam * u;
+    if (a.kind == kCCA) ct[c] = Grow[oth * k + c] + t * Grow[(oth + 1) * k + c];
   }
+  __syncthreads();
+  if (!act) return;
+  const double* Li = st->Linv[v];
+  double u = 0, b = 0, g = 0;
+  for (int q = 0; q < k; ++q) {
+    u += ut[q] * Li[q * k + c];
+    b += bt[q] * Li[q * k + c];
+  }
+  if (a.kind == kCCA) {
+    const double* Lo = st->Linv[1 - v];
+    for (int q = 0; q < k; ++q) g += ct[q] * Lo[q * k + c];
+  } else {
+    // egrad = -S_B W+ N = -Yhat^T (Yhat W+) N
+    for (int cl = 0; cl < a.l; ++cl) g += a.Yhat[(int64_t)cl * a.d[0] + j] * st->YW[cl * k + c];
+  }
+  g = -g * st->mu[c];
   double* LLr = a.LL[v] + (int64_t)j * k4;
   double* RRr = a.RR[v] + (int64_t)j * k4;
   // old direction and gradient (and their M-images) move to the Gram buffers
-  for (int q = 0; q < k; ++q) {
-    LLr[2 * k + q] = Phi[k + q];
-    LLr[3 * k + q] = a.gold[v][(int64_t)j * k + q];
-    RRr[2 * k + q] = a.Meta[v][(int64_t)j * k + q];
-    RRr[3 * k + q] = a.Mgold[v][(int64_t)j * k + q];
-  }
-  for (int c = 0; c < k; ++c) {
-    double u = 0, b = 0, g = 0;
-    for (int q = 0; q < k; ++q) {
-      u += ut[q] * Li[q * k + c];
-      b += bt[q] * Li[q * k + c];
-    }
-    if (a.kind == kCCA) {
-      const double* Lo = st->Linv[1 - v];
-      for (int q = 0; q < k; ++q) g += ct[q] * Lo[q * k + c];
-      g = -g * st->mu[c];
-    } else {
-      // egrad = -S_B W+ N = -Yhat^T (Yhat W+) N
-      for (int cl = 0; cl < a.l; ++cl) g += a.Yhat[(int64_t)cl * a.d[0] + j] * st->YW[cl * k + c];
-      g = -g * st->mu[c];
-    }
-    Phi[c] = u;
-    RRr[c] = b;
-    RRr[k + c] = g;
+  LLr[2 * k + c] = Phi[k + c];
+  LLr[3 * k + c] = a.gold[v][(int64_t)j * k + c];
+  RRr[2 * k + c] = a.Meta[v][(int64_t)j * k + c];
+  RRr[3 * k + c] = a.Mgold[v][(int64_t)j * k + c];
+  Phi[c] = u;  // every thread of this row has read U (barrier above)
+  RRr[c] = b;
+  RRr[k + c] = g;
+  if (a.RRh[v] != nullptr) {
+    const float bh = (float)b, gh = (float)g;
+    a.RRh[v][(int64_t)j * k2 + c] = bh;
+    a.RRl[v][(int64_t)j * k2 + c] = (float)(b - (double)bh);
+    a.RRh[v][(int64_t)j * k2 + k + c] = gh;
+    a.RRl[v][(int64_t)j * k2 + k + c] = (float)(g - (double)gh);
   }
 }
 
@@ -729,10 +698,11 @@ __global__ void direction_kernel(DirArgs a) {
   R* T = lam + kMaxK;              // 3 kk
   R* T2 = T + 3 * kk;              // 3 kk
   R* S = T2 + 3 * kk;              // 3 kk (this view's S_g, S_e, S_o)
-  for (int v = 0; v < a.nviews; ++v)
-    sum_blocks(a.crosspart + (int64_t)v * a.nblk * 16 * kk, a.nblk, 16 * kk, X + v * 16 * kk);
+  // one CTA per view; the last CTA to finish combines the views' sums
+  const int v = blockIdx.x;
+  sum_blocks(a.crosspart + (int64_t)v * a.nblk * 16 * kk, a.nblk, 16 * kk, X + v * 16 * kk);
   double acc[6] = {0, 0, 0, 0, 0, 0};  // gg, g_Tg, Te_g, Te_Tg, dfg, dfTe
-  for (int v = 0; v < a.nviews; ++v) {
+  {
     const double* Xv = X + v * 16 * kk;
     auto XB = [&](int ab, int bb, int i, int j) { return Xv[(ab * k + i) * k4 + bb * k + j]; };
     // warm start: rotate A into the previous iteration's eigenbasis Q0 (A
@@ -871,6 +841,23 @@ __global__ void direction_kernel(DirArgs a) {
     __syncthreads();
   }
   blk_sum<6>(acc, red);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 6; ++q) st->dacc[v][q] = acc[q];
+    __threadfence();
+    last = atomicAdd(&st->dcount, 1) == a.nviews - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    volatile double* da = &st->dacc[0][0];
+    for (int q = 0; q < 6; ++q) {
+      acc[q] = 0;
+      for (int w = 0; w < a.nviews; ++w) acc[q] += da[w * 6 + q];  // view order: deterministic
+    }
+    st->dcount = 0;
+  }
   const double gg = acc[0], g_Tg = acc[1], Te_g = acc[2], Te_Tg = acc[3], dfg = acc[4], dfTe = acc[5];
   if (threadIdx.x == 0) {
     double beta = 0;
@@ -929,31 +916,30 @@ __global__ void newdir_kernel(NewArgs a) {
   DevState* st = a.st;
   if (st->done) return;
   const int v = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = a.k, k4 = 4 * k;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (row j, column c)
+  const int j = e / k, c = e - j * k;
   if (j >= a.d[v]) return;
   const double* L = a.LL[v] + (int64_t)j * k4;
   const double* R = a.RR[v] + (int64_t)j * k4;
   const double* Sg = st->S[v][0];
   const double* Se = st->S[v][1];
   const double beta = st->beta;
-  for (int c = 0; c < k; ++c) {
-    double wg = 0, bg = 0, we = 0, be = 0;
-    for (int q = 0; q < k; ++q) {
-      wg += L[q] * Sg[q * k + c];
-      bg += R[q] * Sg[q * k + c];
-      we += L[q] * Se[q * k + c];
-      be += R[q] * Se[q * k + c];
-    }
-    double g = L[k + c] - wg;          // grad = xi - Wn Sg
-    double Mg = R[k + c] - bg;         // M grad = egrad - BU Sg
-    double Te = L[2 * k + c] - we;     // T eta = eta - Wn Se
-    double MTe = R[2 * k + c] - be;    // M T eta = M eta - BU Se
-    a.gold[v][(int64_t)j * k + c] = g;
-    a.Mgold[v][(int64_t)j * k + c] = Mg;
-    a.Phi[v][(int64_t)j * 2 * k + k + c] = -g + beta * Te;
-    a.Meta[v][(int64_t)j * k + c] = -Mg + beta * MTe;
+  double wg = 0, bg = 0, we = 0, be = 0;
+  for (int q = 0; q < k; ++q) {
+    wg += L[q] * Sg[q * k + c];
+    bg += R[q] * Sg[q * k + c];
+    we += L[q] * Se[q * k + c];
+    be += R[q] * Se[q * k + c];
   }
+  const double g = L[k + c] - wg;          // grad = xi - Wn Sg
+  const double Mg = R[k + c] - bg;         // M grad = egrad - BU Sg
+  const double Te = L[2 * k + c] - we;     // T eta = eta - Wn Se
+  const double MTe = R[2 * k + c] - be;    // M T eta = M eta - BU Se
+  a.gold[v][(int64_t)j * k + c] = g;
+  a.Mgold[v][(int64_t)j * k + c] = Mg;
+  a.Phi[v][(int64_t)j * 2 * k + k + c] = -g + beta * Te;
+  a.Meta[v][(int64_t)j * k + c] = -Mg + beta * MTe;
 }
 
 // ===================================================== Rayleigh-Ritz (end)
@@ -1109,10 +1095,10 @@ int minv(Plan& p, int v, cudaStream_t st) {
   return GBCCA_OK;
 }
 
-int phigram(Plan& p, cudaStream_t st, const int* done) {
+int phigram(Plan& p, cudaStream_t st, const int* done, double* out = nullptr) {
   const int k2 = 2 * p.k;
   return thin_gram(p, p.v[0].Phi, p.nviews > 1 ? p.v[1].Phi : nullptr, k2, p.v[0].Phi,
-                   p.nviews > 1 ? p.v[1].Phi : nullptr, k2, k2, k2, p.phipart, st, done);
+                   p.nviews > 1 ? p.v[1].Phi : nullptr, k2, k2, k2, p.phipart, st, done, out);
 }
 
 int yphi(Plan& p, cudaStream_t st, int check_done) {
@@ -1134,17 +1120,19 @@ int thin_blocks(const Plan& p) {
 int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   const int k = p.k, kk = k * k;
   const int* done = &p.st->done;
-  if (e0 != nullptr) GB_CUDA(cudaEventRecord(e0, st));
-  GB_TRY(fused_pass(p, low, false, st, 0, done));
-  if (e1 != nullptr) GB_CUDA(cudaEventRecord(e1, st));
-  GB_TRY(phigram(p, st, done));
+  p.kev0 = e0;
+  p.kev1 = e1;
+  const int prc = fused_pass(p, low, false, st, 0, done);
+  p.kev0 = p.kev1 = nullptr;
+  GB_TRY(prc);
+  GB_TRY(phigram(p, st, done, p.phired));
   GB_TRY(yphi(p, st, 1));
   {
     LSArgs a{};
     a.st = p.st;
     a.Gram = p.Gram;
-    a.phipart = p.phipart;
-    a.nblk = thin_blocks(p);
+    a.phipart = p.phired;
+    a.nblk = 1;
     a.NC = p.NC;
     a.k = k;
     a.nviews = p.nviews;
@@ -1153,9 +1141,11 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
     a.l = p.l;
     a.history = p.history;
     a.max_iter = p.opt.max_iter;
-    size_t smem = sizeof(double) * (9 * kk + 8 * kk + kLSWarps * (4 * kk + 2 * kMaxK));
+    a.ls_f = p.ls_f;
+    a.ls_L = p.ls_L;
+    size_t smem = sizeof(double) * (9 * kk + 8 * kk + 4 * kk + 2 * kMaxK);
     GB_CUDA(cudaFuncSetAttribute(linesearch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    linesearch_kernel<<<1, 32 * kLSWarps, smem, st>>>(a);
+    linesearch_kernel<<<kNTrials, 32, smem, st>>>(a);
     GB_CHECK_LAUNCH();
   }
   {
@@ -1174,6 +1164,8 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
       a.Phi[v] = p.v[v].Phi;
       a.LL[v] = p.v[v].LL;
       a.RR[v] = p.v[v].RR;
+      a.RRh[v] = p.v[v].RRh;
+      a.RRl[v] = p.v[v].RRl;
       a.Meta[v] = p.v[v].Meta;
       a.gold[v] = p.v[v].gold;
       a.Mgold[v] = p.v[v].Mgold;
@@ -1182,17 +1174,29 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
       dofs += p.v[v].d;
       dmax = std::max(dmax, p.v[v].d);
     }
-    update_kernel<<<dim3(ceil_div(dmax, 64), p.nviews), 64, 0, st>>>(a);
+    const int rows = std::max(1, 128 / k);
+    update_kernel<<<dim3(ceil_div(dmax, rows), p.nviews), rows * k, sizeof(double) * 3 * k * rows, st>>>(a);
     GB_CHECK_LAUNCH();
   }
-  for (int v = 0; v < p.nviews; ++v) GB_TRY(minv(p, v, st));
+  if (p.v[0].Minv_hi != nullptr) {
+    // LL[:, 0:2k] = M^{-1} RR[:, 0:2k] for every view in one launch
+    DfmvArgs m{};
+    for (int v = 0; v < p.nviews; ++v)
+      m.p[v] = DfmvProblem{p.v[v].Minv_hi, p.v[v].Minv_lo, p.v[v].RRh, p.v[v].RRl, p.v[v].LL,
+                           p.v[v].d,       p.v[v].d,       2 * k,       4 * k};
+    m.c = 2 * k;
+    m.done = done;
+    GB_TRY(dfmv(m, p.nviews, st));
+  } else {
+    for (int v = 0; v < p.nviews; ++v) GB_TRY(minv(p, v, st));
+  }
   GB_TRY(thin_gram(p, p.v[0].LL, p.nviews > 1 ? p.v[1].LL : nullptr, 4 * k, p.v[0].RR,
-                   p.nviews > 1 ? p.v[1].RR : nullptr, 4 * k, 4 * k, 4 * k, p.crosspart, st, done));
+                   p.nviews > 1 ? p.v[1].RR : nullptr, 4 * k, 4 * k, 4 * k, p.crosspart, st, done, p.cross));
   {
     DirArgs a{};
     a.st = p.st;
-    a.crosspart = p.crosspart;
-    a.nblk = thin_blocks(p);
+    a.crosspart = p.cross;
+    a.nblk = 1;
     a.k = k;
     a.nviews = p.nviews;
     a.history = p.history;
@@ -1200,11 +1204,11 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
     size_t smem = sizeof(double) * (2 * 16 * kk + 5 * kk + 100 + 6 * 256 + 11 * kk + kMaxK);
     if (low) {
       GB_CUDA(cudaFuncSetAttribute(direction_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      direction_kernel<float><<<1, 256, smem, st>>>(a);
+      direction_kernel<float><<<p.nviews, 256, smem, st>>>(a);
     } else {
       GB_CUDA(cudaFuncSetAttribute(direction_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-      direction_kernel<double><<<1, 256, smem, st>>>(a);
+      direction_kernel<double><<<p.nviews, 256, smem, st>>>(a);
     }
     GB_CHECK_LAUNCH();
   }
@@ -1224,7 +1228,7 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
       a.d[v] = p.v[v].d;
       dmax = std::max(dmax, p.v[v].d);
     }
-    newdir_kernel<<<dim3(ceil_div(dmax, 64), p.nviews), 64, 0, st>>>(a);
+    newdir_kernel<<<dim3(ceil_div(dmax * k, 128), p.nviews), 128, 0, st>>>(a);
     GB_CHECK_LAUNCH();
   }
   return GBCCA_OK;
@@ -1245,6 +1249,8 @@ __global__ void state_init_kernel(DevState* st, double gtol, int max_iter, doubl
   st->gtol = gtol;
   st->max_iter = max_iter;
   st->qsyl_valid = 0;
+  st->dcount = 0;
+  st->ls_count = 0;
   st->lam[0] = lam0;
   st->lam[1] = lam1;
 }
@@ -1537,16 +1543,47 @@ int warm_start(Plan& p, cudaStream_t st) {
     double* Ub = x.wsU;  // dx x c
     double* part = p.crosspart;
     double* small = p.phigram;
-    // the power iterations stay in FP64 for every storage type: with FP32
-    // copies of R^{-1} (kappa ~ 1e4) the start point is visibly worse and
-    // the solve needs more iterations than the FP64 products cost
+    // Products of the power iteration.  FP64 plans: FP64 triangular / dense
+    // products.  FP32/BF16 plans: the same products with double-float copies
+    // of R_x^{-1}, R_y^{-1}, Cxy and their transposes (~2^-44 relative, at
+    // FP32 instruction rates); FP32 copies of R^{-1} (kappa ~ 1e4) give a
+    // visibly worse start point and more solver iterations.
+    const bool low = p.dtype != GBCCA_FP64 && (c & 1) == 0;
+    float* F = reinterpret_cast<float*>(p.ws);
+    const int64_t nx = (int64_t)dx * dx, ny = (int64_t)dy * dy, nc = (int64_t)dx * dy;
+    float* Rx[2] = {F, F + nx};              // R_x^{-1} hi, lo
+    float* RxT[2] = {F + 2 * nx, F + 3 * nx};
+    float* Ry[2] = {F + 4 * nx, F + 4 * nx + ny};
+    float* RyT[2] = {F + 4 * nx + 2 * ny, F + 4 * nx + 3 * ny};
+    float* Cf[2] = {F + 4 * nx + 4 * ny, F + 4 * nx + 4 * ny + nc};
+    float* CfT[2] = {F + 4 * nx + 4 * ny + 2 * nc, F + 4 * nx + 4 * ny + 3 * nc};
+    if (low) {
+      GB_TRY(split_df(x.Rinv, dx, dx, false, Rx[0], Rx[1], st));
+      GB_TRY(split_df(x.Rinv, dx, dx, true, RxT[0], RxT[1], st));
+      GB_TRY(split_df(y.Rinv, dy, dy, false, Ry[0], Ry[1], st));
+      GB_TRY(split_df(y.Rinv, dy, dy, true, RyT[0], RyT[1], st));
+      GB_TRY(split_df(Cxy, dx, dy, false, Cf[0], Cf[1], st));
+      GB_TRY(split_df(Cxy, dx, dy, true, CfT[0], CfT[1], st));
+    }
+    auto dmv = [&](float* const* A, int m, int K, const double* B, double* C) {
+      float* bh = p.dfx;
+      float* bl = p.dfx + (int64_t)K * c;
+      GB_TRY(split_rows(B, K, c, c, bh, bl, st));
+      DfmvArgs g{};
+      g.p[0] = DfmvProblem{A[0], A[1], bh, bl, C, m, K, c, c};
+      g.c = c;
+      return dfmv(g, 1, st);
+    };
     auto rx = [&](bool tr, const double* B, double* C, int cc) {
+      if (low && cc == c) return dmv(tr ? RxT : Rx, dx, dx, B, C);
       return mat_thin<double>(x.Rinv, dx, dx, tr, true, B, cc, C, cc, cc, p.mt_part, st);
     };
     auto ry = [&](bool tr, const double* B, double* C, int cc) {
+      if (low && cc == c) return dmv(tr ? RyT : Ry, dy, dy, B, C);
       return mat_thin<double>(y.Rinv, dy, dy, tr, true, B, cc, C, cc, cc, p.mt_part, st);
     };
     auto cxy = [&](bool tr, const double* B, double* C) {
+      if (low) return tr ? dmv(CfT, dy, dx, B, C) : dmv(Cf, dx, dy, B, C);
       return mat_thin<double>(Cxy, dx, dy, tr, false, B, c, C, c, c, p.mt_part, st);
     };
     rand_block_kernel<<<ceil_div(dy * c, 256), 256, 0, st>>>(Vb, dy, c, p.opt.seed);

@@ -117,12 +117,14 @@ def test_solve_separated_fp64(gb):
     assert subspace_sin(U, Uo, Sxx) < 1e-6
 
 
-def test_warm_start_is_sketched_cca(gb):
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_warm_start_is_sketched_cca(gb, dt):
+    """f64: FP64 products; f32: the double-float products of FP32/BF16 plans."""
     import torch
     n, dx, dy, k, lam, s = 2000, 30, 26, 3, 1e-2, 240
-    P = cca_latent_problem(n, dx, dy, latent=4, noise=0.6, dtype="f64", seed=6, latent_scale=SEP)
+    P = cca_latent_problem(n, dx, dy, latent=4, noise=0.6, dtype=dt, seed=6, latent_scale=SEP)
     h, g = countsketch_draws(n, s, seed=7)
-    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, s=s, h=torch.from_numpy(h).cuda(),
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, dt, lam, s=s, h=torch.from_numpy(h).cuda(),
                        g=torch.from_numpy(g).cuda())
     SX, SY = countsketch_apply(P["X64"], h, g, s), countsketch_apply(P["Y64"], h, g, s)
     _, Uw, Vw = OC.cca_whiten(SX, SY, lam, lam, k)
