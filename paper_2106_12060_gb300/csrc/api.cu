@@ -42,7 +42,7 @@ void free_plan(Plan* p) {
   if (p == nullptr) return;
   for (int v = 0; v < 2; ++v) {
     View& w = p->v[v];
-    for (void* q : {(void*)w.SZ, (void*)w.R, (void*)w.Rinv, (void*)w.Rinv32, (void*)w.Minv_hi, (void*)w.Minv_lo, (void*)w.RRh, (void*)w.RRl, (void*)w.Phi, (void*)w.Phi32,
+    for (void* q : {(void*)w.SZ, (void*)w.R, (void*)w.Rinv, (void*)w.Rinv32, (void*)w.Minv_hi, (void*)w.Minv_lo, (void*)w.SZh, (void*)w.SZl, (void*)w.RRh, (void*)w.RRl, (void*)w.Phi, (void*)w.Phi32,
                     (void*)w.Meta, (void*)w.gold, (void*)w.Mgold, (void*)w.LL, (void*)w.RR, (void*)w.tmp,
                     (void*)w.warm, (void*)w.wsU, (void*)w.wsT})
       dfree(q);
@@ -51,7 +51,7 @@ void free_plan(Plan* p) {
                   (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
                   (void*)p->phigram, (void*)p->phipart, (void*)p->phired, (void*)p->cross, (void*)p->crosspart, (void*)p->history,
-                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->ls_f, (void*)p->ls_L})
+                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->mv_part, (void*)p->mv_cnt, (void*)p->ls_f, (void*)p->ls_L})
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
@@ -74,6 +74,8 @@ int alloc_plan(Plan* p) {
       GB_TRY(dalloc(&w.Minv_lo, (int64_t)d * d));
       GB_TRY(dalloc(&w.RRh, (int64_t)d * k2));
       GB_TRY(dalloc(&w.RRl, (int64_t)d * k2));
+      GB_TRY(dalloc(&w.SZh, p->s * d));
+      GB_TRY(dalloc(&w.SZl, p->s * d));
     }
     GB_TRY(dalloc(&w.Phi, (int64_t)d * k2));
     GB_TRY(dalloc(&w.Phi32, (int64_t)d * k2));
@@ -157,6 +159,12 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->ws, p->ws_len));
   GB_TRY(dalloc(&p->mt_part, (int64_t)ceil_div(dmax, 64) * dmax * 40));
   GB_TRY(dalloc(&p->dfx, 2 * (int64_t)dmax * k2));
+  // double-float products: up to 2 problems x 16 slices x dmax rows x 40 columns x 2
+  p->mv_part_len = 2 * 16 * (int64_t)(dmax + 32) * 40 * 2;
+  GB_TRY(dalloc(&p->mv_part, p->mv_part_len));
+  p->mv_cnt_len = 2 * (dmax + 8);
+  GB_TRY(dalloc(&p->mv_cnt, p->mv_cnt_len));
+  GB_CUDA(cudaMemset(p->mv_cnt, 0, sizeof(int) * p->mv_cnt_len));
   GB_TRY(dalloc(&p->ls_f, 64));
   GB_TRY(dalloc(&p->ls_L, 64 * 2 * (int64_t)kMaxK * kMaxK));
   GB_TRY(dalloc(&p->flag, 1));
@@ -300,8 +308,14 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
   }
   for (int v = 0; v < p.nviews; ++v) {
     View& w = p.v[v];
-    GB_TRY(gram_tn(w.SZ, w.d, w.SZ, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st,
-                   p.dtype != GBCCA_FP64));
+    if (w.SZh != nullptr) {
+      // FP32/BF16 data: the Gram only shapes the preconditioner; double-float
+      // arithmetic (~2^-44 relative per product) at FP32 instruction rates
+      GB_TRY(split_rows(w.SZ, (int)p.s, w.d, w.d, w.SZh, w.SZl, st));
+      GB_TRY(gram_df_split(w.SZh, w.SZl, w.d, w.SZh, w.SZl, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st));
+    } else {
+      GB_TRY(gram_tn(w.SZ, w.d, w.SZ, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st));
+    }
     GB_TRY(cholesky_upper(w.R, w.d, p.flag, st));
     GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, p.ws, p.ws_len, st));
   }

@@ -56,6 +56,10 @@ __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162flo
 __device__ __forceinline__ double to_f64(float v) { return (double)v; }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+// conversion to a kernel's working type T (FP32 work stays on FP32 units)
+template <typename T> __device__ __forceinline__ T to_work(float v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T to_work(double v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T to_work(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
 
 template <typename T> __device__ __forceinline__ T cvt(float v);
 template <typename T> __device__ __forceinline__ T cvt(double v);
@@ -77,6 +81,21 @@ template <> __device__ __forceinline__ double ld_as<double, __nv_bfloat16>(const
 }
 
 // ---------------------------------------------------------------- reductions
+// 1/sqrt(x) for x > 0 in FP64: the single-precision estimate refined by two
+// Newton-Raphson steps for f(y) = 1/y^2 - x, y <- y (3 - x y^2) / 2 (each
+// step doubles the correct bits: ~2^-22 -> 2^-44 -> full precision).  Short
+// dependent chains of FMAs instead of FP64 square root and division, which
+// are long sequences on this GPU.  Outside the float range: 1 / sqrt(x).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-37f && xf < 1e37f)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf(xf);
+  const double hx = 0.5 * x;
+  y = y * fma(-hx * y, y, 1.5);
+  y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

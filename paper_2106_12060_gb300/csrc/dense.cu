@@ -70,10 +70,9 @@ __global__ void sum_parts_kernel(const double* __restrict__ part, int nparts, in
   }
 }
 
-// Gram in double-float arithmetic (each FP64 input split into an FP32 pair
-// hi + lo; products hi*hi formed exactly as an FP32 pair with fma, the cross
-// terms hi*lo + lo*hi added to the compensation; sums kept as FP32 pairs with
-// TwoSum).  About 2^-44 relative accuracy per term at FP32 instruction rates:
+// Double-float multiply-add (inputs split into FP32 pairs hi + lo; products
+// hi*hi formed exactly as an FP32 pair with fma, the cross terms hi*lo +
+// lo*hi added to the compensation; sums kept as FP32 pairs with TwoSum).  About 2^-44 relative accuracy per term at FP32 instruction rates:
 // GB300 executes FP64 at ~1/60 of its FP32 rate.
 __device__ __forceinline__ void df_acc(float& S, float& Cc, float ah, float al, float bh, float bl) {
   const float p = ah * bh;
@@ -85,29 +84,40 @@ __device__ __forceinline__ void df_acc(float& S, float& Cc, float ah, float al, 
   Cc += err + e + fmaf(ah, bl, al * bh);
 }
 
-template <typename Tout>
+// The same double-float Gram from inputs already split into float pairs
+// (A = Ah + Al, B = Bh + Bl, row-major with leading dimensions lda, ldb):
+// the tile loads are plain float loads, batched, with no FP64 conversions.
+// tri: A and B lower triangular (A[q][i] = 0 for i > q), so rows
+// q < max(i0, j0) contribute nothing to a tile.
 __global__ void __launch_bounds__(256)
-gram_df_kernel(const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb, int64_t m,
-               int d1, int d2, int64_t kchunk, Tout* __restrict__ part, int tri) {
+gram_dfs_kernel(const float* __restrict__ Ahg, const float* __restrict__ Alg, int64_t lda, const float* __restrict__ Bhg,
+                const float* __restrict__ Blg, int64_t ldb, int64_t m, int d1, int d2, int64_t kchunk,
+                double* __restrict__ part, int tri) {
   __shared__ float Ah[kGK][kGT], Al[kGK][kGT], Bh[kGK][kGT], Bl[kGK][kGT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
-  // tri: A and B lower triangular (A[q][i] = 0 for i > q), so rows
-  // q < max(i0, j0) contribute nothing to this tile
   const int64_t k1 = min(m, (int64_t)blockIdx.z * kchunk + kchunk);
   const int64_t k0 = tri ? max((int64_t)blockIdx.z * kchunk, (int64_t)max(i0, j0)) : (int64_t)blockIdx.z * kchunk;
   float S[4][4] = {}, Cc[4][4] = {};
   for (int64_t kk = k0; kk < k1; kk += kGK) {
-    for (int e = tid; e < kGK * kGT; e += 256) {
-      int r = e / kGT, c = e % kGT;
-      int64_t row = kk + r;
-      double a = (row < k1 && i0 + c < d1) ? A[row * lda + i0 + c] : 0.0;
-      double b = (row < k1 && j0 + c < d2) ? B[row * ldb + j0 + c] : 0.0;
-      float ah = (float)a, bh = (float)b;
-      Ah[r][c] = ah;
-      Al[r][c] = (float)(a - (double)ah);
-      Bh[r][c] = bh;
-      Bl[r][c] = (float)(b - (double)bh);
+    float v[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, r = e / kGT, c = e % kGT;
+      const int64_t row = kk + r;
+      const bool ia = row < k1 && i0 + c < d1, ib = row < k1 && j0 + c < d2;
+      v[u][0] = ia ? Ahg[row * lda + i0 + c] : 0.f;
+      v[u][1] = ia ? Alg[row * lda + i0 + c] : 0.f;
+      v[u][2] = ib ? Bhg[row * ldb + j0 + c] : 0.f;
+      v[u][3] = ib ? Blg[row * ldb + j0 + c] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, r = e / kGT, c = e % kGT;
+      Ah[r][c] = v[u][0];
+      Al[r][c] = v[u][1];
+      Bh[r][c] = v[u][2];
+      Bl[r][c] = v[u][3];
     }
     __syncthreads();
 #pragma unroll
@@ -131,13 +141,33 @@ gram_df_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      int i = i0 + ty + 16 * u, j = j0 + tx + 16 * w;
-      if (i < d1 && j < d2) part[((int64_t)blockIdx.z * d1 + i) * d2 + j] = (Tout)((double)S[u][w] + (double)Cc[u][w]);
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * w;
+      if (i < d1 && j < d2) part[((int64_t)blockIdx.z * d1 + i) * d2 + j] = (double)S[u][w] + (double)Cc[u][w];
     }
 }
 
+int gram_df_split(const float* Ah, const float* Al, int64_t lda, const float* Bh, const float* Bl, int64_t ldb,
+                  int64_t m, int d1, int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
+                  bool tri) {
+  const int tiles = ceil_div(d1, kGT) * ceil_div(d2, kGT);
+  int ks = std::max(1, std::min<int>(ceil_div(tri ? 2 * 304 : 304, tiles), ceil_div(m, 64)));
+  const int64_t len = (int64_t)d1 * d2;
+  while (ks > 1 && (int64_t)ks * len > ws_len) --ks;
+  if ((int64_t)ks * len > ws_len) {
+    set_last_error("gram_df_split: workspace too small");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  const int64_t kchunk = (m + ks - 1) / ks;
+  dim3 grid(ceil_div(d2, kGT), ceil_div(d1, kGT), ks);
+  gram_dfs_kernel<<<grid, 256, 0, st>>>(Ah, Al, lda, Bh, Bl, ldb, m, d1, d2, kchunk, ws, tri ? 1 : 0);
+  GB_CHECK_LAUNCH();
+  sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
 int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1, int d2, double* C,
-            double diag_add, double* ws, int64_t ws_len, cudaStream_t st, bool df, bool tri) {
+            double diag_add, double* ws, int64_t ws_len, cudaStream_t st) {
   int tiles = ceil_div(d1, kGT) * ceil_div(d2, kGT);
   int ks = std::max(1, std::min<int>(ceil_div(304, tiles), ceil_div(m, 64)));
   int64_t len = (int64_t)d1 * d2;
@@ -148,10 +178,7 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
   }
   int64_t kchunk = (m + ks - 1) / ks;
   dim3 grid(ceil_div(d2, kGT), ceil_div(d1, kGT), ks);
-  if (df)
-    gram_df_kernel<double><<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws, tri ? 1 : 0);
-  else
-    gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
+  gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, m, d1, d2, kchunk, ws);
   GB_CHECK_LAUNCH();
   sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
   GB_CHECK_LAUNCH();
@@ -166,13 +193,6 @@ int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t 
 // replaces two dependent triangular products per view; its rounding error is
 // ~2^-44 sqrt(d) kappa(M), below that of FP32 triangular products
 // (~2^-24 kappa(R) each).
-__global__ void transpose_sq_kernel(const double* __restrict__ A, int d, double* __restrict__ At) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= (int64_t)d * d) return;
-  const int i = (int)(e / d), j = (int)(e % d);
-  At[(int64_t)j * d + i] = A[e];
-}
-
 __global__ void split_df_kernel(const double* __restrict__ A, int64_t len, float* __restrict__ hi,
                                 float* __restrict__ lo) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -189,12 +209,12 @@ int minv_df_build(const double* Rinv, int d, float* hi, float* lo, double* ws, i
     set_last_error("minv_df_build: workspace too small");
     return GBCCA_ERR_INVALID_ARG;
   }
-  double* T = ws;
+  // T = R^{-T} (lower triangular) as a float pair, then C = T^T T = R^{-1} R^{-T}
+  float* Th = reinterpret_cast<float*>(ws);
+  float* Tl = Th + dd;
   double* C = ws + dd;
-  transpose_sq_kernel<<<ceil_div(dd, 256), 256, 0, st>>>(Rinv, d, T);
-  GB_CHECK_LAUNCH();
-  // C = T^T T = R^{-1} R^{-T}
-  GB_TRY(gram_tn(T, d, T, d, d, d, d, C, 0.0, ws + 2 * dd, ws_len - 2 * dd, st, true, true));
+  GB_TRY(split_df(Rinv, d, d, true, Th, Tl, st));
+  GB_TRY(gram_df_split(Th, Tl, d, Th, Tl, d, d, d, d, C, 0.0, ws + 2 * dd, ws_len - 2 * dd, st, true));
   split_df_kernel<<<ceil_div(dd, 256), 256, 0, st>>>(C, dd, hi, lo);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
@@ -208,111 +228,140 @@ __device__ __forceinline__ void df_add(float& S, float& Cc, float s2, float c2) 
   Cc += err + c2;
 }
 
-constexpr int kMvRows = 8, kMvChunk = 256, kMvCols = 10;  // c <= 4 * kMvCols
+constexpr int kMvChunk = 256, kMvCols = 10;  // c <= 4 * kMvCols
+constexpr int kMvMaxSlices = 16;
 constexpr int kMvBatch = 8;                                  // loads in flight per thread while staging
 
-// Y_b (rows r0..r0+7, c columns) = A_b X_b for problem b = blockIdx.y, A_b
-// (m x K, row-major) and X_b (K x c) as double-float pairs hi + lo.  Per
-// 256-wide K chunk: X and the 8 rows of A are staged in shared memory (loads
-// batched, several in flight per thread); warp w takes the K
-// slice [32 w, 32 w + 32) of the chunk; lane = (row r = lane & 7, column
-// group cg = lane >> 3: columns cg, cg + 4, ...).  The 8 warps' double-float
-// partials are added in fixed order.
+// Y_b (rows r0 .. r0 + R - 1, c columns) = A_b X_b for problem b =
+// blockIdx.y, A_b (m x K, row-major) and X_b (K x c) as double-float pairs
+// hi + lo.  The K range is split over gridDim.z CTAs (K slices) so that the
+// whole GPU works on these small products.  Lane = (row r = lane % R,
+// column group cg = lane / R: columns cg, cg + G, ...) with G = 32 / R
+// chosen so each lane owns up to kMvCols columns (R = 32, 16, 8 for c <= 10,
+// 20, 40).  X and the R rows of A of the slice are staged in shared memory
+// (loads batched); warp w takes a contiguous eighth of the slice.  The 8
+// warps' double-float partials are added in fixed order, written per slice,
+// and the last CTA of a row block (atomic counter) adds the slices in slice
+// order: deterministic.
 __global__ void __launch_bounds__(256) dfmv_kernel(DfmvArgs a) {
   const int b = blockIdx.y;
   const DfmvProblem& P = a.p[b];
   if (a.done != nullptr && *a.done) return;
   const int m = P.m, K = P.K, c = a.c;
-  const int r0 = blockIdx.x * kMvRows;
-  if (r0 >= m) return;
+  const int G = c <= kMvCols ? 1 : (c <= 2 * kMvCols ? 2 : 4);
+  const int R = 32 / G;
+  const int r0 = blockIdx.x * R;
+  if (r0 >= m) return;  // uniform over the slices of this row block
+  const int S = gridDim.z, z = blockIdx.z;
+  const int ks = (K + S - 1) / S;
+  const int kb = min(K, z * ks), kn = min(K, kb + ks) - kb;  // kn <= kMvChunk
   extern __shared__ float msm[];
   float* Xh = msm;                              // [kMvChunk][c]
   float* Xl = Xh + kMvChunk * c;
-  float* Ah = Xl + kMvChunk * c;                // [kMvRows][kMvChunk + 1]
-  float* Al = Ah + kMvRows * (kMvChunk + 1);
-  float* red = Al + kMvRows * (kMvChunk + 1);   // [8 warps][kMvRows][c][2]
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, r = lane & 7, cg = lane >> 3;
-  float S[kMvCols], Cc[kMvCols];
+  float* Ah = Xl + kMvChunk * c;                // [R][kMvChunk + 1]
+  float* Al = Ah + R * (kMvChunk + 1);
+  float* red = Al + R * (kMvChunk + 1);         // [8 warps][R][c][2]
+  __shared__ int last;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, r = lane % R, cg = lane / R;
+  float S1[kMvCols], Cc[kMvCols];
 #pragma unroll
-  for (int u = 0; u < kMvCols; ++u) S[u] = Cc[u] = 0.f;
+  for (int u = 0; u < kMvCols; ++u) S1[u] = Cc[u] = 0.f;
   const int c2 = c >> 1;  // c is even: X rows are read as float2
-  for (int k0 = 0; k0 < K; k0 += kMvChunk) {
-    const int kn = min(kMvChunk, K - k0);
-    const int nx = kn * c2;
-    for (int base = 0; base < nx; base += 256 * kMvBatch) {
-      float2 vh[kMvBatch], vl[kMvBatch];
+  const int nx = kn * c2;
+  for (int base = 0; base < nx; base += 256 * kMvBatch) {
+    float2 vh[kMvBatch], vl[kMvBatch];
 #pragma unroll
-      for (int u = 0; u < kMvBatch; ++u) {
-        const int e = base + tid + 256 * u;
-        if (e < nx) {
-          const int q = e / c2, cp = e - q * c2;
-          const int64_t o = (int64_t)(k0 + q) * P.ldx + 2 * cp;
-          vh[u] = *reinterpret_cast<const float2*>(P.Xh + o);
-          vl[u] = *reinterpret_cast<const float2*>(P.Xl + o);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kMvBatch; ++u) {
-        const int e = base + tid + 256 * u;
-        if (e < nx) {
-          reinterpret_cast<float2*>(Xh)[e] = vh[u];
-          reinterpret_cast<float2*>(Xl)[e] = vl[u];
-        }
+    for (int u = 0; u < kMvBatch; ++u) {
+      const int e = base + tid + 256 * u;
+      if (e < nx) {
+        const int q = e / c2, cp = e - q * c2;
+        const int64_t o = (int64_t)(kb + q) * P.ldx + 2 * cp;
+        vh[u] = *reinterpret_cast<const float2*>(P.Xh + o);
+        vl[u] = *reinterpret_cast<const float2*>(P.Xl + o);
       }
     }
-    const int na = kMvRows * kn;
-    for (int base = 0; base < na; base += 256 * kMvBatch) {
-      float vh[kMvBatch], vl[kMvBatch];
 #pragma unroll
-      for (int u = 0; u < kMvBatch; ++u) {
-        const int e = base + tid + 256 * u;
-        vh[u] = vl[u] = 0.f;
-        if (e < na) {
-          const int rr = e / kn, q = e - rr * kn;
-          if (r0 + rr < m) {
-            vh[u] = P.hi[(int64_t)(r0 + rr) * K + k0 + q];
-            vl[u] = P.lo[(int64_t)(r0 + rr) * K + k0 + q];
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kMvBatch; ++u) {
-        const int e = base + tid + 256 * u;
-        if (e < na) {
-          const int rr = e / kn, q = e - rr * kn;
-          Ah[rr * (kMvChunk + 1) + q] = vh[u];
-          Al[rr * (kMvChunk + 1) + q] = vl[u];
-        }
+    for (int u = 0; u < kMvBatch; ++u) {
+      const int e = base + tid + 256 * u;
+      if (e < nx) {
+        reinterpret_cast<float2*>(Xh)[e] = vh[u];
+        reinterpret_cast<float2*>(Xl)[e] = vl[u];
       }
     }
-    __syncthreads();
-    const int qe = min(32 * w + 32, kn);
-    for (int q = 32 * w; q < qe; ++q) {
-      const float ah = Ah[r * (kMvChunk + 1) + q], al = Al[r * (kMvChunk + 1) + q];
-#pragma unroll
-      for (int u = 0; u < kMvCols; ++u) {
-        const int col = cg + 4 * u;
-        if (col < c) df_acc(S[u], Cc[u], ah, al, Xh[q * c + col], Xl[q * c + col]);
-      }
-    }
-    __syncthreads();
   }
+  const int na = R * kn;
+  for (int base = 0; base < na; base += 256 * kMvBatch) {
+    float vh[kMvBatch], vl[kMvBatch];
 #pragma unroll
-  for (int u = 0; u < kMvCols; ++u) {
-    const int col = cg + 4 * u;
-    if (col < c) {
-      red[((w * kMvRows + r) * c + col) * 2 + 0] = S[u];
-      red[((w * kMvRows + r) * c + col) * 2 + 1] = Cc[u];
+    for (int u = 0; u < kMvBatch; ++u) {
+      const int e = base + tid + 256 * u;
+      vh[u] = vl[u] = 0.f;
+      if (e < na) {
+        const int rr = e / kn, q = e - rr * kn;
+        if (r0 + rr < m) {
+          vh[u] = P.hi[(int64_t)(r0 + rr) * K + kb + q];
+          vl[u] = P.lo[(int64_t)(r0 + rr) * K + kb + q];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMvBatch; ++u) {
+      const int e = base + tid + 256 * u;
+      if (e < na) {
+        const int rr = e / kn, q = e - rr * kn;
+        Ah[rr * (kMvChunk + 1) + q] = vh[u];
+        Al[rr * (kMvChunk + 1) + q] = vl[u];
+      }
     }
   }
   __syncthreads();
-  for (int e = tid; e < kMvRows * c; e += 256) {
+  const int per = (kn + 7) >> 3;
+  const int qb = w * per, qe = min(kn, qb + per);
+  for (int q = qb; q < qe; ++q) {
+    const float ah = Ah[r * (kMvChunk + 1) + q], al = Al[r * (kMvChunk + 1) + q];
+#pragma unroll
+    for (int u = 0; u < kMvCols; ++u) {
+      const int col = cg + G * u;
+      if (col < c) df_acc(S1[u], Cc[u], ah, al, Xh[q * c + col], Xl[q * c + col]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kMvCols; ++u) {
+    const int col = cg + G * u;
+    if (col < c) {
+      red[((w * R + r) * c + col) * 2 + 0] = S1[u];
+      red[((w * R + r) * c + col) * 2 + 1] = Cc[u];
+    }
+  }
+  __syncthreads();
+  // this slice's partial of the row block
+  const int mpad = gridDim.x * R;
+  float* part = a.part + (((int64_t)b * S + z) * mpad + r0) * c * 2;
+  for (int e = tid; e < R * c; e += 256) {
+    const int rr = e / c, col = e - rr * c;
+    float s = 0.f, cc = 0.f;
+    for (int w2 = 0; w2 < 8; ++w2)
+      df_add(s, cc, red[((w2 * R + rr) * c + col) * 2], red[((w2 * R + rr) * c + col) * 2 + 1]);
+    part[e * 2] = s;
+    part[e * 2 + 1] = cc;
+  }
+  __threadfence();
+  __syncthreads();
+  int* cnt = a.cnt + (int64_t)b * gridDim.x + blockIdx.x;
+  if (tid == 0) last = atomicAdd(cnt, 1) == S - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (tid == 0) *cnt = 0;
+  for (int e = tid; e < R * c; e += 256) {
     const int rr = e / c, col = e - rr * c;
     const int row = r0 + rr;
     if (row >= m) continue;
     float s = 0.f, cc = 0.f;
-    for (int w2 = 0; w2 < 8; ++w2)
-      df_add(s, cc, red[((w2 * kMvRows + rr) * c + col) * 2], red[((w2 * kMvRows + rr) * c + col) * 2 + 1]);
+    for (int z2 = 0; z2 < S; ++z2) {
+      const volatile float* pz = a.part + (((int64_t)b * S + z2) * mpad + r0) * c * 2;
+      df_add(s, cc, pz[e * 2], pz[e * 2 + 1]);
+    }
     P.Y[(int64_t)row * P.ldy + col] = (double)s + (double)cc;
   }
 }
@@ -322,7 +371,7 @@ int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st) {
     set_last_error("dfmv: unsupported column count");
     return GBCCA_ERR_INVALID_ARG;
   }
-  int mmax = 0;
+  int mmax = 0, kmax = 0;
   for (int b = 0; b < nprob; ++b) {
     if ((a.p[b].ldx & 1) || (reinterpret_cast<uintptr_t>(a.p[b].Xh) & 7) ||
         (reinterpret_cast<uintptr_t>(a.p[b].Xl) & 7)) {
@@ -330,10 +379,23 @@ int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st) {
       return GBCCA_ERR_INVALID_ARG;
     }
     mmax = std::max(mmax, a.p[b].m);
+    kmax = std::max(kmax, a.p[b].K);
   }
-  const size_t smem = sizeof(float) * (2 * kMvChunk * a.c + 2 * kMvRows * (kMvChunk + 1) + 8 * kMvRows * a.c * 2);
+  const int G = a.c <= kMvCols ? 1 : (a.c <= 2 * kMvCols ? 2 : 4);
+  const int R = 32 / G;
+  const int rb = ceil_div(mmax, R);
+  // K slices: at least ceil(K / 256) (one staged chunk each), and enough CTAs
+  // to cover the GPU about twice
+  int S = std::max(ceil_div(kmax, kMvChunk), ceil_div(2 * a.sm_count, rb * nprob));
+  S = std::min(S, std::min(kMvMaxSlices, kmax));
+  if ((int64_t)nprob * S * rb * R * a.c * 2 > a.part_len || nprob * rb > a.cnt_len ||
+      ceil_div(kmax, S) > kMvChunk) {
+    set_last_error("dfmv: scratch too small for this shape");
+    return GBCCA_ERR_INVALID_ARG;
+  }
+  const size_t smem = sizeof(float) * (2 * kMvChunk * a.c + 2 * R * (kMvChunk + 1) + 8 * R * a.c * 2);
   GB_CUDA(cudaFuncSetAttribute(dfmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dfmv_kernel<<<dim3(ceil_div(mmax, kMvRows), nprob), 256, smem, st>>>(a);
+  dfmv_kernel<<<dim3(rb, nprob, S), 256, smem, st>>>(a);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }
@@ -477,8 +539,8 @@ __global__ void chol_diag_kernel(double* A, int d, int p, int* flag) {
         bad = true;
         piv = 1.0;  // keep going with a harmless value; the result is discarded
       }
-      const double ljj = sqrt(piv);
-      const double rj = 1.0 / ljj;
+      const double rj = rsqrt_nr(piv);
+      const double ljj = piv * rj;
       if (lane == j) row[j] = ljj;
       if (lane > j) row[j] *= rj;
       const double lij = row[j];

@@ -43,36 +43,40 @@ namespace gbcca {
 namespace tc {
 
 constexpr int kRows = 64;             // rows per tile (MMA M of GEMM 1, K of GEMM 2)
-constexpr int kNW = 48;               // N of both GEMMs
-constexpr int kHalf = 24;             // per view: B rows of Phi hi (0..23) / lo (24..47); W rows of a view
+constexpr int kNW = 48;               // N of GEMM 2: W rows [W_x | W_y], 24 per view
+constexpr int kHalf = 24;             // W rows of a view (2k <= 24)
 constexpr int kTileSlots = 4;         // pair slots of one tile (512 columns)
-constexpr int kStages = 2 * kTileSlots;  // two resident tiles
 constexpr int kSlot = 16384;          // two 64 x 64 BF16 boxes
 constexpr int kBox = 8192;
-constexpr int kPhiView = 49152;       // per view: 8 K-boxes x 48 rows x 128 B
-constexpr int kKBox = 6144;           // 48 rows x 128 B
-constexpr int kWs = kKBox;            // W operand (hi or lo) of one tile: 1 K-box (64 rows)
+constexpr int kPhiView = 49152;       // stride of the views' Phi images in the plan buffer
+constexpr int kWs = kNW * 128;        // W operand (hi or lo) of one tile: 1 K-box (64 rows)
 constexpr int kWBuf = 2 * kWs;        // hi + lo
 constexpr int kWHalf = kHalf * 128;   // one view's rows of the W operand
-constexpr int kRingOff = kPhiView;
-constexpr int kWsOff = kRingOff + kStages * kSlot;
-constexpr int kBarOff = kWsOff + 2 * kWBuf;
-constexpr int kSmemBytes = kBarOff + 256 + 1024;  // + alignment slack
+constexpr int kMaxSmem = 232448;      // dynamic shared memory of one CTA
 constexpr uint32_t kTmemCols = 512;   // W: 48 b (b = 0, 1), G: 2 kNW + kNW p (p < 4 pairs)
 constexpr long long kTimeout = 2000000000ll;      // cycles (~1 s)
 
-enum Bar {
-  kFull = 0,
-  kEmpty = kStages,
-  kD1Full = 2 * kStages,   // [2]
-  kD1Free = kD1Full + 2,   // [2]
-  kEpiSync = kD1Free + 2,
-  kWReady,                 // [2]
-  kWPeer = kWReady + 2,    // [2]
-  kWFree = kWPeer + 2,     // [2]
-  kGDone = kWFree + 2,
-  kFinal,                  // [2]: one per MMA-issuing thread
-  kNumBars = kFinal + 2
+// Shared-memory layout and barriers for GEMM 1 with N = 2 kH1 (Phi columns as
+// bf16 hi rows 0 .. kH1 - 1 and lo rows kH1 .. 2 kH1 - 1; kH1 = 20 serves
+// 2k <= 20 and leaves room for a 10-slot ring, kH1 = 24 a 9-slot ring).
+template <int kH1>
+struct Lay {
+  static constexpr int kN1 = 2 * kH1;
+  static constexpr int kKBox1 = kN1 * 128;       // one K-box (64 columns) of the Phi image
+  static constexpr int kPhiBytes = 8 * kKBox1;   // 512 columns
+  static constexpr int kStages = (kMaxSmem - kPhiBytes - 2 * kWBuf - 512 - 1024) / kSlot;
+  static constexpr int kRingOff = kPhiBytes;
+  static constexpr int kWsOff = kRingOff + kStages * kSlot;
+  static constexpr int kBarOff = kWsOff + 2 * kWBuf;
+  static constexpr int kSmemBytes = kBarOff + 512 + 1024;  // barriers + alignment slack
+  // barrier indices
+  static constexpr int kFull = 0, kEmpty = kStages, kD1Full = 2 * kStages;  // [stages], [stages], [2]
+  static constexpr int kD1Free = kD1Full + 2, kEpiSync = kD1Free + 2, kWReady = kEpiSync + 1;  // [2], 1, [2]
+  static constexpr int kWPeer = kWReady + 2, kWFree = kWPeer + 2, kGDone = kWFree + 2;      // [2], [2], 1
+  static constexpr int kFinal = kGDone + 1, kNumBars = kFinal + 2;  // [2]: one per MMA-issuing thread
+  static_assert(kStages >= 2 * kTileSlots, "two resident tiles");
+  static_assert(kNumBars * 8 + 8 <= 512, "barrier area");
+  static_assert(kSmemBytes <= kMaxSmem, "shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -228,15 +232,21 @@ struct Args {
   const int* done;
 };
 
+template <int kH1>
 __global__ void __launch_bounds__(256, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, Args a) {
+  using L = Lay<kH1>;
+  constexpr int kStages = L::kStages;
+  constexpr int kFull = L::kFull, kEmpty = L::kEmpty, kD1Full = L::kD1Full, kD1Free = L::kD1Free;
+  constexpr int kEpiSync = L::kEpiSync, kWReady = L::kWReady, kWPeer = L::kWPeer, kWFree = L::kWFree;
+  constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kNumBars = L::kNumBars;
   if (a.done != nullptr && *a.done) return;  // uniform over the cluster: no remote access yet
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* phi_s = smem;
-  uint8_t* ring = smem + kRingOff;
-  uint8_t* ws = smem + kWsOff;  // [buffer][hi | lo][48 rows][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  uint8_t* ring = smem + L::kRingOff;
+  uint8_t* ws = smem + L::kWsOff;  // [buffer][hi | lo][48 rows][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -251,7 +261,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.phi_img + view * kPhiView);
     uint4* dst = reinterpret_cast<uint4*>(phi_s);
-    for (int i = threadIdx.x; i < kPhiView / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < L::kPhiBytes / 16; i += blockDim.x) dst[i] = src[i];
     uint4* wz = reinterpret_cast<uint4*>(ws);
     for (int i = threadIdx.x; i < 2 * kWBuf / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
   }
@@ -324,7 +334,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     // warp 1: GEMM 1 of every tile; warp 3: GEMM 2 of every tile.  Separate
     // issuers keep GEMM 2 of tile j (which frees its ring slots) from waiting
     // behind the arrival of tile j + 1's data.
-    constexpr uint32_t id1 = idesc_bf16(64, kNW, 0, 0);
+    constexpr uint32_t id1 = idesc_bf16(64, L::kN1, 0, 0);
     constexpr uint32_t id2 = idesc_bf16(128, kNW, 1, 0);
     bool ok = true;
     if (warp == 1) {
@@ -345,7 +355,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           for (int s = 0; s < 8; ++s) {
             const int box = s >> 2, kin = s & 3;
             const uint64_t ad = sdesc(abase + box * kBox + kin * 32, 16, 1024);
-            const uint64_t bd = sdesc(bbase + (2 * p + box) * kKBox + kin * 32, 16, 1024);
+            const uint64_t bd = sdesc(bbase + (2 * p + box) * L::kKBox1 + kin * 32, 16, 1024);
             mma_bf16(d1, ad, bd, id1, (p > 0 || s > 0) ? 1u : 0u);
           }
         }
@@ -394,7 +404,6 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     // ------------------------------------------------------------ epilogue
     const int q = warp - 4;             // TMEM lane quarter
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-    const int r = 16 * q + lane;        // tile row held by this lane of the M = 64 result (lane < 16)
     bool ok = true;
     for (int j = 0; j < my_tiles && ok; ++j) {
       const int b = j & 1;
@@ -409,15 +418,21 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       // both CTAs' GEMM 2 of tile j - 2 must be done with both halves of buffer b
       if (j >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((j - 2) >> 1) & 1, abort_flag))) break;
       uint8_t* wb = ws + b * kWBuf;
-      if (lane < 16) {
-        // W_v row r = hi part (TMEM column c) + lo part (column kHalf + c), c < 2k
+      {
+        // W_v row rr = hi part (TMEM column c) + lo part (column kH1 + c),
+        // c < 2k.  Lanes 0..15 hold the rows (M = 64 layout); lanes 16..31
+        // take the upper half of the columns of the same rows by shuffle.
+        const int hsplit = (a.k2 + 1) >> 1;
+        const bool upper = lane >= 16;
+        const int rr = 16 * q + (lane & 15);
 #pragma unroll
-        for (int c = 0; c < kHalf; ++c) {
-          if (c < a.k2) {
-            const float w = d1[c] + d1[kHalf + c];
+        for (int c = 0; c < kH1; ++c) {
+          const float x = d1[c] + d1[kH1 + c];
+          const float w = __shfl_sync(0xffffffffu, x, lane & 15);
+          if (c < a.k2 && (upper ? c >= hsplit : c < hsplit)) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(w);
             const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
-            const uint32_t off = swz(view * kHalf + c, r);
+            const uint32_t off = swz(view * kHalf + c, rr);
             *reinterpret_cast<__nv_bfloat16*>(wb + off) = hi;
             *reinterpret_cast<__nv_bfloat16*>(wb + kWs + off) = lo;
           }
@@ -490,7 +505,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
 // element of Phi (both views in one launch); the padding of the image is
 // zero from its allocation and never written.
 __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__ Phiy, int dx, int dy, int k2,
-                                 uint8_t* __restrict__ img) {
+                                 int h1, uint8_t* __restrict__ img) {
   const int v = blockIdx.y;
   const int d = v == 0 ? dx : dy;
   double* Phi = v == 0 ? Phix : Phiy;
@@ -500,9 +515,9 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
   const double x = Phi[e];
   const __nv_bfloat16 hi = __double2bfloat16(x);
   const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
-  uint8_t* base = img + (int64_t)v * kPhiView + (int64_t)(j >> 6) * kKBox;
+  uint8_t* base = img + (int64_t)v * kPhiView + (int64_t)(j >> 6) * (2 * h1 * 128);
   *reinterpret_cast<__nv_bfloat16*>(base + swz(c, j & 63)) = hi;
-  *reinterpret_cast<__nv_bfloat16*>(base + swz(kHalf + c, j & 63)) = lo;
+  *reinterpret_cast<__nv_bfloat16*>(base + swz(h1 + c, j & 63)) = lo;
   Phi[e] = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
 }
 
@@ -649,10 +664,11 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     a.d[v] = p.v[v].d;
     a.pairs[v] = ceil_div(p.v[v].d, 128);
   }
+  const int h1 = k2 <= 20 ? 20 : tc::kHalf;  // Phi image rows per half (GEMM 1 N = 2 h1)
   {
     const int dmax = std::max(p.v[0].d, p.v[1].d);
     tc::phi_image_kernel<<<dim3(ceil_div(dmax * k2, 256), 2), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d,
-                                                                           p.v[1].d, k2, p.tc_img);
+                                                                           p.v[1].d, k2, h1, p.tc_img);
     GB_CHECK_LAUNCH();
   }
   a.k2 = k2;
@@ -661,7 +677,9 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   a.partG = p.tc_part;
   a.err = p.flag;
   a.done = done;
-  GB_CUDA(cudaFuncSetAttribute(tc::tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+  auto kern = h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalf>;
+  const int smem = h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalf>::kSmemBytes;
+  GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -669,7 +687,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(256, 1, 1);
-  cfg.dynamicSmemBytes = tc::kSmemBytes;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -677,7 +695,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     // persistent grid: as many 2-CTA clusters as can be resident at once
     cfg.gridDim = dim3(2 * (p.sm_count / 2), 1, 1);
     int ncl = 0;
-    GB_CUDA(cudaOccupancyMaxActiveClusters(&ncl, tc::tc_pass_kernel, &cfg));
+    GB_CUDA(cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg));
     p.tc_clusters = std::max(1, std::min(ncl, p.sm_count / 2));
   }
   const int ncl = std::min(p.tc_clusters, a.ntiles);
@@ -685,7 +703,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(p.tc_map[0]);
   const CUtensorMap* my = reinterpret_cast<const CUtensorMap*>(p.tc_map[1]);
   if (p.kev0 != nullptr) GB_CUDA(cudaEventRecord(p.kev0, st));
-  GB_CUDA(cudaLaunchKernelEx(&cfg, tc::tc_pass_kernel, *mx, *my, a));
+  GB_CUDA(cudaLaunchKernelEx(&cfg, kern, *mx, *my, a));
   GB_CHECK_LAUNCH();
   if (p.kev1 != nullptr) GB_CUDA(cudaEventRecord(p.kev1, st));
   const int grid = ncl;  // partial slabs, one per cluster

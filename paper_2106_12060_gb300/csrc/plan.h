@@ -42,6 +42,8 @@ struct View {
   double lam = 0;
   int ocol = 0;             // first column of this view's block in the pass W
   double* SZ = nullptr;     // sketch S Z (s x d)
+  float* SZh = nullptr;     // S Z as a float pair (FP32/BF16 plans)
+  float* SZl = nullptr;
   double* R = nullptr;      // d x d upper triangular, R^T R = M
   double* Rinv = nullptr;   // d x d, R^{-1}
   float* Rinv32 = nullptr;  // FP32 copy for the low-precision path
@@ -117,6 +119,10 @@ struct Plan {
   double* history = nullptr;    // 3 (max_iter + 1)
   double* mt_part = nullptr;    // slice partials of mat_thin
   float* dfx = nullptr;         // 2 x dmax x 2k floats: split blocks for double-float products
+  float* mv_part = nullptr;     // K-slice partials of the double-float products
+  int64_t mv_part_len = 0;
+  int* mv_cnt = nullptr;        // their slice counters (zero between calls)
+  int mv_cnt_len = 0;
   double* ls_f = nullptr;       // line-search trial values (kNTrials)
   double* ls_L = nullptr;       // line-search trial factors (kNTrials x 2 x kMaxK^2)
   double* ws = nullptr;         // FP64 scratch for dense routines
@@ -145,13 +151,15 @@ int countsketch_prepare(Plan& p, cudaStream_t st);
 int srht_apply(Plan& p, int view, cudaStream_t st);
 
 // dense.cu
-// C = A^T B + diag_add I over m rows.  df = true: double-float arithmetic
-// (~2^-44 relative per product instead of FP64's 2^-53) at FP32 rates, used
-// where the data itself is FP32/BF16 and C only shapes a preconditioner.
-// tri = true (double-float only): A and B lower triangular, zero rows skipped.
+// C = A^T B + diag_add I over m rows, FP64 (split-K partials in ws).
 int gram_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m, int d1,
-            int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
-            bool df = false, bool tri = false);
+            int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st);
+// The same in double-float arithmetic (~2^-44 relative per product) from
+// float-pair inputs (m x d1 and m x d2, row-major) at FP32 instruction rates;
+// tri: A and B lower triangular (zero rows of a tile skipped).
+int gram_df_split(const float* Ah, const float* Al, int64_t lda, const float* Bh, const float* Bl, int64_t ldb,
+                  int64_t m, int d1, int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
+                  bool tri = false);
 int cholesky_upper(double* A, int d, int* flag, cudaStream_t st);
 // C = A^T A + lambda I (A: m x d FP64, row stride lda) with the split-K
 // partials in a static device scratch instead of plan memory; d <= noalloc_max_d().
@@ -173,6 +181,11 @@ struct DfmvArgs {
   DfmvProblem p[2];
   int c;
   const int* done;
+  float* part;       // K-slice partials (plan scratch, part_len floats)
+  int64_t part_len;
+  int* cnt;          // per row-block slice counters, zero between calls (cnt_len)
+  int cnt_len;
+  int sm_count;
 };
 int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st);
 // hi/lo split of the first c columns of X (rows x ldx) into rows x c floats

@@ -29,7 +29,6 @@ constexpr double kC1 = 1e-4;
 constexpr int kMaxLS = 25;
 constexpr int kMaxExpand = 10;
 constexpr int kNTrials = kMaxLS + kMaxExpand + 1;  // last one: t = 0 (Armijo reference)
-constexpr int kLSWarps = 8;
 
 // ================================================================ helpers
 // Block-wide small dense routines on shared memory (row-major, FP64).
@@ -160,6 +159,95 @@ __device__ void blk_jacobi(R* A, R* Q, R* lam, int n, double* rot) {
   __syncthreads();
 }
 
+// The same parallel Jacobi sweeps for n <= 32 by one warp: rotation pairs
+// on lanes, warp-level barriers only (the block version spends most of its
+// time in block-wide barriers for matrices this small).  Called by all 32
+// lanes of one warp.
+template <typename R>
+__device__ void warp_jacobi(R* A, R* Q, R* lam, int n) {
+  const int lane = threadIdx.x & 31;
+  __shared__ R w_cs[16], w_sn[16];
+  __shared__ int w_p[16], w_q[16];
+  for (int e = lane; e < n * n; e += 32) Q[e] = (e / n == e % n) ? R(1) : R(0);
+  __syncwarp();
+  const int m = n + (n & 1);
+  for (int sweep = 0; sweep < 20 && n > 1; ++sweep) {
+    R off = 0, dg = 0;
+    for (int e = lane; e < n * n; e += 32) {
+      const R v = A[e] * A[e];
+      if (e / n == e % n) dg += v;
+      else off += v;
+    }
+    off = warp_sum(off);
+    dg = warp_sum(dg);
+    if (off <= R(sizeof(R) == 8 ? 1e-26 : 1e-12) * dg || off == R(0)) break;
+    for (int r = 0; r < m - 1; ++r) {
+      if (lane < m / 2) {
+        const int i = lane;
+        const int a = (i == 0) ? 0 : 1 + ((i - 1 + r) % (m - 1));
+        const int b = 1 + ((m - 2 - i + r) % (m - 1));
+        const int p = min(a, b), q = max(a, b);
+        R c = 1, sv = 0;
+        if (q < n) {
+          const R apq = A[p * n + q];
+          const R eps = R(sizeof(R) == 8 ? 1e-17 : 1e-8);
+          if (apq * apq > eps * eps * fabs(A[p * n + p] * A[q * n + q])) {
+            const R tau = (A[q * n + q] - A[p * n + p]) / (R(2) * apq);
+            const R t = (tau >= 0 ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+            c = R(1) / sqrt(R(1) + t * t);
+            sv = t * c;
+          }
+        }
+        w_cs[i] = c;
+        w_sn[i] = sv;
+        w_p[i] = p;
+        w_q[i] = q < n ? q : -1;
+      }
+      __syncwarp();
+      for (int e = lane; e < (m / 2) * n; e += 32) {  // rows: A <- J^T A
+        const int i = e / n, j = e % n;
+        if (w_q[i] < 0) continue;
+        const int p = w_p[i], q = w_q[i];
+        const R ap = A[p * n + j], aq = A[q * n + j];
+        A[p * n + j] = w_cs[i] * ap - w_sn[i] * aq;
+        A[q * n + j] = w_sn[i] * ap + w_cs[i] * aq;
+      }
+      __syncwarp();
+      for (int e = lane; e < (m / 2) * n; e += 32) {  // columns: A <- A J, Q <- Q J
+        const int i = e / n, j = e % n;
+        if (w_q[i] < 0) continue;
+        const int p = w_p[i], q = w_q[i];
+        const R ap = A[j * n + p], aq = A[j * n + q];
+        A[j * n + p] = w_cs[i] * ap - w_sn[i] * aq;
+        A[j * n + q] = w_sn[i] * ap + w_cs[i] * aq;
+        const R qp = Q[j * n + p], qv = Q[j * n + q];
+        Q[j * n + p] = w_cs[i] * qp - w_sn[i] * qv;
+        Q[j * n + q] = w_sn[i] * qp + w_cs[i] * qv;
+      }
+      __syncwarp();
+    }
+  }
+  if (lane == 0) {  // sort descending, swapping Q columns
+    for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+    for (int i = 0; i < n; ++i) {
+      int b = i;
+      for (int j = i + 1; j < n; ++j)
+        if (lam[j] > lam[b]) b = j;
+      if (b != i) {
+        const R t = lam[i];
+        lam[i] = lam[b];
+        lam[b] = t;
+        for (int rr = 0; rr < n; ++rr) {
+          const R u = Q[rr * n + i];
+          Q[rr * n + i] = Q[rr * n + b];
+          Q[rr * n + b] = u;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // In-place Cholesky A = L L^T (lower; upper part zeroed).  Returns false
 // (uniformly in the block) if a pivot is not positive.
 __device__ bool blk_chol(double* A, int n) {
@@ -214,8 +302,8 @@ __device__ bool warp_chol(double* A, int n, double* invd) {
       ok = false;
       dj = 1.0;
     }
-    const double ljj = sqrt(dj);
-    const double rj = 1.0 / ljj;
+    const double rj = rsqrt_nr(dj);
+    const double ljj = dj * rj;
     __syncwarp();
     if (lane == j) {
       A[j * n + j] = ljj;
@@ -734,7 +822,8 @@ __global__ void direction_kernel(DirArgs a) {
       for (int e = threadIdx.x; e < kk; e += blockDim.x) A[e] = T2[e];
     }
     __syncthreads();
-    blk_jacobi<R>(A, T2, lam, k, rot);  // A' = J diag(lam) J^T, J in T2
+    if (threadIdx.x < 32) warp_jacobi<R>(A, T2, lam, k);  // A' = J diag(lam) J^T, J in T2
+    __syncthreads();
     if (warm) {
       for (int e = threadIdx.x; e < kk; e += blockDim.x) {  // Q = Q0 J
         int i = e / k, j = e % k;
@@ -1186,6 +1275,11 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
                            p.v[v].d,       p.v[v].d,       2 * k,       4 * k};
     m.c = 2 * k;
     m.done = done;
+    m.part = p.mv_part;
+    m.part_len = p.mv_part_len;
+    m.cnt = p.mv_cnt;
+    m.cnt_len = p.mv_cnt_len;
+    m.sm_count = p.sm_count;
     GB_TRY(dfmv(m, p.nviews, st));
   } else {
     for (int v = 0; v < p.nviews; ++v) GB_TRY(minv(p, v, st));
@@ -1537,8 +1631,11 @@ int warm_start(Plan& p, cudaStream_t st) {
     const int c = std::min(2 * k, std::min(dx, dy));
     // Cxy = X_S^T Y_S (dx x dy), kept in ws after the Gram partials
     double* Cxy = p.ws + (p.ws_len - (int64_t)dx * dy);
-    GB_TRY(gram_tn(x.SZ, dx, y.SZ, dy, p.s, dx, dy, Cxy, 0.0, p.ws, p.ws_len - (int64_t)dx * dy, st,
-                   p.dtype != GBCCA_FP64));
+    if (x.SZh != nullptr)
+      GB_TRY(gram_df_split(x.SZh, x.SZl, dx, y.SZh, y.SZl, dy, p.s, dx, dy, Cxy, 0.0, p.ws,
+                           p.ws_len - (int64_t)dx * dy, st));
+    else
+      GB_TRY(gram_tn(x.SZ, dx, y.SZ, dy, p.s, dx, dy, Cxy, 0.0, p.ws, p.ws_len - (int64_t)dx * dy, st));
     double* Vb = y.wsU;  // dy x c
     double* Ub = x.wsU;  // dx x c
     double* part = p.crosspart;
@@ -1572,6 +1669,11 @@ int warm_start(Plan& p, cudaStream_t st) {
       DfmvArgs g{};
       g.p[0] = DfmvProblem{A[0], A[1], bh, bl, C, m, K, c, c};
       g.c = c;
+      g.part = p.mv_part;
+      g.part_len = p.mv_part_len;
+      g.cnt = p.mv_cnt;
+      g.cnt_len = p.mv_cnt_len;
+      g.sm_count = p.sm_count;
       return dfmv(g, 1, st);
     };
     auto rx = [&](bool tr, const double* B, double* C, int cc) {

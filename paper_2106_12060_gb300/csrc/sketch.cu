@@ -233,71 +233,133 @@ int countsketch_apply(Plan& p, int view, bool center, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- SRHT
-// In-place unnormalized Walsh-Hadamard transform of length N (power of two)
-// on CB columns held in shared memory as buf[N][CB].
-template <typename T, int CB>
-__device__ void fwht_smem(T* buf, int N) {
-  for (int h = 1; h < N; h <<= 1) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < (N / 2) * CB; e += blockDim.x) {
-      int pair = e / CB, c = e % CB;
-      int blk = pair / h, off = pair % h;
-      int i = blk * 2 * h + off, j = i + h;
-      T a = buf[i * CB + c], b = buf[j * CB + c];
-      buf[i * CB + c] = a + b;
-      buf[j * CB + c] = a - b;
+// Unnormalized Walsh-Hadamard transform of one column of length N (32 <= N
+// <= 1024, power of two) held in shared memory with row stride `stride`, by
+// one warp: lane l holds rows l + 32 t; butterflies of span < 32 go across
+// lanes (shuffles), larger spans within the lane's registers.
+template <typename T>
+__device__ __forceinline__ void fwht_warp_col(T* col, int stride, int N) {
+  const int lane = threadIdx.x & 31;
+  const int nt = N >> 5;
+  T v[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) v[t] = t < nt ? col[(lane + 32 * t) * stride] : T(0);
+#pragma unroll
+  for (int h = 1; h < 32; h <<= 1) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t < nt) {
+        const T x = v[t];
+        const T y = __shfl_xor_sync(0xffffffffu, x, h);
+        v[t] = (lane & h) ? (y - x) : (x + y);
+      }
     }
   }
-  __syncthreads();
+#pragma unroll
+  for (int hb = 1; hb < 32; hb <<= 1) {  // span 32 hb rows = hb register slots
+    if (hb < nt) {
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        if ((t & hb) == 0 && t + hb < 32) {
+          const T a = v[t], b = v[t + hb];
+          v[t] = a + b;
+          v[t + hb] = a - b;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 32; ++t)
+    if (t < nt) col[(lane + 32 * t) * stride] = v[t];
 }
 
-template <typename Tin, typename T, int CB>
+// Transform of length N < 32 (tiny n): one thread per column
+template <typename T>
+__device__ __forceinline__ void fwht_thread_col(T* col, int stride, int N) {
+  for (int h = 1; h < N; h <<= 1)
+    for (int i = 0; i < N; ++i)
+      if ((i & h) == 0) {
+        const T a = col[i * stride], b = col[(i + h) * stride];
+        col[i * stride] = a + b;
+        col[(i + h) * stride] = a - b;
+      }
+}
+
+// Stage 1: per block of N1 consecutive rows and CB = 32 columns, D Z
+// (signs, and the class means for LDA) then the N1-point transform along the
+// rows of each column, written to the intermediate buffer.  Tile in shared
+// memory as [N1][33] (padded: column reads are conflict-free); FP32 data is
+// converted on FP32 units.
+template <typename Tin, typename T>
 __global__ void __launch_bounds__(512)
 srht_stage1_kernel(const Tin* __restrict__ Z, int64_t ld, int64_t n, int d, int N1, const int8_t* __restrict__ sg,
                    const int32_t* __restrict__ labels, const double* __restrict__ means, T* __restrict__ Tmid) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);
-  const int64_t i2 = blockIdx.x;
-  const int c0 = blockIdx.y * CB;
+  constexpr int CB = 32, LD = 33;
+  const int64_t i2 = blockIdx.y;   // column blocks of one row block run next to each other
+  const int c0 = blockIdx.x * CB;
   for (int e = threadIdx.x; e < N1 * CB; e += blockDim.x) {
-    int r = e / CB, c = e % CB;
-    int64_t row = i2 * N1 + r;
-    T val = 0;
+    const int r = e >> 5, c = e & 31;
+    const int64_t row = i2 * N1 + r;
+    T val = T(0);
     if (row < n && c0 + c < d) {
-      double x = to_f64(Z[row * ld + c0 + c]);
-      if (labels != nullptr) x -= means[(int64_t)labels[row] * d + c0 + c];
-      val = (T)(sg[row] < 0 ? -x : x);
+      if (labels != nullptr) {
+        const double x = to_f64(Z[row * ld + c0 + c]) - means[(int64_t)labels[row] * d + c0 + c];
+        val = (T)(sg[row] < 0 ? -x : x);
+      } else {
+        const T x = to_work<T>(Z[row * ld + c0 + c]);
+        val = sg[row] < 0 ? -x : x;
+      }
     }
-    buf[r * CB + c] = val;
+    buf[r * LD + c] = val;
   }
-  fwht_smem<T, CB>(buf, N1);
+  __syncthreads();
+  if (N1 >= 32) {
+    for (int c = threadIdx.x >> 5; c < CB; c += blockDim.x >> 5) fwht_warp_col<T>(buf + c, LD, N1);
+  } else if (threadIdx.x < CB) {
+    fwht_thread_col<T>(buf + threadIdx.x, LD, N1);
+  }
+  __syncthreads();
+  // intermediate row r * N2 + i2: stage 2 then reads N2 consecutive rows
+  const int64_t N2 = gridDim.y;
   for (int e = threadIdx.x; e < N1 * CB; e += blockDim.x) {
-    int r = e / CB, c = e % CB;
-    if (c0 + c < d) Tmid[(i2 * N1 + r) * d + c0 + c] = buf[r * CB + c];
+    const int r = e >> 5, c = e & 31;
+    if (c0 + c < d) Tmid[((int64_t)r * N2 + i2) * d + c0 + c] = buf[r * LD + c];
   }
 }
 
-template <typename T, int CB>
+// Stage 2: for one residue a1 of the low m1 row bits, the N2-point transform
+// across the row blocks of each column, kept only at the sampled rows and
+// scaled by sqrt(n'/s) / sqrt(n') = 1 / sqrt(s) (App. A).
+template <typename T>
 __global__ void __launch_bounds__(512)
 srht_stage2_kernel(const T* __restrict__ Tmid, int d, int N1, int N2, int m1, const int32_t* __restrict__ off1,
                    const int32_t* __restrict__ list, const int32_t* __restrict__ rows, double scale,
                    double* __restrict__ SZ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);
-  const int a1 = blockIdx.x;
-  const int c0 = blockIdx.y * CB;
+  constexpr int CB = 32, LD = 33;
+  const int a1 = blockIdx.y;
+  const int c0 = blockIdx.x * CB;
   const int nsel = off1[a1 + 1] - off1[a1];
   if (nsel == 0) return;
   for (int e = threadIdx.x; e < N2 * CB; e += blockDim.x) {
-    int r = e / CB, c = e % CB;
-    buf[r * CB + c] = (c0 + c < d) ? Tmid[((int64_t)r * N1 + a1) * d + c0 + c] : T(0);
+    const int r = e >> 5, c = e & 31;
+    buf[r * LD + c] = (c0 + c < d) ? Tmid[((int64_t)a1 * N2 + r) * d + c0 + c] : T(0);
   }
-  fwht_smem<T, CB>(buf, N2);
+  __syncthreads();
+  if (N2 >= 32) {
+    for (int c = threadIdx.x >> 5; c < CB; c += blockDim.x >> 5) fwht_warp_col<T>(buf + c, LD, N2);
+  } else if (threadIdx.x < CB) {
+    fwht_thread_col<T>(buf + threadIdx.x, LD, N2);
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < nsel * CB; e += blockDim.x) {
-    int q = e / CB, c = e % CB;
-    int j = list[off1[a1] + q];
-    int a2 = rows[j] >> m1;
-    if (c0 + c < d) SZ[(int64_t)j * d + c0 + c] = scale * (double)buf[a2 * CB + c];
+    const int q = e >> 5, c = e & 31;
+    const int j = list[off1[a1] + q];
+    const int a2 = rows[j] >> m1;
+    if (c0 + c < d) SZ[(int64_t)j * d + c0 + c] = scale * (double)buf[a2 * LD + c];
   }
 }
 
@@ -327,8 +389,9 @@ __global__ void srht_group_kernel(const int32_t* __restrict__ rows, int64_t s, i
   }
 }
 
-template <typename Tin, typename T, int CB>
+template <typename Tin, typename T>
 int srht_run(Plan& p, View& v, cudaStream_t st) {
+  constexpr int CB = 32;
   int m = 0;
   while ((1ll << m) < p.n_pad) ++m;
   const int m1 = std::min(m, 9), m2 = m - m1;
@@ -339,10 +402,10 @@ int srht_run(Plan& p, View& v, cudaStream_t st) {
   }
   T* Tmid = reinterpret_cast<T*>(p.srht_T);
   const int32_t* lab = p.kind == kLDA ? p.labels : nullptr;
-  size_t sm1 = sizeof(T) * N1 * CB;
-  auto k1 = srht_stage1_kernel<Tin, T, CB>;
+  size_t sm1 = sizeof(T) * N1 * (CB + 1);
+  auto k1 = srht_stage1_kernel<Tin, T>;
   GB_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-  k1<<<dim3(N2, ceil_div(v.d, CB)), 512, sm1, st>>>((const Tin*)v.Z, v.ld, p.n, v.d, N1, p.g, lab, p.means, Tmid);
+  k1<<<dim3(ceil_div(v.d, CB), N2), 512, sm1, st>>>((const Tin*)v.Z, v.ld, p.n, v.d, N1, p.g, lab, p.means, Tmid);
   GB_CHECK_LAUNCH();
   int32_t* cnt = p.cs_tab;
   int32_t* off1 = p.cs_off;
@@ -354,10 +417,10 @@ int srht_run(Plan& p, View& v, cudaStream_t st) {
   GB_CHECK_LAUNCH();
   srht_group_kernel<<<ceil_div(p.s, 256), 256, 0, st>>>(p.h, p.s, N1, cnt, off1, list, 2);
   GB_CHECK_LAUNCH();
-  size_t sm2 = sizeof(T) * N2 * CB;
-  auto k2 = srht_stage2_kernel<T, CB>;
+  size_t sm2 = sizeof(T) * N2 * (CB + 1);
+  auto k2 = srht_stage2_kernel<T>;
   GB_CUDA(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-  k2<<<dim3(N1, ceil_div(v.d, CB)), 512, sm2, st>>>(Tmid, v.d, N1, N2, m1, off1, list, p.h,
+  k2<<<dim3(ceil_div(v.d, CB), N1), 512, sm2, st>>>(Tmid, v.d, N1, N2, m1, off1, list, p.h,
                                                      1.0 / sqrt((double)p.s), v.SZ);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
@@ -366,9 +429,9 @@ int srht_run(Plan& p, View& v, cudaStream_t st) {
 int srht_apply(Plan& p, int view, cudaStream_t st) {
   View& v = p.v[view];
   switch (p.dtype) {
-    case GBCCA_FP64: return srht_run<double, double, 16>(p, v, st);
-    case GBCCA_FP32: return srht_run<float, float, 32>(p, v, st);
-    default: return srht_run<__nv_bfloat16, float, 32>(p, v, st);
+    case GBCCA_FP64: return srht_run<double, double>(p, v, st);
+    case GBCCA_FP32: return srht_run<float, float>(p, v, st);
+    default: return srht_run<__nv_bfloat16, float>(p, v, st);
   }
 }
 
