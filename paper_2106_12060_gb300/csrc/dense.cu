@@ -522,40 +522,51 @@ int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, 
 // *flag = 1 (the caller reports GBCCA_ERR_NOT_SPD).
 constexpr int kNB = 32;
 
-__global__ void chol_diag_kernel(double* A, int d, int p, int* flag) {
-  // lane i holds row i of the 32 x 32 diagonal block in registers; the
-  // column j multipliers come from lane j by shuffles
-  const int lane = threadIdx.x;
+__global__ void __launch_bounds__(128) chol_diag_kernel(double* A, int d, int p, int* flag) {
+  // The 32 x 32 diagonal block in shared memory, factored by 4 warps: GB300
+  // issues FP64 at a small fraction of its FP32 rate on each of the SM's four
+  // schedulers, so the trailing updates of every step are spread over all four.
+  __shared__ double L[kNB][kNB + 1];
+  __shared__ double s_r;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
   const int o = p * kNB, nb = min(kNB, d - o);
-  double row[kNB];
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) row[c] = (lane < nb && c < nb) ? A[(int64_t)(o + lane) * d + o + c] : 0.0;
-  bool bad = false;
-#pragma unroll
-  for (int j = 0; j < kNB; ++j) {
-    if (j < nb) {
-      double piv = __shfl_sync(0xffffffffu, row[j], j);
+  for (int e = tid; e < kNB * kNB; e += blockDim.x) {
+    const int r = e / kNB, c = e % kNB;
+    L[r][c] = (r < nb && c <= r) ? A[(int64_t)(o + r) * d + o + c] : 0.0;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      double piv = L[j][j];
       if (!(piv > 0.0)) {
-        bad = true;
+        s_bad = 1;
         piv = 1.0;  // keep going with a harmless value; the result is discarded
       }
       const double rj = rsqrt_nr(piv);
-      const double ljj = piv * rj;
-      if (lane == j) row[j] = ljj;
-      if (lane > j) row[j] *= rj;
-      const double lij = row[j];
-#pragma unroll
-      for (int c = j + 1; c < kNB; ++c) {
-        const double lcj = __shfl_sync(0xffffffffu, row[j], c);  // L[c][j] from lane c
-        if (lane >= c) row[c] -= lij * lcj;
-      }
+      L[j][j] = piv * rj;
+      s_r = rj;
     }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) L[i][j] *= s_r;
+    __syncthreads();
+    // trailing lower triangle (i, c), j < c <= i < nb, enumerated row by row
+    const int m = nb - j - 1, cnt = m * (m + 1) / 2;
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      int i1 = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while ((i1 + 1) * (i1 + 2) / 2 <= e) ++i1;
+      while (i1 * (i1 + 1) / 2 > e) --i1;
+      const int i = j + 1 + i1, c = j + 1 + (e - i1 * (i1 + 1) / 2);
+      L[i][c] -= L[i][j] * L[c][j];
+    }
+    __syncthreads();
   }
-  if (bad && lane == 0) atomicExch(flag, 1);
-  if (lane < nb)
-#pragma unroll
-    for (int c = 0; c < kNB; ++c)
-      if (c <= lane && c < nb) A[(int64_t)(o + lane) * d + o + c] = row[c];
+  if (tid == 0 && s_bad) atomicExch(flag, 1);
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    if (c <= r) A[(int64_t)(o + r) * d + o + c] = L[r][c];
+  }
 }
 
 // A[i-block, p] <- A[i-block, p] L_pp^{-T}: each thread solves one row by
@@ -625,7 +636,7 @@ __global__ void lower_to_upper_kernel(double* A, int d) {
 int cholesky_upper(double* A, int d, int* flag, cudaStream_t st) {
   int nbk = ceil_div(d, kNB);
   for (int p = 0; p < nbk; ++p) {
-    chol_diag_kernel<<<1, 32, 0, st>>>(A, d, p, flag);
+    chol_diag_kernel<<<1, 128, 0, st>>>(A, d, p, flag);
     GB_CHECK_LAUNCH();
     int below = d - (p + 1) * kNB;
     if (below > 0) {

@@ -424,6 +424,11 @@ static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const
 }
 
 __device__ void sum_blocks(const double* part, int nblk, int len, double* out) {
+  if (nblk == 1) {  // already summed: a copy (no FP64 additions of zeros)
+    for (int e = threadIdx.x; e < len; e += blockDim.x) out[e] = part[e];
+    __syncthreads();
+    return;
+  }
   // loads are issued 8 at a time (independent), then added in block order
   for (int e = threadIdx.x; e < len; e += blockDim.x) {
     double s = 0;
@@ -497,6 +502,63 @@ __device__ double ls_eval(const LSArgs& a, const double* coef, double t, double*
   return f;
 }
 
+// CCA trial by three warps of the CTA (called by all threads): warp 0
+// factors Gx(t), warp 1 factors Gy(t) and inverts L_y at the same time (GB300
+// issues FP64 slowly on each scheduler, so the two chains run side by side);
+// then warp 0 forms f(t) while warp 2 inverts L_x for the stored factors.
+// w: Gx, Gy, Cx, Ly^{-1}, Lx^{-1} (kk each), ix, iy (kMaxK each).
+__device__ double ls_eval_cca_cta(const LSArgs& a, const double* coef, double t, double* w, const double* mu) {
+  const int k = a.k, kk = k * k, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double* Gx = w;
+  double* Gy = w + kk;
+  double* Cx = w + 2 * kk;
+  double* Li = w + 3 * kk;
+  double* Lt = w + 4 * kk;
+  double* ix = w + 5 * kk;
+  double* iy = ix + kMaxK;
+  __shared__ int s_ok[2];
+  __shared__ double s_f;
+  for (int e = tid; e < kk; e += blockDim.x) {
+    Gx[e] = coef[e] + t * coef[kk + e] + t * t * coef[2 * kk + e];
+    Gy[e] = coef[3 * kk + e] + t * coef[4 * kk + e] + t * t * coef[5 * kk + e];
+    Cx[e] = coef[6 * kk + e] + t * coef[7 * kk + e] + t * t * coef[8 * kk + e];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const bool ok = warp_chol(Gx, k, ix);
+    if (lane == 0) s_ok[0] = ok;
+  } else if (warp == 1) {
+    const bool ok = warp_chol(Gy, k, iy);
+    if (lane == 0) s_ok[1] = ok;
+    warp_lower_inv(Gy, iy, Li, k);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // Y = Lx^{-1} Cross (lane c solves column c); f = -tr(N Y Ly^{-T})
+    if (lane < k) {
+      for (int i = 0; i < k; ++i) {
+        double sv = Cx[i * k + lane];
+        for (int q = 0; q < i; ++q) sv -= Gx[i * k + q] * Cx[q * k + lane];
+        Cx[i * k + lane] = sv * ix[i];
+      }
+    }
+    __syncwarp();
+    double part = 0;
+    if (lane < k) {
+      double z = 0;
+      for (int j = 0; j <= lane; ++j) z += Cx[lane * k + j] * Li[lane * k + j];
+      part = mu[lane] * z;
+    }
+    double f = -warp_sum(part);
+    if (!(s_ok[0] && s_ok[1]) || !(f == f)) f = INFINITY;
+    if (lane == 0) s_f = f;
+  } else if (warp == 2) {
+    warp_lower_inv(Gx, ix, Lt, k);
+  }
+  __syncthreads();
+  return s_f;
+}
+
 // Every trial step of the sequential Armijo rule is evaluated at once, one
 // CTA (one warp) per trial, so the FP64 work of the k x k Cholesky factors
 // is spread over kNTrials SMs instead of queueing on one SM's FP64 pipe:
@@ -518,20 +580,22 @@ __global__ void linesearch_kernel(LSArgs a) {
   if (st->done) return;
   extern __shared__ double lsm[];
   const int k = a.k, kk = k * k, k2 = 2 * k;
-  const int i = blockIdx.x, lane = threadIdx.x;
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   const bool zero_step = st->force_zero_step != 0;
   double* coef = lsm;                       // 9 kk
   double* phig = coef + 9 * kk;             // 2 views x 4 kk
-  double* w = phig + 8 * kk;                // 4 kk + 2 kMaxK
+  double* w = phig + 8 * kk;                // 5 kk + 2 kMaxK
   __shared__ double mu_s[kMaxK];
   __shared__ int last;
   if (!zero_step || i == 0) {
-    if (lane < k) mu_s[lane] = st->mu[lane];
-    for (int e = lane; e < a.nviews * 4 * kk; e += blockDim.x) phig[e] = a.phipart[e];
-    __syncwarp();
+    // the whole CTA loads (several loads in flight per thread); warp 0 then
+    // evaluates the trial
+    if (tid < k) mu_s[tid] = st->mu[tid];
+    for (int e = tid; e < a.nviews * 4 * kk; e += blockDim.x) phig[e] = a.phipart[e];
+    __syncthreads();
     // coefficient matrices: Gram_v(t) = A + t B + t^2 C, Cross(t) = X0 + t X1 + t^2 X2
     const int NC = a.NC;
-    for (int e = lane; e < kk; e += blockDim.x) {
+    for (int e = tid; e < kk; e += blockDim.x) {
       const int r = e / k, c = e % k;
       auto G = [&](int bi, int bj) { return a.Gram[(bi * k + r) * NC + bj * k + c]; };
       for (int v = 0; v < a.nviews; ++v) {
@@ -562,36 +626,36 @@ __global__ void linesearch_kernel(LSArgs a) {
         coef[8 * kk + e] = s2;
       }
     }
-    __syncwarp();
+    __syncthreads();
     const double t = ls_trial_t(i, st->t0);
-    const double f = ls_eval(a, coef, t, w, mu_s);
     // factors L_v(t)^{-T} of this trial (row-major), kept for the decision
     double* Lout = a.ls_L + (int64_t)i * 2 * kMaxK * kMaxK;
-    double* Gx = w;
-    double* Lt = w + 2 * kk;
-    double* Li = w + 3 * kk;
-    double* ix = w + 4 * kk;
     if (a.kind == kCCA) {
-      warp_lower_inv(Gx, ix, Lt, k);
-      for (int e = lane; e < kk; e += 32) {
+      const double f = ls_eval_cca_cta(a, coef, t, w, mu_s);
+      const double* Li = w + 3 * kk;
+      const double* Lt = w + 4 * kk;
+      for (int e = tid; e < kk; e += blockDim.x) {
         const int r = e / k, c = e % k;
         Lout[e] = Lt[c * k + r];
         Lout[kMaxK * kMaxK + e] = Li[c * k + r];
       }
-    } else {
+      if (tid == 0) a.ls_f[i] = f;
+    } else if (tid < 32) {
+      const double f = ls_eval(a, coef, t, w, mu_s);
+      const double* Li = w + 3 * kk;
       for (int e = lane; e < kk; e += 32) {
         const int r = e / k, c = e % k;
         Lout[e] = Li[c * k + r];
       }
+      if (lane == 0) a.ls_f[i] = f;
     }
-    if (lane == 0) a.ls_f[i] = f;
   }
-  // the last CTA to finish decides
+  // the last CTA to finish decides (warp 0 of it)
   __threadfence();
-  __syncwarp();
-  if (lane == 0) last = atomicAdd(&st->ls_count, 1) == (int)gridDim.x - 1;
-  __syncwarp();
-  if (!last) return;
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&st->ls_count, 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last || tid >= 32) return;
   __threadfence();
   if (lane == 0) st->ls_count = 0;
   volatile const double* fv = a.ls_f;
@@ -843,9 +907,11 @@ __global__ void direction_kernel(DirArgs a) {
     // residual correction follows: E = RHS - (A S + S A) in FP64, S += the
     // R-arithmetic solve of A dS + dS A = E.
     double* Sd = Y + 2 * kk;  // 3 kk doubles
+    double* A64 = Y;          // sym(X00) in FP64 for the residual (Y is free until the end)
     for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
       int r = e / kk, f = e % kk, i = f / k, j = f % k;
       T2[e] = R(XB(r + 1, 0, i, j) + XB(r + 1, 0, j, i));
+      if (r == 0) A64[f] = 0.5 * (XB(0, 0, i, j) + XB(0, 0, j, i));
     }
     __syncthreads();
     for (int pass = 0; pass < (sizeof(R) == 8 ? 1 : 2); ++pass) {
@@ -885,11 +951,7 @@ __global__ void direction_kernel(DirArgs a) {
           int r = e / kk, f = e % kk, i = f / k, j = f % k;
           const double* Sr = Sd + r * kk;
           double sum = XB(r + 1, 0, i, j) + XB(r + 1, 0, j, i);
-          for (int q = 0; q < k; ++q) {
-            const double aiq = 0.5 * (XB(0, 0, i, q) + XB(0, 0, q, i));
-            const double aqj = 0.5 * (XB(0, 0, q, j) + XB(0, 0, j, q));
-            sum -= aiq * Sr[q * k + j] + Sr[i * k + q] * aqj;
-          }
+          for (int q = 0; q < k; ++q) sum -= A64[i * k + q] * Sr[q * k + j] + Sr[i * k + q] * A64[q * k + j];
           T2[e] = R(sum);
         }
         __syncthreads();
@@ -1136,18 +1198,33 @@ __global__ void rr_apply_kernel(DevState* st, const double* Phi, int d, int k, i
 }
 
 // sign[c] from view 0: +1 if the largest-magnitude entry of column c is > 0
+// Sign convention: the entry of largest magnitude of u_c (first one on ties)
+// is made positive, v_c flips with it.  One warp per column.
 __global__ void sign_fix_kernel(double* U, int dx, double* V, int dy, int k) {
-  const int c = threadIdx.x;
+  const int c = blockIdx.x, lane = threadIdx.x;
   if (c >= k) return;
   double best = 0;
-  for (int j = 0; j < dx; ++j) {
-    double u = U[(int64_t)j * k + c];
-    if (fabs(u) > fabs(best)) best = u;
+  int bj = 0x7fffffff;
+  for (int j = lane; j < dx; j += 32) {
+    const double u = U[(int64_t)j * k + c];
+    if (fabs(u) > fabs(best)) {
+      best = u;
+      bj = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+    if (fabs(ob) > fabs(best) || (fabs(ob) == fabs(best) && oj < bj)) {
+      best = ob;
+      bj = oj;
+    }
   }
   if (best < 0) {
-    for (int j = 0; j < dx; ++j) U[(int64_t)j * k + c] = -U[(int64_t)j * k + c];
+    for (int j = lane; j < dx; j += 32) U[(int64_t)j * k + c] = -U[(int64_t)j * k + c];
     if (V != nullptr)
-      for (int j = 0; j < dy; ++j) V[(int64_t)j * k + c] = -V[(int64_t)j * k + c];
+      for (int j = lane; j < dy; j += 32) V[(int64_t)j * k + c] = -V[(int64_t)j * k + c];
   }
 }
 
@@ -1232,9 +1309,9 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
     a.max_iter = p.opt.max_iter;
     a.ls_f = p.ls_f;
     a.ls_L = p.ls_L;
-    size_t smem = sizeof(double) * (9 * kk + 8 * kk + 4 * kk + 2 * kMaxK);
+    size_t smem = sizeof(double) * (9 * kk + 8 * kk + 5 * kk + 2 * kMaxK);
     GB_CUDA(cudaFuncSetAttribute(linesearch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    linesearch_kernel<<<kNTrials, 32, smem, st>>>(a);
+    linesearch_kernel<<<kNTrials, 256, smem, st>>>(a);
     GB_CHECK_LAUNCH();
   }
   {
@@ -1457,7 +1534,7 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     rr_apply_kernel<<<ceil_div(p.v[v].d, 128), 128, 0, st>>>(p.st, p.v[v].Phi, p.v[v].d, k, v, out);
     GB_CHECK_LAUNCH();
   }
-  sign_fix_kernel<<<1, 32, 0, st>>>(out0, p.v[0].d, p.nviews > 1 ? out1 : nullptr, p.nviews > 1 ? p.v[1].d : 0, k);
+  sign_fix_kernel<<<k, 32, 0, st>>>(out0, p.v[0].d, p.nviews > 1 ? out1 : nullptr, p.nviews > 1 ? p.v[1].d : 0, k);
   GB_CHECK_LAUNCH();
   copy_sigma_kernel<<<1, 32, 0, st>>>(p.st, vals, k);
   GB_CHECK_LAUNCH();

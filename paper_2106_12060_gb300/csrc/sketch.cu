@@ -233,6 +233,8 @@ int countsketch_apply(Plan& p, int view, bool center, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- SRHT
+constexpr int kLoadBatch = 8;
+
 // Unnormalized Walsh-Hadamard transform of one column of length N (32 <= N
 // <= 1024, power of two) held in shared memory with row stride `stride`, by
 // one warp: lane l holds rows l + 32 t; butterflies of span < 32 go across
@@ -299,20 +301,37 @@ srht_stage1_kernel(const Tin* __restrict__ Z, int64_t ld, int64_t n, int d, int 
   constexpr int CB = 32, LD = 33;
   const int64_t i2 = blockIdx.y;   // column blocks of one row block run next to each other
   const int c0 = blockIdx.x * CB;
-  for (int e = threadIdx.x; e < N1 * CB; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    const int64_t row = i2 * N1 + r;
-    T val = T(0);
-    if (row < n && c0 + c < d) {
-      if (labels != nullptr) {
-        const double x = to_f64(Z[row * ld + c0 + c]) - means[(int64_t)labels[row] * d + c0 + c];
-        val = (T)(sg[row] < 0 ? -x : x);
-      } else {
-        const T x = to_work<T>(Z[row * ld + c0 + c]);
-        val = sg[row] < 0 ? -x : x;
-      }
+  // loads batched (kLoadBatch in flight per thread), then signs and stores
+  for (int base = 0; base < N1 * CB; base += blockDim.x * kLoadBatch) {
+    Tin z[kLoadBatch];
+    int8_t g[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = base + threadIdx.x + blockDim.x * u;
+      const int r = e >> 5, c = e & 31;
+      const int64_t row = i2 * N1 + r;
+      const bool in = e < N1 * CB && row < n && c0 + c < d;
+      z[u] = in ? Z[row * ld + c0 + c] : Tin(0.0f);
+      g[u] = in ? sg[row] : int8_t(0);
     }
-    buf[r * LD + c] = val;
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = base + threadIdx.x + blockDim.x * u;
+      if (e >= N1 * CB) continue;
+      const int r = e >> 5, c = e & 31;
+      const int64_t row = i2 * N1 + r;
+      T val = T(0);
+      if (g[u] != 0) {
+        if (labels != nullptr) {
+          const double x = to_f64(z[u]) - means[(int64_t)labels[row] * d + c0 + c];
+          val = (T)(g[u] < 0 ? -x : x);
+        } else {
+          const T x = to_work<T>(z[u]);
+          val = g[u] < 0 ? -x : x;
+        }
+      }
+      buf[r * LD + c] = val;
+    }
   }
   __syncthreads();
   if (N1 >= 32) {
@@ -344,9 +363,19 @@ srht_stage2_kernel(const T* __restrict__ Tmid, int d, int N1, int N2, int m1, co
   const int c0 = blockIdx.x * CB;
   const int nsel = off1[a1 + 1] - off1[a1];
   if (nsel == 0) return;
-  for (int e = threadIdx.x; e < N2 * CB; e += blockDim.x) {
-    const int r = e >> 5, c = e & 31;
-    buf[r * LD + c] = (c0 + c < d) ? Tmid[((int64_t)a1 * N2 + r) * d + c0 + c] : T(0);
+  for (int base = 0; base < N2 * CB; base += blockDim.x * kLoadBatch) {
+    T v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = base + threadIdx.x + blockDim.x * u;
+      const int r = e >> 5, c = e & 31;
+      v[u] = (e < N2 * CB && c0 + c < d) ? Tmid[((int64_t)a1 * N2 + r) * d + c0 + c] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int e = base + threadIdx.x + blockDim.x * u;
+      if (e < N2 * CB) buf[(e >> 5) * LD + (e & 31)] = v[u];
+    }
   }
   __syncthreads();
   if (N2 >= 32) {
