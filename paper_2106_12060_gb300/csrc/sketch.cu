@@ -239,40 +239,46 @@ constexpr int kLoadBatch = 8;
 // <= 1024, power of two) held in shared memory with row stride `stride`, by
 // one warp: lane l holds rows l + 32 t; butterflies of span < 32 go across
 // lanes (shuffles), larger spans within the lane's registers.
-template <typename T>
-__device__ __forceinline__ void fwht_warp_col(T* col, int stride, int N) {
+template <typename T, int NT>
+__device__ __forceinline__ void fwht_warp_col_n(T* col, int stride) {
   const int lane = threadIdx.x & 31;
-  const int nt = N >> 5;
-  T v[32];
+  T v[NT];
 #pragma unroll
-  for (int t = 0; t < 32; ++t) v[t] = t < nt ? col[(lane + 32 * t) * stride] : T(0);
+  for (int t = 0; t < NT; ++t) v[t] = col[(lane + 32 * t) * stride];
 #pragma unroll
   for (int h = 1; h < 32; h <<= 1) {
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      if (t < nt) {
-        const T x = v[t];
-        const T y = __shfl_xor_sync(0xffffffffu, x, h);
-        v[t] = (lane & h) ? (y - x) : (x + y);
+    for (int t = 0; t < NT; ++t) {
+      const T x = v[t];
+      const T y = __shfl_xor_sync(0xffffffffu, x, h);
+      v[t] = (lane & h) ? (y - x) : (x + y);
+    }
+  }
+#pragma unroll
+  for (int hb = 1; hb < NT; hb <<= 1) {  // span 32 hb rows = hb register slots
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if ((t & hb) == 0) {
+        const T a = v[t], b = v[t + hb];
+        v[t] = a + b;
+        v[t + hb] = a - b;
       }
     }
   }
 #pragma unroll
-  for (int hb = 1; hb < 32; hb <<= 1) {  // span 32 hb rows = hb register slots
-    if (hb < nt) {
-#pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        if ((t & hb) == 0 && t + hb < 32) {
-          const T a = v[t], b = v[t + hb];
-          v[t] = a + b;
-          v[t + hb] = a - b;
-        }
-      }
-    }
+  for (int t = 0; t < NT; ++t) col[(lane + 32 * t) * stride] = v[t];
+}
+
+template <typename T>
+__device__ __forceinline__ void fwht_warp_col(T* col, int stride, int N) {
+  switch (N >> 5) {
+    case 1: fwht_warp_col_n<T, 1>(col, stride); break;
+    case 2: fwht_warp_col_n<T, 2>(col, stride); break;
+    case 4: fwht_warp_col_n<T, 4>(col, stride); break;
+    case 8: fwht_warp_col_n<T, 8>(col, stride); break;
+    case 16: fwht_warp_col_n<T, 16>(col, stride); break;
+    default: fwht_warp_col_n<T, 32>(col, stride); break;
   }
-#pragma unroll
-  for (int t = 0; t < 32; ++t)
-    if (t < nt) col[(lane + 32 * t) * stride] = v[t];
 }
 
 // Transform of length N < 32 (tiny n): one thread per column
