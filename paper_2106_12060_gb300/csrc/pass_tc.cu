@@ -420,21 +420,44 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       uint8_t* wb = ws + b * kWBuf;
       {
         // W_v row rr = hi part (TMEM column c) + lo part (column kH1 + c),
-        // c < 2k.  Lanes 0..15 hold the rows (M = 64 layout); lanes 16..31
-        // take the upper half of the columns of the same rows by shuffle.
-        const int hsplit = (a.k2 + 1) >> 1;
+        // c < 2k.  Lanes 0..15 hold the rows (M = 64 layout, rows 16 q ..
+        // 16 q + 15).  Lanes 0..15 convert column c, lanes 16..31 column
+        // c + kH1/2 of the same rows (by shuffle); then even lanes store the
+        // bf16 pair of rows (rr, rr + 1), which are adjacent in the K-major
+        // operand.
+        constexpr int kSplit = kH1 / 2;
         const bool upper = lane >= 16;
         const int rr = 16 * q + (lane & 15);
+        // in phases over all columns, so that the shuffles of different
+        // columns are in flight together
+        float w[kSplit];
+        uint32_t hs[kSplit], ls[kSplit];
 #pragma unroll
-        for (int c = 0; c < kH1; ++c) {
-          const float x = d1[c] + d1[kH1 + c];
-          const float w = __shfl_sync(0xffffffffu, x, lane & 15);
-          if (c < a.k2 && (upper ? c >= hsplit : c < hsplit)) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));
-            const uint32_t off = swz(view * kHalf + c, rr);
-            *reinterpret_cast<__nv_bfloat16*>(wb + off) = hi;
-            *reinterpret_cast<__nv_bfloat16*>(wb + kWs + off) = lo;
+        for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = d1[c0 + kSplit] + d1[kH1 + c0 + kSplit];
+#pragma unroll
+        for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
+#pragma unroll
+        for (int c0 = 0; c0 < kSplit; ++c0) {
+          const float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
+          const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+          hs[c0] = __bfloat16_as_ushort(hi);
+          ls[c0] = __bfloat16_as_ushort(lo);
+        }
+#pragma unroll
+        for (int c0 = 0; c0 < kSplit; ++c0) {
+          hs[c0] |= __shfl_down_sync(0xffffffffu, hs[c0], 1) << 16;
+          ls[c0] |= __shfl_down_sync(0xffffffffu, ls[c0], 1) << 16;
+        }
+        if ((lane & 1) == 0) {
+#pragma unroll
+          for (int c0 = 0; c0 < kSplit; ++c0) {
+            const int c = upper ? c0 + kSplit : c0;
+            if (c < a.k2) {
+              const uint32_t off = swz(view * kHalf + c, rr);
+              *reinterpret_cast<uint32_t*>(wb + off) = hs[c0];
+              *reinterpret_cast<uint32_t*>(wb + kWs + off) = ls[c0];
+            }
           }
         }
       }

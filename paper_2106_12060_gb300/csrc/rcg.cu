@@ -1775,8 +1775,10 @@ int warm_start(Plan& p, cudaStream_t st) {
       GB_TRY(cxy(false, y.wsT, x.wsT));
       GB_TRY(rx(true, x.wsT, Ub, c));
       if (it == iters) break;  // Ub = C V (unnormalized) for the Rayleigh-Ritz step
-      GB_TRY(orth(p, Ub, dx, c, part, small, st));
-      // V = orth(R_y^{-T} Cxy^T R_x^{-1} U)
+      // V = orth(C^T U) with C = R_x^{-T} Cxy R_y^{-1}: U = C V needs no
+      // orthonormalization of its own (span(C^T C V) is the same either way,
+      // and one step changes the conditioning of the block only by the
+      // spread of the top 2k singular values)
       GB_TRY(rx(false, Ub, x.wsT, c));
       GB_TRY(cxy(true, x.wsT, y.wsT));
       GB_TRY(ry(true, y.wsT, Vb, c));
