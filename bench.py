@@ -36,6 +36,26 @@ GTOL = 3e-3
 REFINE = 2
 
 
+# DRAM traffic of one full-size tc_pass_kernel launch (read + write bytes),
+# from the ncu capture summarised in profiles/tc_pass_kernel_cca_tall_bf16.md
+# (131072 rows; reads scaled by rows to 262144, partial writes as measured).
+# Valid only for the kernel source it was taken on; any other source reports
+# null.
+PASS_TRAFFIC_BYTES = 268.757248e6 * 2 + 5.793280e6
+PASS_TRAFFIC_SRC_SHA256 = "dacb2de3a78877bb839689fbe8976362b16c978715bd3b9c2fe48fb782e8268b"
+
+
+def pass_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2106_12060_gb300", "csrc", "pass_tc.cu")
+    try:
+        with open(path, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return PASS_TRAFFIC_BYTES if h == PASS_TRAFFIC_SRC_SHA256 else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -158,6 +178,46 @@ def cpu_baseline(P, budget_s: float = 20.0):
                       f"{reps} reps, time scaled by n/{ns}"}
 
 
+def fp64_comparison(gb, P, sig_bf16, steps: int = 2):
+    """The same solve (same sketch draws, stopping rule and refinement) with
+    the data stored in FP64 (the BF16 values, exactly: the same problem) and
+    the FP64 CUDA-core pass: the plain FP64 form on the same GPU."""
+    import torch
+    c = P["config"]
+    n, dx, dy, k = c["n"], c["dx"], c["dy"], c["k"]
+    X = torch.from_numpy(np.ascontiguousarray(P["X64"])).cuda()
+    Y = torch.from_numpy(np.ascontiguousarray(P["Y64"])).cuda()
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
+                             check_every=8)
+    plan = gb.cca_plan(n, dx, dy, k, "f64", opt)
+    U = torch.empty(dx, k, dtype=torch.float64, device="cuda")
+    V = torch.empty(dy, k, dtype=torch.float64, device="cuda")
+    sig = torch.empty(k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        gb.cca_precondition(plan, X, Y, LAM, LAM)
+        return gb.cca_solve(plan, U=U, V=V, sigma=sig)[3]
+
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [step() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s64 = sig.cpu().numpy()
+    s16 = sig_bf16.cpu().numpy()
+    plan.close()
+    del X, Y
+    torch.cuda.empty_cache()
+    return {"ms": ms, "steps": steps, "storage": "f64", "iterations": float(np.mean([i["iters"] for i in infos])),
+            "passes_per_solve": float(np.mean([i["passes"] for i in infos])),
+            "sigma_max_rel_diff_vs_bf16": float(np.max(np.abs(s64 - s16) / np.abs(s64)))}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -256,6 +316,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     clocks = sampler.stop()
+    fp64 = None if args.no_fp64_compare else fp64_comparison(gb, P, sig)
 
     hbm, peak_src = peaks()
     elt = {"bf16": 2, "f32": 4, "f64": 8}[dt]
@@ -275,7 +336,7 @@ def run_ours(args, ws, rank, local):
         "passes_per_solve": float(np.mean([i["passes"] for i in infos])),
         "fused_pass": {"ms": pass_ms, "GBps": achieved, "frac_of_hbm": achieved / hbm},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                     "frac": achieved / hbm, "traffic": pass_traffic(), "peak_source": peak_src,
                      "kernel": "tc_pass_kernel: fused CCA data pass (X^T W, Y^T W with W = [X Phi_x, Y Phi_y])",
                      "algorithmic_bytes": pass_bytes},
         "e2e": {"value": e2e_ms / (args.steps * ws), "unit": "ms",
@@ -284,6 +345,9 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if fp64 is not None:
+        fp64["bf16_speedup"] = fp64["ms"] / value
+        line["fp64_gpu"] = fp64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P)
     if rank == 0:
@@ -352,6 +416,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the timed solve of the same workload stored in FP64")
     ap.add_argument("--pass-only", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--solve-rows", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()

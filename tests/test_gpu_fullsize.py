@@ -54,6 +54,19 @@ def test_tall_cca_bench_settings(gb, tall, refine):
     assert rel(s, ref) < 1e-6, (s, ref, info)
 
 
+def test_tall_cca_fp64_storage(gb, tall):
+    """The plain FP64 form (the same BF16 values stored in FP64, FP64 pass):
+    canonical correlations within 1e-8 of the oracle."""
+    P, ref = tall
+    c = P["config"]
+    o = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=1e-6)
+    plan = gb.cca_plan(c["n"], c["dx"], c["dy"], c["k"], "f64", o)
+    X, Y = to_dev(P["X64"], "f64"), to_dev(P["Y64"], "f64")
+    gb.cca_precondition(plan, X, Y, c["lam"], c["lam"])
+    sig, U, V, info = gb.cca_solve(plan)
+    assert rel(np64(sig), ref) < 1e-8, (np64(sig), ref, info)
+
+
 def test_lda_workload(gb):
     import torch
     P = make_workload("lda_f32")
