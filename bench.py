@@ -41,8 +41,8 @@ REFINE = 2
 # (131072 rows; reads scaled by rows to 262144, partial writes as measured).
 # Valid only for the kernel source it was taken on; any other source reports
 # null.
-PASS_TRAFFIC_BYTES = 268.757248e6 * 2 + 5.793280e6
-PASS_TRAFFIC_SRC_SHA256 = "dacb2de3a78877bb839689fbe8976362b16c978715bd3b9c2fe48fb782e8268b"
+PASS_TRAFFIC_BYTES = 268.716544e6 * 2 + 5.929472e6
+PASS_TRAFFIC_SRC_SHA256 = "ec22e5aa4545792b41f28eb4bef771b95b6f0377885c5838536a3087a4191cc8"
 
 
 def pass_traffic():

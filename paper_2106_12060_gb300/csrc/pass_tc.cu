@@ -12,25 +12,34 @@
 // 64 x d_v BF16 block (<= 64 KB) in shared memory for both GEMMs and every
 // byte of the data is read from HBM exactly once.  Two tiles are resident per
 // CTA (double buffering): the next tile streams in while the current one is
-// in its epilogue and second GEMM.  Per tile:
-//   GEMM 1  (tcgen05, M = 64, per CTA): W_v = Z_v Phi_v, 64 x 48 FP32 in TMEM
-//           (B = Phi_v split into bf16 hi|lo columns, 24 each; rows 16 q ..
+// in its epilogue and second GEMM.  Per tile (h = 20 for 2k <= 20, else 24):
+//   GEMM 1  (tcgen05, M = 64, per CTA): W_v = Z_v Phi_v, 64 x 2h FP32 in TMEM
+//           (B = Phi_v split into bf16 hi|lo columns, h each; rows 16 q ..
 //           16 q + 15 of the M = 64 result sit in lanes 32 q .. 32 q + 15);
 //   epilogue warps read W_v from TMEM, add the hi and lo halves, split W_v
 //           into bf16 hi/lo and write it into the K-major B operand of GEMM 2
-//           (N rows 24 v .. 24 v + 23) of their own CTA, then push that half
-//           into the peer CTA's operand with a bulk shared::cluster copy;
-//   GEMM 2  (tcgen05, M = 128, per CTA): G_v += Z_v^T [W_x | W_y] over the
-//           same shared-memory blocks read as MN-major A (128 columns of Z_v
-//           per MMA), accumulated in TMEM over all tiles of the cluster.
+//           (rows h v .. h v + h - 1 of the hi part and of the lo part) of
+//           their own CTA, then push those rows into the peer CTA's operand
+//           with bulk shared::cluster copies;
+//   GEMM 2  (tcgen05, M = 128, N = 4h, per CTA): G_v += Z_v^T [W_x | W_y]
+//           for the hi and the lo parts at once (separate accumulator
+//           columns, added when G is drained), over the same shared-memory
+//           blocks read as MN-major A (128 columns of Z_v per MMA),
+//           accumulated in TMEM over all tiles of the cluster.  One MMA per
+//           K step reads each block of the tile once: the operand reads from
+//           shared memory, not the tensor arithmetic, bound these small-N
+//           products.
 // The end of GEMM 2 is signalled to both CTAs (multicast commit), which
 // frees both CTAs' W operand buffer of that tile.  At the end the epilogue
 // warps drain G to a per-cluster FP32 partial; a second kernel sums the
 // partials in fixed order.
 //
-// Roles per CTA: warp 0 lane 0 = TMA producer, warp 1 lane 0 = GEMM 1
-// issuer, warp 3 lane 0 = GEMM 2 issuer, warp 2 = TMEM allocator, warps 4-7 =
-// epilogue (TMEM lane quarters 0-3).
+// Roles per CTA: warp 0 lane 0 = TMA producer (it first issues the bulk copy
+// of the own view's Phi image, so the ring starts filling at once); warp 1
+// lane 0 = GEMM 1 issuer (with 2k <= 20: for the first half of the pairs,
+// warp 2 lane 0 for the second half, into a second accumulator that the
+// epilogue adds); warp 3 lane 0 = GEMM 2 issuer; warp 2 = TMEM allocator;
+// warps 4-7 = epilogue (TMEM lane quarters 0-3).
 // Every mbarrier wait is bounded in time; on expiry the CTA records an error
 // code, waits (bounded) for its own copies and MMAs, frees TMEM and leaves
 // after a cluster barrier (no remote access can target an exited CTA).
@@ -43,17 +52,14 @@ namespace gbcca {
 namespace tc {
 
 constexpr int kRows = 64;             // rows per tile (MMA M of GEMM 1, K of GEMM 2)
-constexpr int kNW = 48;               // N of GEMM 2: W rows [W_x | W_y], 24 per view
-constexpr int kHalf = 24;             // W rows of a view (2k <= 24)
+constexpr int kHalfMax = 24;          // W rows of a view at most (2k <= 24)
 constexpr int kTileSlots = 4;         // pair slots of one tile (512 columns)
 constexpr int kSlot = 16384;          // two 64 x 64 BF16 boxes
 constexpr int kBox = 8192;
 constexpr int kPhiView = 49152;       // stride of the views' Phi images in the plan buffer
-constexpr int kWs = kNW * 128;        // W operand (hi or lo) of one tile: 1 K-box (64 rows)
-constexpr int kWBuf = 2 * kWs;        // hi + lo
-constexpr int kWHalf = kHalf * 128;   // one view's rows of the W operand
 constexpr int kMaxSmem = 232448;      // dynamic shared memory of one CTA
-constexpr uint32_t kTmemCols = 512;   // W: 48 b (b = 0, 1), G: 2 kNW + kNW p (p < 4 pairs)
+constexpr uint32_t kTmemCols = 512;   // W: columns kTW (nacc b + a); G: kTG + kN2 p (p < 4 pairs)
+constexpr int kTW = 48;               // TMEM column stride of the W accumulators
 constexpr long long kTimeout = 2000000000ll;      // cycles (~1 s)
 
 // Shared-memory layout and barriers for GEMM 1 with N = 2 kH1 (Phi columns as
@@ -64,6 +70,23 @@ struct Lay {
   static constexpr int kN1 = 2 * kH1;
   static constexpr int kKBox1 = kN1 * 128;       // one K-box (64 columns) of the Phi image
   static constexpr int kPhiBytes = 8 * kKBox1;   // 512 columns
+  // W operand of GEMM 2 (K-major, one K-box of 64 tile rows): rows
+  // [W_x | W_y] of the hi parts (kH1 rows per view; rows 2k .. kH1 - 1 stay
+  // zero), then the same rows of the lo parts, so that one MMA with
+  // N = kN2 reads the tile's columns once for both parts.
+  static constexpr int kHalf = kH1;              // W rows of a view
+  static constexpr int kNW = 2 * kH1;            // rows of one part (hi or lo)
+  static constexpr int kN2 = 2 * kNW;            // N of GEMM 2
+  static constexpr int kWs = kNW * 128;          // bytes of one part
+  static constexpr int kWBuf = 2 * kWs;          // hi + lo
+  static constexpr int kWHalf = kHalf * 128;     // one view's rows of one part
+  static constexpr int kD1Cols = ((kN1 + 15) / 16) * 16;  // TMEM columns read back for W
+  // GEMM 1 is issued by two threads (pairs [0, ceil(np / 2)) and the rest),
+  // each into its own accumulator, when TMEM has room for 2 x 2 W
+  // accumulators and the G accumulators: one thread issues an MMA only about
+  // every 50 cycles, two streams overlap in the tensor pipe.
+  static constexpr int kNAcc = (4 * kTW + kTileSlots * kN2 <= (int)kTmemCols) ? 2 : 1;
+  static constexpr int kTG = 2 * kNAcc * kTW;    // first TMEM column of the G accumulators
   static constexpr int kStages = (kMaxSmem - kPhiBytes - 2 * kWBuf - 512 - 1024) / kSlot;
   static constexpr int kRingOff = kPhiBytes;
   static constexpr int kWsOff = kRingOff + kStages * kSlot;
@@ -73,8 +96,13 @@ struct Lay {
   static constexpr int kFull = 0, kEmpty = kStages, kD1Full = 2 * kStages;  // [stages], [stages], [2]
   static constexpr int kD1Free = kD1Full + 2, kEpiSync = kD1Free + 2, kWReady = kEpiSync + 1;  // [2], 1, [2]
   static constexpr int kWPeer = kWReady + 2, kWFree = kWPeer + 2, kGDone = kWFree + 2;      // [2], [2], 1
-  static constexpr int kFinal = kGDone + 1, kNumBars = kFinal + 2;  // [2]: one per MMA-issuing thread
+  static constexpr int kFinal = kGDone + 1;                         // [3]: one per MMA-issuing thread
+  static constexpr int kPhiFull = kFinal + 3, kNumBars = kPhiFull + 1;  // Phi image in shared memory
   static_assert(kStages >= 2 * kTileSlots, "two resident tiles");
+  static_assert(kN1 <= kTW && kD1Cols <= kTW, "W buffers in TMEM");
+  static_assert(kN2 % 16 == 0 && kTG + kTileSlots * kN2 <= (int)kTmemCols, "G accumulators in TMEM");
+  static_assert(kPhiBytes % 16 == 0 && kWHalf % 16 == 0 && kWs % 1024 == 0, "bulk copy and swizzle alignment");
+  static_assert(kRows == 64, "GEMM 2 issues four K steps of 16 rows");
   static_assert(kNumBars * 8 + 8 <= 512, "barrier area");
   static_assert(kSmemBytes <= kMaxSmem, "shared memory");
 };
@@ -200,6 +228,14 @@ __device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_
                : "memory");
 }
 
+// Bulk copy of `bytes` from global memory into this CTA's shared memory;
+// completion is counted on `bar` (this CTA).
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -239,13 +275,14 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   constexpr int kStages = L::kStages;
   constexpr int kFull = L::kFull, kEmpty = L::kEmpty, kD1Full = L::kD1Full, kD1Free = L::kD1Free;
   constexpr int kEpiSync = L::kEpiSync, kWReady = L::kWReady, kWPeer = L::kWPeer, kWFree = L::kWFree;
-  constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kNumBars = L::kNumBars;
+  constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kPhiFull = L::kPhiFull, kNumBars = L::kNumBars;
+  constexpr int kTG = L::kTG;
   if (a.done != nullptr && *a.done) return;  // uniform over the cluster: no remote access yet
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* phi_s = smem;
   uint8_t* ring = smem + L::kRingOff;
-  uint8_t* ws = smem + L::kWsOff;  // [buffer][hi | lo][48 rows][128 B]
+  uint8_t* ws = smem + L::kWsOff;  // [buffer][hi | lo][kNW rows][128 B]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -254,16 +291,18 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   const uint32_t peer = 1u - (uint32_t)view;
   const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
   const int npairs = a.pairs[view];
+  // GEMM 1 issuers: warp 1 takes pairs [0, split), warp 2 (after allocating
+  // TMEM) pairs [split, npairs) into the second accumulator
+  const int split = L::kNAcc == 2 ? (npairs + 1) / 2 : npairs;
+  const int nissue1 = split < npairs ? 2 : 1;
   const int k4 = 2 * a.k2;
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
-  // own view's Phi image -> shared memory (generic proxy); zero W operands
+  // zero the W operands (the own view's Phi image arrives later by a bulk
+  // copy that the producer issues ahead of the first tile)
   {
-    const uint4* src = reinterpret_cast<const uint4*>(a.phi_img + view * kPhiView);
-    uint4* dst = reinterpret_cast<uint4*>(phi_s);
-    for (int i = threadIdx.x; i < L::kPhiBytes / 16; i += blockDim.x) dst[i] = src[i];
     uint4* wz = reinterpret_cast<uint4*>(ws);
-    for (int i = threadIdx.x; i < 2 * kWBuf / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < 2 * L::kWBuf / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
   }
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -271,7 +310,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       mbar_init(bar(kEmpty + s), 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(bar(kD1Full + b), 1);
+      mbar_init(bar(kD1Full + b), nissue1);  // one commit per GEMM 1 issuer
       mbar_init(bar(kD1Free + b), 128);
       mbar_init(bar(kWReady + b), 1);
       mbar_init(bar(kWPeer + b), 1);   // + the peer's bytes
@@ -281,6 +320,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     mbar_init(bar(kGDone), 1);
     mbar_init(bar(kFinal), 1);
     mbar_init(bar(kFinal + 1), 1);
+    mbar_init(bar(kFinal + 2), 1);
+    mbar_init(bar(kPhiFull), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -305,6 +346,14 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     int last_use[kStages];
     for (int s = 0; s < kStages; ++s) last_use[s] = -1;
     const CUtensorMap* map = view == 0 ? &tmx : &tmy;
+    if (nitems > 0) {
+      // own view's Phi image (GEMM 1's B operand), one bulk copy per K-box;
+      // GEMM 1 waits for it, so no copy is left in flight at exit
+      const uint32_t pb = bar(kPhiFull);
+      mbar_expect_tx(pb, L::kPhiBytes);
+      for (int kb = 0; kb < 8; ++kb)
+        bulk_g2s(smem_u32(phi_s + kb * L::kKBox1), a.phi_img + view * kPhiView + kb * L::kKBox1, L::kKBox1, pb);
+    }
     for (int it = 0; it < nitems; ++it) {
       const int j = it / npairs, p = it - j * npairs;
       const int row0 = (cid + j * ncl) * kRows;
@@ -322,6 +371,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     }
     if (!ok) {
       // wait (bounded) for the copies this thread issued before leaving
+      if (nitems > 0) {
+        const long long t0 = clock64();
+        while (!mbar_try(bar(kPhiFull), 0) && clock64() - t0 < kTimeout) {
+        }
+      }
       for (int s = 0; s < kStages; ++s) {
         if (last_use[s] < 0) continue;
         const long long t0 = clock64();
@@ -329,35 +383,56 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         }
       }
     }
-  } else if ((warp == 1 || warp == 3) && lane == 0) {
+  } else if ((warp == 1 || warp == 3 || (warp == 2 && nissue1 == 2)) && lane == 0) {
     // ------------------------------------------------------------ MMA issuers
-    // warp 1: GEMM 1 of every tile; warp 3: GEMM 2 of every tile.  Separate
-    // issuers keep GEMM 2 of tile j (which frees its ring slots) from waiting
-    // behind the arrival of tile j + 1's data.
+    // warps 1 and 2: GEMM 1 of every tile (half of the pairs each when there
+    // are two accumulators); warp 3: GEMM 2 of every tile.  Separate issuers
+    // keep GEMM 2 of tile j (which frees its ring slots) from waiting behind
+    // the arrival of tile j + 1's data.
     constexpr uint32_t id1 = idesc_bf16(64, L::kN1, 0, 0);
-    constexpr uint32_t id2 = idesc_bf16(128, kNW, 1, 0);
+    constexpr uint32_t id2 = idesc_bf16(128, L::kN2, 1, 0);
     bool ok = true;
-    if (warp == 1) {
-      const uint32_t bbase = smem_u32(phi_s);
+    // One thread issues an MMA only about every 50 cycles at best, which for
+    // these small shapes is slower than the tensor pipe; the issue loops
+    // therefore do no descriptor arithmetic beyond one add of a compile-time
+    // offset (a descriptor's low bits are the shared-memory address / 16,
+    // and every operand address here is below 2^18).
+    if (warp == 1 || warp == 2) {
+      const int acc_i = warp - 1;  // accumulator of this issuer
+      const int pb = acc_i == 0 ? 0 : split, pe = acc_i == 0 ? split : npairs;
+      const uint64_t bdesc0 = sdesc(smem_u32(phi_s), 16, 1024);
+      if (my_tiles > 0) ok = mbar_wait(bar(kPhiFull), 0, abort_flag);
       for (int j = 0; j < my_tiles && ok; ++j) {
         const int b = j & 1;
         // W buffer b was last read by the epilogue of tile j - 2
         if (j >= 2 && !(ok = mbar_wait(bar(kD1Free + b), ((j - 2) >> 1) & 1, abort_flag))) break;
         tc_fence_after();
-        const uint32_t d1 = tmem + (uint32_t)(b * kNW);
-        for (int p = 0; p < npairs; ++p) {
+        const uint32_t d1 = tmem + (uint32_t)((L::kNAcc * b + acc_i) * kTW);
+        for (int p = pb; p < pe; ++p) {
           const int it = j * npairs + p;
           const int slot = it % kStages, use = it / kStages;
           if (!(ok = mbar_wait(bar(kFull + slot), use & 1, abort_flag))) break;
           tc_fence_after();
-          const uint32_t abase = smem_u32(ring + slot * kSlot);
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            const int box = s >> 2, kin = s & 3;
-            const uint64_t ad = sdesc(abase + box * kBox + kin * 32, 16, 1024);
-            const uint64_t bd = sdesc(bbase + (2 * p + box) * L::kKBox1 + kin * 32, 16, 1024);
-            mma_bf16(d1, ad, bd, id1, (p > 0 || s > 0) ? 1u : 0u);
+          const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), 16, 1024);
+          const uint64_t bd0 = bdesc0 + (uint64_t)((2 * p * L::kKBox1) >> 4);
+          // K steps of 16 columns: box s / 4 of the slot, 32-byte step s % 4
+          // inside its 128-byte swizzled rows
+#define GB_G1_MMA(s, acc)                                                                        \
+  mma_bf16(d1, ad0 + (uint64_t)((((s) >> 2) * kBox + ((s) & 3) * 32) >> 4),                      \
+           bd0 + (uint64_t)((((s) >> 2) * L::kKBox1 + ((s) & 3) * 32) >> 4), id1, acc)
+          if (p == pb) {
+            GB_G1_MMA(0, 0u);
+          } else {
+            GB_G1_MMA(0, 1u);
           }
+          GB_G1_MMA(1, 1u);
+          GB_G1_MMA(2, 1u);
+          GB_G1_MMA(3, 1u);
+          GB_G1_MMA(4, 1u);
+          GB_G1_MMA(5, 1u);
+          GB_G1_MMA(6, 1u);
+          GB_G1_MMA(7, 1u);
+#undef GB_G1_MMA
         }
         if (!ok) break;
         mma_commit(bar(kD1Full + b));
@@ -366,25 +441,25 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       for (int j = 0; j < my_tiles && ok; ++j) {
         const int b = j & 1;
         // both halves of this tile's W operand: ours and the peer's
-        mbar_expect_tx(bar(kWPeer + b), 2 * kWHalf);
+        mbar_expect_tx(bar(kWPeer + b), 2 * L::kWHalf);
         if (!(ok = mbar_wait(bar(kWReady + b), (j >> 1) & 1, abort_flag))) break;
         if (!(ok = mbar_wait(bar(kWPeer + b), (j >> 1) & 1, abort_flag))) break;
         tc_fence_after();
-        const uint32_t wbase = smem_u32(ws + b * kWBuf);
+        const uint64_t wd0 = sdesc(smem_u32(ws + b * L::kWBuf), 16, 1024);
+        const uint32_t acc0 = j > 0 ? 1u : 0u;
         for (int p = 0; p < npairs; ++p) {
           const int it = j * npairs + p;
           const int slot = it % kStages;
-          const uint32_t g = tmem + (uint32_t)(2 * kNW + p * kNW);
-          const uint32_t abase = smem_u32(ring + slot * kSlot);
-#pragma unroll
-          for (int s = 0; s < kRows / 16; ++s) {
-            const uint64_t ad = sdesc(abase + s * 2048, kBox, 1024);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint64_t bd = sdesc(wbase + h * kWs + s * 32, 16, 1024);
-              mma_bf16(g, ad, bd, id2, (j > 0 || s > 0 || h > 0) ? 1u : 0u);
-            }
-          }
+          const uint32_t g = tmem + (uint32_t)(kTG + p * L::kN2);
+          const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), kBox, 1024);
+          // B = the hi rows and then the lo rows of W (N = kN2): the tile's
+          // columns are read once per K step of 16 rows (A: 8-row groups of
+          // 1024 bytes, B: 32-byte steps inside the swizzled rows); the lo
+          // products accumulate in their own columns of G
+          mma_bf16(g, ad0, wd0, id2, acc0);
+          mma_bf16(g, ad0 + (uint64_t)(2048 >> 4), wd0 + (uint64_t)(32 >> 4), id2, 1u);
+          mma_bf16(g, ad0 + (uint64_t)(4096 >> 4), wd0 + (uint64_t)(64 >> 4), id2, 1u);
+          mma_bf16(g, ad0 + (uint64_t)(6144 >> 4), wd0 + (uint64_t)(96 >> 4), id2, 1u);
           mma_commit(bar(kEmpty + slot));
         }
         // both CTAs learn that this CTA's GEMM 2 has consumed buffer b
@@ -394,7 +469,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     }
     if (!ok) {
       // let the MMAs this thread issued finish before the CTA frees its memory
-      const int f = kFinal + (warp == 3 ? 1 : 0);
+      const int f = kFinal + (warp == 3 ? 1 : (warp == 2 ? 2 : 0));
       mma_commit(bar(f));
       const long long t0 = clock64();
       while (!mbar_try(bar(f), 0) && clock64() - t0 < kTimeout) {
@@ -409,15 +484,26 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       const int b = j & 1;
       if (!(ok = mbar_wait(bar(kD1Full + b), (j >> 1) & 1, abort_flag))) break;
       tc_fence_after();
-      float d1[kNW];
+      float d1[L::kD1Cols];
 #pragma unroll
-      for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(b * kNW + c), &d1[c]);
+      for (int c = 0; c < L::kD1Cols; c += 16)
+        tmem_ld16(tmem + lane_off + (uint32_t)(L::kNAcc * b * kTW + c), &d1[c]);
+      if (nissue1 == 2) {
+        // second GEMM 1 accumulator (the other half of the pairs)
+        float d2[L::kD1Cols];
+#pragma unroll
+        for (int c = 0; c < L::kD1Cols; c += 16)
+          tmem_ld16(tmem + lane_off + (uint32_t)((L::kNAcc * b + 1) * kTW + c), &d2[c]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < L::kD1Cols; ++c) d1[c] += d2[c];
+      }
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(bar(kD1Free + b));
       // both CTAs' GEMM 2 of tile j - 2 must be done with both halves of buffer b
       if (j >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((j - 2) >> 1) & 1, abort_flag))) break;
-      uint8_t* wb = ws + b * kWBuf;
+      uint8_t* wb = ws + b * L::kWBuf;
       {
         // W_v row rr = hi part (TMEM column c) + lo part (column kH1 + c),
         // c < 2k.  Lanes 0..15 hold the rows (M = 64 layout, rows 16 q ..
@@ -454,9 +540,9 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           for (int c0 = 0; c0 < kSplit; ++c0) {
             const int c = upper ? c0 + kSplit : c0;
             if (c < a.k2) {
-              const uint32_t off = swz(view * kHalf + c, rr);
+              const uint32_t off = swz(view * L::kHalf + c, rr);
               *reinterpret_cast<uint32_t*>(wb + off) = hs[c0];
-              *reinterpret_cast<uint32_t*>(wb + kWs + off) = ls[c0];
+              *reinterpret_cast<uint32_t*>(wb + L::kWs + off) = ls[c0];
             }
           }
         }
@@ -470,8 +556,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint32_t src = smem_u32(wb + h * kWs + view * kWHalf);
-          bulk_to_peer(map_peer(src, peer), src, kWHalf, pbar);
+          const uint32_t src = smem_u32(wb + h * L::kWs + view * L::kWHalf);
+          bulk_to_peer(map_peer(src, peer), src, L::kWHalf, pbar);
         }
         mbar_arrive(bar(kWReady + b));
       }
@@ -484,17 +570,17 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       const int D = a.d[0] + a.d[1];
       float* out = a.partG + (int64_t)cid * D * k4;
       for (int p = 0; p < npairs; ++p) {
-        float g[kNW];
+        float g[L::kN2];
 #pragma unroll
-        for (int c = 0; c < kNW; c += 16) tmem_ld16(tmem + g_lane_off + (uint32_t)(2 * kNW + p * kNW + c), &g[c]);
+        for (int c = 0; c < L::kN2; c += 16) tmem_ld16(tmem + g_lane_off + (uint32_t)(kTG + p * L::kN2 + c), &g[c]);
         tmem_ld_wait();
         const int col = 128 * p + rg;
         if (col < a.d[view]) {
           float* o = out + (int64_t)(view * D0 + col) * k4;
 #pragma unroll
-          for (int c = 0; c < kNW; ++c) {
-            const int vv = c / kHalf, cc = c - vv * kHalf;
-            if (cc < a.k2) o[vv * a.k2 + cc] = g[c];
+          for (int c = 0; c < L::kNW; ++c) {
+            const int vv = c / L::kHalf, cc = c - vv * L::kHalf;
+            if (cc < a.k2) o[vv * a.k2 + cc] = g[c] + g[L::kNW + c];  // hi + lo products
           }
         }
       }
@@ -665,7 +751,7 @@ int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
 // MMA columns), dx, dy <= 512 (TMEM and shared-memory budget), 16-byte
 // aligned rows (ld a multiple of 8) and 16-byte aligned bases.
 bool tc_pass_eligible(const Plan& p) {
-  if (p.kind != kCCA || p.dtype != GBCCA_BF16 || 2 * p.k > tc::kHalf || p.v[0].d > 512 || p.v[1].d > 512)
+  if (p.kind != kCCA || p.dtype != GBCCA_BF16 || 2 * p.k > tc::kHalfMax || p.v[0].d > 512 || p.v[1].d > 512)
     return false;
   for (int v = 0; v < 2; ++v) {
     if (p.v[v].ld % 8 != 0 || (reinterpret_cast<uintptr_t>(p.v[v].Z) & 15) != 0) return false;
@@ -687,7 +773,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     a.d[v] = p.v[v].d;
     a.pairs[v] = ceil_div(p.v[v].d, 128);
   }
-  const int h1 = k2 <= 20 ? 20 : tc::kHalf;  // Phi image rows per half (GEMM 1 N = 2 h1)
+  const int h1 = k2 <= 20 ? 20 : tc::kHalfMax;  // Phi image rows per half (GEMM 1 N = 2 h1)
   {
     const int dmax = std::max(p.v[0].d, p.v[1].d);
     tc::phi_image_kernel<<<dim3(ceil_div(dmax * k2, 256), 2), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d,
@@ -700,8 +786,8 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   a.partG = p.tc_part;
   a.err = p.flag;
   a.done = done;
-  auto kern = h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalf>;
-  const int smem = h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalf>::kSmemBytes;
+  auto kern = h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>;
+  const int smem = h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes;
   GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
