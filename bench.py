@@ -28,9 +28,11 @@ METRIC = "CCA solve time to 1e-6 rel. objective; fused pass % of HBM peak; p50/p
 WORKLOAD = "cca_tall_bf16"
 LAM = 1e-4
 # Stopping rule: ||grad||_M <= GTOL ||grad_0||_M.  On this workload it gives a
-# relative objective suboptimality below 1e-7 and canonical correlations
-# within 1e-6 of the FP64 oracle (checked by tests/test_gpu_fullsize.py).
-GTOL = 3e-3
+# relative objective suboptimality below 1e-7 and every canonical correlation
+# within 1e-6 of the FP64 oracle (checked by tests/test_gpu_fullsize.py);
+# 3e-3 left the smallest correlation at 1.0-1.4e-6, depending on rounding
+# order, so the rule keeps a margin.
+GTOL = 2e-3
 # Final Rayleigh-Ritz step from the Grams of the tensor-core pass (refine = 2;
 # the same test checks this setting against the FP64 oracle).
 REFINE = 2
@@ -315,6 +317,28 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    # the same solves with the iteration batches replayed from CUDA graphs
+    # (the library's default; per-pass event timing needs direct launches)
+    gopt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
+                              check_every=8, time_passes=0, refine=REFINE, graphs=1)
+    gplan = gb.cca_plan(n, dx, dy, k, dt, gopt)
+
+    def gstep():
+        gb.cca_precondition(gplan, X, Y, LAM, LAM)
+        return gb.cca_solve(gplan, U=U, V=V, sigma=sig)[3]
+
+    for _ in range(args.warmup):
+        gstep()
+    barrier(ws)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    ginfos = [gstep() for _ in range(args.steps)]
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = max_over_ranks(ws, g0.elapsed_time(g1)) / args.steps
+    gplan.close()
     clocks = sampler.stop()
     fp64 = None if args.no_fp64_compare else fp64_comparison(gb, P, sig)
 
@@ -344,6 +368,11 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": int(8 * (dx * k + dy * k + k))},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "graph_replay": {"ms_per_solve": graph_ms, "steps": args.steps,
+                         "iterations": float(np.mean([i["iters"] for i in ginfos])),
+                         "note": "same solves, iteration batches replayed from captured CUDA graphs; "
+                                 "the headline value uses direct launches so that CUDA events can "
+                                 "bracket every pass kernel"},
     }
     if fp64 is not None:
         fp64["bf16_speedup"] = fp64["ms"] / value

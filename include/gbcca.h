@@ -83,6 +83,12 @@ typedef struct {
   int32_t time_passes;   /* 1: time the data kernel of every fused pass (the
                             kernel that streams X and Y) with CUDA events on
                             the solve's stream (reported in gbcca_info)         */
+  int32_t graphs;        /* 1: each batch of check_every iterations is replayed
+                            from a CUDA graph that the plan captures on its own
+                            stream at the first solve (re-captured when the
+                            data pointers change); 0, or time_passes = 1: the
+                            kernels are launched one by one.  Both run the
+                            same kernels in the same order.                     */
 } gbcca_options;
 
 /* Per-solve report (host struct filled by the solve calls). */
@@ -101,7 +107,7 @@ typedef struct {
 } gbcca_info;
 
 /* Fills `opt` with defaults (CountSketch, s = 0, seed 0, max_iter 1000,
- * gtol 1e-8, refine 1, warm_start 1, check_every 8, time_passes 0).
+ * gtol 1e-8, refine 1, warm_start 1, check_every 8, time_passes 0, graphs 1).
  * Returns GBCCA_OK or
  * GBCCA_ERR_INVALID_ARG if opt is NULL. */
 int gbcca_default_options(gbcca_options* opt);

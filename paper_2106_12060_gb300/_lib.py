@@ -27,6 +27,7 @@ class Options(C.Structure):
         ("warm_start", C.c_int32),
         ("check_every", C.c_int32),
         ("time_passes", C.c_int32),
+        ("graphs", C.c_int32),
     ]
 
 

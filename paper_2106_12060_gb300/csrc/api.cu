@@ -55,6 +55,8 @@ void free_plan(Plan* p) {
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
+  if (p->batch_exec != nullptr) cudaGraphExecDestroy(p->batch_exec);
+  if (p->cap_stream != nullptr) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
 
@@ -373,6 +375,7 @@ int gbcca_default_options(gbcca_options* opt) {
   opt->refine = 1;
   opt->warm_start = 1;
   opt->check_every = 8;
+  opt->graphs = 1;
   return GBCCA_OK;
 }
 

@@ -21,7 +21,8 @@ struct DevState {
   double Linv[2][kMaxK * kMaxK];    // L^{-T} of the accepted retraction, per view
   double S[2][3][kMaxK * kMaxK];    // Sylvester solutions (grad, eta, old grad)
   double sigma[kMaxK];              // Rayleigh-Ritz values at the end
-  double rot[2][kMaxK * kMaxK];     // Rayleigh-Ritz rotation per view
+  double rot[2][2 * kMaxK * kMaxK]; // Rayleigh-Ritz rotation per view (rr_m x k)
+  int rr_m;                         // dimension of the Rayleigh-Ritz subspace used (k or 2k)
   double YW[kMaxClasses * kMaxK];   // FDA: Yhat times the current W (l x k)
   double ftrial[64];                // line-search trial values (diagnostics)
   double Qsyl[2][kMaxK * kMaxK];    // eigenvectors of the last Sylvester coefficient
@@ -139,6 +140,16 @@ struct Plan {
   uint8_t* tc_img = nullptr;
   float* tc_part = nullptr;
   int tc_clusters = 0;
+  // one batch of RCG iterations as a CUDA graph: captured on the plan's own
+  // stream (the caller's may be the legacy default stream, which cannot be
+  // captured), replayed on the solve's stream; the key records what the
+  // captured launches depend on besides plan-owned memory
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;
+  const void* batch_key_ptr[3] = {nullptr, nullptr, nullptr};
+  int batch_key_n = 0;
+  bool batch_key_timed = false;
+  long long batch_launches = 0;  // kernels in one replay (for the launch counter)
   cudaEvent_t kev0 = nullptr;  // when set: recorded around the data kernel of the next pass
   cudaEvent_t kev1 = nullptr;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
 };

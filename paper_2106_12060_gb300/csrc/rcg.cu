@@ -311,9 +311,16 @@ __device__ bool warp_chol(double* A, int n, double* invd) {
     }
     if (lane > j && lane < n) A[lane * n + j] *= rj;
     __syncwarp();
-    if (lane > j && lane < n) {
-      const double lij = A[lane * n + j];
-      for (int c = j + 1; c <= lane; ++c) A[lane * n + c] -= lij * A[c * n + j];
+    // trailing update, one element (r, c), j < c <= r < n, per lane: FP64
+    // instructions are slow to issue on this GPU, so as few warp-wide ones
+    // as possible (the triangle of m rows has m (m + 1) / 2 elements)
+    const int m = n - j - 1;
+    for (int e = lane; e < m * (m + 1) / 2; e += 32) {
+      int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);  // e = r (r + 1) / 2 + c'
+      if ((r + 1) * (r + 2) / 2 <= e) ++r;
+      if (r * (r + 1) / 2 > e) --r;
+      const int rr = j + 1 + r, cc = j + 1 + (e - r * (r + 1) / 2);
+      A[rr * n + cc] -= A[rr * n + j] * A[cc * n + j];
     }
     __syncwarp();
   }
@@ -424,8 +431,20 @@ static int thin_gram(Plan& p, const double* A0, const double* A1, int lda, const
 }
 
 __device__ void sum_blocks(const double* part, int nblk, int len, double* out) {
-  if (nblk == 1) {  // already summed: a copy (no FP64 additions of zeros)
-    for (int e = threadIdx.x; e < len; e += blockDim.x) out[e] = part[e];
+  if (nblk == 1) {  // already summed: a copy (no FP64 additions of zeros), 8 loads in flight
+    for (int e0 = threadIdx.x; e0 < len; e0 += 8 * blockDim.x) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        t[u] = e < len ? part[e] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < len) out[e] = t[u];
+      }
+    }
     __syncthreads();
     return;
   }
@@ -813,17 +832,22 @@ struct DirArgs {
   int max_iter;
 };
 
-// Block-wide sum of NV per-thread values (blockDim <= 256).
+// Block-wide sum of NV per-thread values (blockDim a multiple of 32, <= 256):
+// a shuffle tree per warp, then the warps' sums added in warp order
+// (deterministic).
 template <int NV>
 __device__ void blk_sum(double (&v)[NV], double* red) {
-  for (int q = 0; q < NV; ++q) red[q * 256 + threadIdx.x] = v[q];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0)
+    for (int q = 0; q < NV; ++q) red[q * 8 + w] = v[q];
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-      for (int q = 0; q < NV; ++q) red[q * 256 + threadIdx.x] += red[q * 256 + threadIdx.x + o];
-    __syncthreads();
+  for (int q = 0; q < NV; ++q) {
+    double t = 0;
+    for (int i = 0; i < nw; ++i) t += red[q * 8 + i];
+    v[q] = t;
   }
-  for (int q = 0; q < NV; ++q) v[q] = red[q * 256];
   __syncthreads();
 }
 
@@ -1106,93 +1130,136 @@ struct RRArgs {
   const double* phipart;  // [view][nblk][2k x 2k] Gram of Phi (U^T U in the corner)
   int nblk, k, kind, l;
   const double* YPhi;     // FDA (l x 2k)
+  int m0;                 // subspace: k (columns U) or 2k (columns [U, eta])
 };
 
+// Rayleigh-Ritz on span(Phi_v[:, :m]) per view: m = 2k uses the point and
+// the last search direction ([U, eta], [V, eta_V]; the pass Grams of the
+// final point hold every product needed), a larger subspace than the point
+// alone, so its Ritz values are at least as close to the canonical
+// correlations; when that Gram is numerically rank deficient (eta ~ 0 or
+// nearly dependent on U: a pivot below 1e-12 of the largest diagonal) the
+// kernel falls back to m = k.
 __global__ void rr_kernel(RRArgs a) {
   extern __shared__ double rsm[];
   DevState* st = a.st;
-  const int k = a.k, kk = k * k, k2 = 2 * k;
+  const int k = a.k, k2 = 2 * k, mm0 = a.m0 * a.m0;
   double* Gx = rsm;
-  double* Gy = Gx + kk;
-  double* C = Gy + kk;
-  double* Lxi = C + kk;
-  double* Lyi = Lxi + kk;
-  double* T1 = Lyi + kk;
-  double* T2 = T1 + kk;
-  double* Q = T2 + kk;
-  double* lam = Q + kk;
-  double* rot = lam + kMaxK;
-  double* phig = rot + 100;  // 2 x 4kk
+  double* Gy = Gx + mm0;
+  double* C = Gy + mm0;
+  double* Lxi = C + mm0;
+  double* Lyi = Lxi + mm0;
+  double* T1 = Lyi + mm0;
+  double* T2 = T1 + mm0;
+  double* Q = T2 + mm0;
+  double* lam = Q + mm0;
+  double* rot = lam + 2 * kMaxK;
+  double* phig = rot + 100;  // 2 x (2k)^2
+  __shared__ int s_ok;
   const int nv = a.kind == kCCA ? 2 : 1;
-  for (int v = 0; v < nv; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * kk, a.nblk, 4 * kk, phig + v * 4 * kk);
+  for (int v = 0; v < nv; ++v) sum_blocks(a.phipart + (int64_t)v * a.nblk * 4 * k * k, a.nblk, 4 * k * k, phig + v * 4 * k * k);
   const int NC = a.gnc, ox = a.offx, oy = a.offy;
-  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-    int i = e / k, j = e % k;
-    Gx[e] = a.Gram[(ox + i) * NC + ox + j] + st->lam[0] * phig[i * k2 + j];
-    if (a.kind == kCCA) {
-      Gy[e] = a.Gram[(oy + i) * NC + oy + j] + st->lam[1] * phig[4 * kk + i * k2 + j];
-      C[e] = a.Gram[(ox + i) * NC + oy + j];
-    } else {
-      double s = 0;
-      for (int c = 0; c < a.l; ++c) s += a.YPhi[c * k2 + i] * a.YPhi[c * k2 + j];
-      C[e] = s;
+  int m = a.m0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    const int mm = m * m;
+    for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+      int i = e / m, j = e % m;
+      Gx[e] = a.Gram[(ox + i) * NC + ox + j] + st->lam[0] * phig[i * k2 + j];
+      if (a.kind == kCCA) {
+        Gy[e] = a.Gram[(oy + i) * NC + oy + j] + st->lam[1] * phig[4 * k * k + i * k2 + j];
+        C[e] = a.Gram[(ox + i) * NC + oy + j];
+      } else {
+        double s = 0;
+        for (int c = 0; c < a.l; ++c) s += a.YPhi[c * k2 + i] * a.YPhi[c * k2 + j];
+        C[e] = s;
+      }
     }
+    __syncthreads();
+    // largest diagonals, for the rank test after the factorization
+    if (threadIdx.x == 0) {
+      double dx = 0, dy = 0;
+      for (int i = 0; i < m; ++i) {
+        dx = fmax(dx, Gx[i * m + i]);
+        if (a.kind == kCCA) dy = fmax(dy, Gy[i * m + i]);
+      }
+      T1[0] = dx;
+      T1[1] = dy;
+    }
+    __syncthreads();
+    const double dxmax = T1[0], dymax = T1[1];
+    __syncthreads();
+    bool ok = blk_chol(Gx, m);
+    if (a.kind == kCCA) ok = blk_chol(Gy, m) && ok;
+    if (threadIdx.x == 0) {
+      bool full = ok;
+      for (int i = 0; i < m && full; ++i) {
+        if (Gx[i * m + i] * Gx[i * m + i] < 1e-12 * dxmax) full = false;
+        if (a.kind == kCCA && Gy[i * m + i] * Gy[i * m + i] < 1e-12 * dymax) full = false;
+      }
+      s_ok = full ? 1 : (ok ? 2 : 0);  // 1: full rank, 2: factored but near rank deficient
+    }
+    __syncthreads();
+    if (s_ok == 1 || m == k) {
+      if (s_ok == 0) {
+        if (threadIdx.x == 0) st->status = GBCCA_ERR_NOT_SPD;
+        return;
+      }
+      break;
+    }
+    m = k;  // fall back to the point alone
+    __syncthreads();
   }
-  __syncthreads();
-  bool ok = blk_chol(Gx, k);
-  if (a.kind == kCCA) ok = blk_chol(Gy, k) && ok;
-  if (!ok) {
-    if (threadIdx.x == 0) st->status = GBCCA_ERR_NOT_SPD;
-    return;
-  }
-  blk_lower_inv(Gx, Lxi, k);
-  if (a.kind == kCCA) blk_lower_inv(Gy, Lyi, k);
+  blk_lower_inv(Gx, Lxi, m);
+  if (a.kind == kCCA) blk_lower_inv(Gy, Lyi, m);
   else
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) Lyi[e] = Lxi[e];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Lyi[e] = Lxi[e];
   __syncthreads();
-  blk_mm(Lxi, false, C, false, T1, k, k, k, k, k);   // Lx^{-1} C
-  blk_mm(T1, false, Lyi, true, C, k, k, k, k, k);    // ... Ly^{-T}  => whitened cross (or FDA matrix)
+  blk_mm(Lxi, false, C, false, T1, m, m, m, m, m);   // Lx^{-1} C
+  blk_mm(T1, false, Lyi, true, C, m, m, m, m, m);    // ... Ly^{-T}  => whitened cross (or FDA matrix)
   if (a.kind == kCCA) {
-    blk_mm(C, true, C, false, T1, k, k, k, k, k);    // C^T C
+    blk_mm(C, true, C, false, T1, m, m, m, m, m);    // C^T C
   } else {
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
-      int i = e / k, j = e % k;
-      T1[e] = 0.5 * (C[i * k + j] + C[j * k + i]);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = e / m, j = e % m;
+      T1[e] = 0.5 * (C[i * m + j] + C[j * m + i]);
     }
     __syncthreads();
   }
-  blk_jacobi(T1, Q, lam, k, rot);                    // right singular vectors (CCA) / eigvecs (FDA)
-  // CCA: sigma_i = ||C q_i||, left vectors a_i = C q_i / sigma_i
+  blk_jacobi(T1, Q, lam, m, rot);                    // right singular vectors (CCA) / eigvecs (FDA), descending
+  // the leading k: CCA sigma_i = ||C q_i||, left vectors a_i = C q_i / sigma_i
   if (a.kind == kCCA) {
-    blk_mm(C, false, Q, false, T2, k, k, k, k, k);   // C Q (columns a_i sigma_i)
+    blk_mm(C, false, Q, false, T2, m, m, k, m, m);   // C Q[:, :k] (columns a_i sigma_i), m x k
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
       double s = 0;
-      for (int r = 0; r < k; ++r) s += T2[r * k + i] * T2[r * k + i];
+      for (int r = 0; r < m; ++r) s += T2[r * k + i] * T2[r * k + i];
       st->sigma[i] = sqrt(s);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
       int c = e % k;
       double sg = st->sigma[c];
       T2[e] = sg > 0 ? T2[e] / sg : 0.0;
     }
     __syncthreads();
+    blk_mm(Lxi, true, T2, false, st->rot[0], m, m, k, m, k);  // rot_x = Lx^{-T} A (m x k)
+    blk_mm(Lyi, true, Q, false, st->rot[1], m, m, k, m, m);   // rot_y = Ly^{-T} Q[:, :k]
   } else {
     for (int i = threadIdx.x; i < k; i += blockDim.x) st->sigma[i] = lam[i];
     __syncthreads();
+    blk_mm(Lxi, true, Q, false, st->rot[0], m, m, k, m, m);
   }
-  // rot_x = Lx^{-T} A (A = T2 for CCA, Q for FDA); rot_y = Ly^{-T} Q
-  blk_mm(Lxi, true, a.kind == kCCA ? T2 : Q, false, st->rot[0], k, k, k, k, k);
-  if (a.kind == kCCA) blk_mm(Lyi, true, Q, false, st->rot[1], k, k, k, k, k);
+  if (threadIdx.x == 0) st->rr_m = m;
 }
 
-// out_v (d x k) = Phi_v[:, :k] rot_v, then the sign convention.
+// out_v (d x k) = Phi_v[:, :m] rot_v (m = the Rayleigh-Ritz subspace used),
+// then the sign convention.
 __global__ void rr_apply_kernel(DevState* st, const double* Phi, int d, int k, int v, double* out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d) return;
+  const int m = st->rr_m;
   for (int c = 0; c < k; ++c) {
     double s = 0;
-    for (int q = 0; q < k; ++q) s += Phi[(int64_t)j * 2 * k + q] * st->rot[v][q * k + c];
+    for (int q = 0; q < m; ++q) s += Phi[(int64_t)j * 2 * k + q] * st->rot[v][q * k + c];
     out[(int64_t)j * k + c] = s;
   }
 }
@@ -1405,6 +1472,64 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
   return GBCCA_OK;
 }
 
+// A batch of nb iterations launched one by one (pass b of the batch timed
+// with event pair b when timing is on).
+int run_batch_direct(Plan& p, bool low, int nb, bool timed, cudaStream_t st) {
+  for (int b = 0; b < nb; ++b)
+    GB_TRY(iteration(p, low, st, timed ? p.ev[2 * b] : nullptr, timed ? p.ev[2 * b + 1] : nullptr));
+  return GBCCA_OK;
+}
+
+// The same batch replayed from a CUDA graph.  The graph is captured on the
+// plan's own stream and holds plan-owned pointers, the data pointers (X, Y,
+// labels; the TMA descriptors are captured by value) and the batch shape; it
+// is captured again when any of those differ.  Every kernel reads its
+// per-iteration state (step, direction, convergence flag) from device memory,
+// so one capture serves every batch of every solve.  Pass timing records
+// events around single kernels, so timed batches are launched directly.
+int run_batch_graph(Plan& p, bool low, int nb, bool timed, cudaStream_t st) {
+  const void* key[3] = {p.v[0].Z, p.nviews > 1 ? (const void*)p.v[1].Z : nullptr, (const void*)p.labels};
+  const bool same = p.batch_exec != nullptr && p.batch_key_n == nb && p.batch_key_timed == timed &&
+                    key[0] == p.batch_key_ptr[0] && key[1] == p.batch_key_ptr[1] && key[2] == p.batch_key_ptr[2];
+  if (!same) {
+    if (p.batch_exec != nullptr) {
+      GB_CUDA(cudaGraphExecDestroy(p.batch_exec));
+      p.batch_exec = nullptr;
+    }
+    if (p.cap_stream == nullptr) GB_CUDA(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+    const long long l0 = g_launches.load();
+    GB_CUDA(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeRelaxed));
+    const int rc = run_batch_direct(p, low, nb, timed, p.cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p.cap_stream, &g);
+    if (rc != GBCCA_OK || ec != cudaSuccess) {
+      if (g != nullptr) cudaGraphDestroy(g);
+      g_launches.fetch_sub(g_launches.load() - l0);
+      cudaGetLastError();  // leave no capture error behind for later calls
+      if (rc != GBCCA_OK) return rc;
+      set_last_error(std::string("capture of the iteration batch: ") + cudaGetErrorString(ec));
+      return GBCCA_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&p.batch_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      p.batch_exec = nullptr;
+      cudaGetLastError();
+      set_last_error(std::string("instantiation of the iteration batch: ") + cudaGetErrorString(ei));
+      return GBCCA_ERR_CUDA;
+    }
+    // the launches made while capturing ran nothing: count them per replay
+    p.batch_launches = g_launches.load() - l0;
+    g_launches.fetch_sub(p.batch_launches);
+    p.batch_key_n = nb;
+    p.batch_key_timed = timed;
+    for (int i = 0; i < 3; ++i) p.batch_key_ptr[i] = key[i];
+  }
+  GB_CUDA(cudaGraphLaunch(p.batch_exec, st));
+  g_launches.fetch_add(p.batch_launches);
+  return GBCCA_OK;
+}
+
 }  // namespace
 
 __global__ void state_init_kernel(DevState* st, double gtol, int max_iter, double lam0, double lam1) {
@@ -1486,11 +1611,15 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     if (timed) GB_TRY(harvest(pending_first, pending_n, p.st_host->iter));
     if (p.st_host->done || launched >= p.opt.max_iter) break;
     pending_first = launched + 1;
-    pending_n = 0;
-    for (int b = 0; b < batch && launched < p.opt.max_iter; ++b, ++launched) {
-      GB_TRY(iteration(p, low, st, timed ? p.ev[2 * b] : nullptr, timed ? p.ev[2 * b + 1] : nullptr));
-      pending_n += timed ? 1 : 0;
-    }
+    const int nb = std::min(batch, p.opt.max_iter - launched);
+    // full batches replay a captured graph; a shorter last batch is launched
+    // kernel by kernel (same kernels, same order)
+    if (p.opt.graphs && !timed && nb == batch)
+      GB_TRY(run_batch_graph(p, low, nb, false, st));
+    else
+      GB_TRY(run_batch_direct(p, low, nb, timed, st));
+    launched += nb;
+    pending_n = timed ? nb : 0;
   }
   const DevState& hs = *p.st_host;
   passes += hs.iter;
@@ -1524,7 +1653,10 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     a.kind = p.kind;
     a.l = p.l;
     a.YPhi = p.YPhi;
-    size_t smem = sizeof(double) * (9 * k * k + kMaxK + 100 + 8 * k * k);
+    // the pass Grams of [U, eta] (low-precision pass) allow the 2k subspace;
+    // the exact refinement pass forms the U columns only
+    a.m0 = exact_refine ? k : 2 * k;
+    size_t smem = sizeof(double) * (8 * a.m0 * a.m0 + 2 * kMaxK + 100 + 8 * k * k);
     GB_CUDA(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     rr_kernel<<<1, 256, smem, st>>>(a);
     GB_CHECK_LAUNCH();

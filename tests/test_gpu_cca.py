@@ -181,3 +181,43 @@ def test_solve_small_fp64_workload(gb):
     sig, U, V, info = gb.cca_solve(plan)
     ref, _, _ = OC.cca_qr(P["X64"], P["Y64"], lam, lam, k)
     assert rel(np64(sig), ref) < 1e-8, (np64(sig), ref, info)
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f64"])
+def test_graph_replay_matches_direct_launches(gb, dt):
+    """Batches of iterations replayed from a captured CUDA graph run the same
+    kernels in the same order as direct launches: results, iteration counts and
+    the library's launch count agree exactly.  A second precondition with
+    copies of X and Y at new addresses must re-capture (the captured TMA
+    descriptors and data pointers change) and still give the same results."""
+    import torch
+    n, dx, dy, k, lam = 20000, 192, 136, 5, 1e-3
+    P = cca_latent_problem(n, dx, dy, latent=8, dtype=dt, seed=21)
+    out = {}
+    for graphs in (0, 1):
+        plan, X, Y = _plan(gb, P, n, dx, dy, k, dt, lam, s=1400, max_iter=300, gtol=1e-7, check_every=4,
+                           graphs=graphs)
+        l0 = gb.launch_count()
+        sig, U, V, info = gb.cca_solve(plan)
+        torch.cuda.synchronize()
+        launches = gb.launch_count() - l0
+        out[graphs] = (np64(sig), np64(U), np64(V), info["iters"], launches)
+        if graphs:
+            X2, Y2 = X.clone(), Y.clone()
+            del X, Y
+            gb.cca_precondition(plan, X2, Y2, lam, lam)
+            sig2, U2, V2, info2 = gb.cca_solve(plan)
+            assert np.array_equal(np64(sig2), out[1][0]) and np.array_equal(np64(U2), out[1][1])
+            assert info2["iters"] == out[1][3]
+        plan.close()
+    # with the data pass timed (events around the pass kernel): direct launches
+    plan, X, Y = _plan(gb, P, n, dx, dy, k, dt, lam, s=1400, max_iter=300, gtol=1e-7, check_every=4,
+                       graphs=1, time_passes=1)
+    sig3, U3, V3, info3 = gb.cca_solve(plan)
+    assert np.array_equal(np64(sig3), out[1][0])
+    assert info3["pass_count"] == info3["iters"] + 1 and info3["pass_ms"] > 0, info3
+    plan.close()
+    a, b = out[0], out[1]
+    assert a[3] == b[3] and a[3] > 8, (a[3], b[3])
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert a[4] == b[4], (a[4], b[4])
