@@ -27,12 +27,13 @@ if ROOT not in sys.path:
 METRIC = "CCA solve time to 1e-6 rel. objective; fused pass % of HBM peak; p50/p99 latency"
 WORKLOAD = "cca_tall_bf16"
 LAM = 1e-4
-# Stopping rule: ||grad||_M <= GTOL ||grad_0||_M.  On this workload it gives a
-# relative objective suboptimality below 1e-7 and every canonical correlation
-# within 1e-6 of the FP64 oracle (checked by tests/test_gpu_fullsize.py);
-# 3e-3 left the smallest correlation at 1.0-1.4e-6, depending on rounding
-# order, so the rule keeps a margin.
-GTOL = 2e-3
+# Stopping rule: ||grad||_M <= GTOL ||grad_0||_M.  On this workload, with the
+# final Rayleigh-Ritz step over [U, eta] (refine = 2), it gives a relative
+# objective suboptimality near 1e-8 and every canonical correlation within
+# 7.3e-7 of the FP64 oracle after 46 iterations (checked against 1e-6 by
+# tests/test_gpu_fullsize.py).  The gradient norm plateaus just below: 3e-3
+# takes 79 iterations.
+GTOL = 4e-3
 # Final Rayleigh-Ritz step from the Grams of the tensor-core pass (refine = 2;
 # the same test checks this setting against the FP64 oracle).
 REFINE = 2

@@ -57,6 +57,9 @@ void free_plan(Plan* p) {
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
   if (p->batch_exec != nullptr) cudaGraphExecDestroy(p->batch_exec);
   if (p->cap_stream != nullptr) cudaStreamDestroy(p->cap_stream);
+  if (p->side_stream != nullptr) cudaStreamDestroy(p->side_stream);
+  if (p->fork_ev != nullptr) cudaEventDestroy(p->fork_ev);
+  if (p->join_ev != nullptr) cudaEventDestroy(p->join_ev);
   delete p;
 }
 
@@ -176,6 +179,9 @@ int alloc_plan(Plan* p) {
     GB_CUDA(cudaMemset(p->tc_img, 0, 2 * 49152));
     GB_TRY(dalloc(&p->tc_part, (int64_t)p->sm_count * p->D * k4));
   }
+  GB_CUDA(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
+  GB_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
+  GB_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
   if (p->opt.time_passes) {
     for (int i = 0; i < 2 * kMaxTimedBatch; ++i) {
       GB_CUDA(cudaEventCreate(&p->ev[i]));
@@ -318,9 +324,22 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
     } else {
       GB_TRY(gram_tn(w.SZ, w.d, w.SZ, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st));
     }
-    GB_TRY(cholesky_upper(w.R, w.d, p.flag, st));
-    GB_TRY(tri_inverse_upper(w.R, w.Rinv, w.d, p.ws, p.ws_len, st));
   }
+  // The views' blocked Cholesky factorizations touch only their own R (and
+  // the error flag) and are latency bound: view 1 runs on the plan's side
+  // stream, between a fork and a join event, while view 0 runs on `st`.
+  if (p.nviews > 1) {
+    GB_CUDA(cudaEventRecord(p.fork_ev, st));
+    GB_CUDA(cudaStreamWaitEvent(p.side_stream, p.fork_ev, 0));
+    GB_TRY(cholesky_upper(p.v[1].R, p.v[1].d, p.flag, p.side_stream));
+    GB_TRY(cholesky_upper(p.v[0].R, p.v[0].d, p.flag, st));
+    GB_CUDA(cudaEventRecord(p.join_ev, p.side_stream));
+    GB_CUDA(cudaStreamWaitEvent(st, p.join_ev, 0));
+  } else {
+    GB_TRY(cholesky_upper(p.v[0].R, p.v[0].d, p.flag, st));
+  }
+  // the triangular inverses share the split-K workspace: one after the other
+  for (int v = 0; v < p.nviews; ++v) GB_TRY(tri_inverse_upper(p.v[v].R, p.v[v].Rinv, p.v[v].d, p.ws, p.ws_len, st));
   GB_TRY(read_flag(p, st));
   for (int v = 0; v < p.nviews; ++v) GB_TRY(finish_factor(p, v, st));
   if (p.opt.warm_start) {

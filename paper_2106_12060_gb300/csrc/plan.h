@@ -145,6 +145,9 @@ struct Plan {
   // captured), replayed on the solve's stream; the key records what the
   // captured launches depend on besides plan-owned memory
   cudaStream_t cap_stream = nullptr;
+  // side stream and fork/join events for independent per-view work
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t batch_exec = nullptr;
   const void* batch_key_ptr[3] = {nullptr, nullptr, nullptr};
   int batch_key_n = 0;
