@@ -221,6 +221,114 @@ def fp64_comparison(gb, P, sig_bf16, steps: int = 2):
             "sigma_max_rel_diff_vs_bf16": float(np.max(np.abs(s64 - s16) / np.abs(s64)))}
 
 
+def other_workloads(gb, steps: int = 2):
+    """The FP32 forms of the hot path, each one full solve per step with the
+    data kernels of every pass timed by CUDA events: the tall CCA workload
+    stored in FP32 (CUDA-core CCA pass) and the Fisher LDA workload (n =
+    100000, d = 784, 10 classes, FP32; CUDA-core LDA pass, Alg. 2)."""
+    import torch
+    from synth import make_workload
+    hbm, _ = peaks()
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(step):
+        step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [step() for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, infos
+
+    P = make_workload("cca_tall_f32")
+    c = P["config"]
+    n, dx, dy, k = c["n"], c["dx"], c["dy"], c["k"]
+    X = torch.from_numpy(np.ascontiguousarray(P["X"])).cuda()
+    Y = torch.from_numpy(np.ascontiguousarray(P["Y"])).cuda()
+    del P
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, check_every=8,
+                             time_passes=1, refine=REFINE)
+    plan = gb.cca_plan(n, dx, dy, k, "f32", opt)
+
+    def cca_step():
+        gb.cca_precondition(plan, X, Y, LAM, LAM)
+        return gb.cca_solve(plan)[3]
+
+    ms, infos = timed(cca_step)
+    pass_ms = float(np.mean([i["pass_ms"] for i in infos]))
+    gbps = n * (dx + dy) * 4 / (pass_ms * 1e-3) / 1e9
+    out["cca_tall_f32"] = {"solve_ms": ms, "iterations": float(np.mean([i["iters"] for i in infos])),
+                           "pass_ms": pass_ms, "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm,
+                           "pass_algorithmic_bytes": n * (dx + dy) * 4,
+                           "kernels": "pass_w_kernel + pass_g_async_kernel (CUDA cores, FP32 accumulate)"}
+    plan.close()
+    del X, Y
+    torch.cuda.empty_cache()
+
+    P = make_workload("lda_f32")
+    c = P["config"]
+    n, d, l, k = c["n"], c["d"], c["l"], c["k"]
+    Xh = np.ascontiguousarray(P["X"])
+    y = P["y"].astype(np.int32)
+    # lambda = 1e-6 tr(S_w) / d, the LDA workload's regularization rule:
+    # tr(S_w) = sum_i ||x_i||^2 - sum_c n_c ||m_c||^2 (input preparation)
+    x64 = Xh.astype(np.float64)
+    cnt = np.bincount(y, minlength=l).astype(np.float64)
+    sums = np.zeros((l, d))
+    np.add.at(sums, y, x64)
+    trsw = float(np.sum(x64 * x64) - np.sum(sums * sums / cnt[:, None]))
+    lam = 1e-6 * trsw / d
+    del x64
+    X = torch.from_numpy(Xh).cuda()
+    yl = torch.from_numpy(y).cuda()
+    # gtol 3e-4 with the exact (FP64) Rayleigh-Ritz refinement: 218
+    # iterations, every generalized eigenvalue within 2.6e-8 of the oracle
+    # (tests/test_gpu_fullsize.py); below ~1e-4 the gradient norm reaches its
+    # FP32 floor and the solve runs to max_iter
+    opt = gb.default_options(s=c["s"], max_iter=1000, gtol=3e-4, check_every=8, time_passes=1, refine=1)
+    plan = gb.lda_plan(n, d, l, k, "f32", opt)
+
+    def lda_step():
+        return gb.lda_solve(plan, X, yl, lam)[2]
+
+    ms, infos = timed(lda_step)
+    pass_ms = float(np.mean([i["pass_ms"] for i in infos]))
+    nbytes = n * d * 4 + n * 4
+    gbps = nbytes / (pass_ms * 1e-3) / 1e9
+    out["lda_f32"] = {"solve_ms": ms, "iterations": float(np.mean([i["iters"] for i in infos])),
+                      "gtol": 3e-4, "pass_ms": pass_ms, "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm,
+                      "pass_algorithmic_bytes": nbytes,
+                      "kernels": "LDA pass (CUDA cores, FP32 accumulate): X^T (X Phi - class means Phi)"}
+    plan.close()
+    del X
+    torch.cuda.empty_cache()
+
+    # the plain FP64 parity workload (n = 2000, dx = 50, dy = 40, k = 5,
+    # CountSketch s = 360, gtol 1e-10): launch- and latency-bound, so the
+    # figure of interest is the time per iteration
+    P = make_workload("cca_small_fp64")
+    c = P["config"]
+    X = torch.from_numpy(np.ascontiguousarray(P["X"])).cuda()
+    Y = torch.from_numpy(np.ascontiguousarray(P["Y"])).cuda()
+    opt = gb.default_options(sketch=gb.COUNTSKETCH, s=c["s"], seed=c["seed"], max_iter=6000, gtol=1e-10,
+                             check_every=64)
+    plan = gb.cca_plan(c["n"], c["dx"], c["dy"], c["k"], "f64", opt)
+
+    def small_step():
+        gb.cca_precondition(plan, X, Y, c["lam"], c["lam"])
+        return gb.cca_solve(plan)[3]
+
+    ms, infos = timed(small_step)
+    it = float(np.mean([i["iters"] for i in infos]))
+    out["cca_small_fp64"] = {"solve_ms": ms, "iterations": it, "us_per_iteration": 1e3 * ms / max(it, 1.0),
+                             "gtol": 1e-10}
+    plan.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -342,6 +450,7 @@ def run_ours(args, ws, rank, local):
     gplan.close()
     clocks = sampler.stop()
     fp64 = None if args.no_fp64_compare else fp64_comparison(gb, P, sig)
+    others = None if args.no_other_workloads else other_workloads(gb)
 
     hbm, peak_src = peaks()
     elt = {"bf16": 2, "f32": 4, "f64": 8}[dt]
@@ -378,6 +487,8 @@ def run_ours(args, ws, rank, local):
     if fp64 is not None:
         fp64["bf16_speedup"] = fp64["ms"] / value
         line["fp64_gpu"] = fp64
+    if others is not None:
+        line["other_workloads"] = others
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P)
     if rank == 0:
@@ -448,6 +559,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the timed solve of the same workload stored in FP64")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the FP32 CCA and FP32 LDA solves")
     ap.add_argument("--pass-only", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--solve-rows", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -233,6 +233,118 @@ pass_g_kernel(PassViews pv, int64_t n, int NC, int D, const Tacc* __restrict__ W
   }
 }
 
+// The same product for FP32 data with the loads pipelined: each stage is a
+// 32-row x 64-column block of Z (16-byte cp.async copies) and the same 32
+// rows of W (4-byte copies), kGStages stages in flight, zero-filled past the
+// edges.  The arithmetic (per-thread order, FP32 partial sums flushed to FP64
+// every kFlush rows) is that of pass_g_kernel.  Requires d % 4 == 0,
+// ld % 4 == 0 and 16-byte aligned bases (checked by the caller).
+constexpr int kGStages = 4;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int RQ>
+__global__ void __launch_bounds__(256)
+pass_g_async_kernel(PassViews pv, int64_t n, int NC, int D, const float* __restrict__ W,
+                    int64_t rows_per_chunk, int nb0, double* __restrict__ partG) {
+  constexpr int PW = 8 * RQ;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  float* Zs = reinterpret_cast<float*>(gsm);           // [kGStages][kTB][64]
+  float* Ws = Zs + kGStages * kTB * 64;                 // [kGStages][kTB][PW]
+  if (pv.done != nullptr && *pv.done) return;
+  const int tid = threadIdx.x;
+  const int tj = tid & 31, tc = tid >> 5;
+  const int b = blockIdx.y;
+  const int v = b < nb0 ? 0 : 1;
+  const int c0 = 64 * (v == 0 ? b : b - nb0);
+  const int d = pv.d[v];
+  const float* Z = reinterpret_cast<const float*>(pv.Z[v]);
+  const int64_t ld = pv.ld[v];
+  const int64_t r0 = blockIdx.x * rows_per_chunk;
+  const int64_t r1 = min(n, r0 + rows_per_chunk);
+  const int nsteps = r1 > r0 ? (int)((r1 - r0 + kTB - 1) / kTB) : 0;
+  // W columns NC .. PW - 1 are never copied: zero them once
+  for (int e = tid; e < kGStages * kTB * PW; e += 256)
+    if (e % PW >= NC) Ws[e] = 0.f;
+  auto issue = [&](int step) {
+    const int slot = step % kGStages;
+    const int64_t i0 = r0 + (int64_t)step * kTB;
+#pragma unroll
+    for (int u = 0; u < (kTB * 16) / 256; ++u) {
+      const int e = tid + 256 * u;  // 16-byte chunk: row e / 16, columns 4 (e % 16) ..
+      const int r = e >> 4, c = 4 * (e & 15);
+      const int64_t row = i0 + r;
+      const bool ok = row < r1 && c0 + c < d;
+      const float* src = ok ? Z + row * ld + c0 + c : Z;
+      cp_async16((uint32_t)__cvta_generic_to_shared(Zs + (slot * kTB + r) * 64 + c), src, ok ? 16u : 0u);
+    }
+    for (int e = tid; e < kTB * NC; e += 256) {
+      const int r = e / NC, c = e - r * NC;
+      const int64_t row = i0 + r;
+      const bool ok = row < r1;
+      const float* src = ok ? W + row * NC + c : W;
+      cp_async4((uint32_t)__cvta_generic_to_shared(Ws + (slot * kTB + r) * PW + c), src, ok ? 4u : 0u);
+    }
+  };
+  constexpr int kFlush = 4 * kTB;
+  float acc[2][RQ];
+  double acc64[2][RQ];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) acc[a][q] = 0.f, acc64[a][q] = 0.0;
+#pragma unroll
+  for (int s = 0; s < kGStages - 1; ++s) {
+    if (s < nsteps) issue(s);
+    cp_async_commit();
+  }
+  for (int step = 0; step < nsteps; ++step) {
+    cp_async_wait<kGStages - 2>();  // this thread's copies of stage `step` have landed
+    __syncthreads();                // everyone's have; the slot of step - 1 is free
+    if (step + kGStages - 1 < nsteps) issue(step + kGStages - 1);
+    cp_async_commit();
+    if (step > 0 && (step * kTB) % kFlush == 0) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) acc64[a][q] += (double)acc[a][q], acc[a][q] = 0.f;
+    }
+    const float* zs = Zs + (step % kGStages) * kTB * 64;
+    const float* wsl = Ws + (step % kGStages) * kTB * PW;
+#pragma unroll 8
+    for (int i = 0; i < kTB; ++i) {
+      const float z0 = zs[i * 64 + tj], z1 = zs[i * 64 + tj + 32];
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const float w = wsl[i * PW + tc + 8 * q];
+        acc[0][q] += z0 * w;
+        acc[1][q] += z1 * w;
+      }
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    int col = c0 + tj + 32 * a;
+    if (col >= d) continue;
+    int64_t grow = pv.dofs[v] + col;
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      int c = tc + 8 * q;
+      if (c < NC) partG[((int64_t)blockIdx.x * D + grow) * NC + c] = acc64[a][q] + (double)acc[a][q];
+    }
+  }
+}
+
 __global__ void pass_reduce_kernel(const double* __restrict__ partG, int chunks, int64_t nG,
                                    const double* __restrict__ partGram, int ctas, int64_t nGram,
                                    double* __restrict__ G, double* __restrict__ Gram, const int* done) {
@@ -334,9 +446,46 @@ int launch_g(Plan& p, const PassViews& pv, const Tacc* W, cudaStream_t st) {
   return GBCCA_OK;
 }
 
+template <int RQ>
+int launch_g_async(Plan& p, const PassViews& pv, const float* W, cudaStream_t st) {
+  int nb0 = ceil_div(pv.d[0], 64);
+  int nb = nb0 + (pv.nviews > 1 ? ceil_div(pv.d[1], 64) : 0);
+  int64_t rpc = (p.n + p.chunksB - 1) / p.chunksB;
+  dim3 grid(p.chunksB, nb);
+  const size_t smem = sizeof(float) * kGStages * kTB * (64 + 8 * RQ);
+  auto kern = pass_g_async_kernel<RQ>;
+  GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, 256, smem, st>>>(pv, p.n, p.NC, p.D, W, rpc, nb0, reinterpret_cast<double*>(p.partG));
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+// the pipelined FP32 kernel needs whole 16-byte chunks of every data row
+bool g_async_eligible(const PassViews& pv) {
+  for (int v = 0; v < pv.nviews; ++v)
+    if (pv.d[v] % 4 != 0 || pv.ld[v] % 4 != 0 || (reinterpret_cast<uintptr_t>(pv.Z[v]) & 15) != 0) return false;
+  return true;
+}
+
 template <typename Tin, typename Tacc>
 int dispatch_g(Plan& p, const PassViews& pv, const Tacc* W, cudaStream_t st) {
   int rq = (p.NC + 7) / 8;
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<Tacc, float>::value) {
+    if (g_async_eligible(pv)) {
+      switch (rq) {
+        case 1: return launch_g_async<1>(p, pv, W, st);
+        case 2: return launch_g_async<2>(p, pv, W, st);
+        case 3: return launch_g_async<3>(p, pv, W, st);
+        case 4: return launch_g_async<4>(p, pv, W, st);
+        case 5: return launch_g_async<5>(p, pv, W, st);
+        case 6: return launch_g_async<6>(p, pv, W, st);
+        case 7: return launch_g_async<7>(p, pv, W, st);
+        case 8: return launch_g_async<8>(p, pv, W, st);
+        case 9: return launch_g_async<9>(p, pv, W, st);
+        default: return launch_g_async<10>(p, pv, W, st);
+      }
+    }
+  }
   switch (rq) {
     case 1: return launch_g<Tin, Tacc, 1>(p, pv, W, st);
     case 2: return launch_g<Tin, Tacc, 2>(p, pv, W, st);

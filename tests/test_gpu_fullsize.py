@@ -72,10 +72,13 @@ def test_lda_workload(gb):
     P = make_workload("lda_f32")
     c = P["config"]
     lam = 1e-6 * float(np.trace(OL.scatters(P["X64"], P["y"], c["l"])[1])) / c["d"]
-    o = gb.default_options(s=c["s"], max_iter=1000, gtol=1e-6)
+    # gtol 3e-4 converges in about 220 iterations; the FP32 gradient norm
+    # floors near 1e-4, below which the solve runs to max_iter
+    o = gb.default_options(s=c["s"], max_iter=1000, gtol=3e-4)
     plan = gb.lda_plan(c["n"], c["d"], c["l"], c["k"], c["dtype"], o)
     X = to_dev(P["X"], c["dtype"])
     y = torch.from_numpy(P["y"]).cuda()
     rho, W, info = gb.lda_solve(plan, X, y, lam)
     ref, _ = OL.lda_geneig(P["X64"], P["y"], c["l"], lam, c["k"])
+    assert info["status"] == gb.OK, info
     assert rel(np64(rho), ref) < 1e-6, (np64(rho), ref, info)
