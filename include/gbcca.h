@@ -133,7 +133,10 @@ int cca_plan(gbcca_plan_t* plan, int64_t n, int32_t dx, int32_t dy, int32_t k,
  * library draw from opt.seed): CountSketch: h (int32, n entries in [0, s)),
  * g (int8, n entries +-1); SRHT: h = sampled row indices (int32, s entries,
  * distinct, in [0, n_pad)), g = signs (int8, n_pad entries), n_pad the
- * power of two >= n.  Synchronizes `stream` to check the factorizations;
+ * power of two >= n.  The two views' Cholesky factorizations run
+ * concurrently: view 1 on a stream owned by the plan, ordered after the
+ * work already on `stream` and joined back to it by events.  Synchronizes
+ * `stream` to check the factorizations;
  * returns GBCCA_ERR_NOT_SPD if a factor breaks down. */
 int cca_precondition(gbcca_plan_t plan, const void* X, int64_t ldx, const void* Y, int64_t ldy,
                      double lambda_x, double lambda_y, const int32_t* sketch_h,

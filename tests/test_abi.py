@@ -46,6 +46,7 @@ def test_host_only_calls(lib):
     o = _lib.Options()
     assert L.gbcca_default_options(ctypes.byref(o)) == 0
     assert o.max_iter == 1000 and o.warm_start == 1 and o.check_every == 8
+    assert o.graphs == 1 and o.time_passes == 0 and o.refine == 1
     assert L.gbcca_default_options(None) == _lib.ERR_INVALID_ARG
     assert L.gbcca_status_string(_lib.ERR_NOT_SPD) == b"matrix not positive definite"
     h = ctypes.c_void_p()
@@ -53,3 +54,30 @@ def test_host_only_calls(lib):
     assert L.cca_plan(ctypes.byref(h), 100, 5, 4, 6, 2, None) == _lib.ERR_INVALID_ARG
     assert L.lda_plan(ctypes.byref(h), 100, 5, 3, 3, 2, None) == _lib.ERR_INVALID_ARG
     assert b"k" in L.gbcca_last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """gbcca_options and gbcca_info as laid out by the C compiler (size and
+    every field offset) equal the ctypes structures of the binding."""
+    import shutil
+    import subprocess
+    from paper_2106_12060_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gbcca.h"', "int main(void) {"]
+    for cname, py in (("gbcca_options", _lib.Options), ("gbcca_info", _lib.Info)):
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in (("gbcca_options", _lib.Options), ("gbcca_info", _lib.Info)):
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
