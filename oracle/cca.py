@@ -18,6 +18,8 @@ Routes
                 blocks), stable when Sxx is ill-conditioned.
   cca_geneig    brute force for tiny inputs: the positive generalized
                 eigenvalues of ([[0, Sxy], [Sxy^T, 0]], blkdiag(Sxx, Syy)).
+  cca_rayleigh_ritz  the same problem restricted to given subspaces (the
+                refinement step).
 
 Parity: pinned by mutual agreement of the routes, the constraints of
 Def. 4.1, the critical-point equations Sxy V = Sxx U diag(sigma) and
@@ -100,6 +102,32 @@ def cca_geneig(X, Y, lx, ly, k):
     Z = Z[:, idx] * np.sqrt(2.0)  # z^T B z = 1 splits evenly between the views
     U, V = fix_signs(Z[:dx], Z[dx:], Sxy)
     return w[idx], U, V
+
+
+def cca_rayleigh_ritz(Sxx, Syy, Sxy, Bx, By, k):
+    """Rayleigh-Ritz for Def. 4.1 on span(Bx) x span(By): the regularized CCA
+    of the problem restricted to U = Bx A, V = By C.  Its matrices are the
+    projected ones, Bx^T Sxx Bx, By^T Syy By and Bx^T Sxy By; whitening and an
+    SVD (as in cca_whiten) give the Ritz values and the small weights, mapped
+    back through Bx, By.  This is the refinement step a8 on the final point
+    (Bx = U) or on the point and the last search direction (Bx = [U, eta]).
+    Pins: the full space gives the closed form; a subspace that contains the
+    leading canonical weights gives them exactly; every Ritz value is at
+    most the corresponding canonical correlation, and enlarging the subspace
+    raises none of the gaps (tests/test_oracle_cca.py)."""
+    Bx = np.asarray(Bx, dtype=np.float64)
+    By = np.asarray(By, dtype=np.float64)
+    Gx = Bx.T @ Sxx @ Bx
+    Gy = By.T @ Syy @ By
+    Cxy = Bx.T @ Sxy @ By
+    Lx = np.linalg.cholesky(Gx)
+    Ly = np.linalg.cholesky(Gy)
+    Cw = sl.solve_triangular(Lx, sl.solve_triangular(Ly, Cxy.T, lower=True).T, lower=True)
+    A, s, Ct = np.linalg.svd(Cw)
+    U = Bx @ sl.solve_triangular(Lx.T, A[:, :k], lower=False)
+    V = By @ sl.solve_triangular(Ly.T, Ct.T[:, :k], lower=False)
+    U, V = fix_signs(U, V, Sxy)
+    return s[:k], U, V
 
 
 def cca_objective(U, V, Sxy, mu):

@@ -75,3 +75,37 @@ def test_suboptimality_definition():
     mu = np.array([2.0, 1.0])
     assert C.suboptimality(sig, mu, -2.3) == pytest.approx(0.0)
     assert C.suboptimality(sig, mu, -2.0) == pytest.approx(0.3 / 2.3)
+
+
+def test_rayleigh_ritz_pins(cfg_small):
+    """Rayleigh-Ritz on subspaces (the refinement step): the whole space
+    reproduces the closed form; a subspace holding the leading canonical
+    weights (plus junk directions) reproduces them; any subspace gives Ritz
+    values at most the canonical correlations, and a larger subspace that
+    contains a smaller one gives values at least as large (Courant-Fischer for
+    the pencil ([[0, Sxy], [Sxy^T, 0]], blkdiag(Sxx, Syy)))."""
+    P = cfg_small
+    lam, k = 1e-3, 5
+    Sxx, Syy, Sxy = C.sigmas(P["X64"], P["Y64"], lam, lam)
+    dx, dy = Sxy.shape
+    ref, Uref, Vref = C.cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    s_full, U_full, V_full = C.cca_rayleigh_ritz(Sxx, Syy, Sxy, np.eye(dx), np.eye(dy), k)
+    assert np.allclose(s_full, ref, rtol=1e-10, atol=0)
+    rng = np.random.default_rng(7)
+    Bx = np.hstack([Uref, rng.standard_normal((dx, 3))])
+    By = np.hstack([rng.standard_normal((dy, 2)), Vref])
+    s_in, U_in, V_in = C.cca_rayleigh_ritz(Sxx, Syy, Sxy, Bx, By, k)
+    assert np.allclose(s_in, ref, rtol=1e-10, atol=0)
+    # the weights satisfy Def. 4.1's constraints
+    assert np.allclose(U_in.T @ Sxx @ U_in, np.eye(k), atol=1e-9)
+    assert np.allclose(U_in.T @ Sxy @ V_in, np.diag(s_in), atol=1e-9)
+    # variational bound and monotonicity: U plus a perturbation direction
+    Ux = Uref + 0.05 * rng.standard_normal((dx, k))
+    Vy = Vref + 0.05 * rng.standard_normal((dy, k))
+    ex = 0.05 * rng.standard_normal((dx, k))
+    ey = 0.05 * rng.standard_normal((dy, k))
+    s_k, _, _ = C.cca_rayleigh_ritz(Sxx, Syy, Sxy, Ux, Vy, k)
+    s_2k, _, _ = C.cca_rayleigh_ritz(Sxx, Syy, Sxy, np.hstack([Ux, ex]), np.hstack([Vy, ey]), k)
+    assert np.all(s_k <= ref + 1e-12) and np.all(s_2k <= ref + 1e-12)
+    assert np.all(s_2k >= s_k - 1e-12)
+    assert np.max(ref - s_2k) < np.max(ref - s_k)
