@@ -14,6 +14,8 @@ Routes
   lda_geneig  scipy.linalg.eigh(S_B, S_w + lambda I) on the explicit scatters.
   lda_qr      R from the QR of [Xhat; sqrt(lambda) I]; the rho are the squared
               singular values of Yhat R^{-1}.
+  lda_rayleigh_ritz  the same problem restricted to a given subspace (the
+              refinement step).
 
 Parity: pinned by route agreement, the eigen-equation
 S_B W = (S_w + lambda I) W diag(rho), W^T (S_w + lambda I) W = I, rank <= l - 1,
@@ -71,6 +73,20 @@ def lda_qr(X, y, l, lam, k):
     rho[: s.shape[0]] = s ** 2
     W = sl.solve_triangular(R, Vt.T[:, :k], lower=False)
     return rho[:k], fix_signs(W)
+
+
+def lda_rayleigh_ritz(SB, Swl, B, k):
+    """Rayleigh-Ritz for Def. 5.1 on span(B): the generalized eigenproblem
+    (B^T S_B B, B^T (S_w + lambda I) B) of the restricted problem, its leading
+    k eigenpairs mapped back through B (the refinement step on W or on
+    [W, eta]).  Swl = S_w + lambda I.  Pins: the full space gives lda_geneig;
+    a subspace holding the leading eigenvectors gives them exactly; Ritz
+    values never exceed the eigenvalues and do not decrease when the
+    subspace grows (tests/test_oracle_lda.py)."""
+    B = np.asarray(B, dtype=np.float64)
+    w, V = sl.eigh(B.T @ SB @ B, B.T @ Swl @ B)
+    idx = np.argsort(w)[::-1][:k]
+    return w[idx], fix_signs(B @ V[:, idx])
 
 
 def lda_objective(W, SB, mu):

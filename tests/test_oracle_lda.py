@@ -52,3 +52,29 @@ def test_two_class_closed_form():
         w = W[:, 0]
         cos = abs(w @ z) / np.linalg.norm(w) / np.linalg.norm(z)
         assert abs(cos - 1) < 1e-12
+
+
+def test_rayleigh_ritz_pins():
+    """Rayleigh-Ritz on subspaces (the refinement step): full space = the
+    closed form; a subspace holding the leading eigenvectors reproduces them;
+    Ritz values are bounded by the eigenvalues and grow with the subspace
+    (Courant-Fischer for the definite pencil (S_B, S_w + lambda I))."""
+    P = lda_problem(3000, 24, 5, dtype="f64", seed=4)
+    l, lam, k = 5, 1e-3, 4
+    SB, Sw = L.scatters(P["X64"], P["y"], l)
+    Swl = Sw + lam * np.eye(24)
+    ref, Wref = L.lda_geneig(P["X64"], P["y"], l, lam, k)
+    r_full, W_full = L.lda_rayleigh_ritz(SB, Swl, np.eye(24), k)
+    assert np.allclose(r_full, ref, rtol=1e-10, atol=0)
+    rng = np.random.default_rng(3)
+    r_in, W_in = L.lda_rayleigh_ritz(SB, Swl, np.hstack([Wref, rng.standard_normal((24, 3))]), k)
+    assert np.allclose(r_in, ref, rtol=1e-9, atol=0)
+    assert np.allclose(W_in.T @ Swl @ W_in, np.eye(k), atol=1e-9)
+    Wp = Wref + 0.05 * rng.standard_normal((24, k))
+    eta = 0.05 * rng.standard_normal((24, k))
+    r_k, _ = L.lda_rayleigh_ritz(SB, Swl, Wp, k)
+    r_2k, _ = L.lda_rayleigh_ritz(SB, Swl, np.hstack([Wp, eta]), k)
+    scale = ref[0]
+    assert np.all(r_k <= ref + 1e-12 * scale) and np.all(r_2k <= ref + 1e-12 * scale)
+    assert np.all(r_2k >= r_k - 1e-12 * scale)
+    assert np.max(ref - r_2k) < np.max(ref - r_k)
