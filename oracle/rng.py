@@ -21,9 +21,10 @@ bit:
                        F_r(x) = sm64(seed ^ SALT_R, r ^ (x << 8)) masked to the
                        half width; odd m works on m + 1 bits by cycle walking.
 
-Parity: the generator itself is pinned by its distributional properties and
-bijectivity (tests/test_oracle_rng.py); bucket/sign/row values are integer and
-compared bit-exactly with the GPU.
+Parity: the generator is pinned by its published reference sequence for
+seed 0 (tests/golden/splitmix64_seed0.txt), its distributional properties
+and the bijectivity of the permutation (tests/test_oracle_sketch.py);
+bucket/sign/row values are integer and compared bit-exactly with the GPU.
 """
 from __future__ import annotations
 

@@ -116,3 +116,14 @@ def test_feistel_is_a_permutation():
         assert np.unique(p).size == (1 << m)
     rows = R.srht_rows(1 << 18, 4096, seed=3)
     assert np.unique(rows).size == 4096
+
+
+def test_splitmix64_reference_sequence():
+    """The counter form sm64(0, i) reproduces the generator's published
+    reference outputs for seed 0 (tests/golden/splitmix64_seed0.txt)."""
+    import os
+    from oracle import rng
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64_seed0.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for idx, val in rows:
+        assert int(rng.sm64(0, int(idx))) == int(val, 16)
