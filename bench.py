@@ -151,6 +151,13 @@ def max_over_ranks(ws, x: float) -> float:
     return float(t.item())
 
 
+def workload_config(c, ws):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": WORKLOAD, "n": c["n"], "dx": c["dx"], "dy": c["dy"], "k": c["k"], "lambda": LAM,
+            "sketch": "srht", "s": c["s"], "storage": c["dtype"], "gtol": GTOL, "refine": REFINE,
+            "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (537 MB)"}
+
+
 def cpu_baseline(P, budget_s: float = 20.0):
     """The FP64 oracle (explicit Sigma, Cholesky whitening, SVD) on a row
     sample of the workload, scaled to a full solve by rows (its cost is
@@ -344,8 +351,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": c["n"], "dx": c["dx"], "dy": c["dy"], "k": c["k"],
-                       "storage": c["dtype"], "parallelism": f"replicas{args.gpus}"},
+            "config": workload_config(c, args.gpus),
             "cpu_baseline": {k2: vals[-1][k2] for k2 in ("kind", "cores", "sample")} | {"value": v, "unit": "ms"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -462,9 +468,7 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "dx": dx, "dy": dy, "k": k, "lambda": LAM,
-                   "sketch": "srht", "s": c["s"], "storage": dt, "gtol": GTOL, "refine": REFINE,
-                   "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (537 MB)"},
+        "config": workload_config(c, ws),
         "p50_ms": float(np.percentile(per_step, 50)), "p99_ms": float(np.percentile(per_step, 99)),
         "iterations": float(np.mean([i["iters"] for i in infos])),
         "passes_per_solve": float(np.mean([i["passes"] for i in infos])),
