@@ -40,10 +40,9 @@ REFINE = 2
 
 
 # DRAM traffic of one full-size tc_pass_kernel launch (read + write bytes),
-# from the ncu capture summarised in profiles/tc_pass_kernel_cca_tall_bf16.md
-# (131072 rows; reads scaled by rows to 262144, partial writes as measured).
-# Valid only for the kernel source it was taken on; any other source reports
-# null.
+# from an ncu capture of 131072 rows of this workload (reads scaled by rows
+# to 262144, partial writes as measured).  Valid only for the kernel source
+# it was taken on (SHA-256 below); any other source reports null.
 PASS_TRAFFIC_BYTES = 268.716544e6 * 2 + 5.929472e6
 PASS_TRAFFIC_SRC_SHA256 = "ec22e5aa4545792b41f28eb4bef771b95b6f0377885c5838536a3087a4191cc8"
 
@@ -158,34 +157,93 @@ def workload_config(c, ws):
             "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (537 MB)"}
 
 
-def cpu_baseline(P, budget_s: float = 20.0):
-    """The FP64 oracle (explicit Sigma, Cholesky whitening, SVD) on a row
-    sample of the workload, scaled to a full solve by rows (its cost is
-    dominated by forming Sigma, O(n d^2), linear in n)."""
-    from oracle.cca import cca_whiten
+def _threads():
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    blas = None
     try:
         from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+        blas = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
     except Exception:
-        threads = None
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            if os.environ.get(var):
+                blas = int(os.environ[var])
+                break
+    return cores, blas
+
+
+def cpu_baseline(P, reps: int = 3):
+    """The FP64 oracle timed at the FULL workload size on the host cores:
+    route 2 (oracle.cca.cca_whiten: explicit Sigma, Cholesky whitening, SVD;
+    the route the method's definition states) best and median of `reps`
+    runs, and route 1 (oracle.cca.cca_qr: Householder QR of [Z; sqrt(lambda)
+    I], the accurate route) once.  Returns the record and route 1's
+    (sigma, U, V), which the caller also uses as the accuracy reference."""
+    from oracle.cca import cca_whiten, cca_qr
+    cores, blas = _threads()
+    k = P["config"]["k"]
     n = P["X64"].shape[0]
-    ns = 8192
-    reps = 0
-    t_tot = 0.0
-    while True:
-        r0 = (reps * ns) % (n - ns + 1)
+    t2 = []
+    for _ in range(reps):
         t0 = time.perf_counter()
-        cca_whiten(P["X64"][r0:r0 + ns], P["Y64"][r0:r0 + ns], LAM, LAM, P["config"]["k"])
-        t_tot += time.perf_counter() - t0
-        reps += 1
-        if t_tot > budget_s or reps >= 64:
-            break
-    per_sample = t_tot / reps
-    return {"value": per_sample * (n / ns) * 1e3, "unit": "ms", "cores": threads or cores,
-            "host_cores": cores, "kind": "oracle",
-            "sample": f"oracle.cca.cca_whiten (FP64 NumPy) on {ns}-row slices of the {n}-row workload, "
-                      f"{reps} reps, time scaled by n/{ns}"}
+        cca_whiten(P["X64"], P["Y64"], LAM, LAM, k)
+        t2.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    ref = cca_qr(P["X64"], P["Y64"], LAM, LAM, k)
+    t1 = time.perf_counter() - t0
+    rec = {"value": float(np.median(t2)) * 1e3, "unit": "ms", "cores": blas or cores, "host_cores": cores,
+           "blas_threads": blas, "kind": "oracle",
+           "sample": f"the full {n}-row workload (no extrapolation): oracle.cca.cca_whiten (FP64 NumPy, "
+                     f"route 2) median of {reps} runs; route 1 (oracle.cca.cca_qr) timed once",
+           "route2_whiten_ms": {"median": float(np.median(t2)) * 1e3, "best": float(np.min(t2)) * 1e3,
+                                "runs": len(t2)},
+           "route1_qr_ms": {"once": t1 * 1e3}}
+    return rec, ref
+
+
+def accuracy_report(P, sig, U, V, ref):
+    """Error of the GPU result against the FP64 oracle (route 1): canonical
+    correlations, relative objective gap, and the largest sines of the
+    principal angles between the GPU and oracle subspaces of U and V in the
+    Sxx / Syy inner products (Def. 4.1 constraints)."""
+    from oracle.cca import default_mu
+    sr, Ur, Vr = ref
+    s = sig.cpu().numpy()
+    U = U.cpu().numpy()
+    V = V.cpu().numpy()
+    mu = default_mu(len(s))
+    X, Y = P["X64"], P["Y64"]
+
+    def sines(A, B, Z, lam):
+        # principal angles in the (Z^T Z + lam I) inner product, from the thin
+        # products with the data (no d x d Gram needed)
+        def orth(M):
+            ZM = Z @ M
+            G = ZM.T @ ZM + lam * (M.T @ M)
+            L = np.linalg.cholesky(G)
+            return M @ np.linalg.inv(L).T
+        Qa, Qb = orth(A), orth(B)
+        C = (Z @ Qa).T @ (Z @ Qb) + lam * (Qa.T @ Qb)
+        c = np.linalg.svd(C, compute_uv=False)
+        return float(np.sqrt(max(0.0, 1.0 - min(1.0, float(np.min(c))) ** 2)))
+
+    return {"sigma_max_rel_err": float(np.max(np.abs(s - sr) / sr)),
+            "objective_rel_gap": float(abs(np.dot(mu, sr) - np.dot(mu, s)) / np.dot(mu, sr)),
+            "subspace_sin_U": sines(U, Ur, X, LAM), "subspace_sin_V": sines(V, Vr, Y, LAM),
+            "reference": "oracle.cca.cca_qr (FP64, route 1) on the stored BF16 values"}
+
+
+def quantization_gap(P):
+    """The canonical correlations of the stored BF16 values against those of
+    the FP32 values they were rounded from (oracle route 2 on both): how much
+    BF16 storage changes the problem itself, apart from any solver error."""
+    from oracle.cca import cca_whiten
+    from synth import make_workload
+    Q = make_workload("cca_tall_f32", seed=P["config"]["seed"])
+    k = P["config"]["k"]
+    s16 = cca_whiten(P["X64"], P["Y64"], LAM, LAM, k)[0]
+    s32 = cca_whiten(Q["X64"], Q["Y64"], LAM, LAM, k)[0]
+    return {"sigma_max_rel_diff_bf16_vs_f32_data": float(np.max(np.abs(s16 - s32) / s32)),
+            "sigma_f32_data": [float(x) for x in s32], "sigma_bf16_data": [float(x) for x in s16]}
 
 
 def fp64_comparison(gb, P, sig_bf16, steps: int = 2):
@@ -330,29 +388,65 @@ def other_workloads(gb, steps: int = 2):
 
     ms, infos = timed(small_step)
     it = float(np.mean([i["iters"] for i in infos]))
-    out["cca_small_fp64"] = {"solve_ms": ms, "iterations": it, "us_per_iteration": 1e3 * ms / max(it, 1.0),
-                             "gtol": 1e-10}
+    info = infos[-1]
+    # accuracy against the FP64 oracle, and the first iterate whose relative
+    # objective gap |sum mu sigma + f_t| / sum mu sigma is <= 1e-10 (from the
+    # solver's per-iteration log of f)
+    from oracle.cca import cca_qr, default_mu
+    ref = cca_qr(P["X64"], P["Y64"], c["lam"], c["lam"], c["k"])[0]
+    sig = torch.empty(c["k"], dtype=torch.float64, device="cuda")
+    sig, _, _, info = gb.cca_solve(plan, sigma=sig)
+    hist = gb.query(plan, gb.Q_HISTORY).cpu().numpy().reshape(-1, 3)[: info["iters"] + 1]
+    opt_val = float(np.dot(default_mu(c["k"]), ref))
+    gap = np.abs(opt_val + hist[:, 0]) / opt_val
+    hit = np.nonzero(gap <= 1e-10)[0]
+    us_it = 1e3 * ms / max(it, 1.0)
+    out["cca_small_fp64"] = {
+        "solve_ms": ms, "iterations": it, "us_per_iteration": us_it, "gtol": 1e-10,
+        "status": gb.STATUS_NAMES.get(info["status"], info["status"]), "stalled": bool(info["stalled"]),
+        "converged": info["status"] == gb.OK,
+        "grad_ratio_final": info["grad_norm"] / info["grad_norm0"] if info["grad_norm0"] > 0 else None,
+        "sigma_max_rel_err": float(np.max(np.abs(sig.cpu().numpy() - ref) / ref)),
+        "iterations_to_1e-10_objective_gap": int(hit[0]) if hit.size else None,
+        "time_to_1e-10_objective_gap_ms": float(hit[0] * us_it / 1e3) if hit.size else None,
+        "note": "gtol 1e-10 on the gradient norm is below the FP64 rounding floor of this problem; the run ends "
+                "at the iteration cap or when no step lowers f, so the time is time-to-cap"}
     plan.close()
     return out
 
 
 def run_reference(args, ws, rank):
+    """The oracle as it stands on the host cores: every step is one FP64
+    solve of the FULL workload by route 2 (oracle.cca.cca_whiten), timed
+    with a wall clock; no sampling, no extrapolation."""
     if rank != 0:
         return
+    from oracle.cca import cca_whiten
     from synth import make_workload
     P = make_workload(WORKLOAD)
+    c = P["config"]
+    cores, blas = _threads()
+
+    def step():
+        cca_whiten(P["X64"], P["Y64"], LAM, LAM, c["k"])
+
     for _ in range(args.warmup):
-        cpu_baseline(P, budget_s=0.5)
+        step()
     vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(P, budget_s=2.0))
-    v = float(np.mean([x["value"] for x in vals]))
-    c = P["config"]
+        t0 = time.perf_counter()
+        step()
+        vals.append((time.perf_counter() - t0) * 1e3)
+    v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(c, args.gpus),
-            "cpu_baseline": {k2: vals[-1][k2] for k2 in ("kind", "cores", "sample")} | {"value": v, "unit": "ms"},
+            "p50_ms": float(np.percentile(vals, 50)), "p99_ms": float(np.percentile(vals, 99)),
+            "cpu_baseline": {"kind": "oracle", "cores": blas or cores, "host_cores": cores, "blas_threads": blas,
+                             "sample": f"one full {c['n']}-row solve per step by oracle.cca.cca_whiten "
+                                       f"(FP64 NumPy, route 2: explicit Sigma, Cholesky whitening, SVD)",
+                             "value": v, "unit": "ms"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -494,7 +588,9 @@ def run_ours(args, ws, rank, local):
     if others is not None:
         line["other_workloads"] = others
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(P)
+        line["cpu_baseline"], ref = cpu_baseline(P)
+        line["accuracy"] = accuracy_report(P, sig, U, V, ref)
+        line["quantization_gap"] = quantization_gap(P)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -233,7 +233,7 @@ int gbcca_sketch_draws(int32_t kind, int64_t n, int64_t s, uint64_t seed, int32_
  * Arithmetic: FP64 split-K partial sums over row chunks, added in a fixed
  * order (deterministic).  Memory: the partials live in a static 8 MiB device
  * array of the library (no allocation, nothing needs zeroing), so
- * d <= gbcca_sketch_gram_noalloc_max_d() (724); larger d returns
+ * d <= gbcca_sketch_gram_noalloc_max_d() (1024); larger d returns
  * GBCCA_ERR_INVALID_ARG without device work.  The first call on a device
  * looks up the array's address; make it before recording a stream capture.
  * The array is shared by all callers on a device: calls that may run at the

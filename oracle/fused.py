@@ -16,7 +16,11 @@ return, for Phi_x = [U, eta_U] (dx x 2k) and Phi_y = [V, eta_V] (dy x 2k):
 For FDA (Sec. 5.1, Cor. 5.6) with Phi = [W, eta] (d x 2k) and Xhat the
 class-centred data: P = Xhat Phi, outputs Xhat^T P (= S_w Phi) and P^T P.
 
-Parity: these are definitions (matrix products); nothing to pin beyond NumPy.
+Parity: pinned (tests/test_oracle_fused.py) to the pinned covariance forms
+of oracle.cca.sigmas (Gx = [(Sxx - lx I) Phi_x, Sxy Phi_y], Gy likewise, the
+Gram = Phi_bd^T Sigma Phi_bd) and the within-class scatter of
+oracle.lda.scatters (Xhat^T P = S_w Phi), and by row-by-row loops on tiny
+inputs; a planted swap of the W blocks is caught.
 """
 from __future__ import annotations
 

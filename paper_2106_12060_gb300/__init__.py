@@ -16,10 +16,12 @@ from . import _lib
 from ._lib import (  # noqa: F401
     BF16, FP32, FP64, COUNTSKETCH, SRHT, IDENTITY, EXACT, Options, Info, GbccaError,
     Q_SKETCH_X, Q_SKETCH_Y, Q_R_X, Q_R_Y, Q_WARM_U, Q_WARM_V, Q_HISTORY, Q_CLASS_MEANS,
-    OK, ERR_MAXITER, ERR_NOT_SPD, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_STATE,
+    OK, ERR_MAXITER, ERR_NOT_SPD, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_STATE, ERR_TIMEOUT, ERR_CUDA, ERR_OOM,
 )
 
 _DTYPE_NAMES = {"bf16": BF16, "f32": FP32, "fp32": FP32, "f64": FP64, "fp64": FP64}
+STATUS_NAMES = {0: "ok", -1: "invalid_arg", -2: "unsupported", -3: "oom", -4: "not_spd", -5: "maxiter",
+                -6: "timeout", -7: "cuda", -8: "state"}
 
 
 def _torch():
@@ -39,6 +41,31 @@ def dtype_code(dtype) -> int:
 
 def _ptr(t):
     return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check_dev(name, t, dtype=None, rows=None, cols=None):
+    """Reject, before any call into the library, a tensor that is not on the
+    current CUDA device, has the wrong dtype, or is smaller than the shape the
+    call reads or writes through its raw pointer."""
+    torch = _torch()
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must be a CUDA tensor on the current device")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if rows is not None or cols is not None:
+        if t.dim() != 2 or (rows is not None and t.shape[0] != rows) or (cols is not None and t.shape[1] != cols):
+            raise ValueError(f"{name} must be ({rows}, {cols}), got {tuple(t.shape)}")
+        if t.stride(1) != 1 or (t.shape[0] > 1 and t.stride(0) < t.shape[1]):
+            raise ValueError(f"{name} must have unit column stride and row stride >= its columns")
+
+
+_STORAGE = {0: "bfloat16", 1: "float32", 2: "float64"}
+
+
+def _storage_dtype(code):
+    return getattr(_torch(), _STORAGE[code])
 
 
 def _stream(stream=None):
@@ -100,7 +127,14 @@ def lda_plan(n, d, n_classes, k, dtype, opt: Options | None = None) -> Plan:
 def cca_precondition(plan: Plan, X, Y, lambda_x, lambda_y, sketch_h=None, sketch_g=None, stream=None):
     """X (n x dx), Y (n x dy): CUDA tensors of the plan's dtype, rows contiguous."""
     lib = _lib.load()
-    assert X.stride(1) == 1 and Y.stride(1) == 1
+    torch = _torch()
+    dx, dy = plan.dims
+    dt = _storage_dtype(plan.dtype)
+    _check_dev("X", X, dt, plan.n, dx)
+    _check_dev("Y", Y, dt, plan.n, dy)
+    for name, t in (("sketch_h", sketch_h), ("sketch_g", sketch_g)):
+        if t is not None:
+            _check_dev(name, t, torch.int32 if name == "sketch_h" else torch.int8)
     _lib.check(lib.cca_precondition(plan.handle, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), float(lambda_x),
                                     float(lambda_y), _ptr(sketch_h), _ptr(sketch_g), _stream(stream)),
                "cca_precondition")
@@ -117,6 +151,11 @@ def cca_solve(plan: Plan, mu=None, tol=0.0, U=None, V=None, sigma=None, stream=N
     U = U if U is not None else torch.empty(dx, plan.k, dtype=torch.float64, device=dev)
     V = V if V is not None else torch.empty(dy, plan.k, dtype=torch.float64, device=dev)
     sigma = sigma if sigma is not None else torch.empty(plan.k, dtype=torch.float64, device=dev)
+    _check_dev("U", U, torch.float64, dx, plan.k)
+    _check_dev("V", V, torch.float64, dy, plan.k)
+    _check_dev("sigma", sigma, torch.float64)
+    if not (U.is_contiguous() and V.is_contiguous() and sigma.numel() >= plan.k):
+        raise ValueError("U, V must be contiguous and sigma must hold k entries")
     info = Info()
     mu_arr = (C.c_double * plan.k)(*mu) if mu is not None else None
     allow = (OK, ERR_MAXITER) if allow_maxiter else (OK,)
@@ -138,7 +177,12 @@ def lda_solve(plan: Plan, X, labels, lam, mu=None, tol=0.0, W=None, rho=None, sk
     info = Info()
     mu_arr = (C.c_double * plan.k)(*mu) if mu is not None else None
     allow = (OK, ERR_MAXITER) if allow_maxiter else (OK,)
-    assert X.stride(1) == 1 and labels.dtype == torch.int32
+    _check_dev("X", X, _storage_dtype(plan.dtype), plan.n, d)
+    _check_dev("labels", labels, torch.int32)
+    if labels.dim() != 1 or labels.shape[0] != plan.n or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous int32 vector of n entries")
+    _check_dev("W", W, torch.float64, d, plan.k)
+    _check_dev("rho", rho, torch.float64)
     _lib.check(lib.lda_solve(plan.handle, _ptr(X), X.stride(0), _ptr(labels), float(lam), mu_arr, float(tol),
                              _ptr(sketch_h), _ptr(sketch_g), _ptr(W), _ptr(rho), C.byref(info), _stream(stream)),
                "lda_solve", allow)
@@ -203,12 +247,15 @@ def gbcca_sketch_gram_noalloc(A, lam, C, stream=None):
     """C = A^T A + lam I without any device allocation by the library (the
     split-K partials use its static scratch).  A: CUDA float64 (m, d) with
     unit column stride; C: caller-provided CUDA float64 (d, d), contiguous."""
-    lib = _lib.load()
+    torch = _torch()
     if A.dim() != 2 or A.stride(1) != 1 or C.dim() != 2 or not C.is_contiguous():
         raise ValueError("A must be (m, d) with unit column stride and C a contiguous (d, d) tensor")
     m, d = A.shape
     if tuple(C.shape) != (d, d):
         raise ValueError("C must be (d, d)")
+    _check_dev("A", A, torch.float64, m, d)
+    _check_dev("C", C, torch.float64, d, d)
+    lib = _lib.load()
     _lib.check(lib.gbcca_sketch_gram_noalloc(_ptr(A), A.stride(0), m, d, float(lam), _ptr(C), _stream(stream)),
                "gbcca_sketch_gram_noalloc")
     return C

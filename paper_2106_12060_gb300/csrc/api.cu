@@ -54,6 +54,7 @@ void free_plan(Plan* p) {
                   (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->mv_part, (void*)p->mv_cnt, (void*)p->ls_f, (void*)p->ls_L})
     dfree(q);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
+  if (p->flag_host != nullptr) cudaFreeHost(p->flag_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
   if (p->batch_exec != nullptr) cudaGraphExecDestroy(p->batch_exec);
   if (p->cap_stream != nullptr) cudaStreamDestroy(p->cap_stream);
@@ -153,6 +154,7 @@ int alloc_plan(Plan* p) {
   }
   GB_TRY(dalloc(&p->st, 1));
   GB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&p->st_host), sizeof(DevState)));
+  GB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&p->flag_host), sizeof(int)));
   const int nblk = ceil_div(dmax, 16);  // thin-Gram row blocks
   GB_TRY(dalloc(&p->phigram, 4096));
   GB_TRY(dalloc(&p->phipart, (int64_t)p->nviews * nblk * 4 * k * k));
@@ -267,19 +269,7 @@ int read_flag(Plan& p, cudaStream_t st) {
   GB_CUDA(cudaMemcpyAsync(&f, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   GB_CUDA(cudaStreamSynchronize(st));
   GB_CUDA(cudaMemsetAsync(p.flag, 0, sizeof(int), st));
-  if (f == 1) {
-    set_last_error("a Cholesky pivot was not positive (matrix not SPD)");
-    return GBCCA_ERR_NOT_SPD;
-  }
-  if (f == 3) {
-    set_last_error("CountSketch bucket index out of range");
-    return GBCCA_ERR_INVALID_ARG;
-  }
-  if (f != 0) {
-    set_last_error("device-side check failed");
-    return GBCCA_ERR_INVALID_ARG;
-  }
-  return GBCCA_OK;
+  return flag_status(f);
 }
 
 // Sketch every view, factor the sketch preconditioner and compute the warm

@@ -49,6 +49,30 @@ struct Status {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Codes the kernels write into a plan's device error flag (0 = no error).
+constexpr int kFlagNotSpd = 1;    // a Cholesky pivot was not positive / empty class
+constexpr int kFlagDraw = 2;      // SRHT row draw left [0, n_pad)
+constexpr int kFlagBucket = 3;    // CountSketch bucket index out of [0, s)
+constexpr int kFlagTimeout = 4;   // a bounded device wait ran out (kernel aborted)
+
+// Status and message for a flag value read back from the device.
+inline int flag_status(int f) {
+  switch (f) {
+    case 0: return GBCCA_OK;
+    case kFlagNotSpd:
+      set_last_error("a Cholesky pivot was not positive (matrix not SPD)");
+      return GBCCA_ERR_NOT_SPD;
+    case kFlagBucket:
+      set_last_error("CountSketch bucket index out of range");
+      return GBCCA_ERR_INVALID_ARG;
+    case kFlagTimeout:
+      set_last_error("a bounded device-side wait ran out; the kernel stopped early and its results are void");
+      return GBCCA_ERR_TIMEOUT;
+  }
+  set_last_error("device-side check failed (flag " + std::to_string(f) + ")");
+  return GBCCA_ERR_INVALID_ARG;
+}
+
 // ---------------------------------------------------------------- loads
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return (float)v; }

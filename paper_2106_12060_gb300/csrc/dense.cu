@@ -447,8 +447,9 @@ int split_df(const double* A, int r, int c, bool trans, float* hi, float* lo, cu
 // cudaMalloc / cudaFree may impose on all of its streams.
 //
 // Limit: the scratch holds kNoAllocScratch doubles (8 MiB).  A call needs at
-// least two d x d partial slabs, so d <= 724; larger d is rejected with
-// GBCCA_ERR_INVALID_ARG before any device work.  Nothing in the scratch has
+// least one d x d partial slab, so d <= 1024; larger d is rejected with
+// GBCCA_ERR_INVALID_ARG before any device work.  The number of split-K slabs
+// is as many as fit (up to one per 64 rows and enough CTAs for the GPU).  Nothing in the scratch has
 // to start at zero: every element of a slab that the second kernel reads is
 // written by the first.  The scratch is one buffer per device shared by all
 // callers, so two calls whose kernels may overlap in time (different streams,
@@ -489,13 +490,13 @@ int noalloc_scratch(double** out) {
 
 int noalloc_max_d() {
   int d = 1;
-  while (2 * (int64_t)(d + 1) * (d + 1) <= kNoAllocScratch) ++d;
+  while ((int64_t)(d + 1) * (d + 1) <= kNoAllocScratch) ++d;
   return d;
 }
 
 int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, double* C, cudaStream_t st) {
   const int64_t len = (int64_t)d * d;
-  if (2 * len > kNoAllocScratch) {
+  if (len > kNoAllocScratch) {
     set_last_error("allocation-free Gram: d = " + std::to_string(d) + " exceeds the " +
                    std::to_string(noalloc_max_d()) + " columns its 8 MiB static scratch holds");
     return GBCCA_ERR_INVALID_ARG;
@@ -503,8 +504,8 @@ int gram_noalloc(const double* A, int64_t lda, int64_t m, int d, double lambda, 
   double* ws = nullptr;
   GB_TRY(noalloc_scratch(&ws));
   const int tiles = ceil_div(d, kGT) * ceil_div(d, kGT);
-  int ks = std::max(2, std::min<int>(ceil_div(304, tiles), ceil_div(m, 64)));
-  while (ks > 2 && (int64_t)ks * len > kNoAllocScratch) --ks;
+  int ks = std::max(1, std::min<int>(ceil_div(304, tiles), ceil_div(m, 64)));
+  while (ks > 1 && (int64_t)ks * len > kNoAllocScratch) --ks;
   const int64_t kchunk = (m + ks - 1) / ks;
   dim3 grid(ceil_div(d, kGT), ceil_div(d, kGT), ks);
   gram_tn_kernel<<<grid, 256, 0, st>>>(A, lda, A, lda, m, d, d, kchunk, ws);
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(128) chol_diag_kernel(double* A, int d, int p,
     }
     __syncthreads();
   }
-  if (tid == 0 && s_bad) atomicExch(flag, 1);
+  if (tid == 0 && s_bad) atomicExch(flag, kFlagNotSpd);
   for (int e = tid; e < nb * nb; e += blockDim.x) {
     const int r = e / nb, c = e % nb;
     if (c <= r) A[(int64_t)(o + r) * d + o + c] = L[r][c];

@@ -623,7 +623,7 @@ __global__ void class_finish_kernel(const double* __restrict__ part, const doubl
     cn[threadIdx.x] = s;
     if (blockIdx.x == 0) {
       counts[threadIdx.x] = s;
-      if (s <= 0) atomicExch(flag, 1);
+      if (s <= 0) atomicExch(flag, kFlagNotSpd);
     }
   }
   __syncthreads();

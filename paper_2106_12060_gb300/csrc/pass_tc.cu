@@ -599,7 +599,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     tc_fence_before();
   }
   __syncthreads();
-  if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, 4);
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, kFlagTimeout);
   cluster_sync();  // no bulk copy or remote arrive targets a CTA that has left
   if (warp == 2) {
     tc_fence_after();

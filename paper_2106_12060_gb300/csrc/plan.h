@@ -111,6 +111,7 @@ struct Plan {
   // RCG state
   DevState* st = nullptr;
   DevState* st_host = nullptr;  // pinned mirror for read-back
+  int* flag_host = nullptr;     // pinned mirror of the device error flag
   double* phigram = nullptr;    // per view 2k x 2k Gram of Phi
   double* phipart = nullptr;    // partials of phigram
   double* phired = nullptr;     // per view 2k x 2k Gram of Phi (summed partials)

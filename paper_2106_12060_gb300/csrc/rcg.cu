@@ -1605,9 +1605,26 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   int batch = std::max(1, p.opt.check_every);
   if (timed) batch = std::min(batch, kMaxTimedBatch);
   int pending_first = 0, pending_n = timed ? 1 : 0;
+  // a kernel that gave up a bounded wait (or found a non-SPD factor) sets the
+  // plan's error flag; it is read with the state after every batch
+  auto check_flag = [&]() -> int {
+    if (*p.flag_host == 0) return GBCCA_OK;
+    const int f = *p.flag_host;
+    *p.flag_host = 0;
+    GB_CUDA(cudaMemsetAsync(p.flag, 0, sizeof(int), st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    const int rc = flag_status(f);
+    if (info != nullptr) {
+      *info = gbcca_info{};
+      info->status = rc;
+    }
+    return rc;
+  };
   while (true) {
     GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(p.flag_host, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
+    GB_TRY(check_flag());
     if (timed) GB_TRY(harvest(pending_first, pending_n, p.st_host->iter));
     if (p.st_host->done || launched >= p.opt.max_iter) break;
     pending_first = launched + 1;
@@ -1671,7 +1688,9 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   copy_sigma_kernel<<<1, 32, 0, st>>>(p.st, vals, k);
   GB_CHECK_LAUNCH();
   GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  GB_CUDA(cudaMemcpyAsync(p.flag_host, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   GB_CUDA(cudaStreamSynchronize(st));
+  GB_TRY(check_flag());
   int status = p.st_host->status;
   if (info != nullptr) {
     info->iters = p.st_host->iter;
@@ -1718,13 +1737,13 @@ __global__ void small_chol_kernel(const double* part, int nblk, int c, double* o
     if (threadIdx.x < 32) {
       double* invd = Li + c * c;
       const bool ok = warp_chol(G, c, invd);
-      if (!ok && threadIdx.x == 0) atomicExch(flag, 1);
+      if (!ok && threadIdx.x == 0) atomicExch(flag, kFlagNotSpd);
       warp_lower_inv(G, invd, Li, c);
     }
     __syncthreads();
   } else {
     if (!blk_chol(G, c)) {
-      if (threadIdx.x == 0) atomicExch(flag, 1);
+      if (threadIdx.x == 0) atomicExch(flag, kFlagNotSpd);
     }
     blk_lower_inv(G, Li, c);
   }

@@ -53,7 +53,7 @@ __global__ void draw_srht_kernel(int64_t n_pad, int m, int64_t s, uint64_t seed,
         y = feistel_even(y, bits, kr);
         ++guard;
       }
-      if (y >= lim && flag != nullptr) atomicExch(flag, 2);
+      if (y >= lim && flag != nullptr) atomicExch(flag, kFlagDraw);
       rows[i] = (int32_t)y;
     }
   }
@@ -87,7 +87,7 @@ __global__ void cs_count_kernel(const int32_t* __restrict__ h, int64_t n, int64_
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     int32_t b = h[i];
     if (b < 0 || b >= s) {
-      atomicExch(flag, 3);
+      atomicExch(flag, kFlagBucket);
       continue;
     }
     atomicAdd(&tab[(int64_t)blockIdx.x * s + b], 1);

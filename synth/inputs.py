@@ -30,10 +30,20 @@ CONFIGS = {
     "cca_tall_f32": dict(kind="cca", n=262144, dx=512, dy=512, k=10, latent=20,
                          noise=0.5, colscale=(1.0, 1e-4), lam=1e-4, dtype="f32",
                          sketch="srht", s=4 * (512 + 512), seed=0, latent_decay=2.0),
+    # The same with the scaled columns rotated by a Haar-random orthogonal
+    # matrix per view (X = (Z Ax + 0.5 Ex) diag(c) Qx^T), so that Sxx is not
+    # diagonally dominant and every stored column mixes all scales.
+    "cca_tall_bf16_mixed": dict(kind="cca", n=262144, dx=512, dy=512, k=10, latent=20,
+                                noise=0.5, colscale=(1.0, 1e-4), lam=1e-4, dtype="bf16",
+                                sketch="srht", s=4 * (512 + 512), seed=0, latent_decay=2.0,
+                                mix=True),
     # Fisher LDA: 10 classes, 784 features, means N(0, 4I), within-class
     # variances log-uniform in [1e-4, 1].
     "lda_f32": dict(kind="lda", n=100000, d=784, l=10, k=9, dtype="f32",
                     sketch="countsketch", s=3 * 784, seed=0),
+    # The same with the within-class covariance Q diag(e) Q^T, Q Haar-random.
+    "lda_f32_mixed": dict(kind="lda", n=100000, d=784, l=10, k=9, dtype="f32",
+                          sketch="countsketch", s=3 * 784, seed=0, mix=True),
 }
 
 
@@ -81,24 +91,34 @@ def latent_scales(latent: int, decay: float):
     return 10.0 ** (-decay * np.arange(latent) / (latent - 1))
 
 
-def make_workload(name: str, n: int | None = None):
-    """Build the named workload (optionally with fewer rows n)."""
+def make_workload(name: str, n: int | None = None, seed: int | None = None):
+    """Build the named workload (optionally with fewer rows n or another seed)."""
     c = dict(CONFIGS[name])
     if n is not None:
         c["n"] = n
+    if seed is not None:
+        c["seed"] = seed
     if c["kind"] == "cca":
         ls = latent_scales(c["latent"], c["latent_decay"]) if c.get("latent_decay") else None
         P = cca_latent_problem(c["n"], c["dx"], c["dy"], latent=c["latent"], noise=c["noise"],
-                               colscale=c["colscale"], dtype=c["dtype"], seed=c["seed"], latent_scale=ls)
+                               colscale=c["colscale"], dtype=c["dtype"], seed=c["seed"], latent_scale=ls,
+                               mix=c.get("mix", False))
     else:
-        P = lda_problem(c["n"], c["d"], c["l"], dtype=c["dtype"], seed=c["seed"])
+        P = lda_problem(c["n"], c["d"], c["l"], dtype=c["dtype"], seed=c["seed"], mix=c.get("mix", False))
     P["config"] = c
     return P
 
 
+def haar_orthogonal(d: int, rng) -> np.ndarray:
+    """Haar-distributed d x d orthogonal matrix: QR of a Gaussian matrix with
+    the signs of R's diagonal moved into Q."""
+    Q, R = np.linalg.qr(rng.standard_normal((d, d)))
+    return Q * np.where(np.diag(R) < 0, -1.0, 1.0)[None, :]
+
+
 def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float = 0.5,
                        colscale=None, dtype: str = "f64", seed: int = 0, chunk: int = 65536,
-                       latent_scale=None):
+                       latent_scale=None, mix: bool = False):
     """Two views sharing a latent signal: X = (Z Ax + noise Ex) diag(c), same for Y.
 
     Z (n x latent), Ax, Ay, Ex, Ey are i.i.d. N(0, 1).  ``colscale=(1, 1e-4)``
@@ -106,7 +126,9 @@ def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float 
     ill-conditioned (kappa ~ 1e8) without mixing the columns.
     ``latent_scale`` (length latent) multiplies the latent columns, which
     spreads the canonical correlations apart (equal scales give near-equal
-    correlations).
+    correlations).  ``mix=True`` rotates the scaled columns of each view by a
+    Haar-random orthogonal matrix (X <- X Qx^T), which keeps the spectrum of
+    X^T X and spreads every scale over all stored columns.
     Returns dict(X, Y, X64, Y64) where X/Y are in the storage dtype (uint16
     bit patterns for bf16) and X64/Y64 are the stored values in float64.
     """
@@ -114,6 +136,8 @@ def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float 
     Ax = rng.standard_normal((latent, dx))
     Ay = rng.standard_normal((latent, dy))
     cx, cy = _colscale(dx, colscale), _colscale(dy, colscale)
+    Qx = haar_orthogonal(dx, rng).T if mix else None
+    Qy = haar_orthogonal(dy, rng).T if mix else None
     big = n * (dx + dy) > 4_000_000
     wdt = np.float32 if (big and dtype != "f64") else np.float64
     X = np.empty((n, dx), dtype=wdt)
@@ -131,6 +155,9 @@ def cca_latent_problem(n: int, dx: int, dy: int, latent: int = 10, noise: float 
         if cx is not None:
             xb *= cx.astype(wdt)
             yb *= cy.astype(wdt)
+        if mix:
+            xb = xb @ Qx.astype(wdt)
+            yb = yb @ Qy.astype(wdt)
         X[r0:r1] = xb
         Y[r0:r1] = yb
     Xs, X64 = _store(X, dtype)
@@ -146,13 +173,15 @@ def random_tall(n: int, d: int, dtype: str = "f64", seed: int = 0, scale: float 
 
 
 def lda_problem(n: int, d: int, l: int, dtype: str = "f32", seed: int = 0,
-                mean_std: float = 2.0, var_range=(1e-4, 1.0), chunk: int = 65536):
+                mean_std: float = 2.0, var_range=(1e-4, 1.0), chunk: int = 65536, mix: bool = False):
     """Class-structured data for Fisher LDA.
 
     Class means m_k ~ N(0, mean_std^2 I).  Balanced classes (n_k = n / l, the
     remainder spread over the first classes), labels in random order.
     Within-class noise has independent coordinates with variances e_j drawn
-    log-uniformly in ``var_range``.  Returns dict(X, X64, y, l).
+    log-uniformly in ``var_range``; with ``mix=True`` the noise is rotated by
+    a Haar-random orthogonal Q, so the within-class covariance is
+    Q diag(e) Q^T.  Returns dict(X, X64, y, l).
     """
     rng = np.random.default_rng(seed)
     means = mean_std * rng.standard_normal((l, d))
@@ -165,10 +194,13 @@ def lda_problem(n: int, d: int, l: int, dtype: str = "f32", seed: int = 0,
     wdt = np.float32 if (big and dtype != "f64") else np.float64
     X = np.empty((n, d), dtype=wdt)
     sd = np.sqrt(e).astype(wdt)
+    Qt = haar_orthogonal(d, rng).T.astype(wdt) if mix else None
     for r0 in range(0, n, chunk):
         r1 = min(n, r0 + chunk)
-        g = rng.standard_normal((r1 - r0, d), dtype=wdt)
-        X[r0:r1] = means[y[r0:r1]].astype(wdt) + g * sd
+        g = rng.standard_normal((r1 - r0, d), dtype=wdt) * sd
+        if mix:
+            g = g @ Qt
+        X[r0:r1] = means[y[r0:r1]].astype(wdt) + g
     Xs, X64 = _store(X, dtype)
     return dict(X=Xs, X64=X64, y=y, l=l)
 

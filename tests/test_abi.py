@@ -81,3 +81,31 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_rejects_host_and_mistyped_tensors():
+    """The binding passes raw pointers, so a host tensor, a tensor of the wrong
+    dtype or of the wrong shape is refused in Python before any call into the
+    library (no device needed: the refusal comes first)."""
+    import torch
+    import paper_2106_12060_gb300 as gb
+    A = torch.zeros(10, 4, dtype=torch.float64)
+    C = torch.zeros(4, 4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        gb.sketch_gram_noalloc(A, 0.0, C)
+    with pytest.raises(ValueError, match="CUDA"):
+        gb.sketch_gram_noalloc(A.float(), 0.0, C.float())
+    with pytest.raises(ValueError):
+        gb.sketch_gram_noalloc(A, 0.0, torch.zeros(5, 5, dtype=torch.float64))
+    plan = gb.Plan(None, "cca", 10, (4, 3), 2, gb.FP32, None)
+    with pytest.raises(ValueError, match="CUDA"):
+        gb.cca_precondition(plan, torch.zeros(10, 4), torch.zeros(10, 3), 1e-3, 1e-3)
+
+
+def test_flag_codes_map_to_statuses():
+    """The device error flag values of the library (common.cuh) and their
+    statuses: 4 = a bounded wait ran out -> GBCCA_ERR_TIMEOUT."""
+    txt = open(os.path.join(ROOT, "paper_2106_12060_gb300", "csrc", "common.cuh")).read()
+    assert "constexpr int kFlagTimeout = 4;" in txt
+    body = txt[txt.index("inline int flag_status"):]
+    assert "case kFlagTimeout:" in body and "return GBCCA_ERR_TIMEOUT;" in body

@@ -8,7 +8,7 @@ correlations within 1e-6 relative after the FP64 Rayleigh-Ritz refinement.
 import numpy as np
 import pytest
 
-from gpu_util import to_dev, np64, rel, subspace_sin
+from gpu_util import to_dev, np64, rel, subspace_sin, bound_ratio, cca_pass_refs
 from oracle import cca as OC
 from oracle import fused as OF
 from oracle import rcg as ORCG
@@ -85,22 +85,35 @@ def test_srht_sketch(gb, dt, tol):
     assert rel(SX, srht_apply(P["X64"], D, rows)) < tol
 
 
+def gamma_cores(dt, n, d):
+    """Entrywise bounds of the CUDA-core pass, against the sums of |terms|.
+    FP32 accumulation (BF16/FP32 data): Phi rounded to FP32 (1 rounding), W
+    by an FMA chain over d columns (d roundings), G by FP32 partial sums over
+    128 rows flushed to FP64 (128 + 2), the Gram by FP32 sums over 64-row
+    tiles of W products (64 + 2, and W's own error twice).  FP64 data: the
+    same chains in FP64 over at most d + n terms."""
+    if dt == "f64":
+        g = 4 * (d + n + 4) * 2.0 ** -53
+        return g, g
+    return (d + 1 + 128 + 2) * 2.0 ** -24, (2 * (d + 1) + 64 + 2) * 2.0 ** -24
+
+
 @pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
 def test_fused_pass(gb, dt):
+    """Every entry of Gx, Gy and the Gram within its own rounding bound."""
     import torch
     n, dx, dy, k = 4099, 70, 45, 5
-    P = cca_latent_problem(n, dx, dy, latent=6, dtype=dt, seed=5)
+    P = cca_latent_problem(n, dx, dy, latent=6, dtype=dt, seed=5, colscale=(1.0, 1e-3))
     plan, _, _ = _plan(gb, P, n, dx, dy, k, dt, 1e-2)
     rng = np.random.default_rng(0)
     Px, Py = rng.standard_normal((dx, 2 * k)), rng.standard_normal((dy, 2 * k))
     Gx, Gy, Gram = gb.fused_pass(plan, torch.from_numpy(Px).cuda(), torch.from_numpy(Py).cuda())
     ox, oy, og = OF.cca_pass(P["X64"], P["Y64"], Px, Py)
-    # FP32 accumulation: each entry errs by <= ~(sum length) * 6e-8 relative to
-    # the sum of |terms|; compare against the magnitude of the result matrix.
-    tol = 1e-12 if dt == "f64" else 5e-5
-    assert rel(np64(Gx), ox) < tol
-    assert rel(np64(Gy), oy) < tol
-    assert rel(np64(Gram), og) < tol
+    rx, ry, _, aW = cca_pass_refs(P["X64"], P["Y64"], Px, Py)
+    gG, gW = gamma_cores(dt, n, max(dx, dy))
+    assert bound_ratio(np64(Gx), ox, rx, gG) <= 1.0
+    assert bound_ratio(np64(Gy), oy, ry, gG) <= 1.0
+    assert bound_ratio(np64(Gram), og, aW.T @ aW, gW) <= 1.0
 
 
 def test_solve_separated_fp64(gb):
@@ -174,12 +187,16 @@ def test_solve_low_precision_refined(gb, dt):
 def test_solve_small_fp64_workload(gb):
     """The plain FP64 workload (n=2000, dx=50, dy=40, k=5, lambda=1e-3, CountSketch
     s=360).  Its five leading correlations lie within 3e-3 of each other, so CG
-    needs a few thousand iterations; parity is on the canonical correlations."""
+    needs a few thousand iterations.  A gradient reduction of 1e-5 is
+    reachable (the FP64 objective reaches its rounding floor near 3e-7 of the
+    initial gradient norm, where no step can lower it); the run must stop on
+    that rule, not on the iteration cap, with every correlation within 1e-8."""
     n, dx, dy, k, lam = 2000, 50, 40, 5, 1e-3
     P = cca_latent_problem(n, dx, dy, latent=10, noise=0.5, dtype="f64", seed=0)
-    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, s=360, max_iter=6000, gtol=1e-10, check_every=64)
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, "f64", lam, s=360, max_iter=8000, gtol=1e-5, check_every=64)
     sig, U, V, info = gb.cca_solve(plan)
     ref, _, _ = OC.cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    assert info["status"] == gb.OK and info["grad_norm"] <= 1e-5 * info["grad_norm0"], info
     assert rel(np64(sig), ref) < 1e-8, (np64(sig), ref, info)
 
 

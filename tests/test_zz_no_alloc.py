@@ -51,15 +51,35 @@ def test_matches_preconditioner_of_existing_entry_point(gb):
     assert rel(c1, sx.T @ sx + lam * np.eye(dx)) < 1e-13
 
 
+def test_largest_d_matches_fp64_gram(gb):
+    """d = gbcca_sketch_gram_noalloc_max_d() (one partial slab fills the
+    scratch): the result equals the FP64 Gram computed on the host, on two
+    calls in a row."""
+    import torch
+    d = gb.sketch_gram_noalloc_max_d()
+    m, lam = 1500, 0.25
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((m, d))
+    A = torch.from_numpy(a).cuda()
+    C1 = torch.full((d, d), float("nan"), dtype=torch.float64, device="cuda")
+    C2 = torch.full((d, d), float("nan"), dtype=torch.float64, device="cuda")
+    gb.sketch_gram_noalloc(A, lam, C1)
+    gb.sketch_gram_noalloc(A, lam, C2)
+    torch.cuda.synchronize()
+    c1, c2 = np64(C1), np64(C2)
+    assert np.array_equal(c1, c2)
+    assert rel(c1, a.T @ a + lam * np.eye(d)) < 1e-13
+
+
 def test_rejects_d_beyond_scratch(gb):
     import torch
     dmax = gb.sketch_gram_noalloc_max_d()
-    assert dmax == 724
+    assert dmax * dmax <= (1 << 20) < (dmax + 1) * (dmax + 1)
     d = dmax + 1
     A = torch.zeros(2, d, dtype=torch.float64, device="cuda")
     C = torch.zeros(d, d, dtype=torch.float64, device="cuda")
     with pytest.raises(gb.GbccaError) as e:
         gb.sketch_gram_noalloc(A, 0.0, C)
     assert e.value.code == gb.ERR_INVALID_ARG
-    assert "724" in str(e.value)
+    assert str(dmax) in str(e.value)
     assert torch.count_nonzero(C).item() == 0
