@@ -27,16 +27,22 @@ if ROOT not in sys.path:
 METRIC = "CCA solve time to 1e-6 rel. objective; fused pass % of HBM peak; p50/p99 latency"
 WORKLOAD = "cca_tall_bf16"
 LAM = 1e-4
-# Stopping rule: ||grad||_M <= GTOL ||grad_0||_M.  On this workload, with the
-# final Rayleigh-Ritz step over [U, eta] (refine = 2), it gives a relative
-# objective suboptimality near 1e-8 and every canonical correlation within
-# 7.3e-7 of the FP64 oracle after 46 iterations (checked against 1e-6 by
-# tests/test_gpu_fullsize.py).  The gradient norm plateaus just below: 3e-3
-# takes 79 iterations.
-GTOL = 4e-3
+# Stopping rule.  The gradient rule ||grad||_M <= GTOL ||grad_0||_M is off:
+# on this workload the CG gradient norm is not monotone and a threshold chosen
+# on one instance stops other instances early.  The solve stops when the
+# Rayleigh-Ritz values of span([U, eta]) (the values the final refinement
+# reports) change by less than RTOL, relative, at two consecutive checks
+# CHECK_EVERY iterations apart; on seeds 0-6 of the data and of the sketch,
+# BF16 and FP32 storage, that left every correlation within 1e-6 of the FP64
+# oracle (tests/test_gpu_fullsize.py checks seeds 0, 1 and 2).
+GTOL = 0.0
+RTOL = 1e-7
+CHECK_EVERY = 8
 # Final Rayleigh-Ritz step from the Grams of the tensor-core pass (refine = 2;
 # the same test checks this setting against the FP64 oracle).
 REFINE = 2
+# The LDA workload refines with FP64 Grams of W (refine = 1).
+LDA_REFINE = 1
 
 
 # DRAM traffic of one full-size tc_pass_kernel launch (read + write bytes),
@@ -153,7 +159,8 @@ def max_over_ranks(ws, x: float) -> float:
 def workload_config(c, ws):
     """The `config` object of both arms' JSON lines."""
     return {"workload": WORKLOAD, "n": c["n"], "dx": c["dx"], "dy": c["dy"], "k": c["k"], "lambda": LAM,
-            "sketch": "srht", "s": c["s"], "storage": c["dtype"], "gtol": GTOL, "refine": REFINE,
+            "sketch": "srht", "s": c["s"], "storage": c["dtype"], "gtol": GTOL, "rtol": RTOL,
+            "check_every": CHECK_EVERY, "refine": REFINE,
             "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (537 MB)"}
 
 
@@ -255,8 +262,8 @@ def fp64_comparison(gb, P, sig_bf16, steps: int = 2):
     n, dx, dy, k = c["n"], c["dx"], c["dy"], c["k"]
     X = torch.from_numpy(np.ascontiguousarray(P["X64"])).cuda()
     Y = torch.from_numpy(np.ascontiguousarray(P["Y64"])).cuda()
-    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
-                             check_every=8)
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, rtol=RTOL,
+                             check_every=CHECK_EVERY)
     plan = gb.cca_plan(n, dx, dy, k, "f64", opt)
     U = torch.empty(dx, k, dtype=torch.float64, device="cuda")
     V = torch.empty(dy, k, dtype=torch.float64, device="cuda")
@@ -314,7 +321,8 @@ def other_workloads(gb, steps: int = 2):
     X = torch.from_numpy(np.ascontiguousarray(P["X"])).cuda()
     Y = torch.from_numpy(np.ascontiguousarray(P["Y"])).cuda()
     del P
-    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, check_every=8,
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, rtol=RTOL,
+                             check_every=CHECK_EVERY,
                              time_passes=1, refine=REFINE)
     plan = gb.cca_plan(n, dx, dy, k, "f32", opt)
 
@@ -327,8 +335,9 @@ def other_workloads(gb, steps: int = 2):
     gbps = n * (dx + dy) * 4 / (pass_ms * 1e-3) / 1e9
     out["cca_tall_f32"] = {"solve_ms": ms, "iterations": float(np.mean([i["iters"] for i in infos])),
                            "pass_ms": pass_ms, "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm,
-                           "pass_algorithmic_bytes": n * (dx + dy) * 4,
-                           "kernels": "pass_w_kernel + pass_g_async_kernel (CUDA cores, FP32 accumulate)"}
+                           "pass_algorithmic_bytes": n * (dx + dy) * 4, "status": infos[-1]["status"],
+                           "kernels": "split_pass_kernel (tcgen05 + TMA over the BF16 hi/lo copy of the FP32 "
+                                      "data, FP32 accumulate)"}
     plan.close()
     del X, Y
     torch.cuda.empty_cache()
@@ -349,11 +358,11 @@ def other_workloads(gb, steps: int = 2):
     del x64
     X = torch.from_numpy(Xh).cuda()
     yl = torch.from_numpy(y).cuda()
-    # gtol 3e-4 with the exact (FP64) Rayleigh-Ritz refinement: 218
-    # iterations, every generalized eigenvalue within 2.6e-8 of the oracle
-    # (tests/test_gpu_fullsize.py); below ~1e-4 the gradient norm reaches its
-    # FP32 floor and the solve runs to max_iter
-    opt = gb.default_options(s=c["s"], max_iter=1000, gtol=3e-4, check_every=8, time_passes=1, refine=1)
+    # the same Ritz-value stopping rule as the CCA solves, with the exact
+    # (FP64) Rayleigh-Ritz refinement (tests/test_gpu_fullsize.py checks the
+    # generalized eigenvalues against the oracle)
+    opt = gb.default_options(s=c["s"], max_iter=1000, gtol=0.0, rtol=RTOL, check_every=CHECK_EVERY, time_passes=1,
+                             refine=LDA_REFINE)
     plan = gb.lda_plan(n, d, l, k, "f32", opt)
 
     def lda_step():
@@ -361,12 +370,13 @@ def other_workloads(gb, steps: int = 2):
 
     ms, infos = timed(lda_step)
     pass_ms = float(np.mean([i["pass_ms"] for i in infos]))
-    nbytes = n * d * 4 + n * 4
+    nbytes = n * d * 4
     gbps = nbytes / (pass_ms * 1e-3) / 1e9
     out["lda_f32"] = {"solve_ms": ms, "iterations": float(np.mean([i["iters"] for i in infos])),
-                      "gtol": 3e-4, "pass_ms": pass_ms, "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm,
-                      "pass_algorithmic_bytes": nbytes,
-                      "kernels": "LDA pass (CUDA cores, FP32 accumulate): X^T (X Phi - class means Phi)"}
+                      "rtol": RTOL, "refine": LDA_REFINE, "status": infos[-1]["status"], "pass_ms": pass_ms,
+                      "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm, "pass_algorithmic_bytes": nbytes,
+                      "kernels": "split_pass_kernel (tcgen05 + TMA over the BF16 hi/lo copy of the class-centred "
+                                 "FP32 data): Xhat^T (Xhat Phi)"}
     plan.close()
     del X
     torch.cuda.empty_cache()
@@ -473,8 +483,8 @@ def run_ours(args, ws, rank, local):
     X = Xh.cuda()
     Y = Yh.cuda()
     stream = torch.cuda.current_stream()
-    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
-                             check_every=8, time_passes=1, refine=REFINE)
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, rtol=RTOL,
+                             check_every=CHECK_EVERY, time_passes=1, refine=REFINE)
     plan = gb.cca_plan(n, dx, dy, k, dt, opt)
     U = torch.empty(dx, k, dtype=torch.float64, device="cuda")
     V = torch.empty(dy, k, dtype=torch.float64, device="cuda")
@@ -528,8 +538,8 @@ def run_ours(args, ws, rank, local):
     e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1))
     # the same solves with the iteration batches replayed from CUDA graphs
     # (the library's default; per-pass event timing needs direct launches)
-    gopt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
-                              check_every=8, time_passes=0, refine=REFINE, graphs=1)
+    gopt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, rtol=RTOL,
+                              check_every=CHECK_EVERY, time_passes=0, refine=REFINE, graphs=1)
     gplan = gb.cca_plan(n, dx, dy, k, dt, gopt)
 
     def gstep():
@@ -639,8 +649,8 @@ def run_solve_only(args):
     to = (lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).view(torch.bfloat16).cuda()) \
         if dt == "bf16" else (lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda())
     X, Y = to(P["X"]), to(P["Y"])
-    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL,
-                             check_every=8, refine=REFINE)
+    opt = gb.default_options(sketch=gb.SRHT, s=c["s"], seed=c["seed"], max_iter=1000, gtol=GTOL, rtol=RTOL,
+                             check_every=CHECK_EVERY, refine=REFINE)
     plan = gb.cca_plan(n, dx, dy, k, dt, opt)
     for _ in range(args.steps):
         gb.cca_precondition(plan, X, Y, LAM, LAM)

@@ -89,6 +89,22 @@ typedef struct {
                             data pointers change); 0, or time_passes = 1: the
                             kernels are launched one by one.  Both run the
                             same kernels in the same order.                     */
+  double rtol;           /* stop when the Rayleigh-Ritz values of the subspace
+                            span([U, eta]) x span([V, eta_V]) (the values the
+                            final refinement reports) change by less than rtol,
+                            relative, at two consecutive checks (check_every
+                            iterations apart); 0 (default) = off.  Either rule
+                            (gtol or rtol) ends the iteration.               */
+  int32_t tensor_cores;  /* 1 (default): the data pass runs on the tensor-core
+                            kernels where the plan is eligible (BF16 and FP32
+                            data, 2k <= 20 or 24, d within their limits); 0:
+                            the CUDA-core kernels only (for comparisons)     */
+  int64_t wait_cycles;   /* bound, in GPU clock cycles, on one pipeline wait of
+                            the FP32 tensor-core pass (0 = the default 2e9,
+                            about one second).  A wait that runs out stops the
+                            pass early: every CTA drains its own copies and
+                            MMAs, and the call returns GBCCA_ERR_TIMEOUT.
+                            Small values exist to exercise that path.       */
 } gbcca_options;
 
 /* Per-solve report (host struct filled by the solve calls). */
@@ -107,7 +123,8 @@ typedef struct {
 } gbcca_info;
 
 /* Fills `opt` with defaults (CountSketch, s = 0, seed 0, max_iter 1000,
- * gtol 1e-8, refine 1, warm_start 1, check_every 8, time_passes 0, graphs 1).
+ * gtol 1e-8, refine 1, warm_start 1, check_every 8, time_passes 0, graphs 1,
+ * rtol 0, tensor_cores 1, wait_cycles 0).
  * Returns GBCCA_OK or
  * GBCCA_ERR_INVALID_ARG if opt is NULL. */
 int gbcca_default_options(gbcca_options* opt);
@@ -201,7 +218,12 @@ enum gbcca_query {
   GBCCA_Q_WARM_U = 4,     /* warm start U~ (dx x k) before qf_B            */
   GBCCA_Q_WARM_V = 5,     /* warm start V~ (dy x k)                        */
   GBCCA_Q_HISTORY = 6,    /* per iteration (f, ||grad||_M, t): 3 (max_iter+1) */
-  GBCCA_Q_CLASS_MEANS = 7 /* LDA class means (n_classes x d)               */
+  GBCCA_Q_CLASS_MEANS = 7, /* LDA class means (n_classes x d)              */
+  GBCCA_Q_RITZ = 8        /* with opt.rtol > 0: the Ritz values of every check
+                             of the last solve, row r (k values) after
+                             iteration (r + 1) check_every;
+                             (max_iter / check_every + 2) x k, zero rows
+                             after the last check                          */
 };
 int64_t gbcca_query_size(gbcca_plan_t plan, int32_t what);
 int gbcca_query(gbcca_plan_t plan, int32_t what, double* dst, void* stream);

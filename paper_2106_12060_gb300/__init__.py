@@ -15,7 +15,7 @@ import ctypes as C
 from . import _lib
 from ._lib import (  # noqa: F401
     BF16, FP32, FP64, COUNTSKETCH, SRHT, IDENTITY, EXACT, Options, Info, GbccaError,
-    Q_SKETCH_X, Q_SKETCH_Y, Q_R_X, Q_R_Y, Q_WARM_U, Q_WARM_V, Q_HISTORY, Q_CLASS_MEANS,
+    Q_SKETCH_X, Q_SKETCH_Y, Q_R_X, Q_R_Y, Q_WARM_U, Q_WARM_V, Q_HISTORY, Q_CLASS_MEANS, Q_RITZ,
     OK, ERR_MAXITER, ERR_NOT_SPD, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_STATE, ERR_TIMEOUT, ERR_CUDA, ERR_OOM,
 )
 

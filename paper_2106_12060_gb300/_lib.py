@@ -13,7 +13,7 @@ BF16, FP32, FP64 = 0, 1, 2
 COUNTSKETCH, SRHT, IDENTITY, EXACT = 0, 1, 2, 3
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_NOT_SPD, ERR_MAXITER, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
-Q_SKETCH_X, Q_SKETCH_Y, Q_R_X, Q_R_Y, Q_WARM_U, Q_WARM_V, Q_HISTORY, Q_CLASS_MEANS = range(8)
+Q_SKETCH_X, Q_SKETCH_Y, Q_R_X, Q_R_Y, Q_WARM_U, Q_WARM_V, Q_HISTORY, Q_CLASS_MEANS, Q_RITZ = range(9)
 
 
 class Options(C.Structure):
@@ -28,6 +28,9 @@ class Options(C.Structure):
         ("check_every", C.c_int32),
         ("time_passes", C.c_int32),
         ("graphs", C.c_int32),
+        ("rtol", C.c_double),
+        ("tensor_cores", C.c_int32),
+        ("wait_cycles", C.c_int64),
     ]
 
 

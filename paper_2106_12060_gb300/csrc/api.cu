@@ -50,9 +50,12 @@ void free_plan(Plan* p) {
   for (void* q : {(void*)p->h, (void*)p->g, (void*)p->cs_tab, (void*)p->cs_off, (void*)p->perm, p->srht_T,
                   (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
-                  (void*)p->phigram, (void*)p->phipart, (void*)p->phired, (void*)p->cross, (void*)p->crosspart, (void*)p->history,
+                  (void*)p->phigram, (void*)p->phipart, (void*)p->phired, (void*)p->cross, (void*)p->crosspart, (void*)p->history, (void*)p->ritz_hist,
                   (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->mv_part, (void*)p->mv_cnt, (void*)p->ls_f, (void*)p->ls_L})
     dfree(q);
+  for (int v = 0; v < 2; ++v) dfree(p->ts_copy[v]);
+  dfree(p->ts_img);
+  dfree(p->ts_part);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   if (p->flag_host != nullptr) cudaFreeHost(p->flag_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
@@ -162,6 +165,8 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->cross, (int64_t)p->nviews * 16 * k * k));
   GB_TRY(dalloc(&p->crosspart, (int64_t)p->nviews * nblk * std::max(16 * k * k, p->l * p->l)));
   GB_TRY(dalloc(&p->history, 3 * (int64_t)(p->opt.max_iter + 1)));
+  p->ritz_len = p->opt.max_iter / std::max(1, p->opt.check_every) + 2;
+  GB_TRY(dalloc(&p->ritz_hist, (int64_t)p->ritz_len * k));
   p->ws_len = 8 * (int64_t)dmax * dmax + 3 * (int64_t)dmax * std::max(std::max(p->l, k2), 1) + 4096;
   GB_TRY(dalloc(&p->ws, p->ws_len));
   GB_TRY(dalloc(&p->mt_part, (int64_t)ceil_div(dmax, 64) * dmax * 40));
@@ -181,6 +186,7 @@ int alloc_plan(Plan* p) {
     GB_CUDA(cudaMemset(p->tc_img, 0, 2 * 49152));
     GB_TRY(dalloc(&p->tc_part, (int64_t)p->sm_count * p->D * k4));
   }
+  GB_TRY(split_pass_alloc(*p));
   GB_CUDA(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
   GB_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
   GB_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
@@ -195,7 +201,8 @@ int alloc_plan(Plan* p) {
 
 int check_options(const gbcca_options& o) {
   if (o.sketch < 0 || o.sketch > 3) return GBCCA_ERR_INVALID_ARG;
-  if (o.max_iter < 1 || o.s < 0 || !(o.gtol >= 0) || o.check_every < 1) return GBCCA_ERR_INVALID_ARG;
+  if (o.max_iter < 1 || o.s < 0 || !(o.gtol >= 0) || o.check_every < 1 || o.wait_cycles < 0 || !(o.rtol >= 0))
+    return GBCCA_ERR_INVALID_ARG;
   return GBCCA_OK;
 }
 
@@ -285,6 +292,7 @@ int finish_factor(Plan& p, int v, cudaStream_t st) {
 
 int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream_t st) {
   const bool center = p.kind == kLDA;
+  GB_TRY(split_pass_prepare(p, st));
   const bool srht = p.opt.sketch == GBCCA_SKETCH_SRHT;
   if (srht) {
     if (sh != nullptr && sg != nullptr) {
@@ -385,6 +393,7 @@ int gbcca_default_options(gbcca_options* opt) {
   opt->warm_start = 1;
   opt->check_every = 8;
   opt->graphs = 1;
+  opt->tensor_cores = 1;
   return GBCCA_OK;
 }
 
@@ -471,10 +480,11 @@ int lda_solve(gbcca_plan_t plan, const void* X, int64_t ldx, const int32_t* labe
   GB_TRY(lda_class_stats(*p, st));
   {
     int r = read_flag(*p, st);
-    if (r != GBCCA_OK) {
+    if (r == GBCCA_ERR_NOT_SPD) {
       set_last_error("lda_solve: every class needs at least one sample");
       return GBCCA_ERR_INVALID_ARG;
     }
+    if (r != GBCCA_OK) return r;
   }
   GB_TRY(precondition_common(*p, sketch_h, sketch_g, st));
   return rcg_run(*p, mu, tol, W, nullptr, rho, info, st);
@@ -525,6 +535,7 @@ int64_t gbcca_query_size(gbcca_plan_t plan, int32_t what) {
     case GBCCA_Q_WARM_V: return p->kind == kCCA ? (int64_t)p->v[1].d * p->k : -1;
     case GBCCA_Q_HISTORY: return 3 * (int64_t)(p->opt.max_iter + 1);
     case GBCCA_Q_CLASS_MEANS: return p->kind == kLDA ? (int64_t)p->l * p->v[0].d : -1;
+    case GBCCA_Q_RITZ: return (int64_t)p->ritz_len * p->k;
   }
   return -1;
 }
@@ -546,6 +557,7 @@ int gbcca_query(gbcca_plan_t plan, int32_t what, double* dst, void* stream) {
     case GBCCA_Q_WARM_V: src = p->v[1].warm; break;
     case GBCCA_Q_HISTORY: src = p->history; break;
     case GBCCA_Q_CLASS_MEANS: src = p->means; break;
+    case GBCCA_Q_RITZ: src = p->ritz_hist; break;
   }
   GB_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                           reinterpret_cast<cudaStream_t>(stream)));

@@ -54,6 +54,7 @@ constexpr int kFlagNotSpd = 1;    // a Cholesky pivot was not positive / empty c
 constexpr int kFlagDraw = 2;      // SRHT row draw left [0, n_pad)
 constexpr int kFlagBucket = 3;    // CountSketch bucket index out of [0, s)
 constexpr int kFlagTimeout = 4;   // a bounded device wait ran out (kernel aborted)
+constexpr int kFlagLabel = 5;     // an FDA label outside [0, n_classes)
 
 // Status and message for a flag value read back from the device.
 inline int flag_status(int f) {
@@ -64,6 +65,9 @@ inline int flag_status(int f) {
       return GBCCA_ERR_NOT_SPD;
     case kFlagBucket:
       set_last_error("CountSketch bucket index out of range");
+      return GBCCA_ERR_INVALID_ARG;
+    case kFlagLabel:
+      set_last_error("a label is outside [0, n_classes)");
       return GBCCA_ERR_INVALID_ARG;
     case kFlagTimeout:
       set_last_error("a bounded device-side wait ran out; the kernel stopped early and its results are void");

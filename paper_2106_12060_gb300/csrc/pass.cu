@@ -564,8 +564,10 @@ int run_pass(Plan& p, bool gram_only, cudaStream_t st, int phi_cols, const int* 
 // turns the launches into no-ops once the solver has stopped.
 int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols, const int* done) {
   if (phi_cols <= 0) phi_cols = 2 * p.k;
-  if (low && !gram_only && phi_cols == 2 * p.k && p.tc_img != nullptr && tc_pass_eligible(p))
-    return tc_pass(p, st, done);
+  if (low && !gram_only && phi_cols == 2 * p.k && p.opt.tensor_cores) {
+    if (p.tc_img != nullptr && tc_pass_eligible(p)) return tc_pass(p, st, done);
+    if (split_pass_ready(p)) return split_pass(p, st, done);
+  }
   if (p.kev0 != nullptr) GB_CUDA(cudaEventRecord(p.kev0, st));
   const int rc = fused_pass_cores(p, low, gram_only, st, phi_cols, done);
   if (rc == GBCCA_OK && p.kev1 != nullptr) GB_CUDA(cudaEventRecord(p.kev1, st));
@@ -603,7 +605,10 @@ __global__ void class_sums_kernel(const Tin* __restrict__ X, int64_t ld, int64_t
   for (int k = 0; k < l; ++k) acc[k * 256 + threadIdx.x] = 0;
   const int64_t r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
   if (c < d)
-    for (int64_t i = r0; i < r1; ++i) acc[y[i] * 256 + threadIdx.x] += to_f64(X[i * ld + c]);
+    for (int64_t i = r0; i < r1; ++i) {
+      const int yi = y[i];
+      if (yi >= 0 && yi < l) acc[yi * 256 + threadIdx.x] += to_f64(X[i * ld + c]);  // bad labels: see label_check
+    }
   if (c < d)
     for (int k = 0; k < l; ++k) part[((int64_t)blockIdx.x * l + k) * d + c] = acc[k * 256 + threadIdx.x];
   if (blockIdx.y == 0 && threadIdx.x < l) {
@@ -642,7 +647,15 @@ __global__ void class_finish_kernel(const double* __restrict__ part, const doubl
   }
 }
 
+// Every label in [0, l): the later kernels index class tables by label.
+__global__ void label_check_kernel(const int32_t* __restrict__ y, int64_t n, int l, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (y[i] < 0 || y[i] >= l) atomicExch(flag, kFlagLabel);
+}
+
 int lda_class_stats(Plan& p, cudaStream_t st) {
+  label_check_kernel<<<std::min(ceil_div(p.n, 256), 4 * p.sm_count), 256, 0, st>>>(p.labels, p.n, p.l, p.flag);
+  GB_CHECK_LAUNCH();
   const int chunks = 128;
   int64_t rpc = (p.n + chunks - 1) / chunks;
   dim3 grid(chunks, ceil_div(p.D, 256));

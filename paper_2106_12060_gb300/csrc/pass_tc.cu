@@ -43,9 +43,7 @@
 // Every mbarrier wait is bounded in time; on expiry the CTA records an error
 // code, waits (bounded) for its own copies and MMAs, frees TMEM and leaves
 // after a cluster barrier (no remote access can target an exited CTA).
-#include <cuda.h>
-
-#include "plan.h"
+#include "tc_ptx.cuh"
 
 namespace gbcca {
 
@@ -60,7 +58,7 @@ constexpr int kPhiView = 49152;       // stride of the views' Phi images in the 
 constexpr int kMaxSmem = 232448;      // dynamic shared memory of one CTA
 constexpr uint32_t kTmemCols = 512;   // W: columns kTW (nacc b + a); G: kTG + kN2 p (p < 4 pairs)
 constexpr int kTW = 48;               // TMEM column stride of the W accumulators
-constexpr long long kTimeout = 2000000000ll;      // cycles (~1 s)
+constexpr long long kTimeout = kWaitCycles;       // cycles (~1 s)
 
 // Shared-memory layout and barriers for GEMM 1 with N = 2 kH1 (Phi columns as
 // bf16 hi rows 0 .. kH1 - 1 and lo rows kH1 .. 2 kH1 - 1; kH1 = 20 serves
@@ -106,155 +104,6 @@ struct Lay {
   static_assert(kNumBars * 8 + 8 <= 512, "barrier area");
   static_assert(kSmemBytes <= kMaxSmem, "shared memory");
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false when the time limit passes or another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kTimeout) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor, 128-byte swizzle (start, leading and
-// stride byte offsets in 16-byte units; version 1; layout SWIZZLE_128B).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Commit that arrives on the barrier at the same shared-memory offset in every
-// CTA of `mask` (this cluster).
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(bar),
-               "h"(mask)
-               : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// shared::cluster address of the same shared-memory location in CTA `rank`
-__device__ __forceinline__ uint32_t map_peer(uint32_t local, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// Bulk copy of `bytes` from this CTA's shared memory to a shared::cluster
-// address; completion is counted on the destination CTA's barrier.
-__device__ __forceinline__ void bulk_to_peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   dst),
-               "r"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-// Bulk copy of `bytes` from global memory into this CTA's shared memory;
-// completion is counted on `bar` (this CTA).
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// byte offset of element (row, e) inside a K-major 128B-swizzled K-box of
-// 64 bf16 elements per row (8-row groups of 1024 bytes)
-__host__ __device__ __forceinline__ uint32_t swz(int row, int e) {
-  const int chunk = (e >> 3) ^ (row & 7);
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (e & 7) * 2);
-}
 
 struct Args {
   int64_t n;
@@ -636,8 +485,10 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
 // arithmetic (8 loads in flight), then the four (sum, compensation) pairs are
 // combined in fixed order.  Error ~2 ulp of the sum, far below the partials'
 // own rounding.
+// `stride` is the distance of the partial slabs (floats, a multiple of 4, at
+// least len); entries len .. stride - 1 of a slab are padding.
 __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
-                                                        double* __restrict__ G, const int* done) {
+                                                        int64_t stride, double* __restrict__ G, const int* done) {
   if (done != nullptr && *done) return;
   __shared__ float4 red_s[4][64], red_c[4][64];
   const int g = threadIdx.x & 63, qtr = threadIdx.x >> 6;
@@ -648,7 +499,7 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict_
   float s[4] = {0.f, 0.f, 0.f, 0.f}, cp[4] = {0.f, 0.f, 0.f, 0.f};
   if (in) {
     const float4* src = reinterpret_cast<const float4*>(part) + e4;
-    const int64_t stride4 = len / 4;
+    const int64_t stride4 = stride / 4;
     for (int b0 = p0; b0 < p1; b0 += 8) {
       float4 v[8];
 #pragma unroll
@@ -709,40 +560,8 @@ __global__ void tc_gram_kernel(const double* __restrict__ Phix, const double* __
 // ----------------------------------------------------------------- host side
 namespace {
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (fn == nullptr) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
-  EncodeTiledFn fn = encode_fn();
-  if (fn == nullptr) {
-    set_last_error("cuTensorMapEncodeTiled is not available from the driver");
-    return GBCCA_ERR_CUDA;
-  }
-  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)n};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)tc::kRows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_last_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
-    return GBCCA_ERR_CUDA;
-  }
-  return GBCCA_OK;
+  return make_tma_map_bf16(map, base, n, d, ld, tc::kRows);
 }
 
 }  // namespace
@@ -817,7 +636,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   if (p.kev1 != nullptr) GB_CUDA(cudaEventRecord(p.kev1, st));
   const int grid = ncl;  // partial slabs, one per cluster
   const int64_t len = (int64_t)p.D * k4;
-  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, p.G, done);
+  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, len, p.G, done);
   GB_CHECK_LAUNCH();
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
                                                                   p.G, p.Gram, done);

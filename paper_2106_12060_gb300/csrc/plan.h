@@ -23,6 +23,9 @@ struct DevState {
   double sigma[kMaxK];              // Rayleigh-Ritz values at the end
   double rot[2][2 * kMaxK * kMaxK]; // Rayleigh-Ritz rotation per view (rr_m x k)
   int rr_m;                         // dimension of the Rayleigh-Ritz subspace used (k or 2k)
+  int rr_ok;                        // 1 if the last Rayleigh-Ritz step factored its Grams
+  int ritz_checks;                  // Ritz-value checks recorded in this solve
+  int ritz_small;                   // consecutive checks whose change was below rtol
   double YW[kMaxClasses * kMaxK];   // FDA: Yhat times the current W (l x k)
   double ftrial[64];                // line-search trial values (diagnostics)
   double Qsyl[2][kMaxK * kMaxK];    // eigenvectors of the last Sylvester coefficient
@@ -119,6 +122,8 @@ struct Plan {
   double* crosspart = nullptr;  // partials
   int thinCtas = 0;
   double* history = nullptr;    // 3 (max_iter + 1)
+  double* ritz_hist = nullptr;  // Ritz values at every check: (max_iter / check_every + 2) x k
+  int ritz_len = 0;             // rows of ritz_hist
   double* mt_part = nullptr;    // slice partials of mat_thin
   float* dfx = nullptr;         // 2 x dmax x 2k floats: split blocks for double-float products
   float* mv_part = nullptr;     // K-slice partials of the double-float products
@@ -154,6 +159,16 @@ struct Plan {
   int batch_key_n = 0;
   bool batch_key_timed = false;
   long long batch_launches = 0;  // kernels in one replay (for the launch counter)
+  // tensor-core pass for FP32 data: BF16 hi/lo copies of the bound views
+  // (FDA: of the class-centred rows), hi then lo, leading dimension ts_ld;
+  // TMA descriptors [view][hi | lo]; Phi images; per-cluster partials
+  __nv_bfloat16* ts_copy[2] = {nullptr, nullptr};
+  int64_t ts_ld[2] = {0, 0};
+  alignas(64) unsigned char ts_map[4][128] = {};
+  uint8_t* ts_img = nullptr;
+  float* ts_part = nullptr;
+  int ts_clusters = 0;
+  bool ts_ready = false;
   cudaEvent_t kev0 = nullptr;  // when set: recorded around the data kernel of the next pass
   cudaEvent_t kev1 = nullptr;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
 };
@@ -230,6 +245,13 @@ int lda_class_stats(Plan& p, cudaStream_t st);
 // pass_tc.cu
 bool tc_pass_eligible(const Plan& p);
 int tc_pass(Plan& p, cudaStream_t st, const int* done);
+
+// pass_split.cu: the tensor-core pass for FP32 data (CCA and FDA)
+bool split_pass_shape_ok(int kind, int dtype, int k, int d0, int d1);
+bool split_pass_ready(const Plan& p);
+int split_pass_alloc(Plan& p);
+int split_pass_prepare(Plan& p, cudaStream_t st);
+int split_pass(Plan& p, cudaStream_t st, const int* done);
 
 // rcg.cu
 int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals,

@@ -1131,6 +1131,10 @@ struct RRArgs {
   int nblk, k, kind, l;
   const double* YPhi;     // FDA (l x 2k)
   int m0;                 // subspace: k (columns U) or 2k (columns [U, eta])
+  int check;              // 1: the convergence check of option rtol, at the
+                          // start of every `every`-th iteration (a failed
+                          // factorization clears rr_ok and leaves the status)
+  int every;
 };
 
 // Rayleigh-Ritz on span(Phi_v[:, :m]) per view: m = 2k uses the point and
@@ -1143,6 +1147,8 @@ struct RRArgs {
 __global__ void rr_kernel(RRArgs a) {
   extern __shared__ double rsm[];
   DevState* st = a.st;
+  // uniform over the CTA: a check runs at iterations every, 2 every, ... only
+  if (a.check && (st->done || st->force_zero_step || st->iter == 0 || st->iter % a.every != 0)) return;
   const int k = a.k, k2 = 2 * k, mm0 = a.m0 * a.m0;
   double* Gx = rsm;
   double* Gy = Gx + mm0;
@@ -1201,7 +1207,10 @@ __global__ void rr_kernel(RRArgs a) {
     __syncthreads();
     if (s_ok == 1 || m == k) {
       if (s_ok == 0) {
-        if (threadIdx.x == 0) st->status = GBCCA_ERR_NOT_SPD;
+        if (threadIdx.x == 0) {
+          if (!a.check) st->status = GBCCA_ERR_NOT_SPD;
+          st->rr_ok = 0;
+        }
         return;
       }
       break;
@@ -1224,6 +1233,32 @@ __global__ void rr_kernel(RRArgs a) {
       T1[e] = 0.5 * (C[i * m + j] + C[j * m + i]);
     }
     __syncthreads();
+  }
+  if (a.check) {
+    // a convergence check needs the values only: FP32 Jacobi for the
+    // vectors, then FP64 Rayleigh quotients with them, whose error is second
+    // order in the vectors' (the values to ~1e-13 at FP32 vector accuracy)
+    float* Af = reinterpret_cast<float*>(T2);
+    float* Qf = Af + m * m;
+    float* lamf = reinterpret_cast<float*>(Q);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Af[e] = (float)T1[e];
+    __syncthreads();
+    blk_jacobi<float>(Af, Qf, lamf, m, rot);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      double num = 0, den = 0;
+      for (int r = 0; r < m; ++r) {
+        const double qr = (double)Qf[r * m + i];
+        double t = 0;
+        for (int c = 0; c < m; ++c) t += T1[r * m + c] * (double)Qf[c * m + i];
+        num += qr * t;
+        den += qr * qr;
+      }
+      const double rq = den > 0 ? num / den : 0.0;
+      st->sigma[i] = a.kind == kCCA ? sqrt(fmax(rq, 0.0)) : rq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->rr_ok = 1;
+    return;
   }
   blk_jacobi(T1, Q, lam, m, rot);                    // right singular vectors (CCA) / eigvecs (FDA), descending
   // the leading k: CCA sigma_i = ||C q_i||, left vectors a_i = C q_i / sigma_i
@@ -1248,7 +1283,35 @@ __global__ void rr_kernel(RRArgs a) {
     __syncthreads();
     blk_mm(Lxi, true, Q, false, st->rot[0], m, m, k, m, m);
   }
-  if (threadIdx.x == 0) st->rr_m = m;
+  if (threadIdx.x == 0) {
+    st->rr_m = m;
+    st->rr_ok = 1;
+  }
+}
+
+// Convergence check on the Ritz values (option rtol): row idx of the history
+// receives the values the last Rayleigh-Ritz step left in st->sigma; when
+// every value changed by less than rtol (relative) since the previous check,
+// the iteration ends (st->done) with status OK.
+// Two consecutive small changes are required: a single one can be a pause of
+// the iteration rather than convergence.  Runs right after the Rayleigh-Ritz
+// step of the check (same gate); when it ends the iteration the remaining
+// kernels of the iteration return at once, so the point is the one whose
+// values passed the check and the final refinement reproduces them.
+__global__ void ritz_check_kernel(DevState* st, double* hist, int len, int k, double rtol, int every) {
+  if (threadIdx.x != 0 || st->done || st->force_zero_step || st->iter == 0 || st->iter % every != 0) return;
+  const int idx = st->iter / every - 1;
+  if (!st->rr_ok || idx >= len) return;
+  double worst = 0;
+  for (int i = 0; i < k; ++i) {
+    const double s = st->sigma[i];
+    hist[(int64_t)idx * k + i] = s;
+    if (idx > 0) worst = fmax(worst, fabs(s - hist[(int64_t)(idx - 1) * k + i]) / fmax(fabs(s), 1e-300));
+  }
+  st->ritz_checks = idx + 1;
+  const bool small = idx > 0 && hist[(int64_t)(idx - 1) * k] != 0.0 && worst < rtol;
+  st->ritz_small = small ? st->ritz_small + 1 : 0;
+  if (st->ritz_small >= 2) st->done = 1;
 }
 
 // out_v (d x k) = Phi_v[:, :m] rot_v (m = the Rayleigh-Ritz subspace used),
@@ -1360,6 +1423,31 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
   GB_TRY(prc);
   GB_TRY(phigram(p, st, done, p.phired));
   GB_TRY(yphi(p, st, 1));
+  if (p.opt.rtol > 0) {
+    // convergence check on the Rayleigh-Ritz values of span([U, eta]) at this
+    // point (every check_every iterations; the kernels return otherwise)
+    RRArgs a{};
+    a.st = p.st;
+    a.Gram = p.Gram;
+    a.gnc = p.NC;
+    a.offx = 0;
+    a.offy = 2 * k;
+    a.phipart = p.phired;
+    a.nblk = 1;
+    a.k = k;
+    a.kind = p.kind;
+    a.l = p.l;
+    a.YPhi = p.YPhi;
+    a.m0 = 2 * k;
+    a.check = 1;
+    a.every = std::max(1, p.opt.check_every);
+    const size_t smem = sizeof(double) * (8 * a.m0 * a.m0 + 2 * kMaxK + 100 + 8 * k * k);
+    GB_CUDA(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rr_kernel<<<1, 256, smem, st>>>(a);
+    GB_CHECK_LAUNCH();
+    ritz_check_kernel<<<1, 32, 0, st>>>(p.st, p.ritz_hist, p.ritz_len, k, p.opt.rtol, a.every);
+    GB_CHECK_LAUNCH();
+  }
   {
     LSArgs a{};
     a.st = p.st;
@@ -1545,6 +1633,9 @@ __global__ void state_init_kernel(DevState* st, double gtol, int max_iter, doubl
   st->gtol = gtol;
   st->max_iter = max_iter;
   st->qsyl_valid = 0;
+  st->rr_ok = 0;
+  st->ritz_checks = 0;
+  st->ritz_small = 0;
   st->dcount = 0;
   st->ls_count = 0;
   st->lam[0] = lam0;
@@ -1582,6 +1673,7 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     GB_CHECK_LAUNCH();
   }
   GB_CUDA(cudaMemsetAsync(p.history, 0, sizeof(double) * 3 * (p.opt.max_iter + 1), st));
+  GB_CUDA(cudaMemsetAsync(p.ritz_hist, 0, sizeof(double) * p.ritz_len * k, st));
   // qf_B of the start (zero step), then iterations in batches.  With pass
   // timing, event pair b brackets the pass of global iteration index
   // first_index + b (index 0 = the qf_B pass); only passes whose iteration
