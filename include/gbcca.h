@@ -86,9 +86,10 @@ typedef struct {
   int32_t graphs;        /* 1: each batch of check_every iterations is replayed
                             from a CUDA graph that the plan captures on its own
                             stream at the first solve (re-captured when the
-                            data pointers change); 0, or time_passes = 1: the
-                            kernels are launched one by one.  Both run the
-                            same kernels in the same order.                     */
+                            data pointers change; with time_passes the timing
+                            events are recorded by the graph); 0: the kernels
+                            are launched one by one.  Both run the same
+                            kernels in the same order.                          */
   double rtol;           /* stop when the Rayleigh-Ritz values of the subspace
                             span([U, eta]) x span([V, eta_V]) (the values the
                             final refinement reports) change by less than rtol,
@@ -161,8 +162,10 @@ int cca_precondition(gbcca_plan_t plan, const void* X, int64_t ldx, const void* 
 
 /* Alg. 1 step 8: Riemannian CG for max tr(U^T Sxy V N) on
  * St_Sxx(k, dx) x St_Syy(k, dy) with the metric of M (Sec. 4.2-4.4).
- * mu (host, k entries, strictly decreasing, > 0; NULL = k, k-1, ..., 1) is
- * the diagonal of N.  tol overrides opt.gtol when > 0.  U (dx x k), V (dy x k)
+ * mu (host, k entries, strictly decreasing, > 0; NULL = 1 + (k - 1 - i) / 100
+ * for i = 0 .. k - 1) is the diagonal of N; the solution does not depend on
+ * N (Thm 4.1), its conditioning does (Thm 4.4): near-equal weights converge
+ * the subspace fastest and the final Rayleigh-Ritz step separates the pairs.  tol overrides opt.gtol when > 0.  U (dx x k), V (dy x k)
  * and sigma (k) are device buffers (float64, caller-owned); with
  * opt.warm_start = 0, U and V also provide the starting point.  On return
  * sigma holds the canonical correlations sigma_1 >= ... >= sigma_k and U, V

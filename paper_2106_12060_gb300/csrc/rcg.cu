@@ -1243,7 +1243,8 @@ __global__ void rr_kernel(RRArgs a) {
     float* lamf = reinterpret_cast<float*>(Q);
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Af[e] = (float)T1[e];
     __syncthreads();
-    blk_jacobi<float>(Af, Qf, lamf, m, rot);
+    if (threadIdx.x < 32) warp_jacobi<float>(Af, Qf, lamf, m);  // warp-level barriers only
+    __syncthreads();
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
       double num = 0, den = 0;
       for (int r = 0; r < m; ++r) {
@@ -1573,8 +1574,9 @@ int run_batch_direct(Plan& p, bool low, int nb, bool timed, cudaStream_t st) {
 // labels; the TMA descriptors are captured by value) and the batch shape; it
 // is captured again when any of those differ.  Every kernel reads its
 // per-iteration state (step, direction, convergence flag) from device memory,
-// so one capture serves every batch of every solve.  Pass timing records
-// events around single kernels, so timed batches are launched directly.
+// so one capture serves every batch of every solve.  With pass timing the
+// events around the data kernels are captured as external event-record nodes,
+// recorded again at every replay.
 int run_batch_graph(Plan& p, bool low, int nb, bool timed, cudaStream_t st) {
   const void* key[3] = {p.v[0].Z, p.nviews > 1 ? (const void*)p.v[1].Z : nullptr, (const void*)p.labels};
   const bool same = p.batch_exec != nullptr && p.batch_key_n == nb && p.batch_key_timed == timed &&
@@ -1663,7 +1665,12 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   state_init_kernel<<<1, 1, 0, st>>>(p.st, gtol, p.opt.max_iter, p.v[0].lam, p.nviews > 1 ? p.v[1].lam : 0.0);
   GB_CHECK_LAUNCH();
   double muh[kMaxK];
-  for (int i = 0; i < k; ++i) muh[i] = mu ? mu[i] : (double)(k - i);
+  // default weights N = diag(1 + (k - 1 - i) / 100): the solution does not
+  // depend on N (Thm 4.1) but the conditioning does (Thm 4.4); near-equal
+  // weights make the iteration converge the subspace at the rate of the gap
+  // sigma_k - sigma_{k+1}, and the final Rayleigh-Ritz step separates the
+  // pairs inside it
+  for (int i = 0; i < k; ++i) muh[i] = mu ? mu[i] : 1.0 + 0.01 * (double)(k - 1 - i);
   GB_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(p.st) + offsetof(DevState, mu), muh, sizeof(double) * k,
                           cudaMemcpyHostToDevice, st));
   for (int v = 0; v < p.nviews; ++v) {
@@ -1723,8 +1730,8 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     const int nb = std::min(batch, p.opt.max_iter - launched);
     // full batches replay a captured graph; a shorter last batch is launched
     // kernel by kernel (same kernels, same order)
-    if (p.opt.graphs && !timed && nb == batch)
-      GB_TRY(run_batch_graph(p, low, nb, false, st));
+    if (p.opt.graphs && nb == batch)
+      GB_TRY(run_batch_graph(p, low, nb, timed, st));
     else
       GB_TRY(run_batch_direct(p, low, nb, timed, st));
     launched += nb;

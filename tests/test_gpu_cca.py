@@ -158,7 +158,8 @@ def test_trajectory_matches_reference_rcg(gb):
                        g=torch.from_numpy(g).cuda(), warm_start=0, max_iter=iters, gtol=0.0)
     rng = np.random.default_rng(1)
     U0, V0 = rng.standard_normal((dx, k)), rng.standard_normal((dy, k))
-    gb.cca_solve(plan, U=torch.from_numpy(U0.copy()).cuda(), V=torch.from_numpy(V0.copy()).cuda())
+    gb.cca_solve(plan, mu=list(OC.default_mu(k)), U=torch.from_numpy(U0.copy()).cuda(),
+                 V=torch.from_numpy(V0.copy()).cuda())
     hist = np64(gb.query(plan, gb.Q_HISTORY)).reshape(-1, 3)[: iters + 1]
     SX, SY = countsketch_apply(P["X64"], h, g, s), countsketch_apply(P["Y64"], h, g, s)
     Rx, Ry = precond_R(SX, lam), precond_R(SY, lam)
