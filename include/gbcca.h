@@ -74,8 +74,12 @@ typedef struct {
   uint64_t seed;         /* seed of the library's own sketch draws              */
   int32_t max_iter;      /* Riemannian CG iteration cap (default 1000)          */
   double gtol;           /* stop when ||grad||_M <= gtol ||grad_0||_M (1e-8)    */
-  int32_t refine;        /* BF16/FP32 data: FP64 Rayleigh-Ritz refinement at the
-                            end (1, default) or none (0); ignored for FP64 data */
+  int32_t refine;        /* final Rayleigh-Ritz step of BF16/FP32 plans: 1
+                            (default) over span(U) with Grams from an FP64
+                            pass (exact products of the stored data), 2 over
+                            span([U, eta]) with the Grams of the plan's own
+                            pass.  FP64 plans always use span([U, eta]) with
+                            their exact FP64 pass.                           */
   int32_t warm_start;    /* 1: start from the exact solution of the sketched
                             problem (Alg. 1 step 4 / Alg. 2 step 5); 0: start
                             from the U/V (W) buffers passed to the solve call  */

@@ -49,6 +49,17 @@ struct Status {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Records a timing event on `st`; while `st` is being captured into a CUDA
+// graph the record becomes an event-record node of the graph (recorded at
+// every replay).
+inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, st);
+}
+
 // Codes the kernels write into a plan's device error flag (0 = no error).
 constexpr int kFlagNotSpd = 1;    // a Cholesky pivot was not positive / empty class
 constexpr int kFlagDraw = 2;      // SRHT row draw left [0, n_pad)

@@ -568,9 +568,9 @@ int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols,
     if (p.tc_img != nullptr && tc_pass_eligible(p)) return tc_pass(p, st, done);
     if (split_pass_ready(p)) return split_pass(p, st, done);
   }
-  if (p.kev0 != nullptr) GB_CUDA(cudaEventRecordWithFlags(p.kev0, st, cudaEventRecordExternal));
+  if (p.kev0 != nullptr) GB_CUDA(record_timing_event(p.kev0, st));
   const int rc = fused_pass_cores(p, low, gram_only, st, phi_cols, done);
-  if (rc == GBCCA_OK && p.kev1 != nullptr) GB_CUDA(cudaEventRecordWithFlags(p.kev1, st, cudaEventRecordExternal));
+  if (rc == GBCCA_OK && p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
   return rc;
 }
 

@@ -654,10 +654,10 @@ int split_pass(Plan& p, cudaStream_t st, const int* done) {
   const int ncl = std::min(p.ts_clusters, a.ntiles);
   cfg.gridDim = dim3(2 * ncl, 1, 1);
   const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(p.ts_map[0]);
-  if (p.kev0 != nullptr) GB_CUDA(cudaEventRecordWithFlags(p.kev0, st, cudaEventRecordExternal));
+  if (p.kev0 != nullptr) GB_CUDA(record_timing_event(p.kev0, st));
   GB_CUDA(cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], a));
   GB_CHECK_LAUNCH();
-  if (p.kev1 != nullptr) GB_CUDA(cudaEventRecordWithFlags(p.kev1, st, cudaEventRecordExternal));
+  if (p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
   const int nparts = lda ? 2 * ncl : ncl;
   const int64_t len = (int64_t)p.D * p.NC;
   tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.ts_part, nparts, len, a.slab, p.G, done);

@@ -630,10 +630,10 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   cfg.gridDim = dim3(2 * ncl, 1, 1);
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(p.tc_map[0]);
   const CUtensorMap* my = reinterpret_cast<const CUtensorMap*>(p.tc_map[1]);
-  if (p.kev0 != nullptr) GB_CUDA(cudaEventRecordWithFlags(p.kev0, st, cudaEventRecordExternal));
+  if (p.kev0 != nullptr) GB_CUDA(record_timing_event(p.kev0, st));
   GB_CUDA(cudaLaunchKernelEx(&cfg, kern, *mx, *my, a));
   GB_CHECK_LAUNCH();
-  if (p.kev1 != nullptr) GB_CUDA(cudaEventRecordWithFlags(p.kev1, st, cudaEventRecordExternal));
+  if (p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
   const int grid = ncl;  // partial slabs, one per cluster
   const int64_t len = (int64_t)p.D * k4;
   tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, len, p.G, done);

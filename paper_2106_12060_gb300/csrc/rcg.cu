@@ -1234,33 +1234,6 @@ __global__ void rr_kernel(RRArgs a) {
     }
     __syncthreads();
   }
-  if (a.check) {
-    // a convergence check needs the values only: FP32 Jacobi for the
-    // vectors, then FP64 Rayleigh quotients with them, whose error is second
-    // order in the vectors' (the values to ~1e-13 at FP32 vector accuracy)
-    float* Af = reinterpret_cast<float*>(T2);
-    float* Qf = Af + m * m;
-    float* lamf = reinterpret_cast<float*>(Q);
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Af[e] = (float)T1[e];
-    __syncthreads();
-    if (threadIdx.x < 32) warp_jacobi<float>(Af, Qf, lamf, m);  // warp-level barriers only
-    __syncthreads();
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-      double num = 0, den = 0;
-      for (int r = 0; r < m; ++r) {
-        const double qr = (double)Qf[r * m + i];
-        double t = 0;
-        for (int c = 0; c < m; ++c) t += T1[r * m + c] * (double)Qf[c * m + i];
-        num += qr * t;
-        den += qr * qr;
-      }
-      const double rq = den > 0 ? num / den : 0.0;
-      st->sigma[i] = a.kind == kCCA ? sqrt(fmax(rq, 0.0)) : rq;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) st->rr_ok = 1;
-    return;
-  }
   blk_jacobi(T1, Q, lam, m, rot);                    // right singular vectors (CCA) / eigvecs (FDA), descending
   // the leading k: CCA sigma_i = ||C q_i||, left vectors a_i = C q_i / sigma_i
   if (a.kind == kCCA) {
@@ -1294,6 +1267,133 @@ __global__ void rr_kernel(RRArgs a) {
 // receives the values the last Rayleigh-Ritz step left in st->sigma; when
 // every value changed by less than rtol (relative) since the previous check,
 // the iteration ends (st->done) with status OK.
+// Ritz values for the convergence check (option rtol), by one warp: the
+// Rayleigh-Ritz problem of span([U, eta]) x span([V, eta_V]) (CCA; FDA:
+// span([W, eta])) from the pass Grams of the current point.  Cholesky of the
+// two m x m Grams (pivots by Newton reciprocal square roots), two triangular
+// solves for the whitened cross matrix Z = L_x^{-1} C L_y^{-T}, T = Z^T Z (FDA:
+// the symmetric Z itself), FP32 Jacobi vectors of T and FP64 Rayleigh
+// quotients with them (second-order accurate in the vectors).  Writes
+// st->sigma[0 .. k) and st->rr_ok; gated like the check.
+inline size_t ritz_values_smem(int k) {
+  const size_t m = 2 * (size_t)k;
+  return sizeof(double) * (4 * m * m + 2 * m) + sizeof(float) * (2 * m * m + m);
+}
+
+struct RitzArgs {
+  DevState* st;
+  const double* Gram;     // pass Gram, row stride gnc
+  int gnc, offx, offy;
+  const double* phig;     // [view][2k x 2k] Gram of Phi (summed)
+  const double* YPhi;     // FDA (l x 2k)
+  int k, kind, l, every;
+};
+
+__global__ void __launch_bounds__(32) ritz_values_kernel(RitzArgs a) {
+  DevState* st = a.st;
+  if (st->done || st->force_zero_step || st->iter == 0 || st->iter % a.every != 0) return;
+  const int lane = threadIdx.x, k = a.k, m = 2 * k, k2 = 2 * k;
+  extern __shared__ double rz[];  // ritz_values_smem(k) bytes
+  double* Lx = rz;
+  double* Ly = Lx + m * m;
+  double* Cm = Ly + m * m;
+  double* T = Cm + m * m;
+  double* ix = T + m * m;
+  double* iy = ix + m;
+  float* Tf = reinterpret_cast<float*>(iy + m);
+  float* Qf = Tf + m * m;
+  float* lf = Qf + m * m;
+  const bool cca = a.kind == kCCA;
+  for (int e = lane; e < m * m; e += 32) {
+    const int i = e / m, j = e - i * m;
+    Lx[e] = a.Gram[(a.offx + i) * a.gnc + a.offx + j] + st->lam[0] * a.phig[i * k2 + j];
+    if (cca) {
+      Ly[e] = a.Gram[(a.offy + i) * a.gnc + a.offy + j] + st->lam[1] * a.phig[k2 * k2 + i * k2 + j];
+      Cm[e] = a.Gram[(a.offx + i) * a.gnc + a.offy + j];
+    } else {
+      double sb = 0;
+      for (int c = 0; c < a.l; ++c) sb += a.YPhi[c * k2 + i] * a.YPhi[c * k2 + j];
+      Cm[e] = sb;
+    }
+  }
+  __syncwarp();
+  // Cholesky (lower), right-looking; the reciprocals of the pivots kept
+  bool ok = true;
+  for (int v = 0; v < (cca ? 2 : 1); ++v) {
+    double* A = v == 0 ? Lx : Ly;
+    double* inv = v == 0 ? ix : iy;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[j * m + j];
+      if (!(dj > 0.0)) ok = false;
+      const double r = dj > 0.0 ? rsqrt_nr(dj) : 0.0;
+      __syncwarp();
+      for (int i = j + lane; i < m; i += 32) A[i * m + j] *= r;  // L_jj = d r, L_ij = a_ij r
+      if (lane == 0) inv[j] = r;  // 1 / L_jj
+      __syncwarp();
+      for (int e = lane; e < (m - j - 1) * (m - j - 1); e += 32) {
+        const int i = j + 1 + e / (m - j - 1), c = j + 1 + e % (m - j - 1);
+        if (c <= i) A[i * m + c] -= A[i * m + j] * A[c * m + j];
+      }
+      __syncwarp();
+    }
+  }
+  if (!cca) {
+    for (int e = lane; e < m * m; e += 32) Ly[e] = Lx[e];
+    for (int j = lane; j < m; j += 32) iy[j] = ix[j];
+    __syncwarp();
+  }
+  if (!ok) {
+    if (lane == 0) st->rr_ok = 0;
+    return;
+  }
+  // X = L_x^{-1} C (column c of C per lane), into Cm
+  for (int c = lane; c < m; c += 32)
+    for (int i = 0; i < m; ++i) {
+      double s = Cm[i * m + c];
+      for (int q = 0; q < i; ++q) s -= Lx[i * m + q] * Cm[q * m + c];
+      Cm[i * m + c] = s * ix[i];
+    }
+  __syncwarp();
+  // Z = X L_y^{-T}: row r of X per lane (solve L_y z = x_r^T), into Cm
+  for (int r = lane; r < m; r += 32)
+    for (int i = 0; i < m; ++i) {
+      double s = Cm[r * m + i];
+      for (int q = 0; q < i; ++q) s -= Ly[i * m + q] * Cm[r * m + q];
+      Cm[r * m + i] = s * iy[i];
+    }
+  __syncwarp();
+  // T = Z^T Z (CCA: squared singular values) or the symmetric part of Z (FDA)
+  for (int e = lane; e < m * m; e += 32) {
+    const int i = e / m, j = e - i * m;
+    double t;
+    if (cca) {
+      t = 0;
+      for (int r = 0; r < m; ++r) t += Cm[r * m + i] * Cm[r * m + j];
+    } else {
+      t = 0.5 * (Cm[i * m + j] + Cm[j * m + i]);
+    }
+    T[e] = t;
+    Tf[e] = (float)t;
+  }
+  __syncwarp();
+  warp_jacobi<float>(Tf, Qf, lf, m);
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) {
+    double num = 0, den = 0;
+    for (int r = 0; r < m; ++r) {
+      const double qr = (double)Qf[r * m + i];
+      double t = 0;
+      for (int c = 0; c < m; ++c) t += T[r * m + c] * (double)Qf[c * m + i];
+      num += qr * t;
+      den += qr * qr;
+    }
+    const double rq = den > 0 ? num / den : 0.0;
+    st->sigma[i] = cca ? sqrt(fmax(rq, 0.0)) : rq;
+  }
+  __syncwarp();
+  if (lane == 0) st->rr_ok = 1;
+}
+
 // Two consecutive small changes are required: a single one can be a pause of
 // the iteration rather than convergence.  Runs right after the Rayleigh-Ritz
 // step of the check (same gate); when it ends the iteration the remaining
@@ -1427,24 +1527,21 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
   if (p.opt.rtol > 0) {
     // convergence check on the Rayleigh-Ritz values of span([U, eta]) at this
     // point (every check_every iterations; the kernels return otherwise)
-    RRArgs a{};
+    RitzArgs a{};
     a.st = p.st;
     a.Gram = p.Gram;
     a.gnc = p.NC;
     a.offx = 0;
     a.offy = 2 * k;
-    a.phipart = p.phired;
-    a.nblk = 1;
+    a.phig = p.phired;
+    a.YPhi = p.YPhi;
     a.k = k;
     a.kind = p.kind;
     a.l = p.l;
-    a.YPhi = p.YPhi;
-    a.m0 = 2 * k;
-    a.check = 1;
     a.every = std::max(1, p.opt.check_every);
-    const size_t smem = sizeof(double) * (8 * a.m0 * a.m0 + 2 * kMaxK + 100 + 8 * k * k);
-    GB_CUDA(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    rr_kernel<<<1, 256, smem, st>>>(a);
+    const size_t smem = ritz_values_smem(k);
+    GB_CUDA(cudaFuncSetAttribute(ritz_values_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ritz_values_kernel<<<1, 32, smem, st>>>(a);
     GB_CHECK_LAUNCH();
     ritz_check_kernel<<<1, 32, 0, st>>>(p.st, p.ritz_hist, p.ritz_len, k, p.opt.rtol, a.every);
     GB_CHECK_LAUNCH();
@@ -1739,14 +1836,16 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   }
   const DevState& hs = *p.st_host;
   passes += hs.iter;
-  // Rayleigh-Ritz at the final point.  refine = 1: Grams of [X U, Y V] from
-  // an FP64 pass (exact products of the stored data); refine = 2: Grams from
-  // the plan's own pass (FP32 accumulation for BF16/FP32 data).
-  const bool exact_refine = p.opt.refine != 2 || !low;
+  // Rayleigh-Ritz at the final point.  FP64 data: over span([U, eta]) with
+  // the Grams of the plan's FP64 pass (exact products).  BF16/FP32 data,
+  // refine = 1: over span(U) with the Grams of [X U, Y V] from an FP64 pass
+  // (exact products of the stored data); refine = 2: over span([U, eta]) with
+  // the Grams of the plan's own pass (FP32 accumulation).
+  const bool exact_refine = low && p.opt.refine != 2;
   if (exact_refine) {
     GB_TRY(fused_pass(p, false, true, st, k, nullptr));
   } else {
-    GB_TRY(fused_pass(p, true, false, st, 0, nullptr));
+    GB_TRY(fused_pass(p, low, false, st, 0, nullptr));
   }
   GB_TRY(phigram(p, st, nullptr));
   GB_TRY(yphi(p, st, 0));

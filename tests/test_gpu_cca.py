@@ -239,3 +239,28 @@ def test_graph_replay_matches_direct_launches(gb, dt):
     assert a[3] == b[3] and a[3] > 8, (a[3], b[3])
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     assert a[4] == b[4], (a[4], b[4])
+
+
+@pytest.mark.parametrize("dt", ["f64", "bf16"])
+def test_ritz_stopping_rule(gb, dt):
+    """Option rtol: the Ritz values of span([U, eta]) are recorded at every
+    check (GBCCA_Q_RITZ), the last two recorded changes are below rtol, the
+    solve ends with status OK before max_iter, and the returned correlations
+    (the final refinement at the point of the last check) equal the last
+    recorded values and the oracle's."""
+    n, dx, dy, k, lam = 20000, 96, 72, 5, 1e-3
+    P = cca_latent_problem(n, dx, dy, latent=8, noise=0.5, dtype=dt, seed=41,
+                           latent_scale=[1.0, 0.8, 0.6, 0.45, 0.3, 0.2, 0.12, 0.07])
+    rtol = 1e-9 if dt == "f64" else 1e-7
+    plan, _, _ = _plan(gb, P, n, dx, dy, k, dt, lam, max_iter=600, gtol=0.0, rtol=rtol, check_every=4, refine=2)
+    sig, U, V, info = gb.cca_solve(plan)
+    assert info["status"] == gb.OK and info["iters"] < 600, info
+    R = np64(gb.query(plan, gb.Q_RITZ)).reshape(-1, k)
+    R = R[np.any(R != 0, axis=1)]
+    assert R.shape[0] >= 3
+    chg = np.max(np.abs(np.diff(R, axis=0)) / R[1:], axis=1)
+    assert chg[-1] < rtol and chg[-2] < rtol, chg[-3:]
+    s = np64(sig)
+    assert np.max(np.abs(s - R[-1]) / s) < 1e-8, (s, R[-1])  # FP64 vs FP32-vector Rayleigh quotients
+    ref, _, _ = OC.cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    assert rel(s, ref) < (1e-9 if dt == "f64" else 1e-6), (s, ref, info)
