@@ -30,6 +30,7 @@ class Options(C.Structure):
         ("graphs", C.c_int32),
         ("rtol", C.c_double),
         ("tensor_cores", C.c_int32),
+        ("warm_iters", C.c_int32),
         ("wait_cycles", C.c_int64),
     ]
 

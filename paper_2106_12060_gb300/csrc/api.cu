@@ -201,7 +201,8 @@ int alloc_plan(Plan* p) {
 
 int check_options(const gbcca_options& o) {
   if (o.sketch < 0 || o.sketch > 3) return GBCCA_ERR_INVALID_ARG;
-  if (o.max_iter < 1 || o.s < 0 || !(o.gtol >= 0) || o.check_every < 1 || o.wait_cycles < 0 || !(o.rtol >= 0))
+  if (o.max_iter < 1 || o.s < 0 || !(o.gtol >= 0) || o.check_every < 1 || o.wait_cycles < 0 || !(o.rtol >= 0) ||
+      o.warm_iters < 0)
     return GBCCA_ERR_INVALID_ARG;
   return GBCCA_OK;
 }

@@ -59,6 +59,21 @@ gram_tn_kernel(const double* __restrict__ A, int64_t lda, const double* __restri
     }
 }
 
+// C (d x d) from the split-K partials of a symmetric Gram whose tiles were
+// formed on and below the diagonal only: the upper tiles mirror the lower.
+__global__ void sum_parts_sym_kernel(const double* __restrict__ part, int nparts, int d, double diag_add,
+                                     double* __restrict__ C) {
+  const int64_t len = (int64_t)d * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d), j = (int)(e % d);
+    const int64_t src = (i / kGT >= j / kGT) ? e : (int64_t)j * d + i;
+    double s = 0;
+    for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * len + src];
+    if (i == j) s += diag_add;
+    C[e] = s;
+  }
+}
+
 __global__ void sum_parts_kernel(const double* __restrict__ part, int nparts, int64_t len, int d1, int d2,
                                  double diag_add, double* __restrict__ C) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
@@ -92,10 +107,22 @@ __device__ __forceinline__ void df_acc(float& S, float& Cc, float ah, float al, 
 __global__ void __launch_bounds__(256)
 gram_dfs_kernel(const float* __restrict__ Ahg, const float* __restrict__ Alg, int64_t lda, const float* __restrict__ Bhg,
                 const float* __restrict__ Blg, int64_t ldb, int64_t m, int d1, int d2, int64_t kchunk,
-                double* __restrict__ part, int tri) {
+                double* __restrict__ part, int tri, int sym) {
   __shared__ float Ah[kGK][kGT], Al[kGK][kGT], Bh[kGK][kGT], Bl[kGK][kGT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  int i0, j0;
+  if (sym) {
+    // A == B: only the tiles on and below the diagonal, blockIdx.x = ti (ti + 1) / 2 + tj
+    const int t = blockIdx.x;
+    int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    i0 = ti * kGT;
+    j0 = (t - ti * (ti + 1) / 2) * kGT;
+  } else {
+    i0 = blockIdx.y * kGT;
+    j0 = blockIdx.x * kGT;
+  }
   const int64_t k1 = min(m, (int64_t)blockIdx.z * kchunk + kchunk);
   const int64_t k0 = tri ? max((int64_t)blockIdx.z * kchunk, (int64_t)max(i0, j0)) : (int64_t)blockIdx.z * kchunk;
   float S[4][4] = {}, Cc[4][4] = {};
@@ -149,7 +176,11 @@ gram_dfs_kernel(const float* __restrict__ Ahg, const float* __restrict__ Alg, in
 int gram_df_split(const float* Ah, const float* Al, int64_t lda, const float* Bh, const float* Bl, int64_t ldb,
                   int64_t m, int d1, int d2, double* C, double diag_add, double* ws, int64_t ws_len, cudaStream_t st,
                   bool tri) {
-  const int tiles = ceil_div(d1, kGT) * ceil_div(d2, kGT);
+  // the same operand on both sides: a symmetric result, formed from the
+  // tiles on and below the diagonal only
+  const bool sym = Ah == Bh && Al == Bl && lda == ldb && d1 == d2;
+  const int td = ceil_div(d1, kGT);
+  const int tiles = sym ? td * (td + 1) / 2 : ceil_div(d1, kGT) * ceil_div(d2, kGT);
   int ks = std::max(1, std::min<int>(ceil_div(tri ? 2 * 304 : 304, tiles), ceil_div(m, 64)));
   const int64_t len = (int64_t)d1 * d2;
   while (ks > 1 && (int64_t)ks * len > ws_len) --ks;
@@ -158,10 +189,13 @@ int gram_df_split(const float* Ah, const float* Al, int64_t lda, const float* Bh
     return GBCCA_ERR_INVALID_ARG;
   }
   const int64_t kchunk = (m + ks - 1) / ks;
-  dim3 grid(ceil_div(d2, kGT), ceil_div(d1, kGT), ks);
-  gram_dfs_kernel<<<grid, 256, 0, st>>>(Ah, Al, lda, Bh, Bl, ldb, m, d1, d2, kchunk, ws, tri ? 1 : 0);
+  dim3 grid = sym ? dim3(tiles, 1, ks) : dim3(ceil_div(d2, kGT), ceil_div(d1, kGT), ks);
+  gram_dfs_kernel<<<grid, 256, 0, st>>>(Ah, Al, lda, Bh, Bl, ldb, m, d1, d2, kchunk, ws, tri ? 1 : 0, sym ? 1 : 0);
   GB_CHECK_LAUNCH();
-  sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
+  if (sym)
+    sum_parts_sym_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, d1, diag_add, C);
+  else
+    sum_parts_kernel<<<ceil_div(len, 256), 256, 0, st>>>(ws, ks, len, d1, d2, diag_add, C);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -164,14 +164,15 @@ __device__ void blk_jacobi(R* A, R* Q, R* lam, int n, double* rot) {
 // time in block-wide barriers for matrices this small).  Called by all 32
 // lanes of one warp.
 template <typename R>
-__device__ void warp_jacobi(R* A, R* Q, R* lam, int n) {
+__device__ void warp_jacobi(R* A, R* Q, R* lam, int n, int max_sweeps = 20, R tol = R(0)) {
+  if (!(tol > R(0))) tol = R(sizeof(R) == 8 ? 1e-26 : 1e-12);
   const int lane = threadIdx.x & 31;
   __shared__ R w_cs[16], w_sn[16];
   __shared__ int w_p[16], w_q[16];
   for (int e = lane; e < n * n; e += 32) Q[e] = (e / n == e % n) ? R(1) : R(0);
   __syncwarp();
   const int m = n + (n & 1);
-  for (int sweep = 0; sweep < 20 && n > 1; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
     R off = 0, dg = 0;
     for (int e = lane; e < n * n; e += 32) {
       const R v = A[e] * A[e];
@@ -180,7 +181,7 @@ __device__ void warp_jacobi(R* A, R* Q, R* lam, int n) {
     }
     off = warp_sum(off);
     dg = warp_sum(dg);
-    if (off <= R(sizeof(R) == 8 ? 1e-26 : 1e-12) * dg || off == R(0)) break;
+    if (off <= tol * dg || off == R(0)) break;
     for (int r = 0; r < m - 1; ++r) {
       if (lane < m / 2) {
         const int i = lane;
@@ -1376,7 +1377,9 @@ __global__ void __launch_bounds__(32) ritz_values_kernel(RitzArgs a) {
     Tf[e] = (float)t;
   }
   __syncwarp();
-  warp_jacobi<float>(Tf, Qf, lf, m);
+  // FP32 vectors good to ~1e-3 within the clusters of values suffice: the
+  // Rayleigh quotients below are second order in their error
+  warp_jacobi<float>(Tf, Qf, lf, m, 8, 1e-10f);
   __syncwarp();
   for (int i = lane; i < k; i += 32) {
     double num = 0, den = 0;
@@ -2117,7 +2120,7 @@ int warm_start(Plan& p, cudaStream_t st) {
     rand_block_kernel<<<ceil_div(dy * c, 256), 256, 0, st>>>(Vb, dy, c, p.opt.seed);
     GB_CHECK_LAUNCH();
     GB_TRY(orth(p, Vb, dy, c, part, small, st));
-    const int iters = 12;
+    const int iters = p.opt.warm_iters > 0 ? p.opt.warm_iters : 8;
     for (int it = 0; it <= iters; ++it) {
       // U = orth(R_x^{-T} Cxy R_y^{-1} V)
       GB_TRY(ry(false, Vb, y.wsT, c));
