@@ -388,8 +388,8 @@ def other_workloads(gb, steps: int = 2):
     c = P["config"]
     X = torch.from_numpy(np.ascontiguousarray(P["X"])).cuda()
     Y = torch.from_numpy(np.ascontiguousarray(P["Y"])).cuda()
-    opt = gb.default_options(sketch=gb.COUNTSKETCH, s=c["s"], seed=c["seed"], max_iter=6000, gtol=1e-10,
-                             check_every=64)
+    opt = gb.default_options(sketch=gb.COUNTSKETCH, s=c["s"], seed=c["seed"], max_iter=6000, gtol=0.0,
+                             rtol=1e-10, check_every=CHECK_EVERY)
     plan = gb.cca_plan(c["n"], c["dx"], c["dy"], c["k"], "f64", opt)
 
     def small_step():
@@ -412,15 +412,15 @@ def other_workloads(gb, steps: int = 2):
     hit = np.nonzero(gap <= 1e-10)[0]
     us_it = 1e3 * ms / max(it, 1.0)
     out["cca_small_fp64"] = {
-        "solve_ms": ms, "iterations": it, "us_per_iteration": us_it, "gtol": 1e-10,
+        "solve_ms": ms, "iterations": it, "us_per_iteration": us_it, "rtol": 1e-10,
         "status": gb.STATUS_NAMES.get(info["status"], info["status"]), "stalled": bool(info["stalled"]),
         "converged": info["status"] == gb.OK,
         "grad_ratio_final": info["grad_norm"] / info["grad_norm0"] if info["grad_norm0"] > 0 else None,
         "sigma_max_rel_err": float(np.max(np.abs(sig.cpu().numpy() - ref) / ref)),
         "iterations_to_1e-10_objective_gap": int(hit[0]) if hit.size else None,
         "time_to_1e-10_objective_gap_ms": float(hit[0] * us_it / 1e3) if hit.size else None,
-        "note": "gtol 1e-10 on the gradient norm is below the FP64 rounding floor of this problem; the run ends "
-                "at the iteration cap or when no step lowers f, so the time is time-to-cap"}
+        "note": "run to 1e-10: the Rayleigh-Ritz values of span([U, eta]) change by less than 1e-10 at two "
+                "consecutive checks 8 iterations apart"}
     plan.close()
     return out
 

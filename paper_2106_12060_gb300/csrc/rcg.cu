@@ -1268,6 +1268,70 @@ __global__ void rr_kernel(RRArgs a) {
 // receives the values the last Rayleigh-Ritz step left in st->sigma; when
 // every value changed by less than rtol (relative) since the previous check,
 // the iteration ends (st->done) with status OK.
+// One-sided (Hestenes) Jacobi SVD of an m x m matrix (m <= 32) by one warp in
+// FP32 registers: lane c holds column c of A and of V; the tournament order
+// pairs every two columns once per sweep, a pair exchanging its columns by
+// shuffles and both lanes computing the same rotation.  On return lane c has
+// A[:, c] = sigma_c u_c and V[:, c] = v_c with A_in V = U diag(sigma); for a
+// symmetric positive semi-definite input the sigma are its eigenvalues and V
+// its eigenvectors.  Column norms are not sorted.  tol: relative size of the
+// cosine between two columns below which a pair is left alone.
+template <int N>
+__device__ void warp_hestenes(float (&a)[N], float (&v)[N], int m, int max_sweeps, float tol) {
+  const int lane = threadIdx.x & 31;
+  const int mm = m + (m & 1);  // players of the tournament (a bye when m is odd)
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float worst = 0.f;
+    for (int r = 0; r < mm - 1; ++r) {
+      // partner of this lane in round r (circle method; player 0 fixed)
+      int partner = -1;
+      for (int i = 0; i < mm / 2; ++i) {
+        const int pa = (i == 0) ? 0 : 1 + ((i - 1 + r) % (mm - 1));
+        const int pb = 1 + ((mm - 2 - i + r) % (mm - 1));
+        if (pa == lane) partner = pb;
+        if (pb == lane) partner = pa;
+      }
+      const bool active = lane < m && partner >= 0 && partner < m;
+      const int src = active ? partner : lane;
+      float b[N], vb[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        b[q] = __shfl_sync(0xffffffffu, a[q], src);
+        vb[q] = __shfl_sync(0xffffffffu, v[q], src);
+      }
+      if (active) {
+        // the pair (p, q) with p < q: both lanes form alpha, beta, gamma in
+        // the same order, so they compute the same rotation
+        const bool lo = lane < partner;
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const float xp = lo ? a[q] : b[q], xq = lo ? b[q] : a[q];
+          al = fmaf(xp, xp, al);
+          be = fmaf(xq, xq, be);
+          ga = fmaf(xp, xq, ga);
+        }
+        const float den = sqrtf(al * be);
+        if (den > 0.f && fabsf(ga) > tol * den) {
+          worst = fmaxf(worst, fabsf(ga) / den);
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float c = rsqrtf(1.f + t * t), sn = c * t;
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            // column p <- c p - s q; column q <- s p + c q
+            a[q] = lo ? c * a[q] - sn * b[q] : sn * b[q] + c * a[q];
+            v[q] = lo ? c * v[q] - sn * vb[q] : sn * vb[q] + c * v[q];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if (worst <= tol) break;
+  }
+}
+
 // Ritz values for the convergence check (option rtol), by one warp: the
 // Rayleigh-Ritz problem of span([U, eta]) x span([V, eta_V]) (CCA; FDA:
 // span([W, eta])) from the pass Grams of the current point.  Cholesky of the
@@ -1293,6 +1357,7 @@ struct RitzArgs {
 __global__ void __launch_bounds__(32) ritz_values_kernel(RitzArgs a) {
   DevState* st = a.st;
   if (st->done || st->force_zero_step || st->iter == 0 || st->iter % a.every != 0) return;
+  constexpr int kM2 = 2 * kMaxK > 32 ? 32 : 2 * kMaxK;  // register columns (m <= 32 here)
   const int lane = threadIdx.x, k = a.k, m = 2 * k, k2 = 2 * k;
   extern __shared__ double rz[];  // ritz_values_smem(k) bytes
   double* Lx = rz;
@@ -1363,36 +1428,80 @@ __global__ void __launch_bounds__(32) ritz_values_kernel(RitzArgs a) {
       Cm[r * m + i] = s * iy[i];
     }
   __syncwarp();
-  // T = Z^T Z (CCA: squared singular values) or the symmetric part of Z (FDA)
-  for (int e = lane; e < m * m; e += 32) {
-    const int i = e / m, j = e - i * m;
-    double t;
-    if (cca) {
-      t = 0;
-      for (int r = 0; r < m; ++r) t += Cm[r * m + i] * Cm[r * m + j];
-    } else {
-      t = 0.5 * (Cm[i * m + j] + Cm[j * m + i]);
+  // FDA: the symmetric part of Z (its eigenvalues); CCA: Z (its singular
+  // values).  FP32 one-sided Jacobi for the vectors V (lane c: column c), then
+  // FP64 Rayleigh quotients ||Z v||^2 / ||v||^2 (CCA) or v^T Z v / v^T v (FDA)
+  if (!cca) {
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = e / m, j = e - i * m;
+      T[e] = 0.5 * (Cm[i * m + j] + Cm[j * m + i]);
     }
-    T[e] = t;
-    Tf[e] = (float)t;
+    __syncwarp();
   }
-  __syncwarp();
-  // FP32 vectors good to ~1e-3 within the clusters of values suffice: the
-  // Rayleigh quotients below are second order in their error
-  warp_jacobi<float>(Tf, Qf, lf, m, 8, 1e-10f);
-  __syncwarp();
-  for (int i = lane; i < k; i += 32) {
+  const double* Zs = cca ? Cm : T;
+  if (m > kM2) {
+    // wider than a warp (k > 16): two-sided FP32 Jacobi of Z^T Z (CCA) or
+    // of the symmetric part (FDA) in shared memory, FP64 Rayleigh quotients
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = e / m, j = e - i * m;
+      double t = 0;
+      if (cca) {
+        for (int r = 0; r < m; ++r) t += Cm[r * m + i] * Cm[r * m + j];
+        T[e] = t;
+      } else {
+        t = T[e];
+      }
+      Tf[e] = (float)t;
+    }
+    __syncwarp();
+    warp_jacobi<float>(Tf, Qf, lf, m, 8, 1e-10f);
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) {
+      double num = 0, den = 0;
+      for (int r = 0; r < m; ++r) {
+        const double qr = (double)Qf[r * m + i];
+        double t = 0;
+        for (int c = 0; c < m; ++c) t += T[r * m + c] * (double)Qf[c * m + i];
+        num += qr * t;
+        den += qr * qr;
+      }
+      const double rq = den > 0 ? num / den : 0.0;
+      st->sigma[i] = cca ? sqrt(fmax(rq, 0.0)) : rq;
+    }
+    __syncwarp();
+    if (lane == 0) st->rr_ok = 1;
+    return;
+  }
+  float av[kM2], vv[kM2];
+#pragma unroll
+  for (int q = 0; q < kM2; ++q) {
+    av[q] = (lane < m && q < m) ? (float)Zs[q * m + lane] : 0.f;
+    vv[q] = (q == lane) ? 1.f : 0.f;
+  }
+  warp_hestenes<kM2>(av, vv, m, 12, 1e-6f);
+  // one FP64 Rayleigh quotient per lane (column c of V)
+  double rq = -1.0;
+  if (lane < m) {
     double num = 0, den = 0;
     for (int r = 0; r < m; ++r) {
-      const double qr = (double)Qf[r * m + i];
-      double t = 0;
-      for (int c = 0; c < m; ++c) t += T[r * m + c] * (double)Qf[c * m + i];
-      num += qr * t;
-      den += qr * qr;
+      double zr = 0;
+#pragma unroll
+      for (int q = 0; q < kM2; ++q)
+        if (q < m) zr += Zs[r * m + q] * (double)vv[q];
+      num += cca ? zr * zr : (double)vv[r] * zr;
     }
-    const double rq = den > 0 ? num / den : 0.0;
-    st->sigma[i] = cca ? sqrt(fmax(rq, 0.0)) : rq;
+#pragma unroll
+    for (int q = 0; q < kM2; ++q)
+      if (q < m) den += (double)vv[q] * (double)vv[q];
+    rq = den > 0 ? num / den : 0.0;
   }
+  // the k largest, in descending order: rank of each lane's value
+  int rank = 0;
+  for (int j = 0; j < m; ++j) {
+    const double o = __shfl_sync(0xffffffffu, rq, j);
+    if (o > rq || (o == rq && j < lane)) ++rank;
+  }
+  if (lane < m && rank < k) st->sigma[rank] = cca ? sqrt(fmax(rq, 0.0)) : rq;
   __syncwarp();
   if (lane == 0) st->rr_ok = 1;
 }
@@ -2120,7 +2229,7 @@ int warm_start(Plan& p, cudaStream_t st) {
     rand_block_kernel<<<ceil_div(dy * c, 256), 256, 0, st>>>(Vb, dy, c, p.opt.seed);
     GB_CHECK_LAUNCH();
     GB_TRY(orth(p, Vb, dy, c, part, small, st));
-    const int iters = p.opt.warm_iters > 0 ? p.opt.warm_iters : 8;
+    const int iters = p.opt.warm_iters > 0 ? p.opt.warm_iters : 12;
     for (int it = 0; it <= iters; ++it) {
       // U = orth(R_x^{-T} Cxy R_y^{-1} V)
       GB_TRY(ry(false, Vb, y.wsT, c));
