@@ -336,8 +336,9 @@ def other_workloads(gb, steps: int = 2):
     out["cca_tall_f32"] = {"solve_ms": ms, "iterations": float(np.mean([i["iters"] for i in infos])),
                            "pass_ms": pass_ms, "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm,
                            "pass_algorithmic_bytes": n * (dx + dy) * 4, "status": infos[-1]["status"],
-                           "kernels": "split_pass_kernel (tcgen05 + TMA over the BF16 hi/lo copy of the FP32 "
-                                      "data, FP32 accumulate)"}
+                           "kernels": "tc_pass_kernel over the row-interleaved BF16 hi/lo copy of the FP32 "
+                                      "data (2n rows; the hi-row and lo-row products summed in the epilogue), "
+                                      "FP32 accumulate"}
     plan.close()
     del X, Y
     torch.cuda.empty_cache()

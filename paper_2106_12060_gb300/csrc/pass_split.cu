@@ -499,9 +499,12 @@ __global__ void split_phi_image_kernel(double* __restrict__ Phix, double* __rest
 }
 
 // The BF16 hi / lo copy of an FP32 view (FDA: of its class-centred rows).
+// Row i of the data goes to hi + i * hs and lo + i * hs (hs = row stride of
+// the copy): separate hi and lo matrices (lo = hi + n ldo, hs = ldo), or rows
+// interleaved (lo = hi + ldo, hs = 2 ldo: row 2i = hi, row 2i + 1 = lo).
 __global__ void split_copy_kernel(const float* __restrict__ Z, int64_t ld, int64_t n, int d,
                                   const int32_t* __restrict__ y, const double* __restrict__ means,
-                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t ldo) {
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int64_t hs) {
   const int64_t total = n * (int64_t)d;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / d;
@@ -509,8 +512,8 @@ __global__ void split_copy_kernel(const float* __restrict__ Z, int64_t ld, int64
     double v = (double)Z[i * ld + j];
     if (y != nullptr) v -= means[(int64_t)y[i] * d + j];
     const __nv_bfloat16 h = __double2bfloat16(v);
-    hi[i * ldo + j] = h;
-    lo[i * ldo + j] = __double2bfloat16(v - (double)__bfloat162float(h));
+    hi[i * hs + j] = h;
+    lo[i * hs + j] = __double2bfloat16(v - (double)__bfloat162float(h));
   }
 }
 
@@ -544,18 +547,42 @@ __global__ void tc_reduce_kernel(const float* __restrict__ part, int nparts, int
 }
 
 // ----------------------------------------------------------------- host side
+// FDA shapes of this kernel.  (CCA with FP32 data streams a row-interleaved
+// copy through the BF16 kernel of pass_tc.cu, which shares the copy.)
 bool split_pass_shape_ok(int kind, int dtype, int k, int d0, int d1) {
   if (dtype != GBCCA_FP32 || 2 * k > ts::kXC) return false;
-  if (kind == kCCA) return d0 <= 128 * ts::SLay<false>::kMaxPairs && d1 <= 128 * ts::SLay<false>::kMaxPairs;
+  if (kind == kCCA) return false;
+  (void)d1;
   return d0 <= 128 * ts::SLay<true>::kMaxPairs;
 }
 
-bool split_pass_ready(const Plan& p) { return p.ts_img != nullptr && p.ts_ready; }
+// CCA shapes of the interleaved copy for the BF16 kernel (2k <= 24, d <= 512)
+static bool interleaved_shape_ok(const Plan& p) {
+  return p.kind == kCCA && p.dtype == GBCCA_FP32 && 4 * p.k <= 48 && p.v[0].d <= 512 && p.v[1].d <= 512;
+}
+
+bool split_pass_ready(const Plan& p) { return p.ts_img != nullptr && p.ts_ready && !p.ts_interleaved; }
 
 int split_pass_alloc(Plan& p) {
   p.ts_ready = false;
-  if (!p.opt.tensor_cores || !split_pass_shape_ok(p.kind, p.dtype, p.k, p.v[0].d, p.nviews > 1 ? p.v[1].d : 0))
+  p.ts_interleaved = false;
+  if (!p.opt.tensor_cores) return GBCCA_OK;
+  if (interleaved_shape_ok(p)) {
+    for (int v = 0; v < 2; ++v) {
+      const int64_t ldo = (p.v[v].d + 7) / 8 * 8;
+      p.ts_ld[v] = ldo;
+      void* t = nullptr;
+      if (cudaMalloc(&t, sizeof(__nv_bfloat16) * (size_t)2 * p.n * ldo) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error("allocation of the BF16 hi/lo copy of the data failed");
+        return GBCCA_ERR_OOM;
+      }
+      p.ts_copy[v] = static_cast<__nv_bfloat16*>(t);
+    }
+    p.ts_interleaved = true;
     return GBCCA_OK;
+  }
+  if (!split_pass_shape_ok(p.kind, p.dtype, p.k, p.v[0].d, p.nviews > 1 ? p.v[1].d : 0)) return GBCCA_OK;
   for (int v = 0; v < p.nviews; ++v) {
     const int64_t ldo = (p.v[v].d + 7) / 8 * 8;
     p.ts_ld[v] = ldo;
@@ -581,21 +608,24 @@ int split_pass_alloc(Plan& p) {
 // rows, after the class statistics) and their TMA descriptors.
 int split_pass_prepare(Plan& p, cudaStream_t st) {
   p.ts_ready = false;
-  if (p.ts_img == nullptr || !p.opt.tensor_cores) return GBCCA_OK;
+  if (!p.opt.tensor_cores || p.ts_copy[0] == nullptr) return GBCCA_OK;
   for (int v = 0; v < p.nviews; ++v) {
     const int d = p.v[v].d;
     const int64_t ldo = p.ts_ld[v];
     __nv_bfloat16* hi = p.ts_copy[v];
-    __nv_bfloat16* lo = hi + p.n * ldo;
+    __nv_bfloat16* lo = p.ts_interleaved ? hi + ldo : hi + p.n * ldo;
+    const int64_t hs = p.ts_interleaved ? 2 * ldo : ldo;
     const int64_t total = p.n * (int64_t)d;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 8 * (int64_t)p.sm_count);
     ts::split_copy_kernel<<<grid, 256, 0, st>>>(static_cast<const float*>(p.v[v].Z), p.v[v].ld, p.n, d,
                                                 p.kind == kLDA ? p.labels : nullptr,
-                                                p.kind == kLDA ? p.means : nullptr, hi, lo, ldo);
+                                                p.kind == kLDA ? p.means : nullptr, hi, lo, hs);
     GB_CHECK_LAUNCH();
-    auto* m = reinterpret_cast<CUtensorMap*>(p.ts_map[2 * v]);
-    GB_TRY(make_tma_map_bf16(m, hi, p.n, d, ldo, ts::kRows));
-    GB_TRY(make_tma_map_bf16(m + 1, lo, p.n, d, ldo, ts::kRows));
+    if (!p.ts_interleaved) {
+      auto* m = reinterpret_cast<CUtensorMap*>(p.ts_map[2 * v]);
+      GB_TRY(make_tma_map_bf16(m, hi, p.n, d, ldo, ts::kRows));
+      GB_TRY(make_tma_map_bf16(m + 1, lo, p.n, d, ldo, ts::kRows));
+    }
   }
   p.ts_ready = true;
   return GBCCA_OK;

@@ -1,4 +1,6 @@
-// Tensor-core (tcgen05 + TMA) fused CCA data pass for BF16 data on sm_103a.
+// Tensor-core (tcgen05 + TMA) fused CCA data pass for BF16 data on sm_103a,
+// and for FP32 data streamed as a row-interleaved BF16 hi/lo copy (row 2i =
+// bf16(z_i), row 2i + 1 = bf16(z_i - bf16(z_i)); see `pair_sum`).
 //
 // One Riemannian-CG iteration of the CCA solver needs, for the block-diagonal
 // Phi = blkdiag([U, eta_U], [V, eta_V]) (Sec. 4.2 gradient, Table 1
@@ -115,6 +117,10 @@ struct Args {
   float* partG;            // [cluster][D][4k]
   int* err;
   const int* done;
+  int pair_sum;            // 1: rows 2i and 2i+1 of the streamed matrix are the bf16
+                           // hi and lo parts of one data row (FP32 data): W of the
+                           // row is the sum of the two product rows, and both rows
+                           // of GEMM 2's operand carry it
 };
 
 template <int kH1>
@@ -373,7 +379,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
 #pragma unroll
         for (int c0 = 0; c0 < kSplit; ++c0) {
-          const float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
+          float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
+          // FP32 data: the data row's W = hi-row product + lo-row product
+          // (adjacent rows sit in adjacent lanes; a + b == b + a, so both
+          // lanes hold the same value)
+          if (a.pair_sum) x += __shfl_xor_sync(0xffffffffu, x, 1);
           const __nv_bfloat16 hi = __float2bfloat16_rn(x);
           const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
           hs[c0] = __bfloat16_as_ushort(hi);
@@ -570,8 +580,9 @@ int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
 // MMA columns), dx, dy <= 512 (TMEM and shared-memory budget), 16-byte
 // aligned rows (ld a multiple of 8) and 16-byte aligned bases.
 bool tc_pass_eligible(const Plan& p) {
-  if (p.kind != kCCA || p.dtype != GBCCA_BF16 || 2 * p.k > tc::kHalfMax || p.v[0].d > 512 || p.v[1].d > 512)
-    return false;
+  if (p.kind != kCCA || 2 * p.k > tc::kHalfMax || p.v[0].d > 512 || p.v[1].d > 512) return false;
+  if (p.dtype == GBCCA_FP32) return p.ts_ready && p.ts_interleaved;  // the plan's own aligned copy
+  if (p.dtype != GBCCA_BF16) return false;
   for (int v = 0; v < 2; ++v) {
     if (p.v[v].ld % 8 != 0 || (reinterpret_cast<uintptr_t>(p.v[v].Z) & 15) != 0) return false;
   }
@@ -579,11 +590,21 @@ bool tc_pass_eligible(const Plan& p) {
 }
 
 int tc_pass(Plan& p, cudaStream_t st, const int* done) {
-  if (p.tc_map_for[0] != p.v[0].Z || p.tc_map_for[1] != p.v[1].Z) {
+  // FP32 data: the row-interleaved hi/lo copy (2n rows) made when the data
+  // was bound; BF16 data: the caller's matrices
+  const bool fp32 = p.dtype == GBCCA_FP32;
+  const int64_t rows = fp32 ? 2 * p.n : p.n;
+  const void* src[2];
+  int64_t ld[2];
+  for (int v = 0; v < 2; ++v) {
+    src[v] = fp32 ? (const void*)p.ts_copy[v] : p.v[v].Z;
+    ld[v] = fp32 ? p.ts_ld[v] : p.v[v].ld;
+  }
+  if (p.tc_map_for[0] != src[0] || p.tc_map_for[1] != src[1]) {
     for (int v = 0; v < 2; ++v)
-      GB_TRY(make_map(reinterpret_cast<CUtensorMap*>(p.tc_map[v]), p.v[v].Z, p.n, p.v[v].d, p.v[v].ld));
-    p.tc_map_for[0] = p.v[0].Z;
-    p.tc_map_for[1] = p.v[1].Z;
+      GB_TRY(make_map(reinterpret_cast<CUtensorMap*>(p.tc_map[v]), src[v], rows, p.v[v].d, ld[v]));
+    p.tc_map_for[0] = src[0];
+    p.tc_map_for[1] = src[1];
   }
   const int k2 = 2 * p.k, k4 = 4 * p.k;
   tc::Args a{};
@@ -600,7 +621,8 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     GB_CHECK_LAUNCH();
   }
   a.k2 = k2;
-  a.ntiles = ceil_div(p.n, tc::kRows);
+  a.ntiles = ceil_div(rows, tc::kRows);
+  a.pair_sum = fp32 ? 1 : 0;
   a.phi_img = p.tc_img;
   a.partG = p.tc_part;
   a.err = p.flag;

@@ -169,6 +169,7 @@ struct Plan {
   float* ts_part = nullptr;
   int ts_clusters = 0;
   bool ts_ready = false;
+  bool ts_interleaved = false;  // CCA: rows 2i / 2i + 1 hold hi / lo (streamed by the BF16 kernel)
   cudaEvent_t kev0 = nullptr;  // when set: recorded around the data kernel of the next pass
   cudaEvent_t kev1 = nullptr;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
 };

@@ -1,28 +1,38 @@
-"""GPU parity of the tensor-core (tcgen05 + TMA) pass for FP32 data, CCA and
-FDA, through the C ABI.
+"""GPU parity of the tensor-core (tcgen05 + TMA) passes for FP32 data, CCA
+and FDA, through the C ABI.
 
-The pass streams a BF16 hi/lo copy of the data (FDA: of the class-centred
-rows): Z' = Z_hi + Z_lo with |Z - Z'| <= 2^-18 |Z| entrywise, and evaluates
-Phi' = bf16 hi + lo of Phi (the point the solver then holds).  Products of
-BF16 operands are exact in FP32; the remaining errors are the representation
-of Z (entering both products), the bf16 hi + lo split of W (2^-18 |W|) and
-FP32 accumulation.  Each entry is checked against its own bound gamma * ref,
-ref the sum of |terms| (|Z|^T (|Z| |Phi'|); for the Gram (|Z||Phi'|)^T
-(|Z||Phi'|)).
+Both stream a BF16 hi/lo copy of the data (FDA: of the class-centred rows):
+Z' = Z_hi + Z_lo with |Z - Z'| <= 2^-17 |Z| entrywise (z in [2^e, 2^(e+1)):
+|z - hi| <= 2^(e-8), and rounding that remainder to 8 bits errs by at most
+2^(e-17)), and evaluate Phi' = bf16 hi + lo of Phi (the point the solver then
+holds).  Products of BF16 operands are exact in FP32; the remaining errors
+are the representation of Z (entering both products), the bf16 hi + lo split
+of W (2^-17 |W|) and FP32 accumulation.  Each entry is checked against its
+own bound gamma * ref, ref the sum of |terms| (|Z|^T (|Z| |Phi'|); for the
+Gram (|Z||Phi'|)^T (|Z||Phi'|)).
 
-Rounding steps (32-row tiles, 128-column pairs, 2-CTA clusters):
-  GEMM 1  per issuer one FP32 chain of 8 MMAs per pair it owns (CCA: issuer
-          1 the hi part, issuer 2 the lo part; FDA: half of the pairs each),
-          then two epilogue additions (accumulators, hi + lo columns of Phi);
-          FDA adds the two CTAs' products (one more);
-  GEMM 2  4 MMAs per tile into one accumulator (CCA: 2 K steps x hi and lo
-          part of the data; FDA: 2 K steps x hi and lo rows of W), T tiles per
-          cluster, one more addition at the drain (CCA hi + lo columns);
-  reduce  per-cluster partials summed with compensation (<= 2 ulp).
-Counting every MMA as two FP32 roundings of at most 2^-23 of the running sum:
-  gamma = 3 * 2^-18 + 2^-23 (2 (8 P1 + 3) + 2 (4 T + 1) + 4),
-P1 the pairs of the longer GEMM 1 chain, T = ceil(ceil(n / 32) / clusters)
-with at least min(tiles, 64) clusters.
+CCA runs the BF16 kernel over a row-interleaved copy (2n rows: row 2i the hi
+part of data row i, row 2i + 1 its lo part; 64-row tiles):
+  GEMM 1  d / 16 + 2 FP32 roundings along a chain (two issuers, hi and lo
+          columns of Phi), plus the addition of the hi-row and lo-row
+          products of the same data row;
+  GEMM 2  4 MMAs per 64-row tile, T tiles per cluster, one more addition at
+          the drain (hi + lo columns of W);
+  reduce  per-cluster partials summed with compensation (<= 2 ulp);
+  gamma = 3 * 2^-17 + 2^-23 (2 (d / 16 + 2) + 2 + 2 (4 T + 1) + 4),
+T = ceil(ceil(2n / 64) / clusters) with at least min(tiles, 64) clusters.  The
+Gram is Phi_bd^T G formed in FP64: the same gamma against |W|^T |W|.
+
+FDA runs its own kernel (32-row tiles, 128-column pairs, 2-CTA clusters):
+  GEMM 1  per issuer one FP32 chain of 8 MMAs per pair it owns (half of the
+          pairs each), two epilogue additions (accumulators, hi + lo columns
+          of Phi), and the sum of the two CTAs' products (one more);
+  GEMM 2  4 MMAs per tile into one accumulator (2 K steps x hi and lo rows of
+          W), T tiles per cluster;
+  reduce  as above;
+  gamma = 3 * 2^-17 + 2^-23 (2 (8 P1 + 3) + 2 (4 T + 1) + 4),
+P1 the pairs of the longer GEMM 1 chain, T = ceil(ceil(n / 32) / clusters).
+Counting every MMA as two FP32 roundings of at most 2^-23 of the running sum.
 """
 import numpy as np
 import pytest
@@ -58,7 +68,13 @@ def split_round(P):
 def gamma_split(n, p1):
     tiles = -(-n // 32)
     T = -(-tiles // min(tiles, 64))
-    return 3 * 2.0 ** -18 + 2.0 ** -23 * (2 * (8 * p1 + 3) + 2 * (4 * T + 1) + 4)
+    return 3 * 2.0 ** -17 + 2.0 ** -23 * (2 * (8 * p1 + 3) + 2 * (4 * T + 1) + 4)
+
+
+def gamma_interleaved(n, d):
+    tiles = -(-2 * n // 64)
+    T = -(-tiles // min(tiles, 64))
+    return 3 * 2.0 ** -17 + 2.0 ** -23 * (2 * (d / 16 + 2) + 2 + 2 * (4 * T + 1) + 4)
 
 
 def _check(got, exp, refs, gamma):
@@ -87,12 +103,11 @@ def _cca(gb, P, n, dx, dy, k, seed=0):
 
 
 @pytest.mark.parametrize("n,dx,dy,k", [(3001, 192, 136, 5), (4099, 70, 45, 5), (20000, 512, 384, 10),
-                                       (64, 64, 40, 1), (33, 24, 8, 3)])
+                                       (64, 64, 40, 1), (33, 24, 8, 3), (12345, 500, 24, 12)])
 def test_split_cca_pass_ragged(gb, n, dx, dy, k):
     P = cca_latent_problem(n, dx, dy, latent=6, dtype="f32", seed=n, colscale=(1.0, 1e-3))
     got, exp, refs = _cca(gb, P, n, dx, dy, k)
-    p1 = -(-max(dx, dy) // 128)
-    _check(got, exp, refs, gamma_split(n, p1))
+    _check(got, exp, refs, gamma_interleaved(n, max(dx, dy)))
 
 
 def test_split_cca_pass_full_workload(gb):
@@ -100,7 +115,7 @@ def test_split_cca_pass_full_workload(gb):
     P = make_workload("cca_tall_f32")
     c = P["config"]
     got, exp, refs = _cca(gb, P, c["n"], c["dx"], c["dy"], c["k"], seed=3)
-    _check(got, exp, refs, gamma_split(c["n"], 4))
+    _check(got, exp, refs, gamma_interleaved(c["n"], 512))
 
 
 def _lda(gb, P, n, d, l, k, seed=0):
@@ -154,27 +169,26 @@ def test_tall_f32_solve(gb):
 
 
 def test_wait_bound_reports_timeout_and_context_survives(gb):
-    """A pipeline-wait bound of one cycle makes the first wait of the FP32
+    """A pipeline-wait bound of one cycle makes the first wait of the FDA
     tensor-core pass run out: every CTA drains its own copies and MMAs and
     leaves, and the solve returns GBCCA_ERR_TIMEOUT (no hang, no fault).  A
     plan with the default bound then solves the same data correctly."""
     import torch
-    n, dx, dy, k, lam = 6000, 96, 80, 4, 1e-3
-    P = cca_latent_problem(n, dx, dy, latent=6, dtype="f32", seed=31, latent_scale=[1.0, 0.7, 0.5, 0.35, 0.25, 0.2])
-    X, Y = to_dev(P["X"], "f32"), to_dev(P["Y"], "f32")
-    plan = gb.cca_plan(n, dx, dy, k, "f32", gb.default_options(wait_cycles=1, max_iter=50))
-    gb.cca_precondition(plan, X, Y, lam, lam)
+    n, d, l, k, lam = 6000, 96, 5, 4, 1e-2
+    P = lda_problem(n, d, l, dtype="f32", seed=31)
+    X = to_dev(P["X"], "f32")
+    y = torch.from_numpy(P["y"]).cuda()
+    plan = gb.lda_plan(n, d, l, k, "f32", gb.default_options(wait_cycles=1, max_iter=50))
     with pytest.raises(gb.GbccaError) as e:
-        gb.cca_solve(plan)
+        gb.lda_solve(plan, X, y, lam)
     assert e.value.code == gb.ERR_TIMEOUT, str(e.value)
     torch.cuda.synchronize()
     plan.close()
-    plan = gb.cca_plan(n, dx, dy, k, "f32", gb.default_options(max_iter=1000, gtol=0.0, rtol=1e-7))
-    gb.cca_precondition(plan, X, Y, lam, lam)
-    sig, _, _, info = gb.cca_solve(plan)
-    ref, _, _ = cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    plan = gb.lda_plan(n, d, l, k, "f32", gb.default_options(max_iter=2000, gtol=0.0, rtol=1e-7))
+    rho, _, info = gb.lda_solve(plan, X, y, lam)
+    ref, _ = OL.lda_geneig(P["X64"], P["y"], l, lam, k)
     assert info["status"] == gb.OK, info
-    assert rel(np64(sig), ref) < 1e-6, (np64(sig), ref)
+    assert rel(np64(rho), ref) < 1e-6, (np64(rho), ref)
     plan.close()
 
 

@@ -14,7 +14,7 @@ Rounding steps of the kernel (64-row tiles, 2-CTA clusters, one view per CTA):
           into two FP32 accumulators that the epilogue adds, hi and lo
           columns of Phi in separate accumulator columns also added:
           at most d / 16 + 2 FP32 roundings along any chain;
-  split   W -> bf16 hi + lo: |W - (W_hi + W_lo)| <= 2^-18 |W|;
+  split   W -> bf16 hi + lo: |W - (W_hi + W_lo)| <= 2^-17 |W|;
   GEMM 2  G = Z^T W over the rows of a cluster in MMAs of K = 16 (4 per
           64-row tile), hi and lo accumulator columns added at the drain:
           4 T + 1 roundings for T tiles per cluster;
@@ -22,7 +22,7 @@ Rounding steps of the kernel (64-row tiles, 2-CTA clusters, one view per CTA):
 Each FP32 rounding errs by at most 2^-23 of the running magnitude (which the
 sum of |terms| bounds); counting every MMA as two roundings (its internal
 sum and the accumulate) gives
-  gamma = 2^-18 + 2^-23 (2 (d / 16 + 2) + 2 (4 T + 1) + 4),
+  gamma = 2^-17 + 2^-23 (2 (d / 16 + 2) + 2 (4 T + 1) + 4),
 T = ceil(ceil(n / 64) / clusters) with at least min(tiles, 64) clusters (the
 GB300 keeps 76 resident).  The Gram is Phi_bd^T G formed in FP64: the same
 gamma against |Phi_bd|^T ref_G = |W|^T |W|.
@@ -60,7 +60,7 @@ def split_round(P):
 def gamma_tc(n, d):
     tiles = -(-n // 64)
     T = -(-tiles // min(tiles, 64))
-    return 2.0 ** -18 + 2.0 ** -23 * (2 * (d / 16 + 2) + 2 * (4 * T + 1) + 4)
+    return 2.0 ** -17 + 2.0 ** -23 * (2 * (d / 16 + 2) + 2 * (4 * T + 1) + 4)
 
 
 def _run(gb, P, n, dx, dy, k, seed=0):
