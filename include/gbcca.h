@@ -47,7 +47,8 @@ enum gbcca_dtype { GBCCA_BF16 = 0, GBCCA_FP32 = 1, GBCCA_FP64 = 2 };
  *   SRHT         S a subsampled randomized Hadamard transform (App. A).
  *   IDENTITY     M = I (no preconditioning; the "M = I" ablation of Sec. 6).
  *   EXACT        M = Z^T Z + lambda I (the "M = Sigma" ablation of Sec. 6;
- *                S = I, costs O(n d^2)). */
+ *                S = I, costs O(n d^2)); FP64 CCA plans only (cca_plan
+ *                returns GBCCA_ERR_UNSUPPORTED otherwise). */
 enum gbcca_sketch {
   GBCCA_SKETCH_COUNTSKETCH = 0,
   GBCCA_SKETCH_SRHT = 1,
@@ -109,11 +110,20 @@ typedef struct {
                             0 = the default 12, which reaches the exact
                             sketched solution to ~1e-6 in subspace angle     */
   int64_t wait_cycles;   /* bound, in GPU clock cycles, on one pipeline wait of
-                            the FP32 tensor-core pass (0 = the default 2e9,
-                            about one second).  A wait that runs out stops the
-                            pass early: every CTA drains its own copies and
-                            MMAs, and the call returns GBCCA_ERR_TIMEOUT.
-                            Small values exist to exercise that path.       */
+                            the FDA tensor-core pass for FP32 data (0 = the
+                            default 2e9, about one second).  A wait that runs
+                            out stops the pass early: every CTA drains its own
+                            copies and MMAs, and the call returns
+                            GBCCA_ERR_TIMEOUT.  Small values exist to exercise
+                            that path.                                      */
+  int32_t retraction;    /* retraction onto St_B (Table 1): 0 (default) the QR
+                            retraction, computed as (U + xi) L^{-T} with
+                            L L^T = (U + xi)^T B (U + xi); 1 the polar
+                            retraction (U + xi) ((U + xi)^T B (U + xi))^{-1/2}
+                            (for tangent xi: (U + xi)(I + xi^T B xi)^{-1/2}),
+                            the inverse square root from a k x k symmetric
+                            eigendecomposition per line-search trial.  The
+                            starting point is normalized by the same map.   */
 } gbcca_options;
 
 /* Per-solve report (host struct filled by the solve calls). */
@@ -133,7 +143,7 @@ typedef struct {
 
 /* Fills `opt` with defaults (CountSketch, s = 0, seed 0, max_iter 1000,
  * gtol 1e-8, refine 1, warm_start 1, check_every 8, time_passes 0, graphs 1,
- * rtol 0, tensor_cores 1, warm_iters 0 (12), wait_cycles 0).
+ * rtol 0, tensor_cores 1, warm_iters 0 (12), wait_cycles 0, retraction 0).
  * Returns GBCCA_OK or
  * GBCCA_ERR_INVALID_ARG if opt is NULL. */
 int gbcca_default_options(gbcca_options* opt);

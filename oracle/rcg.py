@@ -11,7 +11,8 @@ this module fixes one reading of them, the same one the library implements:
         beta = max(0, g(grad, y) / g(T(eta_prev), y)),  y = grad - T(grad_prev),
     T = projection onto the new tangent space (Table 1 vector transport);
     if g(grad, eta) >= 0 the direction restarts as -grad.
-  * line search along t -> R_X(t eta) (QR retraction): first trial
+  * line search along t -> R_X(t eta) (QR retraction, or the polar one on
+    request): first trial
     t = 1 / ||eta||_M on the first iteration, else t_prev * df_prev / df
     (df = g(grad, eta)); Armijo backtracking with c1 = 1e-4 halving t, at most
     25 trials (Sec. 6.1: manopt rejects a step after 25); if the first trial
@@ -45,17 +46,29 @@ MAX_LS = 25
 MAX_EXPAND = 10
 
 
-def _retr(pts, Bs, etas, t):
-    return [G.retr_qr(x, B, t * e) for x, B, e in zip(pts, Bs, etas)]
+def _retr(pts, Bs, etas, t, retraction="qr"):
+    f = G.retr_polar if retraction == "polar" else G.retr_qr
+    return [f(x, B, t * e) for x, B, e in zip(pts, Bs, etas)]
 
 
-def rcg(problem, Ms, X0s, max_iter=1000, gtol=1e-8, record=False):
+def _normalize(x, B, retraction):
+    """Starting point on St_B: qf_B (the QR retraction at a zero step), or for
+    the polar retraction its own zero-step map x (x^T B x)^{-1/2}."""
+    if retraction == "polar":
+        w, Q = np.linalg.eigh(x.T @ B @ x)
+        return x @ ((Q / np.sqrt(w)) @ Q.T)
+    return G.retr_chol(x, B, np.zeros_like(x))
+
+
+def rcg(problem, Ms, X0s, max_iter=1000, gtol=1e-8, record=False, retraction="qr"):
     """Riemannian CG on the product of St_{B_i} with metrics M_i.
 
+    retraction: "qr" (Table 1 QR retraction) or "polar" (Table 1 polar
+    retraction); the starting point is normalized by the same map.
     Returns dict(points, iters, history=[(f, ||grad||_M, t), ...], status).
     """
     Bs = problem.Bs
-    pts = [G.retr_chol(x, B, np.zeros_like(x)) for x, B in zip(X0s, Bs)]  # qf_B
+    pts = [_normalize(x, B, retraction) for x, B in zip(X0s, Bs)]
     f = problem.cost(pts)
     eg = problem.egrad(pts)
     grads = [G.rgrad(x, B, M, g) for x, B, M, g in zip(pts, Bs, Ms, eg)]
@@ -80,7 +93,7 @@ def rcg(problem, Ms, X0s, max_iter=1000, gtol=1e-8, record=False):
             t = t_prev * df_prev / df
         ok = False
         for j in range(MAX_LS):
-            ft = problem.cost(_retr(pts, Bs, etas, t))
+            ft = problem.cost(_retr(pts, Bs, etas, t, retraction))
             if ft <= f + C1 * t * df:
                 ok = True
                 break
@@ -91,12 +104,12 @@ def rcg(problem, Ms, X0s, max_iter=1000, gtol=1e-8, record=False):
         if j == 0:
             for _ in range(MAX_EXPAND):
                 t2 = 2.0 * t
-                f2 = problem.cost(_retr(pts, Bs, etas, t2))
+                f2 = problem.cost(_retr(pts, Bs, etas, t2, retraction))
                 if f2 < ft and f2 <= f + C1 * t2 * df:
                     t, ft = t2, f2
                 else:
                     break
-        new = _retr(pts, Bs, etas, t)
+        new = _retr(pts, Bs, etas, t, retraction)
         eg = problem.egrad(new)
         g_new = [G.rgrad(x, B, M, g) for x, B, M, g in zip(new, Bs, Ms, eg)]
         eta_T = [G.proj_tangent(x, B, M, e) for x, B, M, e in zip(new, Bs, Ms, etas)]

@@ -32,6 +32,7 @@ class Options(C.Structure):
         ("tensor_cores", C.c_int32),
         ("warm_iters", C.c_int32),
         ("wait_cycles", C.c_int64),
+        ("retraction", C.c_int32),
     ]
 
 

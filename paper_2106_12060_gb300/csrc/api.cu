@@ -51,7 +51,7 @@ void free_plan(Plan* p) {
                   (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
                   (void*)p->phigram, (void*)p->phipart, (void*)p->phired, (void*)p->cross, (void*)p->crosspart, (void*)p->history, (void*)p->ritz_hist,
-                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->mv_part, (void*)p->mv_cnt, (void*)p->ls_f, (void*)p->ls_L})
+                  (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->ls_f, (void*)p->ls_L})
     dfree(q);
   for (int v = 0; v < 2; ++v) dfree(p->ts_copy[v]);
   dfree(p->ts_img);
@@ -171,12 +171,6 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->ws, p->ws_len));
   GB_TRY(dalloc(&p->mt_part, (int64_t)ceil_div(dmax, 64) * dmax * 40));
   GB_TRY(dalloc(&p->dfx, 2 * (int64_t)dmax * k2));
-  // double-float products: up to 2 problems x 16 slices x dmax rows x 40 columns x 2
-  p->mv_part_len = 2 * 16 * (int64_t)(dmax + 32) * 40 * 2;
-  GB_TRY(dalloc(&p->mv_part, p->mv_part_len));
-  p->mv_cnt_len = 2 * (dmax + 8);
-  GB_TRY(dalloc(&p->mv_cnt, p->mv_cnt_len));
-  GB_CUDA(cudaMemset(p->mv_cnt, 0, sizeof(int) * p->mv_cnt_len));
   GB_TRY(dalloc(&p->ls_f, 64));
   GB_TRY(dalloc(&p->ls_L, 64 * 2 * (int64_t)kMaxK * kMaxK));
   GB_TRY(dalloc(&p->flag, 1));
@@ -203,7 +197,7 @@ int alloc_plan(Plan* p) {
 int check_options(const gbcca_options& o) {
   if (o.sketch < 0 || o.sketch > 3) return GBCCA_ERR_INVALID_ARG;
   if (o.max_iter < 1 || o.s < 0 || !(o.gtol >= 0) || o.check_every < 1 || o.wait_cycles < 0 || !(o.rtol >= 0) ||
-      o.warm_iters < 0)
+      o.warm_iters < 0 || o.retraction < 0 || o.retraction > 1)
     return GBCCA_ERR_INVALID_ARG;
   return GBCCA_OK;
 }
@@ -227,6 +221,11 @@ int make_plan(gbcca_plan_t* out, int kind, int64_t n, int d0, int d1, int nviews
     delete p;
     set_last_error("invalid options");
     return GBCCA_ERR_INVALID_ARG;
+  }
+  if (p->opt.sketch == GBCCA_SKETCH_EXACT && (dtype != GBCCA_FP64 || kind != kCCA)) {
+    delete p;
+    set_last_error("the exact metric (M = Sigma) is implemented for FP64 CCA plans");
+    return GBCCA_ERR_UNSUPPORTED;
   }
   p->kind = kind;
   p->n = n;

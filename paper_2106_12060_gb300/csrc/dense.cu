@@ -262,174 +262,86 @@ __device__ __forceinline__ void df_add(float& S, float& Cc, float s2, float c2) 
   Cc += err + c2;
 }
 
-constexpr int kMvChunk = 256, kMvCols = 10;  // c <= 4 * kMvCols
-constexpr int kMvMaxSlices = 16;
-constexpr int kMvBatch = 8;                                  // loads in flight per thread while staging
+constexpr int kMvCols = 20;  // columns per lane and pass over a row
+constexpr int kMvRows = 4;   // rows (warps) per CTA
 
-// Y_b (rows r0 .. r0 + R - 1, c columns) = A_b X_b for problem b =
-// blockIdx.y, A_b (m x K, row-major) and X_b (K x c) as double-float pairs
-// hi + lo.  The K range is split over gridDim.z CTAs (K slices) so that the
-// whole GPU works on these small products.  Lane = (row r = lane % R,
-// column group cg = lane / R: columns cg, cg + G, ...) with G = 32 / R
-// chosen so each lane owns up to kMvCols columns (R = 32, 16, 8 for c <= 10,
-// 20, 40).  X and the R rows of A of the slice are staged in shared memory
-// (loads batched); warp w takes a contiguous eighth of the slice.  The 8
-// warps' double-float partials are added in fixed order, written per slice,
-// and the last CTA of a row block (atomic counter) adds the slices in slice
-// order: deterministic.
-__global__ void __launch_bounds__(256) dfmv_kernel(DfmvArgs a) {
-  const int b = blockIdx.y;
-  const DfmvProblem& P = a.p[b];
+// Y_b (m x c) = A_b X_b for problem b = blockIdx.y, A_b (m x K, row-major)
+// and X_b (K x c, row stride ldx) as double-float pairs hi + lo.  One warp per
+// output row: lane l takes the inner indices q = l, l + 32, ... (the row of A
+// is read coalesced; the rows of X, shared by every warp, come from L1/L2 as
+// float2 pairs) and accumulates up to kMvCols columns in double-float
+// registers; a fixed xor-shuffle tree then adds the 32 lanes' pairs, and lane
+// 0 writes the row.  No scratch, no atomics, one launch for all problems;
+// the result does not depend on scheduling.  Columns beyond kMvCols take
+// further passes over the row.
+__global__ void __launch_bounds__(32 * kMvRows) dfmv_kernel(DfmvArgs a) {
   if (a.done != nullptr && *a.done) return;
-  const int m = P.m, K = P.K, c = a.c;
-  const int G = c <= kMvCols ? 1 : (c <= 2 * kMvCols ? 2 : 4);
-  const int R = 32 / G;
-  const int r0 = blockIdx.x * R;
-  if (r0 >= m) return;  // uniform over the slices of this row block
-  const int S = gridDim.z, z = blockIdx.z;
-  const int ks = (K + S - 1) / S;
-  const int kb = min(K, z * ks), kn = min(K, kb + ks) - kb;  // kn <= kMvChunk
-  extern __shared__ float msm[];
-  float* Xh = msm;                              // [kMvChunk][c]
-  float* Xl = Xh + kMvChunk * c;
-  float* Ah = Xl + kMvChunk * c;                // [R][kMvChunk + 1]
-  float* Al = Ah + R * (kMvChunk + 1);
-  float* red = Al + R * (kMvChunk + 1);         // [8 warps][R][c][2]
-  __shared__ int last;
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, r = lane % R, cg = lane / R;
-  float S1[kMvCols], Cc[kMvCols];
+  // the problem's fields by selection (a dynamic index into the parameter
+  // array would copy it to local memory)
+  const bool b1 = blockIdx.y != 0;
+#define GB_SEL(f) (b1 ? a.p[1].f : a.p[0].f)
+  struct {
+    const float *hi, *lo, *Xh, *Xl;
+    double* Y;
+    int m, K, ldx, ldy;
+  } P{GB_SEL(hi), GB_SEL(lo), GB_SEL(Xh), GB_SEL(Xl), GB_SEL(Y), GB_SEL(m), GB_SEL(K), GB_SEL(ldx), GB_SEL(ldy)};
+#undef GB_SEL
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kMvRows + (threadIdx.x >> 5);
+  if (r >= P.m) return;  // whole warps only: the shuffles below see all 32 lanes
+  const float* Ah = P.hi + (int64_t)r * P.K;
+  const float* Al = P.lo + (int64_t)r * P.K;
+  for (int c0 = 0; c0 < a.c; c0 += kMvCols) {
+    const int cn = min(kMvCols, a.c - c0);  // even
+    float S[kMvCols], C[kMvCols];
 #pragma unroll
-  for (int u = 0; u < kMvCols; ++u) S1[u] = Cc[u] = 0.f;
-  const int c2 = c >> 1;  // c is even: X rows are read as float2
-  const int nx = kn * c2;
-  for (int base = 0; base < nx; base += 256 * kMvBatch) {
-    float2 vh[kMvBatch], vl[kMvBatch];
+    for (int u = 0; u < kMvCols; ++u) S[u] = C[u] = 0.f;
+    for (int q = lane; q < P.K; q += 32) {
+      const float ah = Ah[q], al = Al[q];
+      const float2* xh = reinterpret_cast<const float2*>(P.Xh + (int64_t)q * P.ldx + c0);
+      const float2* xl = reinterpret_cast<const float2*>(P.Xl + (int64_t)q * P.ldx + c0);
 #pragma unroll
-    for (int u = 0; u < kMvBatch; ++u) {
-      const int e = base + tid + 256 * u;
-      if (e < nx) {
-        const int q = e / c2, cp = e - q * c2;
-        const int64_t o = (int64_t)(kb + q) * P.ldx + 2 * cp;
-        vh[u] = *reinterpret_cast<const float2*>(P.Xh + o);
-        vl[u] = *reinterpret_cast<const float2*>(P.Xl + o);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kMvBatch; ++u) {
-      const int e = base + tid + 256 * u;
-      if (e < nx) {
-        reinterpret_cast<float2*>(Xh)[e] = vh[u];
-        reinterpret_cast<float2*>(Xl)[e] = vl[u];
-      }
-    }
-  }
-  const int na = R * kn;
-  for (int base = 0; base < na; base += 256 * kMvBatch) {
-    float vh[kMvBatch], vl[kMvBatch];
-#pragma unroll
-    for (int u = 0; u < kMvBatch; ++u) {
-      const int e = base + tid + 256 * u;
-      vh[u] = vl[u] = 0.f;
-      if (e < na) {
-        const int rr = e / kn, q = e - rr * kn;
-        if (r0 + rr < m) {
-          vh[u] = P.hi[(int64_t)(r0 + rr) * K + kb + q];
-          vl[u] = P.lo[(int64_t)(r0 + rr) * K + kb + q];
+      for (int u = 0; u < kMvCols / 2; ++u) {
+        if (2 * u < cn) {
+          const float2 bh = xh[u], bl = xl[u];
+          df_acc(S[2 * u], C[2 * u], ah, al, bh.x, bl.x);
+          df_acc(S[2 * u + 1], C[2 * u + 1], ah, al, bh.y, bl.y);
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < kMvBatch; ++u) {
-      const int e = base + tid + 256 * u;
-      if (e < na) {
-        const int rr = e / kn, q = e - rr * kn;
-        Ah[rr * (kMvChunk + 1) + q] = vh[u];
-        Al[rr * (kMvChunk + 1) + q] = vl[u];
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int u = 0; u < kMvCols; ++u) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, S[u], o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, C[u], o);
+        df_add(S[u], C[u], s2, c2);
       }
     }
-  }
-  __syncthreads();
-  const int per = (kn + 7) >> 3;
-  const int qb = w * per, qe = min(kn, qb + per);
-  for (int q = qb; q < qe; ++q) {
-    const float ah = Ah[r * (kMvChunk + 1) + q], al = Al[r * (kMvChunk + 1) + q];
+    if (lane == 0) {
+      double* y = P.Y + (int64_t)r * P.ldy + c0;
 #pragma unroll
-    for (int u = 0; u < kMvCols; ++u) {
-      const int col = cg + G * u;
-      if (col < c) df_acc(S1[u], Cc[u], ah, al, Xh[q * c + col], Xl[q * c + col]);
+      for (int u = 0; u < kMvCols; ++u)
+        if (u < cn) y[u] = (double)S[u] + (double)C[u];
     }
-  }
-#pragma unroll
-  for (int u = 0; u < kMvCols; ++u) {
-    const int col = cg + G * u;
-    if (col < c) {
-      red[((w * R + r) * c + col) * 2 + 0] = S1[u];
-      red[((w * R + r) * c + col) * 2 + 1] = Cc[u];
-    }
-  }
-  __syncthreads();
-  // this slice's partial of the row block
-  const int mpad = gridDim.x * R;
-  float* part = a.part + (((int64_t)b * S + z) * mpad + r0) * c * 2;
-  for (int e = tid; e < R * c; e += 256) {
-    const int rr = e / c, col = e - rr * c;
-    float s = 0.f, cc = 0.f;
-    for (int w2 = 0; w2 < 8; ++w2)
-      df_add(s, cc, red[((w2 * R + rr) * c + col) * 2], red[((w2 * R + rr) * c + col) * 2 + 1]);
-    part[e * 2] = s;
-    part[e * 2 + 1] = cc;
-  }
-  __threadfence();
-  __syncthreads();
-  int* cnt = a.cnt + (int64_t)b * gridDim.x + blockIdx.x;
-  if (tid == 0) last = atomicAdd(cnt, 1) == S - 1;
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  if (tid == 0) *cnt = 0;
-  for (int e = tid; e < R * c; e += 256) {
-    const int rr = e / c, col = e - rr * c;
-    const int row = r0 + rr;
-    if (row >= m) continue;
-    float s = 0.f, cc = 0.f;
-    for (int z2 = 0; z2 < S; ++z2) {
-      const volatile float* pz = a.part + (((int64_t)b * S + z2) * mpad + r0) * c * 2;
-      df_add(s, cc, pz[e * 2], pz[e * 2 + 1]);
-    }
-    P.Y[(int64_t)row * P.ldy + col] = (double)s + (double)cc;
   }
 }
 
 int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st) {
-  if (a.c < 2 || a.c > 4 * kMvCols || (a.c & 1)) {
+  if (a.c < 2 || (a.c & 1) || nprob < 1 || nprob > 2) {
     set_last_error("dfmv: unsupported column count");
     return GBCCA_ERR_INVALID_ARG;
   }
-  int mmax = 0, kmax = 0;
+  int mmax = 0;
   for (int b = 0; b < nprob; ++b) {
-    if ((a.p[b].ldx & 1) || (reinterpret_cast<uintptr_t>(a.p[b].Xh) & 7) ||
+    if ((a.p[b].ldx & 1) || a.p[b].ldx < a.c || (reinterpret_cast<uintptr_t>(a.p[b].Xh) & 7) ||
         (reinterpret_cast<uintptr_t>(a.p[b].Xl) & 7)) {
-      set_last_error("dfmv: X rows must be 8-byte aligned");
+      set_last_error("dfmv: X rows must be 8-byte aligned and hold c columns");
       return GBCCA_ERR_INVALID_ARG;
     }
     mmax = std::max(mmax, a.p[b].m);
-    kmax = std::max(kmax, a.p[b].K);
   }
-  const int G = a.c <= kMvCols ? 1 : (a.c <= 2 * kMvCols ? 2 : 4);
-  const int R = 32 / G;
-  const int rb = ceil_div(mmax, R);
-  // K slices: at least ceil(K / 256) (one staged chunk each), and enough CTAs
-  // to cover the GPU about twice
-  int S = std::max(ceil_div(kmax, kMvChunk), ceil_div(2 * a.sm_count, rb * nprob));
-  S = std::min(S, std::min(kMvMaxSlices, kmax));
-  if ((int64_t)nprob * S * rb * R * a.c * 2 > a.part_len || nprob * rb > a.cnt_len ||
-      ceil_div(kmax, S) > kMvChunk) {
-    set_last_error("dfmv: scratch too small for this shape");
-    return GBCCA_ERR_INVALID_ARG;
-  }
-  const size_t smem = sizeof(float) * (2 * kMvChunk * a.c + 2 * R * (kMvChunk + 1) + 8 * R * a.c * 2);
-  GB_CUDA(cudaFuncSetAttribute(dfmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dfmv_kernel<<<dim3(rb, nprob, S), 256, smem, st>>>(a);
+  dfmv_kernel<<<dim3(ceil_div(mmax, kMvRows), nprob), 32 * kMvRows, 0, st>>>(a);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -126,10 +126,6 @@ struct Plan {
   int ritz_len = 0;             // rows of ritz_hist
   double* mt_part = nullptr;    // slice partials of mat_thin
   float* dfx = nullptr;         // 2 x dmax x 2k floats: split blocks for double-float products
-  float* mv_part = nullptr;     // K-slice partials of the double-float products
-  int64_t mv_part_len = 0;
-  int* mv_cnt = nullptr;        // their slice counters (zero between calls)
-  int mv_cnt_len = 0;
   double* ls_f = nullptr;       // line-search trial values (kNTrials)
   double* ls_L = nullptr;       // line-search trial factors (kNTrials x 2 x kMaxK^2)
   double* ws = nullptr;         // FP64 scratch for dense routines
@@ -210,13 +206,8 @@ struct DfmvProblem {
 };
 struct DfmvArgs {
   DfmvProblem p[2];
-  int c;
+  int c;             // columns of X and Y (even)
   const int* done;
-  float* part;       // K-slice partials (plan scratch, part_len floats)
-  int64_t part_len;
-  int* cnt;          // per row-block slice counters, zero between calls (cnt_len)
-  int cnt_len;
-  int sm_count;
 };
 int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st);
 // hi/lo split of the first c columns of X (rows x ldx) into rows x c floats

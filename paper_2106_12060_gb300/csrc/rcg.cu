@@ -167,8 +167,15 @@ template <typename R>
 __device__ void warp_jacobi(R* A, R* Q, R* lam, int n, int max_sweeps = 20, R tol = R(0)) {
   if (!(tol > R(0))) tol = R(sizeof(R) == 8 ? 1e-26 : 1e-12);
   const int lane = threadIdx.x & 31;
-  __shared__ R w_cs[16], w_sn[16];
-  __shared__ int w_p[16], w_q[16];
+  // rotation tables of this warp (up to 8 warps of a CTA may run their own
+  // decompositions side by side)
+  __shared__ R w_cs_all[8][16], w_sn_all[8][16];
+  __shared__ int w_p_all[8][16], w_q_all[8][16];
+  const int wslot = (threadIdx.x >> 5) & 7;
+  R* w_cs = w_cs_all[wslot];
+  R* w_sn = w_sn_all[wslot];
+  int* w_p = w_p_all[wslot];
+  int* w_q = w_q_all[wslot];
   for (int e = lane; e < n * n; e += 32) Q[e] = (e / n == e % n) ? R(1) : R(0);
   __syncwarp();
   const int m = n + (n & 1);
@@ -477,7 +484,31 @@ struct LSArgs {
   int max_iter;
   double* ls_f;           // kNTrials trial values
   double* ls_L;           // kNTrials x 2 x kMaxK^2 trial factors
+  int polar;              // 1: polar retraction (factors Gram(t)^{-1/2})
 };
+
+// Work area of one line-search trial (doubles): Gram_x, Gram_y, Cross, two
+// factors, two eigenvector matrices, one product (kk each), two k-vectors.
+constexpr int ls_work_doubles(int k) { return 8 * k * k + 2 * kMaxK; }
+
+// F = A^{-1/2} for a symmetric positive definite A (n x n, destroyed), by one
+// warp: A = Q diag(w) Q^T by Jacobi rotations, F = Q diag(w^{-1/2}) Q^T.
+// Returns false (on every lane) if an eigenvalue is not positive.
+__device__ bool warp_inv_sqrt(double* A, double* Q, double* w, double* F, int n) {
+  warp_jacobi<double>(A, Q, w, n);
+  const int lane = threadIdx.x & 31;
+  const bool ok = w[n - 1] > 0.0;  // eigenvalues sorted descending
+  if (lane < n) w[lane] = ok ? 1.0 / sqrt(w[lane]) : 0.0;
+  __syncwarp();
+  for (int e = lane; e < n * n; e += 32) {
+    const int r = e / n, c = e - r * n;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += Q[r * n + i] * w[i] * Q[c * n + i];
+    F[e] = s;
+  }
+  __syncwarp();
+  return ok;
+}
 
 // f(t) for one trial, evaluated by one warp from the coefficient matrices.
 // coef layout per view v (k x k each): A_v, B_v, C_v  (Gram(t) = A + t B + t^2 C)
@@ -579,6 +610,65 @@ __device__ double ls_eval_cca_cta(const LSArgs& a, const double* coef, double t,
   return s_f;
 }
 
+// Polar-retraction trial (called by all threads): warps 0 and 1 form
+// F_x = Gram_x(t)^{-1/2} and F_y = Gram_y(t)^{-1/2} side by side (FDA: warp 0
+// F = Gram(t)^{-1/2} only); the cost is f = -tr(N F_x Cross(t) F_y) (FDA:
+// -1/2 tr(N F S_B(t) F)).  F_y (FDA: F) is left at w + 3kk and F_x at w + 4kk,
+// where the Cholesky evaluators leave L_y^{-1} and L_x^{-1}: both factors are
+// symmetric, so the transposed copy the caller makes is the factor itself.
+__device__ double ls_eval_polar(const LSArgs& a, const double* coef, double t, double* w, const double* mu) {
+  const int k = a.k, kk = k * k, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool cca = a.kind == kCCA;
+  double* Gx = w;
+  double* Gy = w + kk;
+  double* Cx = w + 2 * kk;
+  double* Fy = w + 3 * kk;
+  double* Fx = cca ? w + 4 * kk : Fy;
+  double* Qx = w + 5 * kk;
+  double* Qy = w + 6 * kk;
+  double* T = w + 7 * kk;
+  double* ex = w + 8 * kk;
+  double* ey = ex + kMaxK;
+  __shared__ int s_okp[2];
+  __shared__ double s_fp;
+  for (int e = tid; e < kk; e += blockDim.x) {
+    Gx[e] = coef[e] + t * coef[kk + e] + t * t * coef[2 * kk + e];
+    if (cca) Gy[e] = coef[3 * kk + e] + t * coef[4 * kk + e] + t * t * coef[5 * kk + e];
+    Cx[e] = coef[6 * kk + e] + t * coef[7 * kk + e] + t * t * coef[8 * kk + e];
+  }
+  if (tid == 0) s_okp[1] = 1;
+  __syncthreads();
+  if (warp == 0) {
+    const bool ok = warp_inv_sqrt(Gx, Qx, ex, Fx, k);
+    if (lane == 0) s_okp[0] = ok;
+  } else if (warp == 1 && cca) {
+    const bool ok = warp_inv_sqrt(Gy, Qy, ey, Fy, k);
+    if (lane == 0) s_okp[1] = ok;
+  }
+  __syncthreads();
+  for (int e = tid; e < kk; e += blockDim.x) {  // T = F_x Cross
+    const int r = e / k, c = e - r * k;
+    double sv = 0.0;
+    for (int q = 0; q < k; ++q) sv += Fx[r * k + q] * Cx[q * k + c];
+    T[e] = sv;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double part = 0.0;
+    if (lane < k) {
+      double z = 0.0;
+      for (int j = 0; j < k; ++j) z += T[lane * k + j] * Fy[j * k + lane];
+      part = mu[lane] * z;
+    }
+    double f = -warp_sum(part);
+    if (!cca) f *= 0.5;
+    if (!(s_okp[0] && s_okp[1]) || !(f == f)) f = INFINITY;
+    if (lane == 0) s_fp = f;
+  }
+  __syncthreads();
+  return s_fp;
+}
+
 // Every trial step of the sequential Armijo rule is evaluated at once, one
 // CTA (one warp) per trial, so the FP64 work of the k x k Cholesky factors
 // is spread over kNTrials SMs instead of queueing on one SM's FP64 pipe:
@@ -604,7 +694,7 @@ __global__ void linesearch_kernel(LSArgs a) {
   const bool zero_step = st->force_zero_step != 0;
   double* coef = lsm;                       // 9 kk
   double* phig = coef + 9 * kk;             // 2 views x 4 kk
-  double* w = phig + 8 * kk;                // 5 kk + 2 kMaxK
+  double* w = phig + 8 * kk;                // ls_work_doubles(k)
   __shared__ double mu_s[kMaxK];
   __shared__ int last;
   if (!zero_step || i == 0) {
@@ -650,7 +740,16 @@ __global__ void linesearch_kernel(LSArgs a) {
     const double t = ls_trial_t(i, st->t0);
     // factors L_v(t)^{-T} of this trial (row-major), kept for the decision
     double* Lout = a.ls_L + (int64_t)i * 2 * kMaxK * kMaxK;
-    if (a.kind == kCCA) {
+    if (a.polar) {
+      const double f = ls_eval_polar(a, coef, t, w, mu_s);
+      const double* Fy = w + 3 * kk;
+      const double* Fx = a.kind == kCCA ? w + 4 * kk : Fy;
+      for (int e = tid; e < kk; e += blockDim.x) {
+        Lout[e] = Fx[e];
+        Lout[kMaxK * kMaxK + e] = Fy[e];
+      }
+      if (tid == 0) a.ls_f[i] = f;
+    } else if (a.kind == kCCA) {
       const double f = ls_eval_cca_cta(a, coef, t, w, mu_s);
       const double* Li = w + 3 * kk;
       const double* Lt = w + 4 * kk;
@@ -1674,7 +1773,8 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
     a.max_iter = p.opt.max_iter;
     a.ls_f = p.ls_f;
     a.ls_L = p.ls_L;
-    size_t smem = sizeof(double) * (9 * kk + 8 * kk + 5 * kk + 2 * kMaxK);
+    a.polar = p.opt.retraction == 1 ? 1 : 0;
+    size_t smem = sizeof(double) * (9 * kk + 8 * kk + ls_work_doubles(k));
     GB_CUDA(cudaFuncSetAttribute(linesearch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     linesearch_kernel<<<kNTrials, 256, smem, st>>>(a);
     GB_CHECK_LAUNCH();
@@ -1717,11 +1817,6 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
                            p.v[v].d,       p.v[v].d,       2 * k,       4 * k};
     m.c = 2 * k;
     m.done = done;
-    m.part = p.mv_part;
-    m.part_len = p.mv_part_len;
-    m.cnt = p.mv_cnt;
-    m.cnt_len = p.mv_cnt_len;
-    m.sm_count = p.sm_count;
     GB_TRY(dfmv(m, p.nviews, st));
   } else {
     for (int v = 0; v < p.nviews; ++v) GB_TRY(minv(p, v, st));
@@ -2207,11 +2302,6 @@ int warm_start(Plan& p, cudaStream_t st) {
       DfmvArgs g{};
       g.p[0] = DfmvProblem{A[0], A[1], bh, bl, C, m, K, c, c};
       g.c = c;
-      g.part = p.mv_part;
-      g.part_len = p.mv_part_len;
-      g.cnt = p.mv_cnt;
-      g.cnt_len = p.mv_cnt_len;
-      g.sm_count = p.sm_count;
       return dfmv(g, 1, st);
     };
     auto rx = [&](bool tr, const double* B, double* C, int cc) {

@@ -86,3 +86,31 @@ def test_algorithm2_small():
     rho, _ = lda_geneig(X, y, 5, lam, k)
     assert res["status"] in ("converged", "stalled")
     assert np.max(np.abs(res["rho"] - rho) / rho) < 1e-9
+
+
+def test_polar_retraction_variant():
+    """The polar-retraction RCG (Table 1 polar retraction; start normalized by
+    x (x^T B x)^{-1/2}) reaches the same closed form.  Its start is the B-polar
+    factor of x: on the manifold, with x_new^T B x symmetric positive
+    definite; and it agrees with the QR retraction to first order in t."""
+    from oracle import geometry as G
+    P = cca_latent_problem(1500, 12, 9, latent=4, seed=3, latent_scale=[1.0, 0.6, 0.35, 0.2])
+    lam, k = 1e-2, 3
+    Sxx, Syy, Sxy = sigmas(P["X64"], P["Y64"], lam, lam)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((12, k))
+    xn = RC._normalize(x, Sxx, "polar")
+    assert np.max(np.abs(xn.T @ Sxx @ xn - np.eye(k))) < 1e-12
+    S = xn.T @ Sxx @ x
+    assert np.max(np.abs(S - S.T)) < 1e-12 and np.min(np.linalg.eigvalsh(S)) > 0
+    xi = G.proj_tangent(xn, Sxx, np.eye(12), rng.standard_normal((12, k)))
+    for t in (1e-3, 1e-4):
+        d = np.max(np.abs(G.retr_polar(xn, Sxx, t * xi) - G.retr_qr(xn, Sxx, t * xi)))
+        assert d < 50 * t * t * np.max(np.abs(xi)) ** 2 + 1e-13
+    prob = CCAProblem(Sxx, Syy, Sxy, default_mu(k))
+    y0 = rng.standard_normal((9, k))
+    res = RC.rcg(prob, [Sxx, Syy], [x, y0], max_iter=3000, gtol=1e-10, retraction="polar")
+    U, V = res["points"]
+    sig, _, _ = cca_qr(P["X64"], P["Y64"], lam, lam, k)
+    assert res["status"] in ("converged", "stalled")
+    assert np.max(np.abs(np.diag(U.T @ Sxy @ V) - sig) / sig) < 1e-9
