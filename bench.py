@@ -426,6 +426,76 @@ def other_workloads(gb, steps: int = 2):
     return out
 
 
+def batched_workload(gb, count: int = 64, seed: int = 0):
+    """The uneven batched mix: `count` BF16 CCA instances, n log-uniform in
+    [1e4, 2e6], dx, dy uniform over {64, ..., 1024}, k uniform over {1, 5, 10,
+    20} (synth.batch_mix), data drawn on the device, CountSketch s = 4 (dx +
+    dy), lambda 1e-3.  All instances are solved as one batch (one persistent
+    tensor-core launch per iteration for the instances it serves, the others
+    on their own passes) and, for comparison, one after another."""
+    import torch
+    from synth.batch_mix import batch_mix, latent_views_device
+    hbm, _ = peaks()
+    shapes = batch_mix(count, seed=seed)
+    opt = dict(max_iter=1000, gtol=0.0, rtol=RTOL, check_every=CHECK_EVERY, refine=REFINE)
+    plans, data = [], []
+    t0 = time.perf_counter()
+    for i, (n, dx, dy, k) in enumerate(shapes):
+        X, Y = latent_views_device(n, dx, dy, seed=1000 + i)
+        plan = gb.cca_plan(n, dx, dy, k, "bf16", gb.default_options(**opt))
+        gb.cca_precondition(plan, X, Y, 1e-3, 1e-3)
+        plans.append(plan)
+        data.append((X, Y))
+    torch.cuda.synchronize()
+    prep_s = time.perf_counter() - t0
+    batch = gb.Batch(plans)
+    res, rep = gb.batch_solve(batch)  # tunes the schedule, captures the graphs
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res, rep = gb.batch_solve(batch)
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    # the same instances solved one after another
+    e0.record()
+    solo = [gb.cca_solve(p) for p in plans]
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    bytes_i = [n * (dx + dy) * 2 for (n, dx, dy, k) in shapes]
+    passes = [r[3]["passes"] for r in res]
+    moved = float(sum(b * p for b, p in zip(bytes_i, passes)))
+    diff = max(float(torch.max(torch.abs(r[0] - s[0]) / s[0]).item()) for r, s in zip(res, solo))
+    served = [i for i, (n, dx, dy, k) in enumerate(shapes) if max(dx, dy) <= 512 and 2 * k <= 24]
+    gbps = rep["batched_pass_bytes"] / (rep["batched_pass_ms"] * 1e-3) / 1e9 if rep["batched_pass_ms"] > 0 else None
+    out = {
+        "instances": count, "seed": seed, "total_data_GB": sum(bytes_i) / 1e9,
+        "batch_solve_ms": batch_ms, "sequential_solves_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
+        "lockstep_iterations": rep["iterations"],
+        "iterations_mean": float(np.mean([r[3]["iters"] for r in res])),
+        "iterations_max": int(max(r[3]["iters"] for r in res)),
+        "status_ok": int(sum(1 for r in res if r[3]["status"] == gb.OK)),
+        "sigma_max_rel_diff_vs_sequential": diff,
+        "aggregate_GBps_over_solve": moved / (batch_ms * 1e-3) / 1e9,
+        "aggregate_frac_of_hbm": moved / (batch_ms * 1e-3) / 1e9 / hbm,
+        "batched_launch": {"instances": rep["batched_plans"], "clusters": rep["clusters"],
+                           "bytes": rep["batched_pass_bytes"], "ms": rep["batched_pass_ms"],
+                           "GBps": gbps, "frac_of_hbm": gbps / hbm if gbps else None,
+                           "expected_instances": len(served)},
+        "prepare_s": prep_s,
+        "note": "the batched launch serves CCA instances with 2k <= 24 and dx, dy <= 512; the rest (k = 20 or a "
+                "1024-wide view) run their own CUDA-core passes on their graph branches",
+    }
+    batch.close()
+    for p in plans:
+        p.close()
+    del data
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle as it stands on the host cores: every step is one FP64
     solve of the FULL workload by route 2 (oracle.cca.cca_whiten), timed
@@ -581,6 +651,7 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.stop()
     fp64 = None if args.no_fp64_compare else fp64_comparison(gb, P, sig)
     others = None if args.no_other_workloads else other_workloads(gb)
+    batched = None if args.no_batched else batched_workload(gb)
 
     hbm, peak_src = peaks()
     elt = {"bf16": 2, "f32": 4, "f64": 8}[dt]
@@ -622,6 +693,8 @@ def run_ours(args, ws, rank, local):
         line["fp64_gpu"] = fp64
     if others is not None:
         line["other_workloads"] = others
+    if batched is not None:
+        line["batched_uneven_mix"] = batched
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], ref = cpu_baseline(P)
         line["accuracy"] = accuracy_report(P, sig, U, V, ref)
@@ -718,6 +791,8 @@ def main():
                     help="skip the timed solve of the same workload stored in FP64")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the FP32 CCA and FP32 LDA solves")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-mix workload")
+    ap.add_argument("--batched-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--pass-only", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--solve-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default=WORKLOAD, help=argparse.SUPPRESS)
@@ -727,6 +802,14 @@ def main():
         return
     if args.solve_rows:
         run_solve_only(args)
+        return
+    if args.batched_only:
+        import torch
+        import __graft_entry__ as g
+        g.build()
+        import paper_2106_12060_gb300 as gb
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched_uneven_mix": batched_workload(gb)}), flush=True)
         return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -287,6 +287,72 @@ int gbcca_sketch_gram_noalloc(const double* A, int64_t lda, int64_t m, int32_t d
                               void* stream);
 int32_t gbcca_sketch_gram_noalloc_max_d(void);
 
+/* ---------------------------------------------------------------- batches
+ * Several prepared plans solved together.  The paper states one problem at a
+ * time (Alg. 1 / Alg. 2 run per instance); the batch only schedules those
+ * instances on one GPU.  Each plan must have been bound to its data
+ * (cca_precondition / lda_solve's preconditioning through a previous call)
+ * with opt.warm_start on, and stays owned by the caller; its data must stay
+ * valid while the batch exists.  Every iteration, the data passes of the
+ * plans the tensor-core pass serves (CCA, BF16 or FP32 data, 2k <= 24,
+ * dx, dy <= 512) run as ONE persistent launch over a schedule of (instance,
+ * 64-row tile range) segments cut into near-equal work per 2-CTA cluster;
+ * the other plans run their own passes.  Each plan's small kernels run on a
+ * graph branch of their own, and each plan stops on its own rule (its
+ * options); a finished plan leaves the schedule.  The result of every plan
+ * is the one its own cca_solve / lda_solve would give up to the rounding of
+ * its pass. */
+typedef struct gbcca_batch_s* gbcca_batch_t;
+
+typedef struct {
+  int32_t clusters;      /* 2-CTA clusters of the batched launch; 0 (default):
+                            the fastest of a few candidates, timed once per
+                            batch on the plans' start points              */
+  int32_t graphs;        /* 1 (default): batches of iterations replay a
+                            captured CUDA graph; 0: launched one by one    */
+  int32_t batch_iters;   /* iterations per replay (default 8)              */
+} gbcca_batch_options;
+
+typedef struct {
+  int32_t iterations;          /* lockstep iterations run, the qf_B step included */
+  int32_t clusters;            /* clusters of the batched launch                  */
+  int32_t batched_plans;       /* plans whose passes ran in the batched launch    */
+  int32_t reserved;
+  double batched_pass_ms;      /* device time of one batched pass over all of
+                                  them at the chosen schedule (CUDA events)       */
+  double batched_pass_bytes;   /* its algorithmic bytes: sum of n (dx + dy) x the
+                                  element size of each plan's data                */
+} gbcca_batch_report;
+
+/* Fills `opt` with the defaults (clusters 0, graphs 1, batch_iters 8). */
+int gbcca_default_batch_options(gbcca_batch_options* opt);
+
+/* Creates a batch over plans[0 .. count - 1] (host array of handles,
+ * 1 <= count <= 1024, no repeats).  Returns GBCCA_OK, GBCCA_ERR_INVALID_ARG,
+ * GBCCA_ERR_STATE (a plan not bound to data, or without warm start),
+ * GBCCA_ERR_OOM or GBCCA_ERR_CUDA. */
+int gbcca_batch_create(gbcca_batch_t* batch, const gbcca_plan_t* plans, int32_t count,
+                       const gbcca_batch_options* opt);
+
+/* Solves every plan of the batch.  U, V, sigma: host arrays of `count`
+ * device pointers, entry i as for plan i's cca_solve (U dx x k, V dy x k,
+ * sigma k) or lda_solve (W in U, rho in sigma, V unused); infos: host array
+ * of `count` reports or NULL; report: host, or NULL.  Returns GBCCA_OK, the
+ * first plan's GBCCA_ERR_MAXITER (all results still written), or the first
+ * error.  Synchronizes `stream`. */
+int gbcca_batch_solve(gbcca_batch_t batch, double* const* U, double* const* V, double* const* sigma,
+                      gbcca_info* infos, gbcca_batch_report* report, void* stream);
+
+/* One batched data pass alone (every plan of the batch must be served by
+ * the tensor-core pass): for plan i, with Phi_x[i] (dx x 2k) and Phi_y[i]
+ * (dy x 2k), writes G[i] = [X^T W, Y^T W] ((dx + dy) x 4k) and Gram[i] =
+ * W^T W (4k x 4k), W = [X Phi_x, Y Phi_y], as gbcca_fused_pass does for one
+ * plan.  Resets each plan's iteration state.  Synchronizes `stream`. */
+int gbcca_batch_fused_pass(gbcca_batch_t batch, const double* const* Phi_x, const double* const* Phi_y,
+                           double* const* G, double* const* Gram, void* stream);
+
+void gbcca_batch_destroy(gbcca_batch_t batch);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * plans and threads); a host-side counter for profiling. */
 int64_t gbcca_launch_count(void);

@@ -278,3 +278,97 @@ def gbcca_launch_count() -> int:
 
 
 launch_count = gbcca_launch_count
+
+
+def default_batch_options(**kw) -> _lib.BatchOptions:
+    lib = _lib.load()
+    o = _lib.BatchOptions()
+    _lib.check(lib.gbcca_default_batch_options(C.byref(o)), "gbcca_default_batch_options")
+    for key, val in kw.items():
+        setattr(o, key, val)
+    return o
+
+
+class Batch:
+    """Owns a gbcca_batch_t over prepared plans (each bound to its data);
+    keeps the plans alive while it exists."""
+
+    def __init__(self, plans, opt=None):
+        lib = _lib.load()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = C.c_void_p()
+        _lib.check(lib.gbcca_batch_create(C.byref(h), arr, len(self.plans), C.byref(opt) if opt else None),
+                   "gbcca_batch_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle is not None:
+            _lib.load().gbcca_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gbcca_batch_create(plans, opt=None) -> Batch:
+    return Batch(plans, opt)
+
+
+batch_create = gbcca_batch_create
+
+
+def gbcca_batch_solve(batch: Batch, stream=None, allow_maxiter=True):
+    """Solves every plan of the batch.  Returns (results, report): results[i]
+    = (sigma, U, V, info) for a CCA plan, (rho, W, None, info) for an FDA
+    plan; report a dict of the batched launch."""
+    torch = _torch()
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = len(batch.plans)
+    outs = []
+    for p in batch.plans:
+        U = torch.empty(p.dims[0], p.k, dtype=torch.float64, device=dev)
+        V = torch.empty(p.dims[1], p.k, dtype=torch.float64, device=dev) if p.kind == "cca" else None
+        s = torch.empty(p.k, dtype=torch.float64, device=dev)
+        outs.append((s, U, V))
+    Ua = (C.c_void_p * n)(*[o[1].data_ptr() for o in outs])
+    Va = (C.c_void_p * n)(*[o[2].data_ptr() if o[2] is not None else 0 for o in outs])
+    Sa = (C.c_void_p * n)(*[o[0].data_ptr() for o in outs])
+    infos = (Info * n)()
+    rep = _lib.BatchReport()
+    allow = (OK, ERR_MAXITER) if allow_maxiter else (OK,)
+    _lib.check(lib.gbcca_batch_solve(batch.handle, Ua, Va, Sa, infos, C.byref(rep), _stream(stream)),
+               "gbcca_batch_solve", allow)
+    res = [(o[0], o[1], o[2], infos[i].as_dict()) for i, o in enumerate(outs)]
+    report = {f: getattr(rep, f) for f, _ in _lib.BatchReport._fields_ if f != "reserved"}
+    return res, report
+
+
+batch_solve = gbcca_batch_solve
+
+
+def gbcca_batch_fused_pass(batch: Batch, Phi_x, Phi_y, stream=None):
+    """One batched pass: Phi_x[i] (dx_i x 2k_i), Phi_y[i] (dy_i x 2k_i) float64
+    CUDA tensors.  Returns lists (G[i] ((dx + dy) x 4k), Gram[i] (4k x 4k))."""
+    torch = _torch()
+    lib = _lib.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = len(batch.plans)
+    Px = [t.contiguous() for t in Phi_x]
+    Py = [t.contiguous() for t in Phi_y]
+    for i, p in enumerate(batch.plans):
+        _check_dev(f"Phi_x[{i}]", Px[i], torch.float64, p.dims[0], 2 * p.k)
+        _check_dev(f"Phi_y[{i}]", Py[i], torch.float64, p.dims[1], 2 * p.k)
+    G = [torch.empty(sum(p.dims), 4 * p.k, dtype=torch.float64, device=dev) for p in batch.plans]
+    Gram = [torch.empty(4 * p.k, 4 * p.k, dtype=torch.float64, device=dev) for p in batch.plans]
+    arr = lambda ts: (C.c_void_p * n)(*[t.data_ptr() for t in ts])  # noqa: E731
+    _lib.check(lib.gbcca_batch_fused_pass(batch.handle, arr(Px), arr(Py), arr(G), arr(Gram), _stream(stream)),
+               "gbcca_batch_fused_pass")
+    return G, Gram
+
+
+batch_fused_pass = gbcca_batch_fused_pass

@@ -36,6 +36,25 @@ class Options(C.Structure):
     ]
 
 
+class BatchOptions(C.Structure):
+    _fields_ = [
+        ("clusters", C.c_int32),
+        ("graphs", C.c_int32),
+        ("batch_iters", C.c_int32),
+    ]
+
+
+class BatchReport(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32),
+        ("clusters", C.c_int32),
+        ("batched_plans", C.c_int32),
+        ("reserved", C.c_int32),
+        ("batched_pass_ms", C.c_double),
+        ("batched_pass_bytes", C.c_double),
+    ]
+
+
 class Info(C.Structure):
     _fields_ = [
         ("iters", C.c_int32),
@@ -75,6 +94,14 @@ SIGNATURES = {
     "gbcca_sketch_gram_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
                                             C.c_void_p]),
     "gbcca_sketch_gram_noalloc_max_d": (C.c_int32, []),
+    "gbcca_default_batch_options": (C.c_int, [C.POINTER(BatchOptions)]),
+    "gbcca_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
+                                     C.POINTER(BatchOptions)]),
+    "gbcca_batch_solve": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                    C.POINTER(C.c_void_p), C.POINTER(Info), C.POINTER(BatchReport), C.c_void_p]),
+    "gbcca_batch_fused_pass": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "gbcca_batch_destroy": (None, [C.c_void_p]),
     "gbcca_launch_count": (C.c_int64, []),
     "gbcca_plan_destroy": (None, [C.c_void_p]),
     "gbcca_status_string": (C.c_char_p, [C.c_int]),

@@ -45,6 +45,9 @@
 // Every mbarrier wait is bounded in time; on expiry the CTA records an error
 // code, waits (bounded) for its own copies and MMAs, frees TMEM and leaves
 // after a cluster barrier (no remote access can target an exited CTA).
+#include <cstring>
+#include <vector>
+
 #include "tc_ptx.cuh"
 
 namespace gbcca {
@@ -97,7 +100,9 @@ struct Lay {
   static constexpr int kD1Free = kD1Full + 2, kEpiSync = kD1Free + 2, kWReady = kEpiSync + 1;  // [2], 1, [2]
   static constexpr int kWPeer = kWReady + 2, kWFree = kWPeer + 2, kGDone = kWFree + 2;      // [2], [2], 1
   static constexpr int kFinal = kGDone + 1;                         // [3]: one per MMA-issuing thread
-  static constexpr int kPhiFull = kFinal + 3, kNumBars = kPhiFull + 1;  // Phi image in shared memory
+  static constexpr int kPhiFull = kFinal + 3;  // Phi image in shared memory
+  static constexpr int kGFree = kPhiFull + 1;   // G drained (128 arrivals)
+  static constexpr int kPhiFree = kGFree + 1, kNumBars = kPhiFree + 1;  // GEMM 1 done with a segment's Phi
   static_assert(kStages >= 2 * kTileSlots, "two resident tiles");
   static_assert(kN1 <= kTW && kD1Cols <= kTW, "W buffers in TMEM");
   static_assert(kN2 % 16 == 0 && kTG + kTileSlots * kN2 <= (int)kTmemCols, "G accumulators in TMEM");
@@ -107,13 +112,38 @@ struct Lay {
   static_assert(kSmemBytes <= kMaxSmem, "shared memory");
 };
 
+// One instance of a batched pass (device memory; the tensor maps are read by
+// the TMA unit from there; CUtensorMap carries its own 128-byte alignment).
+struct Inst {
+  CUtensorMap map[2];      // views X, Y (BF16 data, or the interleaved hi/lo copy)
+  const uint8_t* phi_img;  // [view][K-box][2 kH1][128 B], pre-swizzled
+  float* partG;            // [slab][D][4k] partials of this instance
+  const int* done;         // the instance's convergence flag: skip it when set
+  int64_t slab;            // floats per partial slab (D * 4k)
+  int d[2];
+  int pairs[2];
+  int k2;
+  int pair_sum;
+};
+
+// A contiguous range of one instance's 64-row tiles, processed by one cluster
+// into partial slab `slab` of that instance.
+struct Seg {
+  int inst;
+  int first;
+  int count;
+  int slab;
+};
+
 struct Args {
+  // one instance (insts == nullptr): cluster c takes tiles c, c + clusters,
+  // ... of the pair of matrices in the kernel's tensor-map parameters
   int64_t n;
   int d[2];
   int pairs[2];
   int k2;        // columns of Phi per view (2k)
   int ntiles;
-  const uint8_t* phi_img;  // [view][K-box][48][128 B], pre-swizzled
+  const uint8_t* phi_img;  // [view][K-box][2 kH1][128 B], pre-swizzled
   float* partG;            // [cluster][D][4k]
   int* err;
   const int* done;
@@ -121,7 +151,63 @@ struct Args {
                            // hi and lo parts of one data row (FP32 data): W of the
                            // row is the sum of the two product rows, and both rows
                            // of GEMM 2's operand carry it
+  // several instances (insts != nullptr): cluster c takes the segments
+  // seg_off[c] .. seg_off[c + 1] - 1 in order
+  const Inst* insts;
+  const Seg* segs;
+  const int* seg_off;      // [clusters + 1]
 };
+
+// What one CTA needs of the segment it is on.
+struct SegView {
+  const CUtensorMap* map;  // this CTA's view
+  const uint8_t* phi;      // this view's Phi image
+  float* out;              // partial slab of the segment
+  int first, stride, count;
+  int d0, d1, npairs, k2, pair_sum;
+  bool skip;
+};
+
+__device__ __forceinline__ int seg_count(const Args& a, int cid, int ncl) {
+  if (a.insts == nullptr) return 1;
+  return a.seg_off[cid + 1] - a.seg_off[cid];
+}
+
+__device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tmx, const CUtensorMap* tmy, int view,
+                                            int cid, int ncl, int s) {
+  SegView v;
+  if (a.insts == nullptr) {
+    v.map = view == 0 ? tmx : tmy;
+    v.phi = a.phi_img + view * kPhiView;
+    v.d0 = a.d[0];
+    v.d1 = a.d[1];
+    v.out = a.partG + (int64_t)cid * (v.d0 + v.d1) * (2 * a.k2);
+    v.first = cid;
+    v.stride = ncl;
+    v.count = (a.ntiles - cid + ncl - 1) / ncl;
+    v.npairs = a.pairs[view];
+    v.k2 = a.k2;
+    v.pair_sum = a.pair_sum;
+    v.skip = false;
+  } else {
+    const Seg sg = a.segs[a.seg_off[cid] + s];
+    const Inst* I = a.insts + sg.inst;
+    v.map = &I->map[view];
+    v.phi = I->phi_img + view * kPhiView;
+    v.out = I->partG + (int64_t)sg.slab * I->slab;
+    v.d0 = I->d[0];
+    v.d1 = I->d[1];
+    v.first = sg.first;
+    v.stride = 1;
+    v.count = sg.count;
+    v.npairs = I->pairs[view];
+    v.k2 = I->k2;
+    v.pair_sum = I->pair_sum;
+    v.skip = I->done != nullptr && *I->done != 0;
+  }
+  if (v.skip) v.count = 0;
+  return v;
+}
 
 template <int kH1>
 __global__ void __launch_bounds__(256, 1)
@@ -130,7 +216,9 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   constexpr int kStages = L::kStages;
   constexpr int kFull = L::kFull, kEmpty = L::kEmpty, kD1Full = L::kD1Full, kD1Free = L::kD1Free;
   constexpr int kEpiSync = L::kEpiSync, kWReady = L::kWReady, kWPeer = L::kWPeer, kWFree = L::kWFree;
-  constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kPhiFull = L::kPhiFull, kNumBars = L::kNumBars;
+  constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kPhiFull = L::kPhiFull, kGFree = L::kGFree;
+  constexpr int kPhiFree = L::kPhiFree;
+  constexpr int kNumBars = L::kNumBars;
   constexpr int kTG = L::kTG;
   if (a.done != nullptr && *a.done) return;  // uniform over the cluster: no remote access yet
   extern __shared__ uint8_t smem_raw[];
@@ -145,16 +233,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   const int view = (int)cluster_ctarank();   // 0: X, 1: Y
   const uint32_t peer = 1u - (uint32_t)view;
   const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
-  const int npairs = a.pairs[view];
-  // GEMM 1 issuers: warp 1 takes pairs [0, split), warp 2 (after allocating
-  // TMEM) pairs [split, npairs) into the second accumulator
-  const int split = L::kNAcc == 2 ? (npairs + 1) / 2 : npairs;
-  const int nissue1 = split < npairs ? 2 : 1;
-  const int k4 = 2 * a.k2;
+  const int nseg = seg_count(a, cid, ncl);
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
-  // zero the W operands (the own view's Phi image arrives later by a bulk
-  // copy that the producer issues ahead of the first tile)
+  // zero the W operands (each view's Phi image arrives by bulk copies that
+  // the producer issues ahead of the first tile of each segment)
   {
     uint4* wz = reinterpret_cast<uint4*>(ws);
     for (int i = threadIdx.x; i < 2 * L::kWBuf / 16; i += blockDim.x) wz[i] = make_uint4(0, 0, 0, 0);
@@ -165,7 +248,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       mbar_init(bar(kEmpty + s), 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(bar(kD1Full + b), nissue1);  // one commit per GEMM 1 issuer
+      mbar_init(bar(kD1Full + b), L::kNAcc);  // one arrival per GEMM 1 issuer
       mbar_init(bar(kD1Free + b), 128);
       mbar_init(bar(kWReady + b), 1);
       mbar_init(bar(kWPeer + b), 1);   // + the peer's bytes
@@ -173,6 +256,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     }
     mbar_init(bar(kEpiSync), 128);
     mbar_init(bar(kGDone), 1);
+    mbar_init(bar(kGFree), 128);
+    mbar_init(bar(kPhiFree), L::kNAcc);  // one arrival per GEMM 1 issuer
     mbar_init(bar(kFinal), 1);
     mbar_init(bar(kFinal + 1), 1);
     mbar_init(bar(kFinal + 2), 1);
@@ -192,43 +277,48 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   cluster_sync();  // both CTAs' barriers and W operands are initialised
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int my_tiles = (a.ntiles - cid + ncl - 1) / ncl;
-  const int nitems = my_tiles * npairs;
 
+  // Every role walks the same segments and tiles; jg counts the tiles and ig
+  // the (tile, pair) items this CTA has processed (barrier phases and ring
+  // slots run on across segments), sp the segments with tiles.
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
     bool ok = true;
     int last_use[kStages];
     for (int s = 0; s < kStages; ++s) last_use[s] = -1;
-    const CUtensorMap* map = view == 0 ? &tmx : &tmy;
-    if (nitems > 0) {
-      // own view's Phi image (GEMM 1's B operand), one bulk copy per K-box;
-      // GEMM 1 waits for it, so no copy is left in flight at exit
+    int jg = 0, ig = 0, sp = 0;
+    for (int s = 0; s < nseg && ok; ++s) {
+      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+      if (sv.count == 0) continue;
+      // the Phi image is rewritten only after every GEMM 1 MMA of the
+      // previous segment has completed (its issuers signal that once per
+      // segment; the barrier of a tile could already be two phases behind
+      // this thread, whose parity test would then pass too early)
+      if (sp > 0 && !(ok = mbar_wait(bar(kPhiFree), (sp - 1) & 1, abort_flag))) break;
+      // this segment's Phi image (GEMM 1's B operand), one bulk copy per K-box
       const uint32_t pb = bar(kPhiFull);
       mbar_expect_tx(pb, L::kPhiBytes);
-      for (int kb = 0; kb < 8; ++kb)
-        bulk_g2s(smem_u32(phi_s + kb * L::kKBox1), a.phi_img + view * kPhiView + kb * L::kKBox1, L::kKBox1, pb);
-    }
-    for (int it = 0; it < nitems; ++it) {
-      const int j = it / npairs, p = it - j * npairs;
-      const int row0 = (cid + j * ncl) * kRows;
-      const int slot = it % kStages, use = it / kStages;
-      if (!mbar_wait(bar(kEmpty + slot), (use & 1) ^ 1, abort_flag)) {
-        ok = false;
-        break;
+      for (int kb = 0; kb < 8; ++kb) bulk_g2s(smem_u32(phi_s + kb * L::kKBox1), sv.phi + kb * L::kKBox1, L::kKBox1, pb);
+      ++sp;
+      for (int t = 0; t < sv.count && ok; ++t, ++jg) {
+        const int row0 = (sv.first + t * sv.stride) * kRows;
+        for (int p = 0; p < sv.npairs; ++p, ++ig) {
+          const int slot = ig % kStages, use = ig / kStages;
+          if (!(ok = mbar_wait(bar(kEmpty + slot), (use & 1) ^ 1, abort_flag))) break;
+          const uint32_t fb = bar(kFull + slot);
+          mbar_expect_tx(fb, kSlot);
+          const uint32_t dst = smem_u32(ring + slot * kSlot);
+          tma_load_2d(dst, sv.map, 128 * p, row0, fb);
+          tma_load_2d(dst + kBox, sv.map, 128 * p + 64, row0, fb);
+          last_use[slot] = use;
+        }
       }
-      const uint32_t fb = bar(kFull + slot);
-      mbar_expect_tx(fb, kSlot);
-      const uint32_t dst = smem_u32(ring + slot * kSlot);
-      tma_load_2d(dst, map, 128 * p, row0, fb);
-      tma_load_2d(dst + kBox, map, 128 * p + 64, row0, fb);
-      last_use[slot] = use;
     }
     if (!ok) {
       // wait (bounded) for the copies this thread issued before leaving
-      if (nitems > 0) {
+      if (sp > 0) {
         const long long t0 = clock64();
-        while (!mbar_try(bar(kPhiFull), 0) && clock64() - t0 < kTimeout) {
+        while (!mbar_try(bar(kPhiFull), (sp - 1) & 1) && clock64() - t0 < kTimeout) {
         }
       }
       for (int s = 0; s < kStages; ++s) {
@@ -238,7 +328,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         }
       }
     }
-  } else if ((warp == 1 || warp == 3 || (warp == 2 && nissue1 == 2)) && lane == 0) {
+  } else if ((warp == 1 || warp == 3 || (warp == 2 && L::kNAcc == 2)) && lane == 0) {
     // ------------------------------------------------------------ MMA issuers
     // warps 1 and 2: GEMM 1 of every tile (half of the pairs each when there
     // are two accumulators); warp 3: GEMM 2 of every tile.  Separate issuers
@@ -247,6 +337,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     constexpr uint32_t id1 = idesc_bf16(64, L::kN1, 0, 0);
     constexpr uint32_t id2 = idesc_bf16(128, L::kN2, 1, 0);
     bool ok = true;
+    int issued = 0;  // MMAs this thread has issued
+    int jg = 0, ig = 0, sp = 0;
     // One thread issues an MMA only about every 50 cycles at best, which for
     // these small shapes is slower than the tensor pipe; the issue loops
     // therefore do no descriptor arithmetic beyond one add of a compile-time
@@ -254,75 +346,111 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     // and every operand address here is below 2^18).
     if (warp == 1 || warp == 2) {
       const int acc_i = warp - 1;  // accumulator of this issuer
-      const int pb = acc_i == 0 ? 0 : split, pe = acc_i == 0 ? split : npairs;
       const uint64_t bdesc0 = sdesc(smem_u32(phi_s), 16, 1024);
-      if (my_tiles > 0) ok = mbar_wait(bar(kPhiFull), 0, abort_flag);
-      for (int j = 0; j < my_tiles && ok; ++j) {
-        const int b = j & 1;
-        // W buffer b was last read by the epilogue of tile j - 2
-        if (j >= 2 && !(ok = mbar_wait(bar(kD1Free + b), ((j - 2) >> 1) & 1, abort_flag))) break;
-        tc_fence_after();
-        const uint32_t d1 = tmem + (uint32_t)((L::kNAcc * b + acc_i) * kTW);
-        for (int p = pb; p < pe; ++p) {
-          const int it = j * npairs + p;
-          const int slot = it % kStages, use = it / kStages;
-          if (!(ok = mbar_wait(bar(kFull + slot), use & 1, abort_flag))) break;
+      for (int s = 0; s < nseg && ok; ++s) {
+        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+        if (sv.count == 0) continue;
+        const int npairs = sv.npairs;
+        const int split = L::kNAcc == 2 ? (npairs + 1) / 2 : npairs;
+        const int pb = acc_i == 0 ? 0 : split, pe = acc_i == 0 ? split : npairs;
+        if (!(ok = mbar_wait(bar(kPhiFull), sp & 1, abort_flag))) break;
+        ++sp;
+        for (int t = 0; t < sv.count && ok; ++t, ++jg, ig += npairs) {
+          const int b = jg & 1;
+          // W buffer b was last read by the epilogue of tile jg - 2
+          if (jg >= 2 && !(ok = mbar_wait(bar(kD1Free + b), ((jg - 2) >> 1) & 1, abort_flag))) break;
           tc_fence_after();
-          const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), 16, 1024);
-          const uint64_t bd0 = bdesc0 + (uint64_t)((2 * p * L::kKBox1) >> 4);
-          // K steps of 16 columns: box s / 4 of the slot, 32-byte step s % 4
-          // inside its 128-byte swizzled rows
+          const uint32_t d1 = tmem + (uint32_t)((L::kNAcc * b + acc_i) * kTW);
+          for (int p = pb; p < pe; ++p) {
+            const int it = ig + p;
+            const int slot = it % kStages, use = it / kStages;
+            if (!(ok = mbar_wait(bar(kFull + slot), use & 1, abort_flag))) break;
+            tc_fence_after();
+            const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), 16, 1024);
+            const uint64_t bd0 = bdesc0 + (uint64_t)((2 * p * L::kKBox1) >> 4);
+            // K steps of 16 columns: box s / 4 of the slot, 32-byte step s % 4
+            // inside its 128-byte swizzled rows
 #define GB_G1_MMA(s, acc)                                                                        \
   mma_bf16(d1, ad0 + (uint64_t)((((s) >> 2) * kBox + ((s) & 3) * 32) >> 4),                      \
            bd0 + (uint64_t)((((s) >> 2) * L::kKBox1 + ((s) & 3) * 32) >> 4), id1, acc)
-          if (p == pb) {
-            GB_G1_MMA(0, 0u);
-          } else {
-            GB_G1_MMA(0, 1u);
-          }
-          GB_G1_MMA(1, 1u);
-          GB_G1_MMA(2, 1u);
-          GB_G1_MMA(3, 1u);
-          GB_G1_MMA(4, 1u);
-          GB_G1_MMA(5, 1u);
-          GB_G1_MMA(6, 1u);
-          GB_G1_MMA(7, 1u);
+            if (p == pb) {
+              GB_G1_MMA(0, 0u);
+            } else {
+              GB_G1_MMA(0, 1u);
+            }
+            GB_G1_MMA(1, 1u);
+            GB_G1_MMA(2, 1u);
+            GB_G1_MMA(3, 1u);
+            GB_G1_MMA(4, 1u);
+            GB_G1_MMA(5, 1u);
+            GB_G1_MMA(6, 1u);
+            GB_G1_MMA(7, 1u);
 #undef GB_G1_MMA
+            issued += 8;
+          }
+          if (!ok) break;
+          // an issuer without pairs in this segment arrives plainly; the
+          // barrier then completes with the other issuer's MMAs
+          if (pe > pb) {
+            mma_commit(bar(kD1Full + b));
+          } else {
+            mbar_arrive(bar(kD1Full + b));
+          }
         }
         if (!ok) break;
-        mma_commit(bar(kD1Full + b));
+        // release the Phi image when a later segment will load its own
+        bool more = false;
+        for (int s2 = s + 1; s2 < nseg && !more; ++s2)
+          more = seg_view(a, &tmx, &tmy, view, cid, ncl, s2).count > 0;
+        if (more) {
+          if (pe > pb) {
+            mma_commit(bar(kPhiFree));
+          } else {
+            mbar_arrive(bar(kPhiFree));
+          }
+        }
       }
     } else {
-      for (int j = 0; j < my_tiles && ok; ++j) {
-        const int b = j & 1;
-        // both halves of this tile's W operand: ours and the peer's
-        mbar_expect_tx(bar(kWPeer + b), 2 * L::kWHalf);
-        if (!(ok = mbar_wait(bar(kWReady + b), (j >> 1) & 1, abort_flag))) break;
-        if (!(ok = mbar_wait(bar(kWPeer + b), (j >> 1) & 1, abort_flag))) break;
+      for (int s = 0; s < nseg && ok; ++s) {
+        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+        if (sv.count == 0) continue;
+        const int npairs = sv.npairs;
+        // the epilogue has drained the G accumulators of the previous segment
+        if (sp > 0 && !(ok = mbar_wait(bar(kGFree), (sp - 1) & 1, abort_flag))) break;
         tc_fence_after();
-        const uint64_t wd0 = sdesc(smem_u32(ws + b * L::kWBuf), 16, 1024);
-        const uint32_t acc0 = j > 0 ? 1u : 0u;
-        for (int p = 0; p < npairs; ++p) {
-          const int it = j * npairs + p;
-          const int slot = it % kStages;
-          const uint32_t g = tmem + (uint32_t)(kTG + p * L::kN2);
-          const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), kBox, 1024);
-          // B = the hi rows and then the lo rows of W (N = kN2): the tile's
-          // columns are read once per K step of 16 rows (A: 8-row groups of
-          // 1024 bytes, B: 32-byte steps inside the swizzled rows); the lo
-          // products accumulate in their own columns of G
-          mma_bf16(g, ad0, wd0, id2, acc0);
-          mma_bf16(g, ad0 + (uint64_t)(2048 >> 4), wd0 + (uint64_t)(32 >> 4), id2, 1u);
-          mma_bf16(g, ad0 + (uint64_t)(4096 >> 4), wd0 + (uint64_t)(64 >> 4), id2, 1u);
-          mma_bf16(g, ad0 + (uint64_t)(6144 >> 4), wd0 + (uint64_t)(96 >> 4), id2, 1u);
-          mma_commit(bar(kEmpty + slot));
+        ++sp;
+        for (int t = 0; t < sv.count && ok; ++t, ++jg, ig += npairs) {
+          const int b = jg & 1;
+          // both halves of this tile's W operand: ours and the peer's
+          mbar_expect_tx(bar(kWPeer + b), 2 * L::kWHalf);
+          if (!(ok = mbar_wait(bar(kWReady + b), (jg >> 1) & 1, abort_flag))) break;
+          if (!(ok = mbar_wait(bar(kWPeer + b), (jg >> 1) & 1, abort_flag))) break;
+          tc_fence_after();
+          const uint64_t wd0 = sdesc(smem_u32(ws + b * L::kWBuf), 16, 1024);
+          const uint32_t acc0 = t > 0 ? 1u : 0u;
+          for (int p = 0; p < npairs; ++p) {
+            const int it = ig + p;
+            const int slot = it % kStages;
+            const uint32_t g = tmem + (uint32_t)(kTG + p * L::kN2);
+            const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), kBox, 1024);
+            // B = the hi rows and then the lo rows of W (N = kN2): the tile's
+            // columns are read once per K step of 16 rows (A: 8-row groups of
+            // 1024 bytes, B: 32-byte steps inside the swizzled rows); the lo
+            // products accumulate in their own columns of G
+            mma_bf16(g, ad0, wd0, id2, acc0);
+            mma_bf16(g, ad0 + (uint64_t)(2048 >> 4), wd0 + (uint64_t)(32 >> 4), id2, 1u);
+            mma_bf16(g, ad0 + (uint64_t)(4096 >> 4), wd0 + (uint64_t)(64 >> 4), id2, 1u);
+            mma_bf16(g, ad0 + (uint64_t)(6144 >> 4), wd0 + (uint64_t)(96 >> 4), id2, 1u);
+            mma_commit(bar(kEmpty + slot));
+            issued += 4;
+          }
+          // both CTAs learn that this CTA's GEMM 2 has consumed buffer b
+          mma_commit_mc(bar(kWFree + b), (uint16_t)0x3);
         }
-        // both CTAs learn that this CTA's GEMM 2 has consumed buffer b
-        mma_commit_mc(bar(kWFree + b), (uint16_t)0x3);
+        if (ok) mma_commit(bar(kGDone));  // this segment's G is complete
       }
-      if (ok) mma_commit(bar(kGDone));
     }
-    if (!ok) {
+    if (!ok && issued > 0) {
       // let the MMAs this thread issued finish before the CTA frees its memory
       const int f = kFinal + (warp == 3 ? 1 : (warp == 2 ? 2 : 0));
       mma_commit(bar(f));
@@ -334,126 +462,136 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     // ------------------------------------------------------------ epilogue
     const int q = warp - 4;             // TMEM lane quarter
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    const int rg = 32 * q + lane;       // Z column of a G pair block (M = 128 layout)
     bool ok = true;
-    for (int j = 0; j < my_tiles && ok; ++j) {
-      const int b = j & 1;
-      if (!(ok = mbar_wait(bar(kD1Full + b), (j >> 1) & 1, abort_flag))) break;
-      tc_fence_after();
-      float d1[L::kD1Cols];
-#pragma unroll
-      for (int c = 0; c < L::kD1Cols; c += 16)
-        tmem_ld16(tmem + lane_off + (uint32_t)(L::kNAcc * b * kTW + c), &d1[c]);
-      if (nissue1 == 2) {
-        // second GEMM 1 accumulator (the other half of the pairs)
-        float d2[L::kD1Cols];
+    int jg = 0, sp = 0;
+    for (int s = 0; s < nseg && ok; ++s) {
+      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+      if (sv.count == 0) continue;
+      const int npairs = sv.npairs;
+      const bool two_acc = L::kNAcc == 2 && (npairs + 1) / 2 < npairs;
+      for (int t = 0; t < sv.count; ++t, ++jg) {
+        const int b = jg & 1;
+        if (!(ok = mbar_wait(bar(kD1Full + b), (jg >> 1) & 1, abort_flag))) break;
+        tc_fence_after();
+        float d1[L::kD1Cols];
 #pragma unroll
         for (int c = 0; c < L::kD1Cols; c += 16)
-          tmem_ld16(tmem + lane_off + (uint32_t)((L::kNAcc * b + 1) * kTW + c), &d2[c]);
+          tmem_ld16(tmem + lane_off + (uint32_t)(L::kNAcc * b * kTW + c), &d1[c]);
+        if (two_acc) {
+          // second GEMM 1 accumulator (the other half of the pairs)
+          float d2[L::kD1Cols];
+#pragma unroll
+          for (int c = 0; c < L::kD1Cols; c += 16)
+            tmem_ld16(tmem + lane_off + (uint32_t)((L::kNAcc * b + 1) * kTW + c), &d2[c]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < L::kD1Cols; ++c) d1[c] += d2[c];
+        }
         tmem_ld_wait();
+        tc_fence_before();
+        mbar_arrive(bar(kD1Free + b));
+        // both CTAs' GEMM 2 of tile jg - 2 must be done with both halves of buffer b
+        if (jg >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((jg - 2) >> 1) & 1, abort_flag))) break;
+        uint8_t* wb = ws + b * L::kWBuf;
+        {
+          // W_v row rr = hi part (TMEM column c) + lo part (column kH1 + c),
+          // c < 2k.  Lanes 0..15 hold the rows (M = 64 layout, rows 16 q ..
+          // 16 q + 15).  Lanes 0..15 convert column c, lanes 16..31 column
+          // c + kH1/2 of the same rows (by shuffle); then even lanes store the
+          // bf16 pair of rows (rr, rr + 1), which are adjacent in the K-major
+          // operand.  Rows 2k .. kH1 - 1 of the operand hold zeros or values
+          // of an earlier segment: they only reach G columns that are not
+          // drained.
+          constexpr int kSplit = kH1 / 2;
+          const bool upper = lane >= 16;
+          const int rr = 16 * q + (lane & 15);
+          // in phases over all columns, so that the shuffles of different
+          // columns are in flight together
+          float w[kSplit];
+          uint32_t hs[kSplit], ls[kSplit];
 #pragma unroll
-        for (int c = 0; c < L::kD1Cols; ++c) d1[c] += d2[c];
-      }
-      tmem_ld_wait();
-      tc_fence_before();
-      mbar_arrive(bar(kD1Free + b));
-      // both CTAs' GEMM 2 of tile j - 2 must be done with both halves of buffer b
-      if (j >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((j - 2) >> 1) & 1, abort_flag))) break;
-      uint8_t* wb = ws + b * L::kWBuf;
-      {
-        // W_v row rr = hi part (TMEM column c) + lo part (column kH1 + c),
-        // c < 2k.  Lanes 0..15 hold the rows (M = 64 layout, rows 16 q ..
-        // 16 q + 15).  Lanes 0..15 convert column c, lanes 16..31 column
-        // c + kH1/2 of the same rows (by shuffle); then even lanes store the
-        // bf16 pair of rows (rr, rr + 1), which are adjacent in the K-major
-        // operand.
-        constexpr int kSplit = kH1 / 2;
-        const bool upper = lane >= 16;
-        const int rr = 16 * q + (lane & 15);
-        // in phases over all columns, so that the shuffles of different
-        // columns are in flight together
-        float w[kSplit];
-        uint32_t hs[kSplit], ls[kSplit];
+          for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = d1[c0 + kSplit] + d1[kH1 + c0 + kSplit];
 #pragma unroll
-        for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = d1[c0 + kSplit] + d1[kH1 + c0 + kSplit];
-#pragma unroll
-        for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
-#pragma unroll
-        for (int c0 = 0; c0 < kSplit; ++c0) {
-          float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
-          // FP32 data: the data row's W = hi-row product + lo-row product
-          // (adjacent rows sit in adjacent lanes; a + b == b + a, so both
-          // lanes hold the same value)
-          if (a.pair_sum) x += __shfl_xor_sync(0xffffffffu, x, 1);
-          const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-          hs[c0] = __bfloat16_as_ushort(hi);
-          ls[c0] = __bfloat16_as_ushort(lo);
-        }
-#pragma unroll
-        for (int c0 = 0; c0 < kSplit; ++c0) {
-          hs[c0] |= __shfl_down_sync(0xffffffffu, hs[c0], 1) << 16;
-          ls[c0] |= __shfl_down_sync(0xffffffffu, ls[c0], 1) << 16;
-        }
-        if ((lane & 1) == 0) {
+          for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
 #pragma unroll
           for (int c0 = 0; c0 < kSplit; ++c0) {
-            const int c = upper ? c0 + kSplit : c0;
-            if (c < a.k2) {
-              const uint32_t off = swz(view * L::kHalf + c, rr);
-              *reinterpret_cast<uint32_t*>(wb + off) = hs[c0];
-              *reinterpret_cast<uint32_t*>(wb + L::kWs + off) = ls[c0];
+            float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
+            // FP32 data: the data row's W = hi-row product + lo-row product
+            // (adjacent rows sit in adjacent lanes; a + b == b + a, so both
+            // lanes hold the same value)
+            if (sv.pair_sum) x += __shfl_xor_sync(0xffffffffu, x, 1);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+            hs[c0] = __bfloat16_as_ushort(hi);
+            ls[c0] = __bfloat16_as_ushort(lo);
+          }
+#pragma unroll
+          for (int c0 = 0; c0 < kSplit; ++c0) {
+            hs[c0] |= __shfl_down_sync(0xffffffffu, hs[c0], 1) << 16;
+            ls[c0] |= __shfl_down_sync(0xffffffffu, ls[c0], 1) << 16;
+          }
+          if ((lane & 1) == 0) {
+#pragma unroll
+            for (int c0 = 0; c0 < kSplit; ++c0) {
+              const int c = upper ? c0 + kSplit : c0;
+              if (c < sv.k2) {
+                const uint32_t off = swz(view * L::kHalf + c, rr);
+                *reinterpret_cast<uint32_t*>(wb + off) = hs[c0];
+                *reinterpret_cast<uint32_t*>(wb + L::kWs + off) = ls[c0];
+              }
             }
           }
         }
-      }
-      fence_proxy_async();
-      mbar_arrive(bar(kEpiSync));
-      if (threadIdx.x == 128) {
-        // all rows written: push this view's rows (hi and lo) into the peer's
-        // buffer b, then release our own GEMM 2
-        if (!(ok = mbar_wait(bar(kEpiSync), j & 1, abort_flag))) break;
-        const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
+        fence_proxy_async();
+        mbar_arrive(bar(kEpiSync));
+        if (threadIdx.x == 128) {
+          // all rows written: push this view's rows (hi and lo) into the peer's
+          // buffer b, then release our own GEMM 2
+          if (!(ok = mbar_wait(bar(kEpiSync), jg & 1, abort_flag))) break;
+          const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t src = smem_u32(wb + h * L::kWs + view * L::kWHalf);
-          bulk_to_peer(map_peer(src, peer), src, L::kWHalf, pbar);
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t src = smem_u32(wb + h * L::kWs + view * L::kWHalf);
+            bulk_to_peer(map_peer(src, peer), src, L::kWHalf, pbar);
+          }
+          mbar_arrive(bar(kWReady + b));
         }
-        mbar_arrive(bar(kWReady + b));
       }
-    }
-    const uint32_t g_lane_off = lane_off;
-    const int rg = 32 * q + lane;       // Z column of a G pair block (M = 128 layout)
-    if (ok && my_tiles > 0 && mbar_wait(bar(kGDone), 0, abort_flag)) {
+      if (!ok) break;
+      // this segment's G: drain to its partial slab, then free the
+      // accumulators for the next segment's GEMM 2
+      if (!(ok = mbar_wait(bar(kGDone), sp & 1, abort_flag))) break;
       tc_fence_after();
-      const int D0 = a.d[0];
-      const int D = a.d[0] + a.d[1];
-      float* out = a.partG + (int64_t)cid * D * k4;
-      for (int p = 0; p < npairs; ++p) {
-        float g[L::kN2];
+      {
+        const int D = sv.d0 + sv.d1;
+        const int k4 = 2 * sv.k2;
+        const int dv = view == 0 ? sv.d0 : sv.d1;
+        for (int p = 0; p < npairs; ++p) {
+          float g[L::kN2];
 #pragma unroll
-        for (int c = 0; c < L::kN2; c += 16) tmem_ld16(tmem + g_lane_off + (uint32_t)(kTG + p * L::kN2 + c), &g[c]);
-        tmem_ld_wait();
-        const int col = 128 * p + rg;
-        if (col < a.d[view]) {
-          float* o = out + (int64_t)(view * D0 + col) * k4;
+          for (int c = 0; c < L::kN2; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(kTG + p * L::kN2 + c), &g[c]);
+          tmem_ld_wait();
+          const int col = 128 * p + rg;
+          if (col < dv) {
+            float* o = sv.out + (int64_t)(view * sv.d0 + col) * k4;
 #pragma unroll
-          for (int c = 0; c < L::kNW; ++c) {
-            const int vv = c / L::kHalf, cc = c - vv * L::kHalf;
-            if (cc < a.k2) o[vv * a.k2 + cc] = g[c] + g[L::kNW + c];  // hi + lo products
+            for (int c = 0; c < L::kNW; ++c) {
+              const int vv = c / L::kHalf, cc = c - vv * L::kHalf;
+              if (cc < sv.k2) o[vv * sv.k2 + cc] = g[c] + g[L::kNW + c];  // hi + lo products
+            }
           }
         }
+        (void)D;
       }
-      // the peer's last end-of-GEMM-2 signals (tiles T - 2 and T - 1, not
+      tc_fence_before();
+      mbar_arrive(bar(kGFree));
+      ++sp;
+    }
+    if (ok) {
+      // the peer's last end-of-GEMM-2 signals (tiles jg - 2 and jg - 1, not
       // waited in the loop) must have reached us before we leave
-      for (int j = std::max(0, my_tiles - 2); j < my_tiles; ++j)
-        mbar_wait(bar(kWFree + (j & 1)), (j >> 1) & 1, abort_flag);
-    } else if (my_tiles > 0) {
-      // rows of a CTA that stopped early are not trustworthy: zero them so the
-      // reduction stays finite; the error flag reports the failure
-      const int D0 = a.d[0];
-      const int D = a.d[0] + a.d[1];
-      float* out = a.partG + (int64_t)cid * D * k4 + (int64_t)view * D0 * k4;
-      for (int e = threadIdx.x - 128; e < a.d[view] * k4; e += 128) out[e] = 0.f;
+      for (int j = max(0, jg - 2); j < jg; ++j) mbar_wait(bar(kWFree + (j & 1)), (j >> 1) & 1, abort_flag);
     }
     tc_fence_before();
   }
@@ -473,7 +611,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
 // element of Phi (both views in one launch); the padding of the image is
 // zero from its allocation and never written.
 __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__ Phiy, int dx, int dy, int k2,
-                                 int h1, uint8_t* __restrict__ img) {
+                                 int h1, uint8_t* __restrict__ img, const int* done) {
+  if (done != nullptr && *done) return;
   const int v = blockIdx.y;
   const int d = v == 0 ? dx : dy;
   double* Phi = v == 0 ? Phix : Phiy;
@@ -498,8 +637,10 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
 // `stride` is the distance of the partial slabs (floats, a multiple of 4, at
 // least len); entries len .. stride - 1 of a slab are padding.
 __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
-                                                        int64_t stride, double* __restrict__ G, const int* done) {
+                                                        int64_t stride, double* __restrict__ G, const int* done,
+                                                        const int* nparts_dev) {
   if (done != nullptr && *done) return;
+  if (nparts_dev != nullptr) nparts = *nparts_dev;  // batched pass: the schedule's slab count
   __shared__ float4 red_s[4][64], red_c[4][64];
   const int g = threadIdx.x & 63, qtr = threadIdx.x >> 6;
   const int64_t e4 = (int64_t)blockIdx.x * 64 + g;  // float4 group
@@ -589,17 +730,36 @@ bool tc_pass_eligible(const Plan& p) {
   return true;
 }
 
-int tc_pass(Plan& p, cudaStream_t st, const int* done) {
-  // FP32 data: the row-interleaved hi/lo copy (2n rows) made when the data
-  // was bound; BF16 data: the caller's matrices
+// The Phi image of a plan (both views) with h1 rows per half; also rounds
+// Phi to the bf16 hi + lo point the pass evaluates.
+int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done) {
+  const int k2 = 2 * p.k;
+  const int dmax = std::max(p.v[0].d, p.v[1].d);
+  tc::phi_image_kernel<<<dim3(ceil_div(dmax * k2, 256), 2), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d,
+                                                                         p.v[1].d, k2, h1, p.tc_img, done);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+// The streamed matrices of an eligible plan: the caller's BF16 matrices, or
+// for FP32 data the plan's row-interleaved hi/lo copy (2n rows).
+static void tc_sources(const Plan& p, const void* src[2], int64_t ld[2], int64_t* rows) {
   const bool fp32 = p.dtype == GBCCA_FP32;
-  const int64_t rows = fp32 ? 2 * p.n : p.n;
-  const void* src[2];
-  int64_t ld[2];
+  *rows = fp32 ? 2 * p.n : p.n;
   for (int v = 0; v < 2; ++v) {
     src[v] = fp32 ? (const void*)p.ts_copy[v] : p.v[v].Z;
     ld[v] = fp32 ? p.ts_ld[v] : p.v[v].ld;
   }
+}
+
+int tc_pass(Plan& p, cudaStream_t st, const int* done) {
+  // FP32 data: the row-interleaved hi/lo copy (2n rows) made when the data
+  // was bound; BF16 data: the caller's matrices
+  const bool fp32 = p.dtype == GBCCA_FP32;
+  int64_t rows = 0;
+  const void* src[2];
+  int64_t ld[2];
+  tc_sources(p, src, ld, &rows);
   if (p.tc_map_for[0] != src[0] || p.tc_map_for[1] != src[1]) {
     for (int v = 0; v < 2; ++v)
       GB_TRY(make_map(reinterpret_cast<CUtensorMap*>(p.tc_map[v]), src[v], rows, p.v[v].d, ld[v]));
@@ -614,12 +774,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     a.pairs[v] = ceil_div(p.v[v].d, 128);
   }
   const int h1 = k2 <= 20 ? 20 : tc::kHalfMax;  // Phi image rows per half (GEMM 1 N = 2 h1)
-  {
-    const int dmax = std::max(p.v[0].d, p.v[1].d);
-    tc::phi_image_kernel<<<dim3(ceil_div(dmax * k2, 256), 2), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d,
-                                                                           p.v[1].d, k2, h1, p.tc_img);
-    GB_CHECK_LAUNCH();
-  }
+  GB_TRY(tc_phi_image(p, h1, st, done));
   a.k2 = k2;
   a.ntiles = ceil_div(rows, tc::kRows);
   a.pair_sum = fp32 ? 1 : 0;
@@ -658,7 +813,224 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   if (p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
   const int grid = ncl;  // partial slabs, one per cluster
   const int64_t len = (int64_t)p.D * k4;
-  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, len, p.G, done);
+  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, len, p.G, done, nullptr);
+  GB_CHECK_LAUNCH();
+  tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
+                                                                  p.G, p.Gram, done);
+  GB_CHECK_LAUNCH();
+  return GBCCA_OK;
+}
+
+
+// ------------------------------------------------------------ batched pass
+// Several plans' passes in one persistent launch (same kernel, segment
+// schedule).  The instance table, the segments and the per-instance slab
+// counts live in device memory, so a captured graph keeps one launch while
+// the schedule is rewritten between replays (finished plans drop out).
+struct TcBatch {
+  int n = 0;                   // instances
+  int h1 = tc::kHalfMax;       // Phi image rows per half, common to the batch
+  std::vector<int64_t> rows;   // streamed rows per instance
+  tc::Inst* inst_h = nullptr;  // pinned host copies of the tables
+  tc::Seg* seg_h = nullptr;
+  int* off_h = nullptr;
+  int* nparts_h = nullptr;
+  tc::Inst* inst_d = nullptr;
+  tc::Seg* seg_d = nullptr;
+  int* off_d = nullptr;
+  int* nparts_d = nullptr;
+  int* err_d = nullptr;
+  int max_clusters = 0;        // clusters the tables have room for
+  int clusters = 0;            // clusters of the current schedule
+  int max_segs = 0;
+};
+
+void tc_batch_destroy(TcBatch* b) {
+  if (b == nullptr) return;
+  cudaFreeHost(b->inst_h);
+  cudaFreeHost(b->seg_h);
+  cudaFreeHost(b->off_h);
+  cudaFreeHost(b->nparts_h);
+  cudaFree(b->inst_d);
+  cudaFree(b->seg_d);
+  cudaFree(b->off_d);
+  cudaFree(b->nparts_d);
+  cudaFree(b->err_d);
+  delete b;
+}
+
+// Instance table of the plans (each eligible for the tensor-core pass, with
+// its data bound); copied to the device on `st`.
+TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
+  *rc = GBCCA_OK;
+  auto* b = new (std::nothrow) TcBatch();
+  if (b == nullptr) {
+    *rc = GBCCA_ERR_OOM;
+    return nullptr;
+  }
+  b->n = n;
+  int k2max = 0, sm = 1;
+  for (int i = 0; i < n; ++i) {
+    k2max = std::max(k2max, 2 * plans[i]->k);
+    sm = std::max(sm, plans[i]->sm_count);
+  }
+  b->h1 = k2max <= 20 ? 20 : tc::kHalfMax;
+  b->max_clusters = std::max(1, sm / 2);
+  b->max_segs = b->max_clusters + n + 1;  // a contiguous partition has at most clusters + instances pieces
+  const int n1 = std::max(n, 1);
+  bool ok = cudaMallocHost(&b->inst_h, sizeof(tc::Inst) * n1) == cudaSuccess &&
+            cudaMallocHost(&b->seg_h, sizeof(tc::Seg) * b->max_segs) == cudaSuccess &&
+            cudaMallocHost(&b->off_h, sizeof(int) * (b->max_clusters + 1)) == cudaSuccess &&
+            cudaMallocHost(&b->nparts_h, sizeof(int) * n1) == cudaSuccess &&
+            cudaMalloc(&b->inst_d, sizeof(tc::Inst) * n1) == cudaSuccess &&
+            cudaMalloc(&b->seg_d, sizeof(tc::Seg) * b->max_segs) == cudaSuccess &&
+            cudaMalloc(&b->off_d, sizeof(int) * (b->max_clusters + 1)) == cudaSuccess &&
+            cudaMalloc(&b->nparts_d, sizeof(int) * n1) == cudaSuccess &&
+            cudaMalloc(&b->err_d, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    tc_batch_destroy(b);
+    set_last_error("allocation of the batch schedule failed");
+    *rc = GBCCA_ERR_OOM;
+    return nullptr;
+  }
+  std::memset(b->inst_h, 0, sizeof(tc::Inst) * n1);
+  b->rows.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    Plan& p = *plans[i];
+    tc::Inst& I = b->inst_h[i];
+    const void* src[2];
+    int64_t ld[2];
+    tc_sources(p, src, ld, &b->rows[i]);
+    for (int v = 0; v < 2; ++v) {
+      *rc = make_map(&I.map[v], src[v], b->rows[i], p.v[v].d, ld[v]);
+      if (*rc != GBCCA_OK) {
+        tc_batch_destroy(b);
+        return nullptr;
+      }
+      I.d[v] = p.v[v].d;
+      I.pairs[v] = ceil_div(p.v[v].d, 128);
+    }
+    I.phi_img = p.tc_img;
+    I.partG = p.tc_part;
+    I.done = &p.st->done;
+    I.k2 = 2 * p.k;
+    I.pair_sum = p.dtype == GBCCA_FP32 ? 1 : 0;
+    I.slab = (int64_t)p.D * 4 * p.k;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->inst_d, b->inst_h, sizeof(tc::Inst) * n1, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->err_d, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("batch table upload: ") + cudaGetErrorString(e));
+    tc_batch_destroy(b);
+    *rc = GBCCA_ERR_CUDA;
+    return nullptr;
+  }
+  return b;
+}
+
+int tc_batch_h1(const TcBatch* b) { return b->h1; }
+int* tc_batch_err(TcBatch* b) { return b->err_d; }
+int tc_batch_max_clusters(const TcBatch* b) { return b->max_clusters; }
+int tc_batch_clusters(const TcBatch* b) { return b->clusters; }
+int64_t tc_batch_bytes(const TcBatch* b, const bool* active) {
+  int64_t s = 0;
+  for (int i = 0; i < b->n; ++i)
+    if (active == nullptr || active[i]) s += b->rows[i] * (int64_t)(b->inst_h[i].d[0] + b->inst_h[i].d[1]) * 2;
+  return s;
+}
+
+// Schedule of the active instances over `clusters` 2-CTA clusters: their
+// 64-row tiles, each weighted by 2 + the pairs of its wider view (the two
+// CTAs of a cluster move through a tile together, and a tile costs a fixed
+// epilogue and exchange on top of its MMAs), are cut into `clusters`
+// contiguous ranges of near-equal weight.  The pieces of instance i (one per
+// cluster it reaches) write its slabs 0, 1, ... in order, and its reduction
+// adds that many slabs.  The tables go
+// to the device on `st`; the pinned host copies are rewritten only by the
+// next schedule, after the caller has synchronized `st`.
+int tc_batch_schedule(TcBatch* b, const bool* active, int clusters, cudaStream_t st) {
+  clusters = std::max(1, std::min(clusters, b->max_clusters));
+  int64_t total = 0;
+  for (int i = 0; i < b->n; ++i) {
+    b->nparts_h[i] = 0;
+    if (active[i])
+      total += ceil_div(b->rows[i], (int64_t)tc::kRows) * (2 + std::max(b->inst_h[i].pairs[0], b->inst_h[i].pairs[1]));
+  }
+  int c = 0, nseg = 0;
+  int64_t cum = 0;
+  b->off_h[0] = 0;
+  auto bound = [&](int cc) { return (total * (cc + 1) + clusters - 1) / clusters; };
+  for (int i = 0; i < b->n; ++i) {
+    if (!active[i]) continue;
+    const int64_t tiles = ceil_div(b->rows[i], (int64_t)tc::kRows);
+    const int64_t w = 2 + std::max(b->inst_h[i].pairs[0], b->inst_h[i].pairs[1]);
+    int pieces = 0;  // segments of instance i so far = its next slab
+    int64_t t = 0;
+    while (t < tiles) {
+      int64_t take = tiles - t;
+      if (c < clusters - 1) take = std::min(take, (bound(c) - cum) / w);
+      if (take <= 0) {  // this cluster is full: close it
+        b->off_h[++c] = nseg;
+        continue;
+      }
+      b->seg_h[nseg++] = tc::Seg{i, (int)t, (int)take, pieces++};
+      t += take;
+      cum += take * w;
+      if (c < clusters - 1 && cum >= bound(c)) b->off_h[++c] = nseg;
+    }
+    b->nparts_h[i] = pieces;
+  }
+  while (c < clusters) b->off_h[++c] = nseg;
+  b->clusters = clusters;
+  GB_CUDA(cudaMemcpyAsync(b->seg_d, b->seg_h, sizeof(tc::Seg) * std::max(nseg, 1), cudaMemcpyHostToDevice, st));
+  GB_CUDA(cudaMemcpyAsync(b->off_d, b->off_h, sizeof(int) * (clusters + 1), cudaMemcpyHostToDevice, st));
+  GB_CUDA(cudaMemcpyAsync(b->nparts_d, b->nparts_h, sizeof(int) * std::max(b->n, 1), cudaMemcpyHostToDevice, st));
+  return GBCCA_OK;
+}
+
+// The Phi images of a batch member (h1 of the batch); nothing once the plan
+// has finished.
+int tc_batch_pre(const TcBatch* b, Plan& p, cudaStream_t st) { return tc_phi_image(p, b->h1, st, &p.st->done); }
+
+// One launch over every scheduled tile of the batch.
+int tc_batch_launch(TcBatch* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  tc::Args a{};
+  a.err = b->err_d;
+  a.insts = b->inst_d;
+  a.segs = b->seg_d;
+  a.seg_off = b->off_d;
+  auto kern = b->h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>;
+  const int smem = b->h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes;
+  GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(2 * std::max(1, b->clusters), 1, 1);
+  // the tensor-map parameters are unused in batch mode; any valid map will do
+  const CUtensorMap* m0 = &b->inst_h[0].map[0];
+  const CUtensorMap* m1 = &b->inst_h[0].map[1];
+  if (e0 != nullptr) GB_CUDA(record_timing_event(e0, st));
+  GB_CUDA(cudaLaunchKernelEx(&cfg, kern, *m0, *m1, a));
+  GB_CHECK_LAUNCH();
+  if (e1 != nullptr) GB_CUDA(record_timing_event(e1, st));
+  return GBCCA_OK;
+}
+
+// Sum of instance i's slabs into its G, then its Gram.
+int tc_batch_post(const TcBatch* b, int i, Plan& p, cudaStream_t st, const int* done) {
+  const int k2 = 2 * p.k, k4 = 4 * p.k;
+  const int64_t len = (int64_t)p.D * k4;
+  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, 1, len, len, p.G, done, b->nparts_d + i);
   GB_CHECK_LAUNCH();
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
                                                                   p.G, p.Gram, done);

@@ -6,6 +6,7 @@ namespace gbcca {
 
 constexpr int kMaxK = 20;       // columns of an iterate (p in the paper)
 constexpr int kMaxD = 1024;     // columns of one data view
+constexpr int kMaxBatch = 1024;  // plans of one batch
 constexpr int kMaxClasses = 64; // LDA classes
 constexpr int kMaxTimedBatch = 256;  // iterations per batch when passes are timed
 
@@ -237,6 +238,20 @@ int lda_class_stats(Plan& p, cudaStream_t st);
 // pass_tc.cu
 bool tc_pass_eligible(const Plan& p);
 int tc_pass(Plan& p, cudaStream_t st, const int* done);
+int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done);
+// batched tensor-core pass over several eligible plans (one persistent launch)
+struct TcBatch;
+TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc);
+void tc_batch_destroy(TcBatch* b);
+int tc_batch_schedule(TcBatch* b, const bool* active, int clusters, cudaStream_t st);
+int tc_batch_pre(const TcBatch* b, Plan& p, cudaStream_t st);
+int tc_batch_launch(TcBatch* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1);
+int tc_batch_post(const TcBatch* b, int i, Plan& p, cudaStream_t st, const int* done);
+int tc_batch_h1(const TcBatch* b);
+int* tc_batch_err(TcBatch* b);
+int tc_batch_max_clusters(const TcBatch* b);
+int tc_batch_clusters(const TcBatch* b);
+int64_t tc_batch_bytes(const TcBatch* b, const bool* active);
 
 // pass_split.cu: the tensor-core pass for FP32 data (CCA and FDA)
 bool split_pass_shape_ok(int kind, int dtype, int k, int d0, int d1);
@@ -248,6 +263,13 @@ int split_pass(Plan& p, cudaStream_t st, const int* done);
 // rcg.cu
 int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals,
             gbcca_info* info, cudaStream_t st);
+// the pieces of rcg_run, for executors that interleave several plans
+int rcg_begin(Plan& p, const double* mu, double tol, const double* start0, const double* start1, cudaStream_t st);
+int iteration_post(Plan& p, bool low, cudaStream_t st);
+int rcg_finish(Plan& p, double* out0, double* out1, double* vals, gbcca_info* info, double pass_ms, int pass_count,
+               cudaStream_t st);
+int read_state_async(Plan& p, cudaStream_t st);
+int check_flag(Plan& p, gbcca_info* info, cudaStream_t st);
 int warm_start(Plan& p, cudaStream_t st);
 
 }  // namespace gbcca

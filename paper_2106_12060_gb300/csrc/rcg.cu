@@ -1723,16 +1723,13 @@ int thin_blocks(const Plan& p) {
   return ceil_div(dmax, kThinRows);
 }
 
-// One iteration (or, with force_zero_step set on the device, the qf_B
-// normalization of the starting point).
-int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+}  // namespace
+
+// Everything of one iteration after its data pass (the pass outputs G and
+// Gram are in place).
+int iteration_post(Plan& p, bool low, cudaStream_t st) {
   const int k = p.k, kk = k * k;
   const int* done = &p.st->done;
-  p.kev0 = e0;
-  p.kev1 = e1;
-  const int prc = fused_pass(p, low, false, st, 0, done);
-  p.kev0 = p.kev1 = nullptr;
-  GB_TRY(prc);
   GB_TRY(phigram(p, st, done, p.phired));
   GB_TRY(yphi(p, st, 1));
   if (p.opt.rtol > 0) {
@@ -1865,6 +1862,19 @@ int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cuda
   return GBCCA_OK;
 }
 
+namespace {
+
+// One iteration (or, with force_zero_step set on the device, the qf_B
+// normalization of the starting point).
+int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+  p.kev0 = e0;
+  p.kev1 = e1;
+  const int prc = fused_pass(p, low, false, st, 0, &p.st->done);
+  p.kev0 = p.kev1 = nullptr;
+  GB_TRY(prc);
+  return iteration_post(p, low, st);
+}
+
 // A batch of nb iterations launched one by one (pass b of the batch timed
 // with event pair b when timing is on).
 int run_batch_direct(Plan& p, bool low, int nb, bool timed, cudaStream_t st) {
@@ -1961,10 +1971,26 @@ __global__ void start_kernel(const double* src, double* Phi, double* Meta, doubl
   }
 }
 
-int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals, gbcca_info* info,
-            cudaStream_t st) {
+// A kernel that gave up a bounded wait (or found a non-SPD factor) sets the
+// plan's error flag; the host reads it with the state after every batch.
+int check_flag(Plan& p, gbcca_info* info, cudaStream_t st) {
+  if (*p.flag_host == 0) return GBCCA_OK;
+  const int f = *p.flag_host;
+  *p.flag_host = 0;
+  GB_CUDA(cudaMemsetAsync(p.flag, 0, sizeof(int), st));
+  GB_CUDA(cudaStreamSynchronize(st));
+  const int rc = flag_status(f);
+  if (info != nullptr) {
+    *info = gbcca_info{};
+    info->status = rc;
+  }
+  return rc;
+}
+
+// Device state, weights N and starting point of a solve (the first
+// iteration, run by the caller, is the qf_B normalization of the start).
+int rcg_begin(Plan& p, const double* mu, double tol, const double* start0, const double* start1, cudaStream_t st) {
   const int k = p.k;
-  const bool low = p.dtype != GBCCA_FP64;
   const double gtol = tol > 0 ? tol : p.opt.gtol;
   state_init_kernel<<<1, 1, 0, st>>>(p.st, gtol, p.opt.max_iter, p.v[0].lam, p.nviews > 1 ? p.v[1].lam : 0.0);
   GB_CHECK_LAUNCH();
@@ -1978,76 +2004,25 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   GB_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(p.st) + offsetof(DevState, mu), muh, sizeof(double) * k,
                           cudaMemcpyHostToDevice, st));
   for (int v = 0; v < p.nviews; ++v) {
-    const double* src = p.opt.warm_start ? p.v[v].warm : (v == 0 ? out0 : out1);
+    const double* src = p.opt.warm_start ? p.v[v].warm : (v == 0 ? start0 : start1);
     start_kernel<<<ceil_div(p.v[v].d, 128), 128, 0, st>>>(src, p.v[v].Phi, p.v[v].Meta, p.v[v].gold, p.v[v].Mgold,
                                                           p.v[v].d, k);
     GB_CHECK_LAUNCH();
   }
   GB_CUDA(cudaMemsetAsync(p.history, 0, sizeof(double) * 3 * (p.opt.max_iter + 1), st));
   GB_CUDA(cudaMemsetAsync(p.ritz_hist, 0, sizeof(double) * p.ritz_len * k, st));
-  // qf_B of the start (zero step), then iterations in batches.  With pass
-  // timing, event pair b brackets the pass of global iteration index
-  // first_index + b (index 0 = the qf_B pass); only passes whose iteration
-  // really ran (index <= iterations done) are counted.
-  const bool timed = p.nev > 0;
-  double pass_ms = 0;
-  int pass_count = 0;
-  auto harvest = [&](int first_index, int nb, int iters_done) -> int {
-    for (int b = 0; b < nb; ++b) {
-      if (first_index + b > iters_done) break;
-      float ms = 0;
-      GB_CUDA(cudaEventElapsedTime(&ms, p.ev[2 * b], p.ev[2 * b + 1]));
-      pass_ms += ms;
-      ++pass_count;
-    }
-    return GBCCA_OK;
-  };
-  GB_TRY(iteration(p, low, st, timed ? p.ev[0] : nullptr, timed ? p.ev[1] : nullptr));
-  int launched = 0;
-  int passes = 1;
-  int batch = std::max(1, p.opt.check_every);
-  if (timed) batch = std::min(batch, kMaxTimedBatch);
-  int pending_first = 0, pending_n = timed ? 1 : 0;
-  // a kernel that gave up a bounded wait (or found a non-SPD factor) sets the
-  // plan's error flag; it is read with the state after every batch
-  auto check_flag = [&]() -> int {
-    if (*p.flag_host == 0) return GBCCA_OK;
-    const int f = *p.flag_host;
-    *p.flag_host = 0;
-    GB_CUDA(cudaMemsetAsync(p.flag, 0, sizeof(int), st));
-    GB_CUDA(cudaStreamSynchronize(st));
-    const int rc = flag_status(f);
-    if (info != nullptr) {
-      *info = gbcca_info{};
-      info->status = rc;
-    }
-    return rc;
-  };
-  while (true) {
-    GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(p.flag_host, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaStreamSynchronize(st));
-    GB_TRY(check_flag());
-    if (timed) GB_TRY(harvest(pending_first, pending_n, p.st_host->iter));
-    if (p.st_host->done || launched >= p.opt.max_iter) break;
-    pending_first = launched + 1;
-    const int nb = std::min(batch, p.opt.max_iter - launched);
-    // full batches replay a captured graph; a shorter last batch is launched
-    // kernel by kernel (same kernels, same order)
-    if (p.opt.graphs && nb == batch)
-      GB_TRY(run_batch_graph(p, low, nb, timed, st));
-    else
-      GB_TRY(run_batch_direct(p, low, nb, timed, st));
-    launched += nb;
-    pending_n = timed ? nb : 0;
-  }
-  const DevState& hs = *p.st_host;
-  passes += hs.iter;
-  // Rayleigh-Ritz at the final point.  FP64 data: over span([U, eta]) with
-  // the Grams of the plan's FP64 pass (exact products).  BF16/FP32 data,
-  // refine = 1: over span(U) with the Grams of [X U, Y V] from an FP64 pass
-  // (exact products of the stored data); refine = 2: over span([U, eta]) with
-  // the Grams of the plan's own pass (FP32 accumulation).
+  return GBCCA_OK;
+}
+
+// Rayleigh-Ritz at the final point, outputs, and the report.  FP64 data: over
+// span([U, eta]) with the Grams of the plan's FP64 pass (exact products).
+// BF16/FP32 data, refine = 1: over span(U) with the Grams of [X U, Y V] from
+// an FP64 pass (exact products of the stored data); refine = 2: over
+// span([U, eta]) with the Grams of the plan's own pass (FP32 accumulation).
+int rcg_finish(Plan& p, double* out0, double* out1, double* vals, gbcca_info* info, double pass_ms, int pass_count,
+               cudaStream_t st) {
+  const int k = p.k;
+  const bool low = p.dtype != GBCCA_FP64;
   const bool exact_refine = low && p.opt.refine != 2;
   if (exact_refine) {
     GB_TRY(fused_pass(p, false, true, st, k, nullptr));
@@ -2095,11 +2070,11 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
   GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   GB_CUDA(cudaMemcpyAsync(p.flag_host, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   GB_CUDA(cudaStreamSynchronize(st));
-  GB_TRY(check_flag());
-  int status = p.st_host->status;
+  GB_TRY(check_flag(p, info, st));
+  const int status = p.st_host->status;
   if (info != nullptr) {
     info->iters = p.st_host->iter;
-    info->passes = passes + 1;
+    info->passes = p.st_host->iter + 2;  // the qf_B pass, one per iteration, the final one
     info->status = status;
     info->stalled = p.st_host->stalled;
     info->grad_norm = p.st_host->gn;
@@ -2109,6 +2084,59 @@ int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, d
     info->pass_count = pass_count;
   }
   return status;
+}
+
+// Enqueue the state and flag reads of a plan (host mirrors) on `st`.
+int read_state_async(Plan& p, cudaStream_t st) {
+  GB_CUDA(cudaMemcpyAsync(p.st_host, p.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  GB_CUDA(cudaMemcpyAsync(p.flag_host, p.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return GBCCA_OK;
+}
+
+int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals, gbcca_info* info,
+            cudaStream_t st) {
+  const bool low = p.dtype != GBCCA_FP64;
+  GB_TRY(rcg_begin(p, mu, tol, out0, out1, st));
+  // qf_B of the start (zero step), then iterations in batches.  With pass
+  // timing, event pair b brackets the pass of global iteration index
+  // first_index + b (index 0 = the qf_B pass); only passes whose iteration
+  // really ran (index <= iterations done) are counted.
+  const bool timed = p.nev > 0;
+  double pass_ms = 0;
+  int pass_count = 0;
+  auto harvest = [&](int first_index, int nb, int iters_done) -> int {
+    for (int b = 0; b < nb; ++b) {
+      if (first_index + b > iters_done) break;
+      float ms = 0;
+      GB_CUDA(cudaEventElapsedTime(&ms, p.ev[2 * b], p.ev[2 * b + 1]));
+      pass_ms += ms;
+      ++pass_count;
+    }
+    return GBCCA_OK;
+  };
+  GB_TRY(iteration(p, low, st, timed ? p.ev[0] : nullptr, timed ? p.ev[1] : nullptr));
+  int launched = 0;
+  int batch = std::max(1, p.opt.check_every);
+  if (timed) batch = std::min(batch, kMaxTimedBatch);
+  int pending_first = 0, pending_n = timed ? 1 : 0;
+  while (true) {
+    GB_TRY(read_state_async(p, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    GB_TRY(check_flag(p, info, st));
+    if (timed) GB_TRY(harvest(pending_first, pending_n, p.st_host->iter));
+    if (p.st_host->done || launched >= p.opt.max_iter) break;
+    pending_first = launched + 1;
+    const int nb = std::min(batch, p.opt.max_iter - launched);
+    // full batches replay a captured graph; a shorter last batch is launched
+    // kernel by kernel (same kernels, same order)
+    if (p.opt.graphs && nb == batch)
+      GB_TRY(run_batch_graph(p, low, nb, timed, st));
+    else
+      GB_TRY(run_batch_direct(p, low, nb, timed, st));
+    launched += nb;
+    pending_n = timed ? nb : 0;
+  }
+  return rcg_finish(p, out0, out1, vals, info, pass_ms, pass_count, st);
 }
 
 // ============================================================ warm start
