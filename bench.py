@@ -496,6 +496,88 @@ def batched_workload(gb, count: int = 64, seed: int = 0):
     return out
 
 
+def serving_workload(gb, count: int = 128, n_max: float = 1e6, seed: int = 0, budget_gib: int = 120):
+    """The serving stream: `count` requests (synth.batch_mix.serving_mix: 70%
+    CCA / 30% FDA, n log-uniform in [1e4, n_max], widths log-uniform in [64,
+    1024], CCA data BF16 or FP32 half and half) arriving as a Poisson process
+    at 0.8x the throughput measured with the first requests all queued at
+    once; HBM budget `budget_gib` GiB.  Every request's data is a row range
+    of a device-resident pool (a latent-factor pair for CCA, a class-structured
+    matrix for FDA) that the server copies in at admission.  Latency = finish
+    - arrival (server clock); p50 / p99 over the stream."""
+    import torch
+    from synth.batch_mix import serving_mix, latent_views_device, lda_views_device
+    reqs = serving_mix(count, n_range=(1e4, n_max), seed=seed)
+    nmax = max(r["n"] for r in reqs)
+    Xp, Yp = latent_views_device(nmax, 1024, 1024, seed=seed + 1)
+    Xp32, Yp32 = Xp.float(), Yp.float()
+    Lp, yp = lda_views_device(nmax, 1024, 21, seed=seed + 2)
+    rng = np.random.default_rng(seed + 3)
+    opt = dict(max_iter=1000, gtol=0.0, rtol=RTOL, check_every=CHECK_EVERY, refine=REFINE)
+
+    def submit(srv, r):
+        off = int(rng.integers(0, nmax - r["n"] + 1))
+        rows = slice(off, off + r["n"])
+        if r["kind"] == "cca":
+            X, Y = (Xp, Yp) if r["dtype"] == "bf16" else (Xp32, Yp32)
+            return srv.submit_cca(X[rows, :r["dx"]], Y[rows, :r["dy"]], r["k"], 1e-3, 1e-3,
+                                  gb.default_options(**opt))
+        labels = (yp[rows] % r["l"]).to(torch.int32).contiguous()
+        return srv.submit_lda(Lp[rows, :r["d"]], labels, r["l"], r["k"], 1e-2, gb.default_options(**opt))
+
+    def run(order, arrivals):
+        srv = gb.Server(gb.default_server_options(hbm_budget=budget_gib << 30))
+        t0 = time.perf_counter()
+        ids, when, done = {}, {}, {}
+        i = 0
+        while i < len(order) or len(done) < len(order):
+            now = time.perf_counter() - t0
+            while i < len(order) and arrivals[i] <= now:
+                rid = submit(srv, reqs[order[i]])
+                ids[rid] = order[i]
+                when[rid] = arrivals[i]
+                i += 1
+            q, r = srv.step()
+            for rid in list(ids):
+                if rid not in done and srv.state(rid) >= 2:
+                    try:
+                        vals, U, V, info, times = srv.result(rid)
+                        done[rid] = (times["finish_s"] - when[rid], info["status"], info["iters"])
+                    except gb.GbccaError as e:
+                        done[rid] = (float("nan"), e.code, 0)
+            if q == 0 and r == 0 and i < len(order):
+                time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
+        span = time.perf_counter() - t0
+        srv.close()
+        return done, span
+
+    # saturated throughput: the first requests all queued at once
+    m = min(32, count)
+    sat, span = run(list(range(m)), [0.0] * m)
+    rate = 0.8 * m / span
+    gaps = rng.exponential(1.0 / rate, size=count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    done, span = run(list(range(count)), list(arrivals))
+    lat = np.array([v[0] for v in done.values()])
+    ok = [v for v in done.values() if v[1] == gb.OK]
+    out = {
+        "requests": count, "n_range": [1e4, n_max], "budget_GiB": budget_gib, "seed": seed,
+        "saturated_solves_per_s": rate / 0.8,
+        "arrival_rate_per_s": rate, "span_s": span, "solves_per_s": count / span,
+        "p50_ms": float(np.nanpercentile(lat, 50) * 1e3), "p99_ms": float(np.nanpercentile(lat, 99) * 1e3),
+        "mean_ms": float(np.nanmean(lat) * 1e3), "ok": len(ok), "failed": count - len(ok),
+        "iterations_mean": float(np.mean([v[2] for v in ok])) if ok else None,
+        "mix": {"cca_bf16": sum(1 for r in reqs if r["kind"] == "cca" and r["dtype"] == "bf16"),
+                "cca_f32": sum(1 for r in reqs if r["kind"] == "cca" and r["dtype"] == "f32"),
+                "lda_f32": sum(1 for r in reqs if r["kind"] == "lda")},
+        "note": "latency from the Poisson arrival time to the server's finish time of the request (admission "
+                "wait, copy-in, preconditioning, iterations, refinement)",
+    }
+    del Xp, Yp, Xp32, Yp32, Lp, yp
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, ws, rank):
     """The oracle as it stands on the host cores: every step is one FP64
     solve of the FULL workload by route 2 (oracle.cca.cca_whiten), timed
@@ -652,6 +734,7 @@ def run_ours(args, ws, rank, local):
     fp64 = None if args.no_fp64_compare else fp64_comparison(gb, P, sig)
     others = None if args.no_other_workloads else other_workloads(gb)
     batched = None if args.no_batched else batched_workload(gb)
+    serving = None if args.no_serving else serving_workload(gb)
 
     hbm, peak_src = peaks()
     elt = {"bf16": 2, "f32": 4, "f64": 8}[dt]
@@ -695,6 +778,8 @@ def run_ours(args, ws, rank, local):
         line["other_workloads"] = others
     if batched is not None:
         line["batched_uneven_mix"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], ref = cpu_baseline(P)
         line["accuracy"] = accuracy_report(P, sig, U, V, ref)
@@ -793,6 +878,8 @@ def main():
                     help="skip the FP32 CCA and FP32 LDA solves")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-mix workload")
     ap.add_argument("--batched-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serving-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--pass-only", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--solve-rows", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default=WORKLOAD, help=argparse.SUPPRESS)
@@ -810,6 +897,14 @@ def main():
         import paper_2106_12060_gb300 as gb
         torch.cuda.set_device(0)
         print(json.dumps({"batched_uneven_mix": batched_workload(gb)}), flush=True)
+        return
+    if args.serving_only:
+        import torch
+        import __graft_entry__ as g
+        g.build()
+        import paper_2106_12060_gb300 as gb
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": serving_workload(gb)}), flush=True)
         return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -353,6 +353,93 @@ int gbcca_batch_fused_pass(gbcca_batch_t batch, const double* const* Phi_x, cons
 
 void gbcca_batch_destroy(gbcca_batch_t batch);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop over solves that arrive over time; like the batch, it only
+ * schedules the paper's per-problem algorithms (Alg. 1 / Alg. 2) on one GPU.
+ * Requests wait in a FIFO queue until the device memory they need (their
+ * data copies, plan workspace and outputs, counted when their plan is made)
+ * fits the budget beside the running ones; a request larger than the whole
+ * budget fails with GBCCA_ERR_OOM.  At admission the server copies the
+ * request's data into its own device buffers (rows padded to 16 bytes),
+ * makes and preconditions the plan, and sets up the iteration.  Every
+ * gbcca_server_step advances all running requests by tick_iters lockstep
+ * iterations (the batch executor: one persistent tensor-core launch per
+ * iteration for the plans it serves), then refines the finished ones, keeps
+ * their outputs and returns their memory to the budget, so queued requests
+ * join the next step.  One thread drives a server. */
+typedef struct gbcca_server_s* gbcca_server_t;
+
+typedef struct {
+  int64_t hbm_budget;    /* device bytes the running requests may hold
+                            (default 120 GiB)                               */
+  int32_t max_active;    /* running requests at most (default 64, <= 1024)   */
+  int32_t tick_iters;    /* lockstep iterations per step (default 8)         */
+  int32_t graphs;        /* 1 (default): a step whose running set is the one
+                            of the previous step replays a captured graph    */
+} gbcca_server_options;
+
+typedef struct {
+  int32_t kind;          /* 0 = CCA, 1 = FDA                                 */
+  int32_t dtype;         /* gbcca_dtype of the data                          */
+  int64_t n;
+  int32_t dx;            /* CCA: columns of X; FDA: d                        */
+  int32_t dy;            /* CCA: columns of Y                                */
+  int32_t k;
+  int32_t n_classes;     /* FDA                                              */
+  double lambda_x;       /* FDA: lambda                                      */
+  double lambda_y;
+  const void* X;         /* row-major n x dx, row stride ldx elements, in
+                            memory the GPU can read (device, or pinned or
+                            registered host memory); read at admission, so it
+                            must stay valid until the request is running     */
+  int64_t ldx;
+  const void* Y;         /* CCA: n x dy, row stride ldy                      */
+  int64_t ldy;
+  const int32_t* labels; /* FDA: n labels in [0, n_classes), same rule       */
+  gbcca_options opt;     /* solver options (warm_start is forced on)         */
+} gbcca_request;
+
+typedef struct {
+  double submit_s;       /* host steady-clock seconds since the server was
+                            created: submission, admission, finish          */
+  double admit_s;
+  double finish_s;
+  int64_t device_bytes;  /* device memory the request held while running:
+                            its plan's allocations, its data copies and
+                            outputs, as requested from the allocator        */
+} gbcca_request_times;
+
+/* Fills `opt` with the defaults above. */
+int gbcca_default_server_options(gbcca_server_options* opt);
+
+int gbcca_server_create(gbcca_server_t* server, const gbcca_server_options* opt);
+
+/* Queues a request (host struct, copied); *id receives its handle.  Only the
+ * request's form is checked here; a request the library cannot serve fails
+ * at admission (its result call reports why).  No device work. */
+int gbcca_server_submit(gbcca_server_t server, const gbcca_request* req, int64_t* id);
+
+/* One tick: admission, tick_iters iterations of every running request,
+ * retirement of the finished ones.  Writes the queued and running counts
+ * (host, may be NULL).  Work is ordered on `stream` and the call
+ * synchronizes it. */
+int gbcca_server_step(gbcca_server_t server, int32_t* queued, int32_t* running, void* stream);
+
+/* 0 queued, 1 running, 2 finished, 3 failed; GBCCA_ERR_INVALID_ARG for an
+ * unknown id. */
+int gbcca_server_state(gbcca_server_t server, int64_t id);
+
+/* Result of a finished or failed request, then forgets it.  U (dx x k), V
+ * (dy x k, CCA), vals (k: correlations or FDA values): float64 buffers in
+ * device or host memory, or NULL to skip; info and times: host, or NULL.
+ * Returns the request's status (GBCCA_OK, GBCCA_ERR_MAXITER with results,
+ * or the error that ended it), GBCCA_ERR_STATE while it is queued or
+ * running.  Synchronous. */
+int gbcca_server_result(gbcca_server_t server, int64_t id, double* U, double* V, double* vals, gbcca_info* info,
+                        gbcca_request_times* times);
+
+void gbcca_server_destroy(gbcca_server_t server);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * plans and threads); a host-side counter for profiling. */
 int64_t gbcca_launch_count(void);

@@ -372,3 +372,94 @@ def gbcca_batch_fused_pass(batch: Batch, Phi_x, Phi_y, stream=None):
 
 
 batch_fused_pass = gbcca_batch_fused_pass
+
+
+def default_server_options(**kw) -> _lib.ServerOptions:
+    lib = _lib.load()
+    o = _lib.ServerOptions()
+    _lib.check(lib.gbcca_default_server_options(C.byref(o)), "gbcca_default_server_options")
+    for key, val in kw.items():
+        setattr(o, key, val)
+    return o
+
+
+class Server:
+    """Owns a gbcca_server_t.  Submitted tensors are kept alive until their
+    request's result is taken (the server reads them at admission)."""
+
+    QUEUED, RUNNING, FINISHED, FAILED = 0, 1, 2, 3
+
+    def __init__(self, opt=None):
+        lib = _lib.load()
+        h = C.c_void_p()
+        _lib.check(lib.gbcca_server_create(C.byref(h), C.byref(opt) if opt else None), "gbcca_server_create")
+        self.handle = h
+        self._keep = {}
+        self._shape = {}
+
+    def _submit(self, req, keep, shape):
+        rid = C.c_int64()
+        _lib.check(_lib.load().gbcca_server_submit(self.handle, C.byref(req), C.byref(rid)), "gbcca_server_submit")
+        self._keep[rid.value] = keep
+        self._shape[rid.value] = shape
+        return rid.value
+
+    def submit_cca(self, X, Y, k, lambda_x, lambda_y, opt=None):
+        """X (n x dx), Y (n x dy): CUDA tensors, or pinned host tensors, of
+        one storage dtype, unit column stride."""
+        n, dx = X.shape
+        dy = Y.shape[1]
+        for name, t in (("X", X), ("Y", Y)):
+            if t.stride(1) != 1 or t.shape[0] != n or t.dtype != X.dtype:
+                raise ValueError(f"{name} must be n x d with unit column stride and X's dtype")
+        r = _lib.Request(kind=0, dtype=dtype_code(X.dtype), n=n, dx=dx, dy=dy, k=k, n_classes=0,
+                         lambda_x=float(lambda_x), lambda_y=float(lambda_y), X=X.data_ptr(), ldx=X.stride(0),
+                         Y=Y.data_ptr(), ldy=Y.stride(0), labels=None, opt=opt or default_options())
+        return self._submit(r, (X, Y), ("cca", dx, dy, k))
+
+    def submit_lda(self, X, labels, n_classes, k, lam, opt=None):
+        n, d = X.shape
+        if X.stride(1) != 1 or labels.dtype != _torch().int32 or labels.numel() != n:
+            raise ValueError("X must be n x d with unit column stride and labels int32 of n entries")
+        r = _lib.Request(kind=1, dtype=dtype_code(X.dtype), n=n, dx=d, dy=0, k=k, n_classes=n_classes,
+                         lambda_x=float(lam), lambda_y=0.0, X=X.data_ptr(), ldx=X.stride(0), Y=None, ldy=0,
+                         labels=labels.data_ptr(), opt=opt or default_options())
+        return self._submit(r, (X, labels), ("lda", d, 0, k))
+
+    def step(self, stream=None):
+        q, r = C.c_int32(), C.c_int32()
+        _lib.check(_lib.load().gbcca_server_step(self.handle, C.byref(q), C.byref(r), _stream(stream)),
+                   "gbcca_server_step")
+        return q.value, r.value
+
+    def state(self, rid):
+        return int(_lib.load().gbcca_server_state(self.handle, rid))
+
+    def result(self, rid):
+        """(vals, U, V, info, times) of a finished request as float64 CUDA
+        tensors (V None for FDA); raises GbccaError if it failed."""
+        torch = _torch()
+        kind, d0, d1, k = self._shape[rid]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        U = torch.empty(d0, k, dtype=torch.float64, device=dev)
+        V = torch.empty(d1, k, dtype=torch.float64, device=dev) if kind == "cca" else None
+        vals = torch.empty(k, dtype=torch.float64, device=dev)
+        info, times = Info(), _lib.RequestTimes()
+        rc = _lib.load().gbcca_server_result(self.handle, rid, _ptr(U), _ptr(V), _ptr(vals), C.byref(info),
+                                             C.byref(times))
+        self._keep.pop(rid, None)
+        self._shape.pop(rid, None)
+        _lib.check(rc, "gbcca_server_result", (OK, ERR_MAXITER))
+        return vals, U, V, info.as_dict(), {f: getattr(times, f) for f, _ in times._fields_}
+
+    def close(self):
+        if self.handle is not None:
+            _lib.load().gbcca_server_destroy(self.handle)
+            self.handle = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -36,6 +36,44 @@ class Options(C.Structure):
     ]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [
+        ("hbm_budget", C.c_int64),
+        ("max_active", C.c_int32),
+        ("tick_iters", C.c_int32),
+        ("graphs", C.c_int32),
+    ]
+
+
+class Request(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32),
+        ("dtype", C.c_int32),
+        ("n", C.c_int64),
+        ("dx", C.c_int32),
+        ("dy", C.c_int32),
+        ("k", C.c_int32),
+        ("n_classes", C.c_int32),
+        ("lambda_x", C.c_double),
+        ("lambda_y", C.c_double),
+        ("X", C.c_void_p),
+        ("ldx", C.c_int64),
+        ("Y", C.c_void_p),
+        ("ldy", C.c_int64),
+        ("labels", C.c_void_p),
+        ("opt", Options),
+    ]
+
+
+class RequestTimes(C.Structure):
+    _fields_ = [
+        ("submit_s", C.c_double),
+        ("admit_s", C.c_double),
+        ("finish_s", C.c_double),
+        ("device_bytes", C.c_int64),
+    ]
+
+
 class BatchOptions(C.Structure):
     _fields_ = [
         ("clusters", C.c_int32),
@@ -102,6 +140,14 @@ SIGNATURES = {
     "gbcca_batch_fused_pass": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                          C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
     "gbcca_batch_destroy": (None, [C.c_void_p]),
+    "gbcca_default_server_options": (C.c_int, [C.POINTER(ServerOptions)]),
+    "gbcca_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(ServerOptions)]),
+    "gbcca_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "gbcca_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
+    "gbcca_server_state": (C.c_int, [C.c_void_p, C.c_int64]),
+    "gbcca_server_result": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Info),
+                                      C.POINTER(RequestTimes)]),
+    "gbcca_server_destroy": (None, [C.c_void_p]),
     "gbcca_launch_count": (C.c_int64, []),
     "gbcca_plan_destroy": (None, [C.c_void_p]),
     "gbcca_status_string": (C.c_char_p, [C.c_int]),

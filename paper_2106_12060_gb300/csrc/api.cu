@@ -18,7 +18,7 @@ template <typename T>
 int dalloc(T** p, int64_t count) {
   *p = nullptr;
   if (count <= 0) count = 1;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)count);
+  cudaError_t e = counted_malloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)count);
   if (e != cudaSuccess) {
     set_last_error(std::string("cudaMalloc of ") + std::to_string(sizeof(T) * count) + " bytes: " +
                    cudaGetErrorString(e));
@@ -107,7 +107,7 @@ int alloc_plan(Plan* p) {
     GB_TRY(dalloc(&p->perm, p->s));
     size_t tsz = p->dtype == GBCCA_FP64 ? sizeof(double) : sizeof(float);
     void* t = nullptr;
-    cudaError_t e = cudaMalloc(&t, tsz * (size_t)p->n_pad * dmax);
+    cudaError_t e = counted_malloc(&t, tsz * (size_t)p->n_pad * dmax);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_last_error("SRHT scratch allocation failed");
@@ -131,7 +131,7 @@ int alloc_plan(Plan* p) {
   size_t esz = sizeof(double);
   {
     void* t = nullptr;
-    if (cudaMalloc(&t, esz * (size_t)p->n * p->NC) != cudaSuccess) {
+    if (counted_malloc(&t, esz * (size_t)p->n * p->NC) != cudaSuccess) {
       cudaGetLastError();
       set_last_error("pass intermediate allocation failed");
       return GBCCA_ERR_OOM;
@@ -258,7 +258,9 @@ int make_plan(gbcca_plan_t* out, int kind, int64_t n, int d0, int d1, int nviews
   }
   GB_CUDA(cudaGetDevice(&p->dev));
   GB_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->dev));
+  g_alloc_bytes = 0;
   int r = alloc_plan(p);
+  p->dev_bytes = g_alloc_bytes;
   if (r != GBCCA_OK) {
     free_plan(p);
     return r;
@@ -376,6 +378,28 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
 Plan* as_plan(gbcca_plan_t h) { return reinterpret_cast<Plan*>(h); }
 
 }  // namespace
+
+// FDA: bind X and the labels, class statistics, sketch and preconditioner
+// (everything of lda_solve before its iterations).
+int lda_bind(Plan& p, const void* X, int64_t ldx, const int32_t* labels, double lambda, const int32_t* sketch_h,
+             const int8_t* sketch_g, cudaStream_t st) {
+  p.v[0].Z = X;
+  p.v[0].ld = ldx;
+  p.v[0].lam = lambda;
+  p.labels = labels;
+  p.preconditioned = false;
+  GB_TRY(lda_class_stats(p, st));
+  {
+    const int r = read_flag(p, st);
+    if (r == GBCCA_ERR_NOT_SPD) {
+      set_last_error("lda_solve: every class needs at least one sample");
+      return GBCCA_ERR_INVALID_ARG;
+    }
+    if (r != GBCCA_OK) return r;
+  }
+  return precondition_common(p, sketch_h, sketch_g, st);
+}
+
 }  // namespace gbcca
 
 using namespace gbcca;
@@ -473,21 +497,7 @@ int lda_solve(gbcca_plan_t plan, const void* X, int64_t ldx, const int32_t* labe
         return GBCCA_ERR_INVALID_ARG;
       }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  p->v[0].Z = X;
-  p->v[0].ld = ldx;
-  p->v[0].lam = lambda;
-  p->labels = labels;
-  p->preconditioned = false;
-  GB_TRY(lda_class_stats(*p, st));
-  {
-    int r = read_flag(*p, st);
-    if (r == GBCCA_ERR_NOT_SPD) {
-      set_last_error("lda_solve: every class needs at least one sample");
-      return GBCCA_ERR_INVALID_ARG;
-    }
-    if (r != GBCCA_OK) return r;
-  }
-  GB_TRY(precondition_common(*p, sketch_h, sketch_g, st));
+  GB_TRY(lda_bind(*p, X, ldx, labels, lambda, sketch_h, sketch_g, st));
   return rcg_run(*p, mu, tol, W, nullptr, rho, info, st);
 }
 

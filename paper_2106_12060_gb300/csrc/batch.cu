@@ -214,6 +214,114 @@ int autotune(Batch& b, cudaStream_t st) {
 }
 
 }  // namespace
+
+Batch* batch_make(Plan* const* plans, int count, const gbcca_batch_options* opt, int* rc) {
+  *rc = GBCCA_OK;
+  auto* b = new (std::nothrow) Batch();
+  if (b == nullptr) {
+    *rc = GBCCA_ERR_OOM;
+    return nullptr;
+  }
+  gbcca_default_batch_options(&b->opt);
+  if (opt != nullptr) b->opt = *opt;
+  for (int i = 0; i < count; ++i) {
+    Plan* p = plans[i];
+    b->plans.push_back(p);
+    const bool tc = p->kind == kCCA && p->dtype != GBCCA_FP64 && p->opt.tensor_cores && p->tc_img != nullptr &&
+                    tc_pass_eligible(*p);
+    b->tc_index.push_back(tc ? (int)b->tc_plans.size() : -1);
+    if (tc) b->tc_plans.push_back(p);
+  }
+  auto fail = [&](cudaError_t e) {
+    set_last_error(std::string("batch: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    destroy(b);
+    *rc = GBCCA_ERR_CUDA;
+    return nullptr;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(e);
+  b->side.assign(count, nullptr);
+  b->join_a.assign(count, nullptr);
+  b->join_b.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    if ((e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&b->join_a[i], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreateWithFlags(&b->join_b[i], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  }
+  if ((e = cudaEventCreateWithFlags(&b->fork_a, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreateWithFlags(&b->fork_b, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreate(&b->ev1)) != cudaSuccess) return fail(e);
+  if (!b->tc_plans.empty()) {
+    b->tc = tc_batch_create(b->tc_plans.data(), (int)b->tc_plans.size(), b->cap, rc);
+    if (b->tc == nullptr) {
+      destroy(b);
+      return nullptr;
+    }
+    b->clusters = b->opt.clusters > 0 ? std::min(b->opt.clusters, tc_batch_max_clusters(b->tc))
+                                      : tc_batch_max_clusters(b->tc);
+  }
+  return b;
+}
+
+void batch_free(Batch* b) { destroy(b); }
+
+int batch_size(const Batch& b) { return (int)b.plans.size(); }
+
+// nb lockstep iterations of the active plans (a captured graph when asked
+// and nb is the batch's replay length, else launched one by one), after
+// writing the schedule of the active tensor-core plans.
+int batch_iterate(Batch& b, const std::vector<char>& active, int nb, bool graph, cudaStream_t st) {
+  if (b.tc != nullptr) {
+    std::unique_ptr<bool[]> a(new bool[std::max<size_t>(b.tc_plans.size(), 1)]);
+    for (size_t i = 0; i < b.plans.size(); ++i)
+      if (b.tc_index[i] >= 0) a[b.tc_index[i]] = active[i] != 0;
+    GB_TRY(tc_batch_schedule(b.tc, a.get(), b.clusters, st));
+  }
+  if (graph) return replay(b, active, nb, st);
+  for (int it = 0; it < nb; ++it) GB_TRY(enqueue_iteration(b, active, st));
+  return GBCCA_OK;
+}
+
+// After iterations: reads every active plan's state (synchronizing `st`),
+// returns the first device-reported failure, and clears active[i] for the
+// plans that finished.  err_plan (may be NULL) gets the index of a plan
+// whose own flag reported an error, else -1.
+int batch_poll(Batch& b, std::vector<char>& active, gbcca_info* infos, cudaStream_t st, int* err_plan) {
+  const int n = (int)b.plans.size();
+  if (err_plan != nullptr) *err_plan = -1;
+  for (int i = 0; i < n; ++i)
+    if (active[i]) GB_TRY(read_state_async(*b.plans[i], st));
+  int tc_err = 0;
+  if (b.tc != nullptr)
+    GB_CUDA(cudaMemcpyAsync(&tc_err, tc_batch_err(b.tc), sizeof(int), cudaMemcpyDeviceToHost, st));
+  GB_CUDA(cudaStreamSynchronize(st));
+  if (tc_err != 0) {
+    GB_CUDA(cudaMemsetAsync(tc_batch_err(b.tc), 0, sizeof(int), st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    set_last_error("batched tensor-core pass: a bounded pipeline wait ran out");
+    return flag_status(tc_err);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!active[i]) continue;
+    Plan& p = *b.plans[i];
+    const int rc = check_flag(p, infos != nullptr ? &infos[i] : nullptr, st);
+    if (rc != GBCCA_OK) {
+      if (err_plan != nullptr) *err_plan = i;
+      return rc;
+    }
+    if (p.st_host->done) active[i] = 0;
+  }
+  return GBCCA_OK;
+}
+
+int batch_tune(Batch& b, cudaStream_t st) {
+  if (b.tc == nullptr || b.tuned) return GBCCA_OK;
+  for (Plan* p : b.tc_plans) GB_TRY(tc_batch_pre(b.tc, *p, st));
+  return autotune(b, st);
+}
+
 }  // namespace gbcca
 
 using namespace gbcca;
@@ -236,62 +344,26 @@ int gbcca_batch_create(gbcca_batch_t* out, const gbcca_plan_t* plans, int32_t co
     return GBCCA_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  auto* b = new (std::nothrow) Batch();
-  if (b == nullptr) return GBCCA_ERR_OOM;
-  gbcca_default_batch_options(&b->opt);
-  if (opt != nullptr) b->opt = *opt;
-  if (b->opt.clusters < 0 || b->opt.batch_iters < 1) {
-    delete b;
+  if (opt != nullptr && (opt->clusters < 0 || opt->batch_iters < 1)) {
     set_last_error("gbcca_batch_create: invalid options");
     return GBCCA_ERR_INVALID_ARG;
   }
-  int rc = GBCCA_OK;
+  std::vector<Plan*> ps;
   for (int i = 0; i < count; ++i) {
     Plan* p = reinterpret_cast<Plan*>(plans[i]);
     if (p == nullptr || !p->preconditioned || !p->opt.warm_start) {
-      destroy(b);
       set_last_error("gbcca_batch_create: every plan must be preconditioned (bound to its data) with warm_start on");
       return GBCCA_ERR_STATE;
     }
-    for (int j = 0; j < i; ++j)
-      if (b->plans[j] == p) {
-        destroy(b);
-        set_last_error("gbcca_batch_create: a plan appears twice");
-        return GBCCA_ERR_INVALID_ARG;
-      }
-    b->plans.push_back(p);
-    const bool tc = p->kind == kCCA && p->dtype != GBCCA_FP64 && p->opt.tensor_cores && p->tc_img != nullptr &&
-                    tc_pass_eligible(*p);
-    b->tc_index.push_back(tc ? (int)b->tc_plans.size() : -1);
-    if (tc) b->tc_plans.push_back(p);
-  }
-  auto fail = [&](cudaError_t e) {
-    set_last_error(std::string("gbcca_batch_create: ") + cudaGetErrorString(e));
-    cudaGetLastError();
-    destroy(b);
-    return GBCCA_ERR_CUDA;
-  };
-  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return fail(e);
-  b->side.assign(count, nullptr);
-  b->join_a.assign(count, nullptr);
-  b->join_b.assign(count, nullptr);
-  for (int i = 0; i < count; ++i) {
-    if ((e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
-    if ((e = cudaEventCreateWithFlags(&b->join_a[i], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-    if ((e = cudaEventCreateWithFlags(&b->join_b[i], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  }
-  if ((e = cudaEventCreateWithFlags(&b->fork_a, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  if ((e = cudaEventCreateWithFlags(&b->fork_b, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-  if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess) return fail(e);
-  if ((e = cudaEventCreate(&b->ev1)) != cudaSuccess) return fail(e);
-  if (!b->tc_plans.empty()) {
-    b->tc = tc_batch_create(b->tc_plans.data(), (int)b->tc_plans.size(), b->cap, &rc);
-    if (b->tc == nullptr) {
-      destroy(b);
-      return rc;
+    if (std::find(ps.begin(), ps.end(), p) != ps.end()) {
+      set_last_error("gbcca_batch_create: a plan appears twice");
+      return GBCCA_ERR_INVALID_ARG;
     }
+    ps.push_back(p);
   }
+  int rc = GBCCA_OK;
+  Batch* b = batch_make(ps.data(), count, opt, &rc);
+  if (b == nullptr) return rc;
   *out = reinterpret_cast<gbcca_batch_t>(b);
   return GBCCA_OK;
 }
@@ -312,15 +384,8 @@ int gbcca_batch_solve(gbcca_batch_t h, double* const* U, double* const* V, doubl
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < n; ++i) GB_TRY(rcg_begin(*b->plans[i], nullptr, 0.0, nullptr, nullptr, st));
-  if (b->tc != nullptr) {
-    if (!b->tuned) {
-      // the start points' Phi images, then the schedule trials
-      for (Plan* p : b->tc_plans) GB_TRY(tc_batch_pre(b->tc, *p, st));
-      GB_TRY(autotune(*b, st));
-    }
-  }
+  GB_TRY(batch_tune(*b, st));
   std::vector<char> active(n, 1);
-  std::unique_ptr<bool[]> tc_active(new bool[std::max<size_t>(b->tc_plans.size(), 1)]);
   int max_iter = 0;
   for (Plan* p : b->plans) max_iter = std::max(max_iter, p->opt.max_iter);
   const int nb = b->opt.batch_iters;
@@ -328,37 +393,15 @@ int gbcca_batch_solve(gbcca_batch_t h, double* const* U, double* const* V, doubl
   int lockstep = 0;
   bool first = true;
   while (true) {
-    // schedule of the tensor-core plans still running
-    if (b->tc != nullptr) {
-      for (int i = 0; i < n; ++i)
-        if (b->tc_index[i] >= 0) tc_active[b->tc_index[i]] = active[i] != 0;
-      GB_TRY(tc_batch_schedule(b->tc, tc_active.get(), b->clusters, st));
-    }
     const int m = first ? 1 : std::min(nb, max_iter - launched);
-    if (b->opt.graphs && !first && m == nb) {
-      GB_TRY(replay(*b, active, m, st));
-    } else {
-      for (int it = 0; it < m; ++it) GB_TRY(enqueue_iteration(*b, active, st));
-    }
+    GB_TRY(batch_iterate(*b, active, m, b->opt.graphs && !first && m == nb, st));
     launched += m;
     lockstep += m;
     first = false;
-    for (int i = 0; i < n; ++i) GB_TRY(read_state_async(*b->plans[i], st));
-    int tc_err = 0;
-    if (b->tc != nullptr)
-      GB_CUDA(cudaMemcpyAsync(&tc_err, tc_batch_err(b->tc), sizeof(int), cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaStreamSynchronize(st));
-    if (tc_err != 0) {
-      GB_CUDA(cudaMemsetAsync(tc_batch_err(b->tc), 0, sizeof(int), st));
-      GB_CUDA(cudaStreamSynchronize(st));
-      set_last_error("batched tensor-core pass: a bounded pipeline wait ran out");
-      return flag_status(tc_err);
-    }
+    GB_TRY(batch_poll(*b, active, infos, st, nullptr));
     int running = 0;
     for (int i = 0; i < n; ++i) {
-      Plan& p = *b->plans[i];
-      GB_TRY(check_flag(p, infos != nullptr ? &infos[i] : nullptr, st));
-      if (p.st_host->done || launched >= p.opt.max_iter) active[i] = 0;
+      if (launched >= b->plans[i]->opt.max_iter) active[i] = 0;
       running += active[i] ? 1 : 0;
     }
     if (running == 0 || launched >= max_iter) break;
@@ -403,7 +446,7 @@ int gbcca_batch_fused_pass(gbcca_batch_t h, const double* const* Phi_x, const do
     GB_CUDA(cudaMemcpyAsync(p.v[1].Phi, Phi_y[i], sizeof(double) * p.v[1].d * k2, cudaMemcpyDeviceToDevice, st));
     GB_TRY(tc_batch_pre(b->tc, p, st));
   }
-  std::unique_ptr<bool[]> a(new bool[n]);
+  std::unique_ptr<bool[]> a(new bool[std::max(n, 1)]);
   for (int i = 0; i < n; ++i) a[i] = true;
   GB_TRY(tc_batch_schedule(b->tc, a.get(), b->opt.clusters > 0 ? b->opt.clusters : tc_batch_max_clusters(b->tc), st));
   GB_TRY(tc_batch_launch(b->tc, st, nullptr, nullptr));

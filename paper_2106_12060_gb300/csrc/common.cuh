@@ -16,6 +16,15 @@ namespace gbcca {
 void set_last_error(const std::string& msg);
 extern std::atomic<long long> g_launches;  // kernels launched by this library
 
+// Device bytes allocated by this thread through counted_malloc since the
+// counter was last reset (a plan's workspace is counted while it is made).
+inline thread_local int64_t g_alloc_bytes = 0;
+inline cudaError_t counted_malloc(void** p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_alloc_bytes += (int64_t)bytes;
+  return e;
+}
+
 struct Status {
   int code = GBCCA_OK;
   bool ok() const { return code == GBCCA_OK; }

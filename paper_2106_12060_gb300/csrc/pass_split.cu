@@ -572,7 +572,7 @@ int split_pass_alloc(Plan& p) {
       const int64_t ldo = (p.v[v].d + 7) / 8 * 8;
       p.ts_ld[v] = ldo;
       void* t = nullptr;
-      if (cudaMalloc(&t, sizeof(__nv_bfloat16) * (size_t)2 * p.n * ldo) != cudaSuccess) {
+      if (counted_malloc(&t, sizeof(__nv_bfloat16) * (size_t)2 * p.n * ldo) != cudaSuccess) {
         cudaGetLastError();
         set_last_error("allocation of the BF16 hi/lo copy of the data failed");
         return GBCCA_ERR_OOM;
@@ -587,20 +587,20 @@ int split_pass_alloc(Plan& p) {
     const int64_t ldo = (p.v[v].d + 7) / 8 * 8;
     p.ts_ld[v] = ldo;
     void* t = nullptr;  // the hi and the lo matrix, one after the other
-    if (cudaMalloc(&t, sizeof(__nv_bfloat16) * (size_t)2 * p.n * ldo) != cudaSuccess) {
+    if (counted_malloc(&t, sizeof(__nv_bfloat16) * (size_t)2 * p.n * ldo) != cudaSuccess) {
       cudaGetLastError();
       set_last_error("allocation of the BF16 hi/lo copy of the data failed");
       return GBCCA_ERR_OOM;
     }
     p.ts_copy[v] = static_cast<__nv_bfloat16*>(t);
   }
-  GB_CUDA(cudaMalloc(reinterpret_cast<void**>(&p.ts_img), 2 * (size_t)ts::kPhiStride));
+  GB_CUDA(counted_malloc(reinterpret_cast<void**>(&p.ts_img), 2 * (size_t)ts::kPhiStride));
   GB_CUDA(cudaMemset(p.ts_img, 0, 2 * (size_t)ts::kPhiStride));
   // CCA: one slab of D x 4k per cluster; FDA: one of d x 2k per CTA; each
   // slab padded to a multiple of 4 floats (the reduction reads float4)
   const int64_t slab = ((int64_t)p.D * p.NC + 3) / 4 * 4;
   const int64_t slabs = p.kind == kCCA ? p.sm_count / 2 : 2 * (p.sm_count / 2);
-  GB_CUDA(cudaMalloc(reinterpret_cast<void**>(&p.ts_part), sizeof(float) * (size_t)std::max<int64_t>(1, slabs) * slab));
+  GB_CUDA(counted_malloc(reinterpret_cast<void**>(&p.ts_part), sizeof(float) * (size_t)std::max<int64_t>(1, slabs) * slab));
   return GBCCA_OK;
 }
 

@@ -1,5 +1,7 @@
 // Internal plan of the gbcca library: shapes, options and device workspace.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace gbcca {
@@ -82,6 +84,7 @@ struct Plan {
   int64_t s = 0, n_pad = 0;
   int l = 0;    // LDA classes
   bool preconditioned = false;
+  int64_t dev_bytes = 0;   // device memory the plan allocated (workspace, copies of the data)
   int dev = 0;
   int sm_count = 0;
 
@@ -259,6 +262,19 @@ bool split_pass_ready(const Plan& p);
 int split_pass_alloc(Plan& p);
 int split_pass_prepare(Plan& p, cudaStream_t st);
 int split_pass(Plan& p, cudaStream_t st, const int* done);
+
+// api.cu
+int lda_bind(Plan& p, const void* X, int64_t ldx, const int32_t* labels, double lambda, const int32_t* sketch_h,
+             const int8_t* sketch_g, cudaStream_t st);
+
+// batch.cu: lockstep executor over several plans
+struct Batch;
+Batch* batch_make(Plan* const* plans, int count, const gbcca_batch_options* opt, int* rc);
+void batch_free(Batch* b);
+int batch_size(const Batch& b);
+int batch_tune(Batch& b, cudaStream_t st);
+int batch_iterate(Batch& b, const std::vector<char>& active, int nb, bool graph, cudaStream_t st);
+int batch_poll(Batch& b, std::vector<char>& active, gbcca_info* infos, cudaStream_t st, int* err_plan);
 
 // rcg.cu
 int rcg_run(Plan& p, const double* mu, double tol, double* out0, double* out1, double* vals,

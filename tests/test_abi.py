@@ -57,8 +57,8 @@ def test_host_only_calls(lib):
 
 
 def test_struct_layouts_match_the_header(tmp_path):
-    """gbcca_options and gbcca_info as laid out by the C compiler (size and
-    every field offset) equal the ctypes structures of the binding."""
+    """Every struct of the header as laid out by the C compiler (size and
+    every field offset) equals the ctypes structure of the binding."""
     import shutil
     import subprocess
     from paper_2106_12060_gb300 import _lib
@@ -66,7 +66,11 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gbcca.h"', "int main(void) {"]
-    for cname, py in (("gbcca_options", _lib.Options), ("gbcca_info", _lib.Info)):
+    structs = (("gbcca_options", _lib.Options), ("gbcca_info", _lib.Info),
+               ("gbcca_batch_options", _lib.BatchOptions), ("gbcca_batch_report", _lib.BatchReport),
+               ("gbcca_server_options", _lib.ServerOptions), ("gbcca_request", _lib.Request),
+               ("gbcca_request_times", _lib.RequestTimes))
+    for cname, py in structs:
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
             lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
@@ -77,7 +81,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
-    for cname, py in (("gbcca_options", _lib.Options), ("gbcca_info", _lib.Info)):
+    for cname, py in structs:
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
@@ -100,6 +104,32 @@ def test_binding_rejects_host_and_mistyped_tensors():
     plan = gb.Plan(None, "cca", 10, (4, 3), 2, gb.FP32, None)
     with pytest.raises(ValueError, match="CUDA"):
         gb.cca_precondition(plan, torch.zeros(10, 4), torch.zeros(10, 3), 1e-3, 1e-3)
+
+
+def test_batch_and_server_host_checks(lib):
+    """Host-side argument checks of the batch and serving entry points (no
+    device work): defaults, refusals of bad arguments, unknown requests."""
+    from paper_2106_12060_gb300 import _lib
+    L = _lib.load()
+    bo = _lib.BatchOptions()
+    assert L.gbcca_default_batch_options(ctypes.byref(bo)) == 0
+    assert bo.clusters == 0 and bo.graphs == 1 and bo.batch_iters == 8
+    h = ctypes.c_void_p()
+    assert L.gbcca_batch_create(ctypes.byref(h), None, 0, None) == _lib.ERR_INVALID_ARG
+    so = _lib.ServerOptions()
+    assert L.gbcca_default_server_options(ctypes.byref(so)) == 0
+    assert so.hbm_budget == 120 << 30 and so.max_active == 64 and so.tick_iters == 8 and so.graphs == 1
+    bad = _lib.ServerOptions(hbm_budget=0, max_active=1, tick_iters=1, graphs=0)
+    assert L.gbcca_server_create(ctypes.byref(h), ctypes.byref(bad)) == _lib.ERR_INVALID_ARG
+    assert L.gbcca_server_create(ctypes.byref(h), ctypes.byref(so)) == 0
+    rid = ctypes.c_int64()
+    req = _lib.Request(kind=0, dtype=_lib.BF16, n=100, dx=8, dy=8, k=2)  # no data pointers
+    assert L.gbcca_server_submit(h, ctypes.byref(req), ctypes.byref(rid)) == _lib.ERR_INVALID_ARG
+    req = _lib.Request(kind=2, dtype=_lib.BF16, n=100, dx=8, dy=8, k=2, X=1, ldx=8, Y=1, ldy=8)
+    assert L.gbcca_server_submit(h, ctypes.byref(req), ctypes.byref(rid)) == _lib.ERR_INVALID_ARG
+    assert L.gbcca_server_state(h, 12345) == _lib.ERR_INVALID_ARG
+    assert L.gbcca_server_result(h, 12345, None, None, None, None, None) == _lib.ERR_INVALID_ARG
+    L.gbcca_server_destroy(h)
 
 
 def test_flag_codes_map_to_statuses():
