@@ -49,8 +49,8 @@ LDA_REFINE = 1
 # from an ncu capture of 131072 rows of this workload (reads scaled by rows
 # to 262144, partial writes as measured).  Valid only for the kernel source
 # it was taken on (SHA-256 below); any other source reports null.
-PASS_TRAFFIC_BYTES = 268.716544e6 * 2 + 5.929472e6
-PASS_TRAFFIC_SRC_SHA256 = "ec22e5aa4545792b41f28eb4bef771b95b6f0377885c5838536a3087a4191cc8"
+PASS_TRAFFIC_BYTES = 268.660736e6 * 2 + 7.310848e6
+PASS_TRAFFIC_SRC_SHA256 = "de2a6a224cb1b1884a6ac2a2511519159a6dcaaebf8b72d2657195a0b84e65ce"
 
 
 def pass_traffic():

@@ -64,6 +64,8 @@ void free_plan(Plan* p) {
   if (p->side_stream != nullptr) cudaStreamDestroy(p->side_stream);
   if (p->fork_ev != nullptr) cudaEventDestroy(p->fork_ev);
   if (p->join_ev != nullptr) cudaEventDestroy(p->join_ev);
+  if (p->ritz_fork != nullptr) cudaEventDestroy(p->ritz_fork);
+  if (p->ritz_join != nullptr) cudaEventDestroy(p->ritz_join);
   delete p;
 }
 
@@ -185,6 +187,8 @@ int alloc_plan(Plan* p) {
   GB_CUDA(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
   GB_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
   GB_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
+  GB_CUDA(cudaEventCreateWithFlags(&p->ritz_fork, cudaEventDisableTiming));
+  GB_CUDA(cudaEventCreateWithFlags(&p->ritz_join, cudaEventDisableTiming));
   if (p->opt.time_passes) {
     for (int i = 0; i < 2 * kMaxTimedBatch; ++i) {
       GB_CUDA(cudaEventCreate(&p->ev[i]));

@@ -262,19 +262,28 @@ __device__ __forceinline__ void df_add(float& S, float& Cc, float s2, float c2) 
   Cc += err + c2;
 }
 
-constexpr int kMvCols = 20;  // columns per lane and pass over a row
-constexpr int kMvRows = 4;   // rows (warps) per CTA
+constexpr int kMvRows = 4;            // output rows per CTA
+constexpr int kMvThreads = 256;
+constexpr int kMvStageBytes = 98304;  // shared memory of one staged K chunk (A rows + X rows)
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Y_b (m x c) = A_b X_b for problem b = blockIdx.y, A_b (m x K, row-major)
-// and X_b (K x c, row stride ldx) as double-float pairs hi + lo.  One warp per
-// output row: lane l takes the inner indices q = l, l + 32, ... (the row of A
-// is read coalesced; the rows of X, shared by every warp, come from L1/L2 as
-// float2 pairs) and accumulates up to kMvCols columns in double-float
-// registers; a fixed xor-shuffle tree then adds the 32 lanes' pairs, and lane
-// 0 writes the row.  No scratch, no atomics, one launch for all problems;
-// the result does not depend on scheduling.  Columns beyond kMvCols take
-// further passes over the row.
-__global__ void __launch_bounds__(32 * kMvRows) dfmv_kernel(DfmvArgs a) {
+// and X_b (K x c, row stride ldx) as double-float pairs hi + lo.  A CTA owns
+// kMvRows rows of Y.  The K range is walked in chunks: the chunk's rows of A
+// and of X are copied into shared memory as (hi, lo) pairs by asynchronous
+// copies (all of them in flight at once), then thread t computes output
+// e = t mod (kMvRows c) over the inner indices q = t / (kMvRows c) + j KS of
+// the chunk (KS = the threads per output), in two double-float chains.  The
+// KS partial pairs of an output are added in fixed order through shared
+// memory at the end: no scratch in global memory, no atomics, and the result
+// does not depend on scheduling.
+__global__ void __launch_bounds__(kMvThreads) dfmv_kernel(DfmvArgs a) {
   if (a.done != nullptr && *a.done) return;
   // the problem's fields by selection (a dynamic index into the parameter
   // array would copy it to local memory)
@@ -286,62 +295,89 @@ __global__ void __launch_bounds__(32 * kMvRows) dfmv_kernel(DfmvArgs a) {
     int m, K, ldx, ldy;
   } P{GB_SEL(hi), GB_SEL(lo), GB_SEL(Xh), GB_SEL(Xl), GB_SEL(Y), GB_SEL(m), GB_SEL(K), GB_SEL(ldx), GB_SEL(ldy)};
 #undef GB_SEL
-  const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * kMvRows + (threadIdx.x >> 5);
-  if (r >= P.m) return;  // whole warps only: the shuffles below see all 32 lanes
-  const float* Ah = P.hi + (int64_t)r * P.K;
-  const float* Al = P.lo + (int64_t)r * P.K;
-  for (int c0 = 0; c0 < a.c; c0 += kMvCols) {
-    const int cn = min(kMvCols, a.c - c0);  // even
-    float S[kMvCols], C[kMvCols];
-#pragma unroll
-    for (int u = 0; u < kMvCols; ++u) S[u] = C[u] = 0.f;
-    for (int q = lane; q < P.K; q += 32) {
-      const float ah = Ah[q], al = Al[q];
-      const float2* xh = reinterpret_cast<const float2*>(P.Xh + (int64_t)q * P.ldx + c0);
-      const float2* xl = reinterpret_cast<const float2*>(P.Xl + (int64_t)q * P.ldx + c0);
-#pragma unroll
-      for (int u = 0; u < kMvCols / 2; ++u) {
-        if (2 * u < cn) {
-          const float2 bh = xh[u], bl = xl[u];
-          df_acc(S[2 * u], C[2 * u], ah, al, bh.x, bl.x);
-          df_acc(S[2 * u + 1], C[2 * u + 1], ah, al, bh.y, bl.y);
-        }
+  const int r0 = blockIdx.x * kMvRows;
+  if (r0 >= P.m) return;  // uniform over the CTA
+  extern __shared__ float2 mv[];
+  const int c = a.c, Kc = a.kc;
+  float2* As = mv;                 // [kMvRows][Kc]
+  float2* Xs = mv + kMvRows * Kc;  // [Kc][c]
+  const int t = threadIdx.x;
+  const int nout = kMvRows * c;
+  const int KS = max(1, kMvThreads / nout);
+  const bool active = t < nout * KS;
+  const int e = t % nout, ks = t / nout;
+  const int rr = e / c, col = e - rr * c;
+  float S0 = 0.f, C0 = 0.f, S1 = 0.f, C1 = 0.f;
+  for (int k0 = 0; k0 < P.K; k0 += Kc) {
+    const int kn = min(Kc, P.K - k0);
+    __syncthreads();  // the previous chunk has been consumed
+    for (int i = t; i < kMvRows * kn; i += kMvThreads) {
+      const int r2 = i / kn, q = i - r2 * kn;
+      float2* d = As + r2 * Kc + q;
+      if (r0 + r2 < P.m) {
+        const int64_t o = (int64_t)(r0 + r2) * P.K + k0 + q;
+        cp_async4(&d->x, P.hi + o);
+        cp_async4(&d->y, P.lo + o);
+      } else {
+        *d = make_float2(0.f, 0.f);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int u = 0; u < kMvCols; ++u) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, S[u], o);
-        const float c2 = __shfl_xor_sync(0xffffffffu, C[u], o);
-        df_add(S[u], C[u], s2, c2);
+    for (int i = t; i < kn * c; i += kMvThreads) {
+      const int q = i / c, cc = i - q * c;
+      const int64_t o = (int64_t)(k0 + q) * P.ldx + cc;
+      cp_async4(&Xs[i].x, P.Xh + o);
+      cp_async4(&Xs[i].y, P.Xl + o);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (active) {
+      const float2* ar = As + rr * Kc;
+      int q = ks;
+      for (; q + KS < kn; q += 2 * KS) {
+        const float2 a0 = ar[q], x0 = Xs[q * c + col];
+        const float2 a1 = ar[q + KS], x1 = Xs[(q + KS) * c + col];
+        df_acc(S0, C0, a0.x, a0.y, x0.x, x0.y);
+        df_acc(S1, C1, a1.x, a1.y, x1.x, x1.y);
+      }
+      if (q < kn) {
+        const float2 a0 = ar[q], x0 = Xs[q * c + col];
+        df_acc(S0, C0, a0.x, a0.y, x0.x, x0.y);
       }
     }
-    if (lane == 0) {
-      double* y = P.Y + (int64_t)r * P.ldy + c0;
-#pragma unroll
-      for (int u = 0; u < kMvCols; ++u)
-        if (u < cn) y[u] = (double)S[u] + (double)C[u];
-    }
+  }
+  df_add(S0, C0, S1, C1);
+  __syncthreads();
+  float2* red = mv;  // [KS][nout]
+  if (active) red[ks * nout + e] = make_float2(S0, C0);
+  __syncthreads();
+  if (t < nout && r0 + rr < P.m) {
+    float s = 0.f, cc = 0.f;
+    for (int k2 = 0; k2 < KS; ++k2) df_add(s, cc, red[k2 * nout + t].x, red[k2 * nout + t].y);
+    P.Y[(int64_t)(r0 + rr) * P.ldy + col] = (double)s + (double)cc;
   }
 }
 
 int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st) {
-  if (a.c < 2 || (a.c & 1) || nprob < 1 || nprob > 2) {
+  if (a.c < 1 || kMvRows * a.c > kMvThreads || nprob < 1 || nprob > 2) {
     set_last_error("dfmv: unsupported column count");
     return GBCCA_ERR_INVALID_ARG;
   }
-  int mmax = 0;
+  int mmax = 0, kmax = 0;
   for (int b = 0; b < nprob; ++b) {
-    if ((a.p[b].ldx & 1) || a.p[b].ldx < a.c || (reinterpret_cast<uintptr_t>(a.p[b].Xh) & 7) ||
-        (reinterpret_cast<uintptr_t>(a.p[b].Xl) & 7)) {
-      set_last_error("dfmv: X rows must be 8-byte aligned and hold c columns");
+    if (a.p[b].ldx < a.c) {
+      set_last_error("dfmv: X rows must hold c columns");
       return GBCCA_ERR_INVALID_ARG;
     }
     mmax = std::max(mmax, a.p[b].m);
+    kmax = std::max(kmax, a.p[b].K);
   }
-  dfmv_kernel<<<dim3(ceil_div(mmax, kMvRows), nprob), 32 * kMvRows, 0, st>>>(a);
+  // K chunk: the chunk's rows of A and of X (float pairs) fill at most
+  // kMvStageBytes of shared memory; the final reduction reuses the space
+  DfmvArgs g = a;
+  g.kc = std::max(1, std::min(kmax, kMvStageBytes / (8 * (kMvRows + a.c))));
+  const size_t smem = std::max<size_t>(8 * (size_t)g.kc * (kMvRows + a.c), 8 * (size_t)kMvThreads);
+  GB_CUDA(cudaFuncSetAttribute(dfmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dfmv_kernel<<<dim3(ceil_div(mmax, kMvRows), nprob), kMvThreads, smem, st>>>(g);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -29,6 +29,8 @@ struct DevState {
   int rr_ok;                        // 1 if the last Rayleigh-Ritz step factored its Grams
   int ritz_checks;                  // Ritz-value checks recorded in this solve
   int ritz_small;                   // consecutive checks whose change was below rtol
+  int check_iter;                   // iterations done at this iteration's pass (0: no check)
+  int ritz_stop;                    // the Ritz-value rule has been met (done after the join)
   double YW[kMaxClasses * kMaxK];   // FDA: Yhat times the current W (l x k)
   double ftrial[64];                // line-search trial values (diagnostics)
   double Qsyl[2][kMaxK * kMaxK];    // eigenvectors of the last Sylvester coefficient
@@ -154,6 +156,7 @@ struct Plan {
   // side stream and fork/join events for independent per-view work
   cudaStream_t side_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaEvent_t ritz_fork = nullptr, ritz_join = nullptr;  // the Ritz-check branch of an iteration
   cudaGraphExec_t batch_exec = nullptr;
   const void* batch_key_ptr[3] = {nullptr, nullptr, nullptr};
   int batch_key_n = 0;
@@ -210,8 +213,9 @@ struct DfmvProblem {
 };
 struct DfmvArgs {
   DfmvProblem p[2];
-  int c;             // columns of X and Y (even)
+  int c;             // columns of X and Y (at most 64)
   const int* done;
+  int kc;            // K chunk staged in shared memory (set by dfmv)
 };
 int dfmv(const DfmvArgs& a, int nprob, cudaStream_t st);
 // hi/lo split of the first c columns of X (rows x ldx) into rows x c floats

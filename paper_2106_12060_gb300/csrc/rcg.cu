@@ -1455,7 +1455,9 @@ struct RitzArgs {
 
 __global__ void __launch_bounds__(32) ritz_values_kernel(RitzArgs a) {
   DevState* st = a.st;
-  if (st->done || st->force_zero_step || st->iter == 0 || st->iter % a.every != 0) return;
+  // runs beside the rest of the iteration: gated on the iteration count
+  // taken when the pass finished, not on the live counters
+  if (st->check_iter == 0 || st->check_iter % a.every != 0) return;
   constexpr int kM2 = 2 * kMaxK > 32 ? 32 : 2 * kMaxK;  // register columns (m <= 32 here)
   const int lane = threadIdx.x, k = a.k, m = 2 * k, k2 = 2 * k;
   extern __shared__ double rz[];  // ritz_values_smem(k) bytes
@@ -1611,8 +1613,8 @@ __global__ void __launch_bounds__(32) ritz_values_kernel(RitzArgs a) {
 // kernels of the iteration return at once, so the point is the one whose
 // values passed the check and the final refinement reproduces them.
 __global__ void ritz_check_kernel(DevState* st, double* hist, int len, int k, double rtol, int every) {
-  if (threadIdx.x != 0 || st->done || st->force_zero_step || st->iter == 0 || st->iter % every != 0) return;
-  const int idx = st->iter / every - 1;
+  if (threadIdx.x != 0 || st->check_iter == 0 || st->check_iter % every != 0) return;
+  const int idx = st->check_iter / every - 1;
   if (!st->rr_ok || idx >= len) return;
   double worst = 0;
   for (int i = 0; i < k; ++i) {
@@ -1623,7 +1625,18 @@ __global__ void ritz_check_kernel(DevState* st, double* hist, int len, int k, do
   st->ritz_checks = idx + 1;
   const bool small = idx > 0 && hist[(int64_t)(idx - 1) * k] != 0.0 && worst < rtol;
   st->ritz_small = small ? st->ritz_small + 1 : 0;
-  if (st->ritz_small >= 2) st->done = 1;
+  if (st->ritz_small >= 2) st->ritz_stop = 1;
+}
+
+// Before the Ritz branch forks: the iteration count at this pass (0 when
+// there is nothing to check: a finished solve or the qf_B step).
+__global__ void ritz_snap_kernel(DevState* st) {
+  st->check_iter = (st->done || st->force_zero_step) ? 0 : st->iter;
+}
+
+// After the Ritz branch joins: a met rule ends the solve.
+__global__ void ritz_stop_kernel(DevState* st) {
+  if (st->ritz_stop && !st->done) st->done = 1;
 }
 
 // out_v (d x k) = Phi_v[:, :m] rot_v (m = the Rayleigh-Ritz subspace used),
@@ -1732,9 +1745,17 @@ int iteration_post(Plan& p, bool low, cudaStream_t st) {
   const int* done = &p.st->done;
   GB_TRY(phigram(p, st, done, p.phired));
   GB_TRY(yphi(p, st, 1));
-  if (p.opt.rtol > 0) {
+  const bool ritz = p.opt.rtol > 0;
+  if (ritz) {
     // convergence check on the Rayleigh-Ritz values of span([U, eta]) at this
-    // point (every check_every iterations; the kernels return otherwise)
+    // point (every check_every iterations; the kernels return otherwise), on a
+    // branch beside the rest of the iteration: it reads only this pass's
+    // Grams, which nothing overwrites before the next pass, and its verdict
+    // is applied after the join at the end of the iteration
+    ritz_snap_kernel<<<1, 1, 0, st>>>(p.st);
+    GB_CHECK_LAUNCH();
+    GB_CUDA(cudaEventRecord(p.ritz_fork, st));
+    GB_CUDA(cudaStreamWaitEvent(p.side_stream, p.ritz_fork, 0));
     RitzArgs a{};
     a.st = p.st;
     a.Gram = p.Gram;
@@ -1749,10 +1770,11 @@ int iteration_post(Plan& p, bool low, cudaStream_t st) {
     a.every = std::max(1, p.opt.check_every);
     const size_t smem = ritz_values_smem(k);
     GB_CUDA(cudaFuncSetAttribute(ritz_values_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    ritz_values_kernel<<<1, 32, smem, st>>>(a);
+    ritz_values_kernel<<<1, 32, smem, p.side_stream>>>(a);
     GB_CHECK_LAUNCH();
-    ritz_check_kernel<<<1, 32, 0, st>>>(p.st, p.ritz_hist, p.ritz_len, k, p.opt.rtol, a.every);
+    ritz_check_kernel<<<1, 32, 0, p.side_stream>>>(p.st, p.ritz_hist, p.ritz_len, k, p.opt.rtol, a.every);
     GB_CHECK_LAUNCH();
+    GB_CUDA(cudaEventRecord(p.ritz_join, p.side_stream));
   }
   {
     LSArgs a{};
@@ -1859,6 +1881,11 @@ int iteration_post(Plan& p, bool low, cudaStream_t st) {
     newdir_kernel<<<dim3(ceil_div(dmax * k, 128), p.nviews), 128, 0, st>>>(a);
     GB_CHECK_LAUNCH();
   }
+  if (ritz) {
+    GB_CUDA(cudaStreamWaitEvent(st, p.ritz_join, 0));
+    ritz_stop_kernel<<<1, 1, 0, st>>>(p.st);
+    GB_CHECK_LAUNCH();
+  }
   return GBCCA_OK;
 }
 
@@ -1952,6 +1979,8 @@ __global__ void state_init_kernel(DevState* st, double gtol, int max_iter, doubl
   st->rr_ok = 0;
   st->ritz_checks = 0;
   st->ritz_small = 0;
+  st->check_iter = 0;
+  st->ritz_stop = 0;
   st->dcount = 0;
   st->ls_count = 0;
   st->lam[0] = lam0;
