@@ -406,14 +406,28 @@ __global__ void srht_group_kernel(const int32_t* __restrict__ rows, int64_t s, i
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < s; j += (int64_t)gridDim.x * blockDim.x)
       atomicAdd(&cnt[rows[j] & (N1 - 1)], 1);
   } else if (phase == 1) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      int32_t acc = 0;
-      for (int a = 0; a < N1; ++a) {
+    // exclusive scan of the N1 counts by one warp: lane l sums a contiguous
+    // run of the counts, the lanes' totals are scanned by shuffles, then
+    // each lane writes its run's offsets (and clears its counts)
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const int per = (N1 + 31) / 32;
+      const int a0 = min(N1, lane * per), a1 = min(N1, a0 + per);
+      int32_t tot = 0;
+      for (int a = a0; a < a1; ++a) tot += cnt[a];
+      int32_t inc = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      int32_t acc = inc - tot;
+      for (int a = a0; a < a1; ++a) {
         off1[a] = acc;
         acc += cnt[a];
         cnt[a] = 0;
       }
-      off1[N1] = acc;
+      if (lane == 31) off1[N1] = inc;
     }
   } else {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < s; j += (int64_t)gridDim.x * blockDim.x) {
