@@ -543,7 +543,8 @@ __global__ void split_gram_kernel(const double* __restrict__ Phix, const double*
 // tc_reduce_kernel lives with the BF16 pass
 namespace tc {
 __global__ void tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len, int64_t stride,
-                                 double* __restrict__ G, const int* done, const int* nparts_dev);
+                                 double* __restrict__ G, const int* done, const int* nparts_dev, int ng, int col0,
+                                 int k2);
 }
 
 // ----------------------------------------------------------------- host side
@@ -690,7 +691,8 @@ int split_pass(Plan& p, cudaStream_t st, const int* done) {
   if (p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
   const int nparts = lda ? 2 * ncl : ncl;
   const int64_t len = (int64_t)p.D * p.NC;
-  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.ts_part, nparts, len, a.slab, p.G, done, nullptr);
+  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.ts_part, nparts, len, a.slab, p.G, done, nullptr,
+                                                           0, 0, 0);
   GB_CHECK_LAUNCH();
   const int nc = p.NC;
   ts::split_gram_kernel<<<ceil_div((int64_t)nc * nc * 32, 256), 256, 0, st>>>(

@@ -610,22 +610,25 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
 // the pass evaluates is exactly the point the solver holds.  One thread per
 // element of Phi (both views in one launch); the padding of the image is
 // zero from its allocation and never written.
+// Columns col0 .. col0 + ng - 1 of Phi (row stride k2) form the image (a
+// column group: plans with 2k > 24 run the pass once per group).
 __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__ Phiy, int dx, int dy, int k2,
-                                 int h1, uint8_t* __restrict__ img, const int* done) {
+                                 int col0, int ng, int h1, uint8_t* __restrict__ img, const int* done) {
   if (done != nullptr && *done) return;
   const int v = blockIdx.y;
   const int d = v == 0 ? dx : dy;
   double* Phi = v == 0 ? Phix : Phiy;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (data column j, Phi column c)
-  if (e >= d * k2) return;
-  const int j = e / k2, c = e - j * k2;
-  const double x = Phi[e];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (data column j, group column c)
+  if (e >= d * ng) return;
+  const int j = e / ng, c = e - j * ng;
+  double* px = Phi + (int64_t)j * k2 + col0 + c;
+  const double x = *px;
   const __nv_bfloat16 hi = __double2bfloat16(x);
   const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
   uint8_t* base = img + (int64_t)v * kPhiView + (int64_t)(j >> 6) * (2 * h1 * 128);
   *reinterpret_cast<__nv_bfloat16*>(base + swz(c, j & 63)) = hi;
   *reinterpret_cast<__nv_bfloat16*>(base + swz(h1 + c, j & 63)) = lo;
-  Phi[e] = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
+  *px = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
 }
 
 // G (D x 4k, FP64) = sum over clusters of the FP32 partials, in cluster
@@ -635,10 +638,14 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
 // combined in fixed order.  Error ~2 ulp of the sum, far below the partials'
 // own rounding.
 // `stride` is the distance of the partial slabs (floats, a multiple of 4, at
-// least len); entries len .. stride - 1 of a slab are padding.
+// least len); entries len .. stride - 1 of a slab are padding.  With ng > 0
+// the slabs hold one column group (rows of 2 ng: the view-x then the view-y
+// products of group columns 0 .. ng - 1), and entry (row, vv ng + c) goes to
+// G column vv k2 + col0 + c (rows of 2 k2); with ng = 0, G has the slabs'
+// layout.
 __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
                                                         int64_t stride, double* __restrict__ G, const int* done,
-                                                        const int* nparts_dev) {
+                                                        const int* nparts_dev, int ng, int col0, int k2) {
   if (done != nullptr && *done) return;
   if (nparts_dev != nullptr) nparts = *nparts_dev;  // batched pass: the schedule's slab count
   __shared__ float4 red_s[4][64], red_c[4][64];
@@ -680,8 +687,17 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict_
       out[2] += (double)a.z + (double)c.z;
       out[3] += (double)a.w + (double)c.w;
     }
-    for (int i = 0; i < 4; ++i)
-      if (4 * e4 + i < len) G[4 * e4 + i] = out[i];
+    for (int i = 0; i < 4; ++i) {
+      const int64_t idx = 4 * e4 + i;
+      if (idx >= len) continue;
+      if (ng == 0) {
+        G[idx] = out[i];
+      } else {
+        const int64_t row = idx / (2 * ng);
+        const int col = (int)(idx - row * 2 * ng), vv = col / ng, c = col - vv * ng;
+        G[row * 2 * k2 + vv * k2 + col0 + c] = out[i];
+      }
+    }
   }
 }
 
@@ -717,11 +733,13 @@ int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
 
 }  // namespace
 
-// The tensor-core pass serves CCA plans with BF16 data, k <= 12 (4k <= 48
-// MMA columns), dx, dy <= 512 (TMEM and shared-memory budget), 16-byte
-// aligned rows (ld a multiple of 8) and 16-byte aligned bases.
+// The tensor-core pass serves CCA plans with BF16 data (or FP32 data through
+// the interleaved copy), dx, dy <= 512 (TMEM and shared-memory budget),
+// 16-byte aligned rows (ld a multiple of 8) and 16-byte aligned bases; Phi
+// columns beyond 24 per view (k > 12, up to the library's k <= 20) are taken
+// in a second column group, which reads the data a second time.
 bool tc_pass_eligible(const Plan& p) {
-  if (p.kind != kCCA || 2 * p.k > tc::kHalfMax || p.v[0].d > 512 || p.v[1].d > 512) return false;
+  if (p.kind != kCCA || 2 * p.k > 2 * tc::kHalfMax || p.v[0].d > 512 || p.v[1].d > 512) return false;
   if (p.dtype == GBCCA_FP32) return p.ts_ready && p.ts_interleaved;  // the plan's own aligned copy
   if (p.dtype != GBCCA_BF16) return false;
   for (int v = 0; v < 2; ++v) {
@@ -730,14 +748,44 @@ bool tc_pass_eligible(const Plan& p) {
   return true;
 }
 
-// The Phi image of a plan (both views) with h1 rows per half; also rounds
-// Phi to the bf16 hi + lo point the pass evaluates.
+// Column groups of Phi for the tensor-core pass: one group for 2k <= 24,
+// else two of ng0 = k rounded up to even columns (an even group keeps every
+// partial slab a multiple of 4 floats), each at most 24.
+int tc_groups(const Plan& p) { return 2 * p.k <= tc::kHalfMax ? 1 : 2; }
+static void tc_group(const Plan& p, int g, int* col0, int* ng) {
+  const int k2 = 2 * p.k;
+  if (tc_groups(p) == 1) {
+    *col0 = 0;
+    *ng = k2;
+    return;
+  }
+  const int ng0 = (p.k + 1) / 2 * 2;
+  *col0 = g * ng0;
+  *ng = g == 0 ? ng0 : k2 - ng0;
+}
+static int tc_group_h1(int ng) { return ng <= 20 ? 20 : tc::kHalfMax; }
+static uint8_t* tc_group_img(const Plan& p, int g) { return p.tc_img + (int64_t)g * 2 * tc::kPhiView; }
+// partial slabs of group g: clusters (at most half the SMs) x D x 2 ng floats
+static float* tc_group_part(const Plan& p, int g) {
+  int col0 = 0, ng0 = 0;
+  tc_group(p, 0, &col0, &ng0);
+  return p.tc_part + (int64_t)g * (p.sm_count / 2) * p.D * 2 * ng0;
+}
+
+// The Phi images of a plan (both views, every column group), group g with
+// h1 rows per half (h1 = 0: each group's own); also rounds Phi to the bf16
+// hi + lo point the pass evaluates.
 int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done) {
   const int k2 = 2 * p.k;
   const int dmax = std::max(p.v[0].d, p.v[1].d);
-  tc::phi_image_kernel<<<dim3(ceil_div(dmax * k2, 256), 2), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d,
-                                                                         p.v[1].d, k2, h1, p.tc_img, done);
-  GB_CHECK_LAUNCH();
+  for (int g = 0; g < tc_groups(p); ++g) {
+    int col0 = 0, ng = 0;
+    tc_group(p, g, &col0, &ng);
+    const int hg = h1 > 0 ? h1 : tc_group_h1(ng);
+    tc::phi_image_kernel<<<dim3(ceil_div(dmax * ng, 256), 2), 256, 0, st>>>(
+        p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2, col0, ng, hg, tc_group_img(p, g), done);
+    GB_CHECK_LAUNCH();
+  }
   return GBCCA_OK;
 }
 
@@ -767,54 +815,65 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     p.tc_map_for[1] = src[1];
   }
   const int k2 = 2 * p.k, k4 = 4 * p.k;
-  tc::Args a{};
-  a.n = p.n;
-  for (int v = 0; v < 2; ++v) {
-    a.d[v] = p.v[v].d;
-    a.pairs[v] = ceil_div(p.v[v].d, 128);
-  }
-  const int h1 = k2 <= 20 ? 20 : tc::kHalfMax;  // Phi image rows per half (GEMM 1 N = 2 h1)
-  GB_TRY(tc_phi_image(p, h1, st, done));
-  a.k2 = k2;
-  a.ntiles = ceil_div(rows, tc::kRows);
-  a.pair_sum = fp32 ? 1 : 0;
-  a.phi_img = p.tc_img;
-  a.partG = p.tc_part;
-  a.err = p.flag;
-  a.done = done;
-  auto kern = h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>;
-  const int smem = h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes;
-  GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  cudaLaunchConfig_t cfg{};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(256, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (p.tc_clusters <= 0) {
-    // persistent grid: as many 2-CTA clusters as can be resident at once
-    cfg.gridDim = dim3(2 * (p.sm_count / 2), 1, 1);
-    int ncl = 0;
-    GB_CUDA(cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg));
-    p.tc_clusters = std::max(1, std::min(ncl, p.sm_count / 2));
-  }
-  const int ncl = std::min(p.tc_clusters, a.ntiles);
-  cfg.gridDim = dim3(2 * ncl, 1, 1);
+  GB_TRY(tc_phi_image(p, 0, st, done));
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(p.tc_map[0]);
   const CUtensorMap* my = reinterpret_cast<const CUtensorMap*>(p.tc_map[1]);
+  const int groups = tc_groups(p);
   if (p.kev0 != nullptr) GB_CUDA(record_timing_event(p.kev0, st));
-  GB_CUDA(cudaLaunchKernelEx(&cfg, kern, *mx, *my, a));
-  GB_CHECK_LAUNCH();
+  int ncl = 1;
+  for (int g = 0; g < groups; ++g) {
+    int col0 = 0, ng = 0;
+    tc_group(p, g, &col0, &ng);
+    const int h1 = tc_group_h1(ng);  // Phi image rows per half (GEMM 1 N = 2 h1)
+    tc::Args a{};
+    a.n = p.n;
+    for (int v = 0; v < 2; ++v) {
+      a.d[v] = p.v[v].d;
+      a.pairs[v] = ceil_div(p.v[v].d, 128);
+    }
+    a.k2 = ng;
+    a.ntiles = ceil_div(rows, tc::kRows);
+    a.pair_sum = fp32 ? 1 : 0;
+    a.phi_img = tc_group_img(p, g);
+    a.partG = tc_group_part(p, g);
+    a.err = p.flag;
+    a.done = done;
+    auto kern = h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>;
+    const int smem = h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes;
+    GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (p.tc_clusters <= 0) {
+      // persistent grid: as many 2-CTA clusters as can be resident at once
+      cfg.gridDim = dim3(2 * (p.sm_count / 2), 1, 1);
+      int nc = 0;
+      GB_CUDA(cudaOccupancyMaxActiveClusters(&nc, kern, &cfg));
+      p.tc_clusters = std::max(1, std::min(nc, p.sm_count / 2));
+    }
+    ncl = std::min(p.tc_clusters, a.ntiles);
+    cfg.gridDim = dim3(2 * ncl, 1, 1);
+    GB_CUDA(cudaLaunchKernelEx(&cfg, kern, *mx, *my, a));
+    GB_CHECK_LAUNCH();
+  }
   if (p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
-  const int grid = ncl;  // partial slabs, one per cluster
-  const int64_t len = (int64_t)p.D * k4;
-  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, grid, len, len, p.G, done, nullptr);
-  GB_CHECK_LAUNCH();
+  for (int g = 0; g < groups; ++g) {
+    int col0 = 0, ng = 0;
+    tc_group(p, g, &col0, &ng);
+    // partial slabs, one per cluster
+    const int64_t len = (int64_t)p.D * 2 * ng;
+    tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), ncl, len, len, p.G, done, nullptr,
+                                                             groups > 1 ? ng : 0, col0, k2);
+    GB_CHECK_LAUNCH();
+  }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
                                                                   p.G, p.Gram, done);
   GB_CHECK_LAUNCH();
@@ -828,9 +887,13 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
 // counts live in device memory, so a captured graph keeps one launch while
 // the schedule is rewritten between replays (finished plans drop out).
 struct TcBatch {
-  int n = 0;                   // instances
+  int n = 0;                   // table entries: one per (plan, column group)
+  int nplans = 0;
   int h1 = tc::kHalfMax;       // Phi image rows per half, common to the batch
-  std::vector<int64_t> rows;   // streamed rows per instance
+  std::vector<int64_t> rows;   // streamed rows per entry
+  std::vector<int> first;      // per plan: its first entry (entries first .. first + count - 1)
+  std::vector<int> count;
+  std::vector<int64_t> plan_bytes;  // algorithmic bytes of one pass per plan
   tc::Inst* inst_h = nullptr;  // pinned host copies of the tables
   tc::Seg* seg_h = nullptr;
   int* off_h = nullptr;
@@ -868,16 +931,24 @@ TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
     *rc = GBCCA_ERR_OOM;
     return nullptr;
   }
-  b->n = n;
-  int k2max = 0, sm = 1;
+  b->nplans = n;
+  int entries = 0, h1 = 20, sm = 1;
   for (int i = 0; i < n; ++i) {
-    k2max = std::max(k2max, 2 * plans[i]->k);
+    b->first.push_back(entries);
+    b->count.push_back(tc_groups(*plans[i]));
+    for (int g = 0; g < tc_groups(*plans[i]); ++g) {
+      int col0 = 0, ng = 0;
+      tc_group(*plans[i], g, &col0, &ng);
+      h1 = std::max(h1, tc_group_h1(ng));
+    }
+    entries += tc_groups(*plans[i]);
     sm = std::max(sm, plans[i]->sm_count);
   }
-  b->h1 = k2max <= 20 ? 20 : tc::kHalfMax;
+  b->n = entries;
+  b->h1 = h1;
   b->max_clusters = std::max(1, sm / 2);
-  b->max_segs = b->max_clusters + n + 1;  // a contiguous partition has at most clusters + instances pieces
-  const int n1 = std::max(n, 1);
+  b->max_segs = b->max_clusters + entries + 1;  // a contiguous partition has at most clusters + entries pieces
+  const int n1 = std::max(entries, 1);
   bool ok = cudaMallocHost(&b->inst_h, sizeof(tc::Inst) * n1) == cudaSuccess &&
             cudaMallocHost(&b->seg_h, sizeof(tc::Seg) * b->max_segs) == cudaSuccess &&
             cudaMallocHost(&b->off_h, sizeof(int) * (b->max_clusters + 1)) == cudaSuccess &&
@@ -895,28 +966,36 @@ TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
     return nullptr;
   }
   std::memset(b->inst_h, 0, sizeof(tc::Inst) * n1);
-  b->rows.assign(n, 0);
+  b->rows.assign(entries, 0);
+  b->plan_bytes.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     Plan& p = *plans[i];
-    tc::Inst& I = b->inst_h[i];
     const void* src[2];
-    int64_t ld[2];
-    tc_sources(p, src, ld, &b->rows[i]);
-    for (int v = 0; v < 2; ++v) {
-      *rc = make_map(&I.map[v], src[v], b->rows[i], p.v[v].d, ld[v]);
-      if (*rc != GBCCA_OK) {
-        tc_batch_destroy(b);
-        return nullptr;
+    int64_t ld[2], rows = 0;
+    tc_sources(p, src, ld, &rows);
+    b->plan_bytes[i] = rows * (int64_t)(p.v[0].d + p.v[1].d) * 2;
+    for (int g = 0; g < b->count[i]; ++g) {
+      const int e = b->first[i] + g;
+      tc::Inst& I = b->inst_h[e];
+      b->rows[e] = rows;
+      for (int v = 0; v < 2; ++v) {
+        *rc = make_map(&I.map[v], src[v], rows, p.v[v].d, ld[v]);
+        if (*rc != GBCCA_OK) {
+          tc_batch_destroy(b);
+          return nullptr;
+        }
+        I.d[v] = p.v[v].d;
+        I.pairs[v] = ceil_div(p.v[v].d, 128);
       }
-      I.d[v] = p.v[v].d;
-      I.pairs[v] = ceil_div(p.v[v].d, 128);
+      int col0 = 0, ng = 0;
+      tc_group(p, g, &col0, &ng);
+      I.phi_img = tc_group_img(p, g);
+      I.partG = tc_group_part(p, g);
+      I.done = &p.st->done;
+      I.k2 = ng;
+      I.pair_sum = p.dtype == GBCCA_FP32 ? 1 : 0;
+      I.slab = (int64_t)p.D * 2 * ng;
     }
-    I.phi_img = p.tc_img;
-    I.partG = p.tc_part;
-    I.done = &p.st->done;
-    I.k2 = 2 * p.k;
-    I.pair_sum = p.dtype == GBCCA_FP32 ? 1 : 0;
-    I.slab = (int64_t)p.D * 4 * p.k;
   }
   cudaError_t e = cudaMemcpyAsync(b->inst_d, b->inst_h, sizeof(tc::Inst) * n1, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->err_d, 0, sizeof(int), st);
@@ -934,10 +1013,12 @@ int tc_batch_h1(const TcBatch* b) { return b->h1; }
 int* tc_batch_err(TcBatch* b) { return b->err_d; }
 int tc_batch_max_clusters(const TcBatch* b) { return b->max_clusters; }
 int tc_batch_clusters(const TcBatch* b) { return b->clusters; }
+// Algorithmic bytes of one batched pass over the active plans (each plan's
+// data once, whatever its column groups).
 int64_t tc_batch_bytes(const TcBatch* b, const bool* active) {
   int64_t s = 0;
-  for (int i = 0; i < b->n; ++i)
-    if (active == nullptr || active[i]) s += b->rows[i] * (int64_t)(b->inst_h[i].d[0] + b->inst_h[i].d[1]) * 2;
+  for (int i = 0; i < b->nplans; ++i)
+    if (active == nullptr || active[i]) s += b->plan_bytes[i];
   return s;
 }
 
@@ -950,8 +1031,11 @@ int64_t tc_batch_bytes(const TcBatch* b, const bool* active) {
 // adds that many slabs.  The tables go
 // to the device on `st`; the pinned host copies are rewritten only by the
 // next schedule, after the caller has synchronized `st`.
-int tc_batch_schedule(TcBatch* b, const bool* active, int clusters, cudaStream_t st) {
+int tc_batch_schedule(TcBatch* b, const bool* plan_active, int clusters, cudaStream_t st) {
   clusters = std::max(1, std::min(clusters, b->max_clusters));
+  std::vector<char> active(b->n, 0);  // per entry
+  for (int i = 0; i < b->nplans; ++i)
+    for (int g = 0; g < b->count[i]; ++g) active[b->first[i] + g] = plan_active[i] ? 1 : 0;
   int64_t total = 0;
   for (int i = 0; i < b->n; ++i) {
     b->nparts_h[i] = 0;
@@ -1026,12 +1110,19 @@ int tc_batch_launch(TcBatch* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
   return GBCCA_OK;
 }
 
-// Sum of instance i's slabs into its G, then its Gram.
+// Sum of plan i's slabs (every column group) into its G, then its Gram.
 int tc_batch_post(const TcBatch* b, int i, Plan& p, cudaStream_t st, const int* done) {
   const int k2 = 2 * p.k, k4 = 4 * p.k;
-  const int64_t len = (int64_t)p.D * k4;
-  tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(p.tc_part, 1, len, len, p.G, done, b->nparts_d + i);
-  GB_CHECK_LAUNCH();
+  const int groups = b->count[i];
+  for (int g = 0; g < groups; ++g) {
+    int col0 = 0, ng = 0;
+    tc_group(p, g, &col0, &ng);
+    const int64_t len = (int64_t)p.D * 2 * ng;
+    tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), 1, len, len, p.G, done,
+                                                             b->nparts_d + b->first[i] + g, groups > 1 ? ng : 0,
+                                                             col0, k2);
+    GB_CHECK_LAUNCH();
+  }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
                                                                   p.G, p.Gram, done);
   GB_CHECK_LAUNCH();

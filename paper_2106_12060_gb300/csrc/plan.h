@@ -246,6 +246,7 @@ int lda_class_stats(Plan& p, cudaStream_t st);
 bool tc_pass_eligible(const Plan& p);
 int tc_pass(Plan& p, cudaStream_t st, const int* done);
 int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done);
+int tc_groups(const Plan& p);
 // batched tensor-core pass over several eligible plans (one persistent launch)
 struct TcBatch;
 TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc);

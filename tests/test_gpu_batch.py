@@ -56,9 +56,10 @@ def gamma_batched(rows, d, fp32):
 
 
 # (n, dx, dy, k, storage): ragged sizes, both Phi image widths (2k <= 20 and
-# 2k = 24), one-pair and four-pair views, FP32 data through the interleaved copy
+# 2k = 24), one-pair and four-pair views, FP32 data through the interleaved
+# copy, and k = 20 (two column groups, two table entries for one plan)
 SHAPES = [(9001, 200, 120, 5, "bf16"), (4097, 64, 40, 10, "bf16"), (20000, 512, 296, 12, "bf16"),
-          (3001, 96, 80, 4, "f32"), (150, 24, 16, 3, "bf16")]
+          (3001, 96, 80, 4, "f32"), (150, 24, 16, 3, "bf16"), (6007, 160, 128, 20, "bf16")]
 
 
 def _make(gb, shapes, seed0=0, **opt):
@@ -106,13 +107,14 @@ def test_batched_pass_matches_oracle(gb, clusters):
 
 
 def test_batch_solve_matches_solo_solves(gb):
-    """Six plans in one batch: four served by the batched launch (BF16 and
-    FP32 data), one with 2k = 30 (its own pass on its branch) and an FDA plan
-    (its own FP32 pass).  Each result equals its solo solve within 1e-6 and
-    the oracle within 1e-6."""
+    """Seven plans in one batch: five served by the batched launch (BF16 and
+    FP32 data, and 2k = 30 in two column groups), one with a 600-wide view
+    (its own CUDA-core pass on its branch) and an FDA plan (its own FP32
+    pass).  Each result equals its solo solve within 1e-6 and the oracle
+    within 1e-6."""
     import torch
     shapes = [(9001, 200, 120, 5, "bf16"), (4097, 64, 40, 10, "bf16"), (20000, 512, 296, 12, "bf16"),
-              (3001, 96, 80, 4, "f32"), (5000, 100, 90, 15, "bf16")]
+              (3001, 96, 80, 4, "f32"), (5000, 104, 88, 15, "bf16"), (7000, 600, 64, 4, "bf16")]
     opt = dict(max_iter=3000, gtol=0.0, rtol=1e-7, check_every=8, refine=2)
     plans, probs = _make(gb, shapes, seed0=20, **opt)
     solo = []
@@ -130,7 +132,7 @@ def test_batch_solve_matches_solo_solves(gb):
     allp = plans + [lplan]
     batch = gb.Batch(allp)
     res, report = gb.batch_solve(batch)
-    assert report["batched_plans"] == 4, report
+    assert report["batched_plans"] == 5, report
     assert report["batched_pass_ms"] > 0 and report["clusters"] >= 1, report
     for i, (val, _, _, info) in enumerate(res):
         assert info["status"] == gb.OK, (i, info)
