@@ -567,6 +567,8 @@ def serving_workload(gb, count: int = 128, n_max: float = 1e6, seed: int = 0, bu
         "arrival_rate_per_s": rate, "span_s": span, "solves_per_s": count / span,
         "p50_ms": float(np.nanpercentile(lat, 50) * 1e3), "p99_ms": float(np.nanpercentile(lat, 99) * 1e3),
         "mean_ms": float(np.nanmean(lat) * 1e3), "ok": len(ok), "failed": count - len(ok),
+        "failed_status": {gb.STATUS_NAMES.get(c, str(c)): sum(1 for v in done.values() if v[1] == c)
+                          for c in sorted({v[1] for v in done.values() if v[1] != gb.OK})},
         "iterations_mean": float(np.mean([v[2] for v in ok])) if ok else None,
         "mix": {"cca_bf16": sum(1 for r in reqs if r["kind"] == "cca" and r["dtype"] == "bf16"),
                 "cca_f32": sum(1 for r in reqs if r["kind"] == "cca" and r["dtype"] == "f32"),

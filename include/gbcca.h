@@ -97,10 +97,11 @@ typedef struct {
                             kernels in the same order.                          */
   double rtol;           /* stop when the Rayleigh-Ritz values of the subspace
                             span([U, eta]) x span([V, eta_V]) (the values the
-                            final refinement reports) change by less than rtol,
-                            relative, at two consecutive checks (check_every
-                            iterations apart); 0 (default) = off.  Either rule
-                            (gtol or rtol) ends the iteration.               */
+                            final refinement reports) change by less than rtol
+                            relative to the largest of them, at two consecutive
+                            checks (check_every iterations apart); 0 (default)
+                            = off.  Either rule (gtol or rtol) ends the
+                            iteration.                                      */
   int32_t tensor_cores;  /* 1 (default): the data pass runs on the tensor-core
                             kernels where the plan is eligible (BF16 and FP32
                             data, 2k <= 20 or 24, d within their limits); 0:

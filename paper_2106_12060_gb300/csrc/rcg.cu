@@ -1616,11 +1616,16 @@ __global__ void ritz_check_kernel(DevState* st, double* hist, int len, int k, do
   if (threadIdx.x != 0 || st->check_iter == 0 || st->check_iter % every != 0) return;
   const int idx = st->check_iter / every - 1;
   if (!st->rr_ok || idx >= len) return;
-  double worst = 0;
+  // the change of every value relative to the largest one (the scale of the
+  // objective sum mu_i sigma_i and of the accuracy measure max |d sigma| /
+  // max sigma): small values, whose relative rounding noise is larger, do
+  // not hold the rule back
+  double worst = 0, top = 0;
+  for (int i = 0; i < k; ++i) top = fmax(top, fabs(st->sigma[i]));
   for (int i = 0; i < k; ++i) {
     const double s = st->sigma[i];
     hist[(int64_t)idx * k + i] = s;
-    if (idx > 0) worst = fmax(worst, fabs(s - hist[(int64_t)(idx - 1) * k + i]) / fmax(fabs(s), 1e-300));
+    if (idx > 0) worst = fmax(worst, fabs(s - hist[(int64_t)(idx - 1) * k + i]) / fmax(top, 1e-300));
   }
   st->ritz_checks = idx + 1;
   const bool small = idx > 0 && hist[(int64_t)(idx - 1) * k] != 0.0 && worst < rtol;
