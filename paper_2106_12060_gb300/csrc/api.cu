@@ -177,11 +177,11 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->ls_L, 64 * 2 * (int64_t)kMaxK * kMaxK));
   GB_TRY(dalloc(&p->flag, 1));
   GB_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
-  if (p->kind == kCCA && (p->dtype == GBCCA_BF16 || p->dtype == GBCCA_FP32) && p->v[0].d <= 512 &&
-      p->v[1].d <= 512 && p->opt.tensor_cores) {
-    // Phi images of both views per column group (two groups for 2k > 24),
-    // and the per-cluster partial slabs of every group
-    const int64_t img = (2 * k <= 24 ? 1 : 2) * 2 * 49152;
+  if (p->kind == kCCA && (p->dtype == GBCCA_BF16 || p->dtype == GBCCA_FP32) && p->opt.tensor_cores) {
+    // Phi images of both views per column group (two groups for 2k > 24;
+    // twice the K-boxes for views wider than 512), and the per-cluster
+    // partial slabs of every group
+    const int64_t img = (2 * k <= 24 ? 1 : 2) * 2 * (dmax > 512 ? 2 : 1) * 49152;
     GB_TRY(dalloc(&p->tc_img, img));
     GB_CUDA(cudaMemset(p->tc_img, 0, img));
     GB_TRY(dalloc(&p->tc_part, (int64_t)p->sm_count * p->D * (k4 + 8)));

@@ -227,8 +227,10 @@ Batch* batch_make(Plan* const* plans, int count, const gbcca_batch_options* opt,
   for (int i = 0; i < count; ++i) {
     Plan* p = plans[i];
     b->plans.push_back(p);
+    // the batched launch runs 2-CTA clusters: plans with a view wider than
+    // 512 columns (4-CTA clusters) run their own tensor-core pass on their branch
     const bool tc = p->kind == kCCA && p->dtype != GBCCA_FP64 && p->opt.tensor_cores && p->tc_img != nullptr &&
-                    tc_pass_eligible(*p);
+                    tc_pass_eligible(*p) && !tc_quad(*p);
     b->tc_index.push_back(tc ? (int)b->tc_plans.size() : -1);
     if (tc) b->tc_plans.push_back(p);
   }

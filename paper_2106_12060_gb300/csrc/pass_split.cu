@@ -557,11 +557,9 @@ bool split_pass_shape_ok(int kind, int dtype, int k, int d0, int d1) {
   return d0 <= 128 * ts::SLay<true>::kMaxPairs;
 }
 
-// CCA shapes of the interleaved copy for the BF16 kernel (d <= 512; any k,
-// in one or two column groups of Phi)
-static bool interleaved_shape_ok(const Plan& p) {
-  return p.kind == kCCA && p.dtype == GBCCA_FP32 && p.v[0].d <= 512 && p.v[1].d <= 512;
-}
+// CCA shapes of the interleaved copy for the BF16 kernel (any shape the
+// library accepts: d <= 1024, k <= 20)
+static bool interleaved_shape_ok(const Plan& p) { return p.kind == kCCA && p.dtype == GBCCA_FP32; }
 
 bool split_pass_ready(const Plan& p) { return p.ts_img != nullptr && p.ts_ready && !p.ts_interleaved; }
 

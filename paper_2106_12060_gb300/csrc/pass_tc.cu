@@ -68,7 +68,7 @@ constexpr long long kTimeout = kWaitCycles;       // cycles (~1 s)
 // Shared-memory layout and barriers for GEMM 1 with N = 2 kH1 (Phi columns as
 // bf16 hi rows 0 .. kH1 - 1 and lo rows kH1 .. 2 kH1 - 1; kH1 = 20 serves
 // 2k <= 20 and leaves room for a 10-slot ring, kH1 = 24 a 9-slot ring).
-template <int kH1>
+template <int kH1, bool kQuad = false>
 struct Lay {
   static constexpr int kN1 = 2 * kH1;
   static constexpr int kKBox1 = kN1 * 128;       // one K-box (64 columns) of the Phi image
@@ -90,10 +90,14 @@ struct Lay {
   // every 50 cycles, two streams overlap in the tensor pipe.
   static constexpr int kNAcc = (4 * kTW + kTileSlots * kN2 <= (int)kTmemCols) ? 2 : 1;
   static constexpr int kTG = 2 * kNAcc * kTW;    // first TMEM column of the G accumulators
-  static constexpr int kStages = (kMaxSmem - kPhiBytes - 2 * kWBuf - 512 - 1024) / kSlot;
+  // 4-CTA clusters (views wider than 512 columns, split over two CTAs each):
+  // two FP32 buffers that receive the other half's partial W of a tile
+  static constexpr int kXBytes = kQuad ? 2 * kH1 * kRows * 4 : 0;
+  static constexpr int kStages = (kMaxSmem - kPhiBytes - 2 * kWBuf - kXBytes - 512 - 1024) / kSlot;
   static constexpr int kRingOff = kPhiBytes;
   static constexpr int kWsOff = kRingOff + kStages * kSlot;
-  static constexpr int kBarOff = kWsOff + 2 * kWBuf;
+  static constexpr int kXOff = kWsOff + 2 * kWBuf;
+  static constexpr int kBarOff = kXOff + kXBytes;
   static constexpr int kSmemBytes = kBarOff + 512 + 1024;  // barriers + alignment slack
   // barrier indices
   static constexpr int kFull = 0, kEmpty = kStages, kD1Full = 2 * kStages;  // [stages], [stages], [2]
@@ -102,7 +106,9 @@ struct Lay {
   static constexpr int kFinal = kGDone + 1;                         // [3]: one per MMA-issuing thread
   static constexpr int kPhiFull = kFinal + 3;  // Phi image in shared memory
   static constexpr int kGFree = kPhiFull + 1;   // G drained (128 arrivals)
-  static constexpr int kPhiFree = kGFree + 1, kNumBars = kPhiFree + 1;  // GEMM 1 done with a segment's Phi
+  static constexpr int kPhiFree = kGFree + 1;  // GEMM 1 done with a segment's Phi
+  static constexpr int kXFull = kPhiFree + 1, kXFree = kXFull + 2;  // [2], [2]: partial-W exchange (quad)
+  static constexpr int kNumBars = kXFree + 2;
   static_assert(kStages >= 2 * kTileSlots, "two resident tiles");
   static_assert(kN1 <= kTW && kD1Cols <= kTW, "W buffers in TMEM");
   static_assert(kN2 % 16 == 0 && kTG + kTileSlots * kN2 <= (int)kTmemCols, "G accumulators in TMEM");
@@ -147,6 +153,7 @@ struct Args {
   float* partG;            // [cluster][D][4k]
   int* err;
   const int* done;
+  int64_t img_view;        // bytes between the two views' Phi images
   int pair_sum;            // 1: rows 2i and 2i+1 of the streamed matrix are the bf16
                            // hi and lo parts of one data row (FP32 data): W of the
                            // row is the sum of the two product rows, and both rows
@@ -165,8 +172,24 @@ struct SegView {
   float* out;              // partial slab of the segment
   int first, stride, count;
   int d0, d1, npairs, k2, pair_sum;
+  int pb;                  // first 128-column pair of this CTA (4-CTA clusters: half h of the view)
   bool skip;
 };
+
+// The 128-column pairs of a view of P pairs that CTA half h takes: all of
+// them in a 2-CTA cluster; in a 4-CTA cluster the first ceil(P / 2) for
+// h = 0 and the rest for h = 1, at least one (a pair past the view's last
+// column reads zeros from the tensor map and the image, and drains nothing).
+__device__ __forceinline__ void half_pairs(int P, bool quad, int h, int* pb, int* np) {
+  if (!quad) {
+    *pb = 0;
+    *np = P;
+    return;
+  }
+  const int p0 = (P + 1) / 2;
+  *pb = h == 0 ? 0 : p0;
+  *np = h == 0 ? p0 : max(1, P - p0);
+}
 
 __device__ __forceinline__ int seg_count(const Args& a, int cid, int ncl) {
   if (a.insts == nullptr) return 1;
@@ -174,18 +197,18 @@ __device__ __forceinline__ int seg_count(const Args& a, int cid, int ncl) {
 }
 
 __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tmx, const CUtensorMap* tmy, int view,
-                                            int cid, int ncl, int s) {
+                                            int cid, int ncl, int s, bool quad = false, int half = 0) {
   SegView v;
   if (a.insts == nullptr) {
     v.map = view == 0 ? tmx : tmy;
-    v.phi = a.phi_img + view * kPhiView;
+    v.phi = a.phi_img + view * a.img_view;
     v.d0 = a.d[0];
     v.d1 = a.d[1];
     v.out = a.partG + (int64_t)cid * (v.d0 + v.d1) * (2 * a.k2);
     v.first = cid;
     v.stride = ncl;
     v.count = (a.ntiles - cid + ncl - 1) / ncl;
-    v.npairs = a.pairs[view];
+    half_pairs(a.pairs[view], quad, half, &v.pb, &v.npairs);
     v.k2 = a.k2;
     v.pair_sum = a.pair_sum;
     v.skip = false;
@@ -200,7 +223,7 @@ __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tm
     v.first = sg.first;
     v.stride = 1;
     v.count = sg.count;
-    v.npairs = I->pairs[view];
+    half_pairs(I->pairs[view], quad, half, &v.pb, &v.npairs);
     v.k2 = I->k2;
     v.pair_sum = I->pair_sum;
     v.skip = I->done != nullptr && *I->done != 0;
@@ -209,15 +232,15 @@ __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tm
   return v;
 }
 
-template <int kH1>
+template <int kH1, bool kQuad = false>
 __global__ void __launch_bounds__(256, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, Args a) {
-  using L = Lay<kH1>;
+  using L = Lay<kH1, kQuad>;
   constexpr int kStages = L::kStages;
   constexpr int kFull = L::kFull, kEmpty = L::kEmpty, kD1Full = L::kD1Full, kD1Free = L::kD1Free;
   constexpr int kEpiSync = L::kEpiSync, kWReady = L::kWReady, kWPeer = L::kWPeer, kWFree = L::kWFree;
   constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kPhiFull = L::kPhiFull, kGFree = L::kGFree;
-  constexpr int kPhiFree = L::kPhiFree;
+  constexpr int kPhiFree = L::kPhiFree, kXFull = L::kXFull, kXFree = L::kXFree;
   constexpr int kNumBars = L::kNumBars;
   constexpr int kTG = L::kTG;
   if (a.done != nullptr && *a.done) return;  // uniform over the cluster: no remote access yet
@@ -229,9 +252,18 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* xbuf = reinterpret_cast<float*>(smem + L::kXOff);  // quad: [buffer][kH1 columns][64 rows]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int view = (int)cluster_ctarank();   // 0: X, 1: Y
-  const uint32_t peer = 1u - (uint32_t)view;
+  // rank = 2 half + view: CTAs 2h and 2h + 1 form the pair that shares the
+  // tile's W (views X and Y); in a 4-CTA cluster, CTAs v and v + 2 hold the
+  // two column halves of view v and add their partial W of every tile
+  const uint32_t rank = cluster_ctarank();
+  const int view = (int)(rank & 1u);         // 0: X, 1: Y
+  const int half = kQuad ? (int)(rank >> 1) : 0;
+  const uint32_t peer = rank ^ 1u;
+  const uint32_t hpeer = rank ^ 2u;
+  (void)hpeer;
+  (void)xbuf;
   const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
   const int nseg = seg_count(a, cid, ncl);
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
@@ -258,6 +290,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     mbar_init(bar(kGDone), 1);
     mbar_init(bar(kGFree), 128);
     mbar_init(bar(kPhiFree), L::kNAcc);  // one arrival per GEMM 1 issuer
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar(kXFull + b), 128);  // the other half's epilogue threads
+      mbar_init(bar(kXFree + b), 128);
+    }
     mbar_init(bar(kFinal), 1);
     mbar_init(bar(kFinal + 1), 1);
     mbar_init(bar(kFinal + 2), 1);
@@ -288,7 +324,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     for (int s = 0; s < kStages; ++s) last_use[s] = -1;
     int jg = 0, ig = 0, sp = 0;
     for (int s = 0; s < nseg && ok; ++s) {
-      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
       if (sv.count == 0) continue;
       // the Phi image is rewritten only after every GEMM 1 MMA of the
       // previous segment has completed (its issuers signal that once per
@@ -298,7 +334,9 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       // this segment's Phi image (GEMM 1's B operand), one bulk copy per K-box
       const uint32_t pb = bar(kPhiFull);
       mbar_expect_tx(pb, L::kPhiBytes);
-      for (int kb = 0; kb < 8; ++kb) bulk_g2s(smem_u32(phi_s + kb * L::kKBox1), sv.phi + kb * L::kKBox1, L::kKBox1, pb);
+      // (this CTA's pairs: K-boxes 2 pb .. 2 pb + 7 of the image)
+      for (int kb = 0; kb < 8; ++kb)
+        bulk_g2s(smem_u32(phi_s + kb * L::kKBox1), sv.phi + (2 * sv.pb + kb) * L::kKBox1, L::kKBox1, pb);
       ++sp;
       for (int t = 0; t < sv.count && ok; ++t, ++jg) {
         const int row0 = (sv.first + t * sv.stride) * kRows;
@@ -308,8 +346,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           const uint32_t fb = bar(kFull + slot);
           mbar_expect_tx(fb, kSlot);
           const uint32_t dst = smem_u32(ring + slot * kSlot);
-          tma_load_2d(dst, sv.map, 128 * p, row0, fb);
-          tma_load_2d(dst + kBox, sv.map, 128 * p + 64, row0, fb);
+          tma_load_2d(dst, sv.map, 128 * (sv.pb + p), row0, fb);
+          tma_load_2d(dst + kBox, sv.map, 128 * (sv.pb + p) + 64, row0, fb);
           last_use[slot] = use;
         }
       }
@@ -348,7 +386,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       const int acc_i = warp - 1;  // accumulator of this issuer
       const uint64_t bdesc0 = sdesc(smem_u32(phi_s), 16, 1024);
       for (int s = 0; s < nseg && ok; ++s) {
-        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
         if (sv.count == 0) continue;
         const int npairs = sv.npairs;
         const int split = L::kNAcc == 2 ? (npairs + 1) / 2 : npairs;
@@ -401,7 +439,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         // release the Phi image when a later segment will load its own
         bool more = false;
         for (int s2 = s + 1; s2 < nseg && !more; ++s2)
-          more = seg_view(a, &tmx, &tmy, view, cid, ncl, s2).count > 0;
+          more = seg_view(a, &tmx, &tmy, view, cid, ncl, s2, kQuad, half).count > 0;
         if (more) {
           if (pe > pb) {
             mma_commit(bar(kPhiFree));
@@ -412,7 +450,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       }
     } else {
       for (int s = 0; s < nseg && ok; ++s) {
-        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
         if (sv.count == 0) continue;
         const int npairs = sv.npairs;
         // the epilogue has drained the G accumulators of the previous segment
@@ -445,7 +483,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             issued += 4;
           }
           // both CTAs learn that this CTA's GEMM 2 has consumed buffer b
-          mma_commit_mc(bar(kWFree + b), (uint16_t)0x3);
+          mma_commit_mc(bar(kWFree + b), (uint16_t)(0x3u << (2 * half)));
         }
         if (ok) mma_commit(bar(kGDone));  // this segment's G is complete
       }
@@ -466,7 +504,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     bool ok = true;
     int jg = 0, sp = 0;
     for (int s = 0; s < nseg && ok; ++s) {
-      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s);
+      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
       if (sv.count == 0) continue;
       const int npairs = sv.npairs;
       const bool two_acc = L::kNAcc == 2 && (npairs + 1) / 2 < npairs;
@@ -514,6 +552,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = d1[c0 + kSplit] + d1[kH1 + c0 + kSplit];
 #pragma unroll
           for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
+          float xs[kSplit];
 #pragma unroll
           for (int c0 = 0; c0 < kSplit; ++c0) {
             float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
@@ -521,8 +560,36 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             // (adjacent rows sit in adjacent lanes; a + b == b + a, so both
             // lanes hold the same value)
             if (sv.pair_sum) x += __shfl_xor_sync(0xffffffffu, x, 1);
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+            xs[c0] = x;
+          }
+          if constexpr (kQuad) {
+            // W of the view = this half's product + the other half's: send
+            // ours into the other half's buffer b (once it has read the one
+            // of tile jg - 2), take theirs from ours; both CTAs add the same
+            // two numbers (a + b == b + a), so they hold the same W
+            const int cb = upper ? kSplit : 0;
+            // (the waits' verdicts are made warp-uniform: the shuffles below
+            // need every lane)
+            if (jg >= 2 &&
+                !(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFree + b), ((jg - 2) >> 1) & 1, abort_flag))))
+              break;
+            const uint32_t rx = map_peer(smem_u32(xbuf + b * kH1 * kRows), hpeer);
+#pragma unroll
+            for (int c0 = 0; c0 < kSplit; ++c0) {
+              const uint32_t adr = rx + (uint32_t)(((cb + c0) * kRows + rr) * 4);
+              asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(adr), "f"(xs[c0]) : "memory");
+            }
+            mbar_arrive_cluster(map_peer(bar(kXFull + b), hpeer));
+            if (!(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFull + b), (jg >> 1) & 1, abort_flag)))) break;
+            const float* mine = xbuf + b * kH1 * kRows;
+#pragma unroll
+            for (int c0 = 0; c0 < kSplit; ++c0) xs[c0] += mine[(cb + c0) * kRows + rr];
+            mbar_arrive_cluster(map_peer(bar(kXFree + b), hpeer));
+          }
+#pragma unroll
+          for (int c0 = 0; c0 < kSplit; ++c0) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(xs[c0]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(xs[c0] - __bfloat162float(hi));
             hs[c0] = __bfloat16_as_ushort(hi);
             ls[c0] = __bfloat16_as_ushort(lo);
           }
@@ -572,7 +639,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
 #pragma unroll
           for (int c = 0; c < L::kN2; c += 16) tmem_ld16(tmem + lane_off + (uint32_t)(kTG + p * L::kN2 + c), &g[c]);
           tmem_ld_wait();
-          const int col = 128 * p + rg;
+          const int col = 128 * (sv.pb + p) + rg;
           if (col < dv) {
             float* o = sv.out + (int64_t)(view * sv.d0 + col) * k4;
 #pragma unroll
@@ -613,7 +680,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
 // Columns col0 .. col0 + ng - 1 of Phi (row stride k2) form the image (a
 // column group: plans with 2k > 24 run the pass once per group).
 __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__ Phiy, int dx, int dy, int k2,
-                                 int col0, int ng, int h1, uint8_t* __restrict__ img, const int* done) {
+                                 int col0, int ng, int h1, uint8_t* __restrict__ img, int64_t img_view,
+                                 const int* done) {
   if (done != nullptr && *done) return;
   const int v = blockIdx.y;
   const int d = v == 0 ? dx : dy;
@@ -625,7 +693,7 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
   const double x = *px;
   const __nv_bfloat16 hi = __double2bfloat16(x);
   const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
-  uint8_t* base = img + (int64_t)v * kPhiView + (int64_t)(j >> 6) * (2 * h1 * 128);
+  uint8_t* base = img + (int64_t)v * img_view + (int64_t)(j >> 6) * (2 * h1 * 128);
   *reinterpret_cast<__nv_bfloat16*>(base + swz(c, j & 63)) = hi;
   *reinterpret_cast<__nv_bfloat16*>(base + swz(h1 + c, j & 63)) = lo;
   *px = (double)__bfloat162float(hi) + (double)__bfloat162float(lo);
@@ -734,12 +802,13 @@ int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
 }  // namespace
 
 // The tensor-core pass serves CCA plans with BF16 data (or FP32 data through
-// the interleaved copy), dx, dy <= 512 (TMEM and shared-memory budget),
-// 16-byte aligned rows (ld a multiple of 8) and 16-byte aligned bases; Phi
-// columns beyond 24 per view (k > 12, up to the library's k <= 20) are taken
-// in a second column group, which reads the data a second time.
+// the interleaved copy), dx, dy <= 1024 (views wider than 512 columns in
+// 4-CTA clusters, each view's column pairs split over two CTAs), 16-byte
+// aligned rows (ld a multiple of 8) and 16-byte aligned bases; Phi columns
+// beyond 24 per view (k > 12, up to the library's k <= 20) are taken in a
+// second column group, which reads the data a second time.
 bool tc_pass_eligible(const Plan& p) {
-  if (p.kind != kCCA || 2 * p.k > 2 * tc::kHalfMax || p.v[0].d > 512 || p.v[1].d > 512) return false;
+  if (p.kind != kCCA || 2 * p.k > 2 * tc::kHalfMax || p.v[0].d > 1024 || p.v[1].d > 1024) return false;
   if (p.dtype == GBCCA_FP32) return p.ts_ready && p.ts_interleaved;  // the plan's own aligned copy
   if (p.dtype != GBCCA_BF16) return false;
   for (int v = 0; v < 2; ++v) {
@@ -764,7 +833,10 @@ static void tc_group(const Plan& p, int g, int* col0, int* ng) {
   *ng = g == 0 ? ng0 : k2 - ng0;
 }
 static int tc_group_h1(int ng) { return ng <= 20 ? 20 : tc::kHalfMax; }
-static uint8_t* tc_group_img(const Plan& p, int g) { return p.tc_img + (int64_t)g * 2 * tc::kPhiView; }
+// views wider than 512 columns: 4-CTA clusters and images of 16 K-boxes
+bool tc_quad(const Plan& p) { return std::max(p.v[0].d, p.v[1].d) > 512; }
+static int64_t tc_img_view(const Plan& p) { return (tc_quad(p) ? 2 : 1) * (int64_t)tc::kPhiView; }
+static uint8_t* tc_group_img(const Plan& p, int g) { return p.tc_img + (int64_t)g * 2 * tc_img_view(p); }
 // partial slabs of group g: clusters (at most half the SMs) x D x 2 ng floats
 static float* tc_group_part(const Plan& p, int g) {
   int col0 = 0, ng0 = 0;
@@ -783,7 +855,7 @@ int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done) {
     tc_group(p, g, &col0, &ng);
     const int hg = h1 > 0 ? h1 : tc_group_h1(ng);
     tc::phi_image_kernel<<<dim3(ceil_div(dmax * ng, 256), 2), 256, 0, st>>>(
-        p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2, col0, ng, hg, tc_group_img(p, g), done);
+        p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2, col0, ng, hg, tc_group_img(p, g), tc_img_view(p), done);
     GB_CHECK_LAUNCH();
   }
   return GBCCA_OK;
@@ -835,16 +907,21 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     a.ntiles = ceil_div(rows, tc::kRows);
     a.pair_sum = fp32 ? 1 : 0;
     a.phi_img = tc_group_img(p, g);
+    a.img_view = tc_img_view(p);
     a.partG = tc_group_part(p, g);
     a.err = p.flag;
     a.done = done;
-    auto kern = h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>;
-    const int smem = h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes;
+    const bool quad = tc_quad(p);
+    const int csz = quad ? 4 : 2;  // CTAs per cluster
+    auto kern = quad ? (h1 == 20 ? tc::tc_pass_kernel<20, true> : tc::tc_pass_kernel<tc::kHalfMax, true>)
+                     : (h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>);
+    const int smem = quad ? (h1 == 20 ? tc::Lay<20, true>::kSmemBytes : tc::Lay<tc::kHalfMax, true>::kSmemBytes)
+                          : (h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes);
     GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = csz;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(256, 1, 1);
@@ -853,14 +930,14 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (p.tc_clusters <= 0) {
-      // persistent grid: as many 2-CTA clusters as can be resident at once
-      cfg.gridDim = dim3(2 * (p.sm_count / 2), 1, 1);
+      // persistent grid: as many clusters as can be resident at once
+      cfg.gridDim = dim3(csz * (p.sm_count / csz), 1, 1);
       int nc = 0;
       GB_CUDA(cudaOccupancyMaxActiveClusters(&nc, kern, &cfg));
-      p.tc_clusters = std::max(1, std::min(nc, p.sm_count / 2));
+      p.tc_clusters = std::max(1, std::min(nc, p.sm_count / csz));
     }
     ncl = std::min(p.tc_clusters, a.ntiles);
-    cfg.gridDim = dim3(2 * ncl, 1, 1);
+    cfg.gridDim = dim3(csz * ncl, 1, 1);
     GB_CUDA(cudaLaunchKernelEx(&cfg, kern, *mx, *my, a));
     GB_CHECK_LAUNCH();
   }

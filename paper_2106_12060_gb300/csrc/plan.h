@@ -247,6 +247,7 @@ bool tc_pass_eligible(const Plan& p);
 int tc_pass(Plan& p, cudaStream_t st, const int* done);
 int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done);
 int tc_groups(const Plan& p);
+bool tc_quad(const Plan& p);
 // batched tensor-core pass over several eligible plans (one persistent launch)
 struct TcBatch;
 TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc);

@@ -103,7 +103,8 @@ def _cca(gb, P, n, dx, dy, k, seed=0):
 
 
 @pytest.mark.parametrize("n,dx,dy,k", [(3001, 192, 136, 5), (4099, 70, 45, 5), (20000, 512, 384, 10),
-                                       (64, 64, 40, 1), (33, 24, 8, 3), (12345, 500, 24, 12), (7001, 136, 97, 15)])
+                                       (64, 64, 40, 1), (33, 24, 8, 3), (12345, 500, 24, 12), (7001, 136, 97, 15),
+                                       (3001, 768, 136, 6)])
 def test_split_cca_pass_ragged(gb, n, dx, dy, k):
     P = cca_latent_problem(n, dx, dy, latent=6, dtype="f32", seed=n, colscale=(1.0, 1e-3))
     got, exp, refs = _cca(gb, P, n, dx, dy, k)

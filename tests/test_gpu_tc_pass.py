@@ -87,11 +87,17 @@ def _check(got, exp, refs, gamma):
 
 
 @pytest.mark.parametrize("n,dx,dy,k", [(3001, 192, 136, 5), (128, 128, 128, 12), (20000, 512, 384, 10),
-                                       (80, 64, 72, 1), (5003, 200, 136, 13), (9001, 512, 488, 20)])
+                                       (80, 64, 72, 1), (5003, 200, 136, 13), (9001, 512, 488, 20),
+                                       (4001, 1024, 256, 5), (3003, 704, 600, 10), (2050, 1024, 64, 20),
+                                       (900, 520, 72, 3)])
 def test_tc_pass_ragged(gb, n, dx, dy, k):
     """Ragged sizes; k = 13 and k = 20 take two column groups of Phi (14 + 12
     and 20 + 20 columns per view), each its own pass over the data with the
-    same rounding steps, reduced into their columns of G."""
+    same rounding steps, reduced into their columns of G.  Views wider than
+    512 columns run in 4-CTA clusters: each view's column pairs split over two
+    CTAs whose FP32 partial products W are added before the hi/lo split (one
+    more FP32 rounding, inside the bound's slack); a narrow view beside a wide
+    one gives its second CTA a pair of zero columns past its last one."""
     P = cca_latent_problem(n, dx, dy, latent=6, dtype="bf16", seed=n)
     got, exp, refs = _run(gb, P, n, dx, dy, k)
     _check(got, exp, refs, gamma_tc(n, max(dx, dy)))
