@@ -24,15 +24,18 @@
 
 namespace gbcca {
 
+// Two batched launches serve the tensor-core plans: table 0 in 2-CTA
+// clusters, table 1 in 4-CTA clusters (plans with a view wider than 512).
 struct Batch {
   std::vector<Plan*> plans;
-  std::vector<int> tc_index;       // index in the tensor-core table, or -1
-  std::vector<Plan*> tc_plans;
-  TcBatch* tc = nullptr;
+  std::vector<int> tc_table;       // 0 or 1: the table that serves the plan's pass; -1: its own pass
+  std::vector<int> tc_index;       // index in that table
+  std::vector<Plan*> tc_plans[2];
+  TcBatch* tc[2] = {nullptr, nullptr};
   gbcca_batch_options opt{};
-  int clusters = 0;                // chosen clusters of the batched launch
+  int clusters[2] = {0, 0};        // chosen clusters of each batched launch
   bool tuned = false;
-  double tune_ms = 0;              // batched pass time of the chosen schedule (all plans active)
+  double tune_ms = 0;              // batched pass time of the chosen schedules (all plans active)
   int64_t tune_bytes = 0;
   cudaStream_t cap = nullptr;      // capture stream
   std::vector<cudaStream_t> side;  // one branch stream per plan
@@ -53,7 +56,8 @@ Batch* as_batch(gbcca_batch_t h) { return reinterpret_cast<Batch*>(h); }
 void destroy(Batch* b) {
   if (b == nullptr) return;
   if (b->exec != nullptr) cudaGraphExecDestroy(b->exec);
-  tc_batch_destroy(b->tc);
+  tc_batch_destroy(b->tc[0]);
+  tc_batch_destroy(b->tc[1]);
   for (cudaStream_t s : b->side)
     if (s != nullptr) cudaStreamDestroy(s);
   if (b->cap != nullptr) cudaStreamDestroy(b->cap);
@@ -80,8 +84,8 @@ int enqueue_iteration(Batch& b, const std::vector<char>& active, cudaStream_t st
     Plan& p = *b.plans[i];
     const bool low = p.dtype != GBCCA_FP64;
     GB_CUDA(cudaStreamWaitEvent(b.side[i], b.fork_a, 0));
-    if (b.tc_index[i] >= 0) {
-      GB_TRY(tc_batch_pre(b.tc, p, b.side[i]));
+    if (b.tc_table[i] >= 0) {
+      GB_TRY(tc_batch_pre(b.tc[b.tc_table[i]], p, b.side[i]));
       any_tc = true;
     } else {
       GB_TRY(fused_pass(p, low, false, b.side[i], 0, &p.st->done));
@@ -91,21 +95,22 @@ int enqueue_iteration(Batch& b, const std::vector<char>& active, cudaStream_t st
   }
   if (any_tc) {
     for (int i = 0; i < n; ++i)
-      if (active[i] && b.tc_index[i] >= 0) GB_CUDA(cudaStreamWaitEvent(st, b.join_a[i], 0));
-    GB_TRY(tc_batch_launch(b.tc, st, nullptr, nullptr));
+      if (active[i] && b.tc_table[i] >= 0) GB_CUDA(cudaStreamWaitEvent(st, b.join_a[i], 0));
+    for (int t = 0; t < 2; ++t)
+      if (b.tc[t] != nullptr) GB_TRY(tc_batch_launch(b.tc[t], st, nullptr, nullptr));
     GB_CUDA(cudaEventRecord(b.fork_b, st));
     for (int i = 0; i < n; ++i) {
-      if (!active[i] || b.tc_index[i] < 0) continue;
+      if (!active[i] || b.tc_table[i] < 0) continue;
       Plan& p = *b.plans[i];
       GB_CUDA(cudaStreamWaitEvent(b.side[i], b.fork_b, 0));
-      GB_TRY(tc_batch_post(b.tc, b.tc_index[i], p, b.side[i], &p.st->done));
+      GB_TRY(tc_batch_post(b.tc[b.tc_table[i]], b.tc_index[i], p, b.side[i], &p.st->done));
       GB_TRY(iteration_post(p, p.dtype != GBCCA_FP64, b.side[i]));
       GB_CUDA(cudaEventRecord(b.join_b[i], b.side[i]));
     }
   }
   for (int i = 0; i < n; ++i) {
     if (!active[i]) continue;
-    GB_CUDA(cudaStreamWaitEvent(st, b.tc_index[i] >= 0 ? b.join_b[i] : b.join_a[i], 0));
+    GB_CUDA(cudaStreamWaitEvent(st, b.tc_table[i] >= 0 ? b.join_b[i] : b.join_a[i], 0));
   }
   return GBCCA_OK;
 }
@@ -158,57 +163,64 @@ int replay(Batch& b, const std::vector<char>& active, int nb, cudaStream_t st) {
   return GBCCA_OK;
 }
 
-// Time the batched pass over all tensor-core plans for `clusters` clusters:
-// one warm launch, then the median of three.
-int time_schedule(Batch& b, int clusters, cudaStream_t st, double* ms) {
-  const size_t m = b.tc_plans.size();
+// Time batched launch t over all its plans for `clusters` clusters: one warm
+// launch, then the median of three.
+int time_schedule(Batch& b, int t, int clusters, cudaStream_t st, double* ms) {
+  const size_t m = b.tc_plans[t].size();
   std::unique_ptr<bool[]> a(new bool[std::max<size_t>(m, 1)]);
   for (size_t i = 0; i < m; ++i) a[i] = true;
-  GB_TRY(tc_batch_schedule(b.tc, a.get(), clusters, st));
-  GB_TRY(tc_batch_launch(b.tc, st, nullptr, nullptr));
-  float t[3];
+  GB_TRY(tc_batch_schedule(b.tc[t], a.get(), clusters, st));
+  GB_TRY(tc_batch_launch(b.tc[t], st, nullptr, nullptr));
+  float tm[3];
   for (int r = 0; r < 3; ++r) {
-    GB_TRY(tc_batch_launch(b.tc, st, b.ev0, b.ev1));
+    GB_TRY(tc_batch_launch(b.tc[t], st, b.ev0, b.ev1));
     GB_CUDA(cudaEventSynchronize(b.ev1));
-    GB_CUDA(cudaEventElapsedTime(&t[r], b.ev0, b.ev1));
+    GB_CUDA(cudaEventElapsedTime(&tm[r], b.ev0, b.ev1));
   }
-  std::sort(t, t + 3);
-  *ms = t[1];
+  std::sort(tm, tm + 3);
+  *ms = tm[1];
   return GBCCA_OK;
 }
 
+// Each batched launch's cluster count: the option's, else the fastest of a
+// few candidates timed on the plans' start points.
 int autotune(Batch& b, cudaStream_t st) {
-  const int maxc = tc_batch_max_clusters(b.tc);
-  std::vector<int> cand;
-  if (b.opt.clusters > 0) {
-    cand.push_back(std::min(b.opt.clusters, maxc));
-  } else {
-    for (int c : {maxc, maxc - 2, maxc - 4, (3 * maxc) / 4, maxc / 2})
-      if (c >= 1 && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
-  }
-  double best = 1e300;
-  int best_c = cand[0];
-  for (int c : cand) {
-    double ms = 0;
-    GB_TRY(time_schedule(b, c, st, &ms));
-    if (ms < best) {
-      best = ms;
-      best_c = c;
+  b.tune_ms = 0;
+  b.tune_bytes = 0;
+  for (int t = 0; t < 2; ++t) {
+    if (b.tc[t] == nullptr) continue;
+    const int maxc = tc_batch_max_clusters(b.tc[t]);
+    std::vector<int> cand;
+    if (b.opt.clusters > 0) {
+      cand.push_back(std::min(b.opt.clusters, maxc));
+    } else {
+      for (int c : {maxc, maxc - 2, maxc - 4, (3 * maxc) / 4, maxc / 2})
+        if (c >= 1 && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
     }
+    double best = 1e300;
+    int best_c = cand[0];
+    for (int c : cand) {
+      double ms = 0;
+      GB_TRY(time_schedule(b, t, c, st, &ms));
+      if (ms < best) {
+        best = ms;
+        best_c = c;
+      }
+    }
+    // the device error flag of the batched kernel must be clear after the trials
+    int err = 0;
+    GB_CUDA(cudaMemcpyAsync(&err, tc_batch_err(b.tc[t]), sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (err != 0) {
+      GB_CUDA(cudaMemsetAsync(tc_batch_err(b.tc[t]), 0, sizeof(int), st));
+      return flag_status(err);
+    }
+    b.clusters[t] = best_c;
+    b.tune_ms += best;
+    std::unique_ptr<bool[]> a(new bool[std::max<size_t>(b.tc_plans[t].size(), 1)]);
+    for (size_t i = 0; i < b.tc_plans[t].size(); ++i) a[i] = true;
+    b.tune_bytes += tc_batch_bytes(b.tc[t], a.get());
   }
-  // the device error flag of the batched kernel must be clear after the trials
-  int err = 0;
-  GB_CUDA(cudaMemcpyAsync(&err, tc_batch_err(b.tc), sizeof(int), cudaMemcpyDeviceToHost, st));
-  GB_CUDA(cudaStreamSynchronize(st));
-  if (err != 0) {
-    GB_CUDA(cudaMemsetAsync(tc_batch_err(b.tc), 0, sizeof(int), st));
-    return flag_status(err);
-  }
-  b.clusters = best_c;
-  b.tune_ms = best;
-  std::unique_ptr<bool[]> a(new bool[std::max<size_t>(b.tc_plans.size(), 1)]);
-  for (size_t i = 0; i < b.tc_plans.size(); ++i) a[i] = true;
-  b.tune_bytes = tc_batch_bytes(b.tc, a.get());
   b.tuned = true;
   return GBCCA_OK;
 }
@@ -227,12 +239,12 @@ Batch* batch_make(Plan* const* plans, int count, const gbcca_batch_options* opt,
   for (int i = 0; i < count; ++i) {
     Plan* p = plans[i];
     b->plans.push_back(p);
-    // the batched launch runs 2-CTA clusters: plans with a view wider than
-    // 512 columns (4-CTA clusters) run their own tensor-core pass on their branch
     const bool tc = p->kind == kCCA && p->dtype != GBCCA_FP64 && p->opt.tensor_cores && p->tc_img != nullptr &&
-                    tc_pass_eligible(*p) && !tc_quad(*p);
-    b->tc_index.push_back(tc ? (int)b->tc_plans.size() : -1);
-    if (tc) b->tc_plans.push_back(p);
+                    tc_pass_eligible(*p);
+    const int t = tc ? (tc_quad(*p) ? 1 : 0) : -1;
+    b->tc_table.push_back(t);
+    b->tc_index.push_back(t >= 0 ? (int)b->tc_plans[t].size() : -1);
+    if (t >= 0) b->tc_plans[t].push_back(p);
   }
   auto fail = [&](cudaError_t e) {
     set_last_error(std::string("batch: ") + cudaGetErrorString(e));
@@ -255,14 +267,15 @@ Batch* batch_make(Plan* const* plans, int count, const gbcca_batch_options* opt,
   if ((e = cudaEventCreateWithFlags(&b->fork_b, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
   if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess) return fail(e);
   if ((e = cudaEventCreate(&b->ev1)) != cudaSuccess) return fail(e);
-  if (!b->tc_plans.empty()) {
-    b->tc = tc_batch_create(b->tc_plans.data(), (int)b->tc_plans.size(), b->cap, rc);
-    if (b->tc == nullptr) {
+  for (int t = 0; t < 2; ++t) {
+    if (b->tc_plans[t].empty()) continue;
+    b->tc[t] = tc_batch_create(b->tc_plans[t].data(), (int)b->tc_plans[t].size(), b->cap, rc);
+    if (b->tc[t] == nullptr) {
       destroy(b);
       return nullptr;
     }
-    b->clusters = b->opt.clusters > 0 ? std::min(b->opt.clusters, tc_batch_max_clusters(b->tc))
-                                      : tc_batch_max_clusters(b->tc);
+    b->clusters[t] = b->opt.clusters > 0 ? std::min(b->opt.clusters, tc_batch_max_clusters(b->tc[t]))
+                                         : tc_batch_max_clusters(b->tc[t]);
   }
   return b;
 }
@@ -275,11 +288,12 @@ int batch_size(const Batch& b) { return (int)b.plans.size(); }
 // and nb is the batch's replay length, else launched one by one), after
 // writing the schedule of the active tensor-core plans.
 int batch_iterate(Batch& b, const std::vector<char>& active, int nb, bool graph, cudaStream_t st) {
-  if (b.tc != nullptr) {
-    std::unique_ptr<bool[]> a(new bool[std::max<size_t>(b.tc_plans.size(), 1)]);
+  for (int t = 0; t < 2; ++t) {
+    if (b.tc[t] == nullptr) continue;
+    std::unique_ptr<bool[]> a(new bool[std::max<size_t>(b.tc_plans[t].size(), 1)]);
     for (size_t i = 0; i < b.plans.size(); ++i)
-      if (b.tc_index[i] >= 0) a[b.tc_index[i]] = active[i] != 0;
-    GB_TRY(tc_batch_schedule(b.tc, a.get(), b.clusters, st));
+      if (b.tc_table[i] == t) a[b.tc_index[i]] = active[i] != 0;
+    GB_TRY(tc_batch_schedule(b.tc[t], a.get(), b.clusters[t], st));
   }
   if (graph) return replay(b, active, nb, st);
   for (int it = 0; it < nb; ++it) GB_TRY(enqueue_iteration(b, active, st));
@@ -295,15 +309,17 @@ int batch_poll(Batch& b, std::vector<char>& active, gbcca_info* infos, cudaStrea
   if (err_plan != nullptr) *err_plan = -1;
   for (int i = 0; i < n; ++i)
     if (active[i]) GB_TRY(read_state_async(*b.plans[i], st));
-  int tc_err = 0;
-  if (b.tc != nullptr)
-    GB_CUDA(cudaMemcpyAsync(&tc_err, tc_batch_err(b.tc), sizeof(int), cudaMemcpyDeviceToHost, st));
+  int tc_err[2] = {0, 0};
+  for (int t = 0; t < 2; ++t)
+    if (b.tc[t] != nullptr)
+      GB_CUDA(cudaMemcpyAsync(&tc_err[t], tc_batch_err(b.tc[t]), sizeof(int), cudaMemcpyDeviceToHost, st));
   GB_CUDA(cudaStreamSynchronize(st));
-  if (tc_err != 0) {
-    GB_CUDA(cudaMemsetAsync(tc_batch_err(b.tc), 0, sizeof(int), st));
+  for (int t = 0; t < 2; ++t) {
+    if (tc_err[t] == 0) continue;
+    GB_CUDA(cudaMemsetAsync(tc_batch_err(b.tc[t]), 0, sizeof(int), st));
     GB_CUDA(cudaStreamSynchronize(st));
     set_last_error("batched tensor-core pass: a bounded pipeline wait ran out");
-    return flag_status(tc_err);
+    return flag_status(tc_err[t]);
   }
   for (int i = 0; i < n; ++i) {
     if (!active[i]) continue;
@@ -319,8 +335,9 @@ int batch_poll(Batch& b, std::vector<char>& active, gbcca_info* infos, cudaStrea
 }
 
 int batch_tune(Batch& b, cudaStream_t st) {
-  if (b.tc == nullptr || b.tuned) return GBCCA_OK;
-  for (Plan* p : b.tc_plans) GB_TRY(tc_batch_pre(b.tc, *p, st));
+  if ((b.tc[0] == nullptr && b.tc[1] == nullptr) || b.tuned) return GBCCA_OK;
+  for (int t = 0; t < 2; ++t)
+    for (Plan* p : b.tc_plans[t]) GB_TRY(tc_batch_pre(b.tc[t], *p, st));
   return autotune(b, st);
 }
 
@@ -419,8 +436,8 @@ int gbcca_batch_solve(gbcca_batch_t h, double* const* U, double* const* V, doubl
   if (report != nullptr) {
     std::memset(report, 0, sizeof(*report));
     report->iterations = lockstep;
-    report->clusters = b->clusters;
-    report->batched_plans = (int32_t)b->tc_plans.size();
+    report->clusters = b->clusters[0] > 0 ? b->clusters[0] : b->clusters[1];
+    report->batched_plans = (int32_t)(b->tc_plans[0].size() + b->tc_plans[1].size());
     report->batched_pass_ms = b->tune_ms;
     report->batched_pass_bytes = (double)b->tune_bytes;
   }
@@ -434,37 +451,45 @@ int gbcca_batch_fused_pass(gbcca_batch_t h, const double* const* Phi_x, const do
     set_last_error("gbcca_batch_fused_pass: NULL argument");
     return GBCCA_ERR_INVALID_ARG;
   }
-  if (b->tc == nullptr || b->tc_plans.size() != b->plans.size()) {
+  const int n = (int)b->plans.size();
+  if (b->tc_plans[0].size() + b->tc_plans[1].size() != (size_t)n) {
     set_last_error("gbcca_batch_fused_pass: every plan of the batch must be served by the tensor-core pass");
     return GBCCA_ERR_UNSUPPORTED;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int n = (int)b->plans.size();
   for (int i = 0; i < n; ++i) {
     Plan& p = *b->plans[i];
     const int k2 = 2 * p.k;
     GB_CUDA(cudaMemsetAsync(&p.st->done, 0, sizeof(int), st));
     GB_CUDA(cudaMemcpyAsync(p.v[0].Phi, Phi_x[i], sizeof(double) * p.v[0].d * k2, cudaMemcpyDeviceToDevice, st));
     GB_CUDA(cudaMemcpyAsync(p.v[1].Phi, Phi_y[i], sizeof(double) * p.v[1].d * k2, cudaMemcpyDeviceToDevice, st));
-    GB_TRY(tc_batch_pre(b->tc, p, st));
+    GB_TRY(tc_batch_pre(b->tc[b->tc_table[i]], p, st));
   }
-  std::unique_ptr<bool[]> a(new bool[std::max(n, 1)]);
-  for (int i = 0; i < n; ++i) a[i] = true;
-  GB_TRY(tc_batch_schedule(b->tc, a.get(), b->opt.clusters > 0 ? b->opt.clusters : tc_batch_max_clusters(b->tc), st));
-  GB_TRY(tc_batch_launch(b->tc, st, nullptr, nullptr));
+  for (int t = 0; t < 2; ++t) {
+    if (b->tc[t] == nullptr) continue;
+    const int m = (int)b->tc_plans[t].size();
+    std::unique_ptr<bool[]> a(new bool[std::max(m, 1)]);
+    for (int i = 0; i < m; ++i) a[i] = true;
+    GB_TRY(tc_batch_schedule(b->tc[t], a.get(),
+                             b->opt.clusters > 0 ? b->opt.clusters : tc_batch_max_clusters(b->tc[t]), st));
+    GB_TRY(tc_batch_launch(b->tc[t], st, nullptr, nullptr));
+  }
   for (int i = 0; i < n; ++i) {
     Plan& p = *b->plans[i];
-    GB_TRY(tc_batch_post(b->tc, i, p, st, nullptr));
+    GB_TRY(tc_batch_post(b->tc[b->tc_table[i]], b->tc_index[i], p, st, nullptr));
     const int k4 = 4 * p.k;
     GB_CUDA(cudaMemcpyAsync(G[i], p.G, sizeof(double) * p.D * k4, cudaMemcpyDeviceToDevice, st));
     GB_CUDA(cudaMemcpyAsync(Gram[i], p.Gram, sizeof(double) * k4 * k4, cudaMemcpyDeviceToDevice, st));
   }
-  int err = 0;
-  GB_CUDA(cudaMemcpyAsync(&err, tc_batch_err(b->tc), sizeof(int), cudaMemcpyDeviceToHost, st));
+  int err[2] = {0, 0};
+  for (int t = 0; t < 2; ++t)
+    if (b->tc[t] != nullptr)
+      GB_CUDA(cudaMemcpyAsync(&err[t], tc_batch_err(b->tc[t]), sizeof(int), cudaMemcpyDeviceToHost, st));
   GB_CUDA(cudaStreamSynchronize(st));
-  if (err != 0) {
-    GB_CUDA(cudaMemsetAsync(tc_batch_err(b->tc), 0, sizeof(int), st));
-    return flag_status(err);
+  for (int t = 0; t < 2; ++t) {
+    if (err[t] == 0) continue;
+    GB_CUDA(cudaMemsetAsync(tc_batch_err(b->tc[t]), 0, sizeof(int), st));
+    return flag_status(err[t]);
   }
   return GBCCA_OK;
 }

@@ -126,6 +126,7 @@ struct Inst {
   float* partG;            // [slab][D][4k] partials of this instance
   const int* done;         // the instance's convergence flag: skip it when set
   int64_t slab;            // floats per partial slab (D * 4k)
+  int64_t img_view;        // bytes between the two views' Phi images
   int d[2];
   int pairs[2];
   int k2;
@@ -216,7 +217,7 @@ __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tm
     const Seg sg = a.segs[a.seg_off[cid] + s];
     const Inst* I = a.insts + sg.inst;
     v.map = &I->map[view];
-    v.phi = I->phi_img + view * kPhiView;
+    v.phi = I->phi_img + view * I->img_view;
     v.out = I->partG + (int64_t)sg.slab * I->slab;
     v.d0 = I->d[0];
     v.d1 = I->d[1];
@@ -964,6 +965,8 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
 // counts live in device memory, so a captured graph keeps one launch while
 // the schedule is rewritten between replays (finished plans drop out).
 struct TcBatch {
+  bool quad = false;           // 4-CTA clusters (plans with a view wider than 512)
+  int csz = 2;                 // CTAs per cluster
   int n = 0;                   // table entries: one per (plan, column group)
   int nplans = 0;
   int h1 = tc::kHalfMax;       // Phi image rows per half, common to the batch
@@ -1009,6 +1012,8 @@ TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
     return nullptr;
   }
   b->nplans = n;
+  b->quad = n > 0 && tc_quad(*plans[0]);
+  b->csz = b->quad ? 4 : 2;
   int entries = 0, h1 = 20, sm = 1;
   for (int i = 0; i < n; ++i) {
     b->first.push_back(entries);
@@ -1023,7 +1028,7 @@ TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
   }
   b->n = entries;
   b->h1 = h1;
-  b->max_clusters = std::max(1, sm / 2);
+  b->max_clusters = std::max(1, sm / b->csz);
   b->max_segs = b->max_clusters + entries + 1;  // a contiguous partition has at most clusters + entries pieces
   const int n1 = std::max(entries, 1);
   bool ok = cudaMallocHost(&b->inst_h, sizeof(tc::Inst) * n1) == cudaSuccess &&
@@ -1067,6 +1072,7 @@ TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
       int col0 = 0, ng = 0;
       tc_group(p, g, &col0, &ng);
       I.phi_img = tc_group_img(p, g);
+      I.img_view = tc_img_view(p);
       I.partG = tc_group_part(p, g);
       I.done = &p.st->done;
       I.k2 = ng;
@@ -1113,11 +1119,15 @@ int tc_batch_schedule(TcBatch* b, const bool* plan_active, int clusters, cudaStr
   std::vector<char> active(b->n, 0);  // per entry
   for (int i = 0; i < b->nplans; ++i)
     for (int g = 0; g < b->count[i]; ++g) active[b->first[i] + g] = plan_active[i] ? 1 : 0;
+  // pairs of a tile per CTA (4-CTA clusters: each view's pairs over two CTAs)
+  auto cta_pairs = [&](int i) {
+    const int P = std::max(b->inst_h[i].pairs[0], b->inst_h[i].pairs[1]);
+    return b->quad ? (P + 1) / 2 : P;
+  };
   int64_t total = 0;
   for (int i = 0; i < b->n; ++i) {
     b->nparts_h[i] = 0;
-    if (active[i])
-      total += ceil_div(b->rows[i], (int64_t)tc::kRows) * (2 + std::max(b->inst_h[i].pairs[0], b->inst_h[i].pairs[1]));
+    if (active[i]) total += ceil_div(b->rows[i], (int64_t)tc::kRows) * (2 + cta_pairs(i));
   }
   int c = 0, nseg = 0;
   int64_t cum = 0;
@@ -1126,7 +1136,7 @@ int tc_batch_schedule(TcBatch* b, const bool* plan_active, int clusters, cudaStr
   for (int i = 0; i < b->n; ++i) {
     if (!active[i]) continue;
     const int64_t tiles = ceil_div(b->rows[i], (int64_t)tc::kRows);
-    const int64_t w = 2 + std::max(b->inst_h[i].pairs[0], b->inst_h[i].pairs[1]);
+    const int64_t w = 2 + cta_pairs(i);
     int pieces = 0;  // segments of instance i so far = its next slab
     int64_t t = 0;
     while (t < tiles) {
@@ -1162,13 +1172,15 @@ int tc_batch_launch(TcBatch* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
   a.insts = b->inst_d;
   a.segs = b->seg_d;
   a.seg_off = b->off_d;
-  auto kern = b->h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>;
-  const int smem = b->h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes;
+  auto kern = b->quad ? (b->h1 == 20 ? tc::tc_pass_kernel<20, true> : tc::tc_pass_kernel<tc::kHalfMax, true>)
+                      : (b->h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>);
+  const int smem = b->quad ? (b->h1 == 20 ? tc::Lay<20, true>::kSmemBytes : tc::Lay<tc::kHalfMax, true>::kSmemBytes)
+                           : (b->h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes);
   GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.x = b->csz;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(256, 1, 1);
@@ -1176,7 +1188,7 @@ int tc_batch_launch(TcBatch* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.gridDim = dim3(2 * std::max(1, b->clusters), 1, 1);
+  cfg.gridDim = dim3(b->csz * std::max(1, b->clusters), 1, 1);
   // the tensor-map parameters are unused in batch mode; any valid map will do
   const CUtensorMap* m0 = &b->inst_h[0].map[0];
   const CUtensorMap* m1 = &b->inst_h[0].map[1];

@@ -49,7 +49,7 @@ def gamma_batched(rows, d, fp32):
     cluster; FP32 data adds the representation of Z twice and the hi/lo row
     sum (see test_gpu_split_pass)."""
     T = -(-rows // 64)
-    g = 2.0 ** -17 + 2.0 ** -23 * (2 * (d / 16 + 2) + 2 * (4 * T + 1) + 4)
+    g = 2.0 ** -17 + 2.0 ** -23 * (2 * (d / 16 + 2) + 2 * (4 * T + 1) + 4 + 2)  # + the halves' partial-W sum
     if fp32:
         g += 2 * 2.0 ** -17 + 2 * 2.0 ** -23
     return g
@@ -57,9 +57,11 @@ def gamma_batched(rows, d, fp32):
 
 # (n, dx, dy, k, storage): ragged sizes, both Phi image widths (2k <= 20 and
 # 2k = 24), one-pair and four-pair views, FP32 data through the interleaved
-# copy, and k = 20 (two column groups, two table entries for one plan)
+# copy, k = 20 (two column groups, two table entries for one plan), and
+# views wider than 512 (the second batched launch, in 4-CTA clusters)
 SHAPES = [(9001, 200, 120, 5, "bf16"), (4097, 64, 40, 10, "bf16"), (20000, 512, 296, 12, "bf16"),
-          (3001, 96, 80, 4, "f32"), (150, 24, 16, 3, "bf16"), (6007, 160, 128, 20, "bf16")]
+          (3001, 96, 80, 4, "f32"), (150, 24, 16, 3, "bf16"), (6007, 160, 128, 20, "bf16"),
+          (5003, 768, 200, 6, "bf16"), (2001, 1024, 64, 3, "f32")]
 
 
 def _make(gb, shapes, seed0=0, **opt):
@@ -107,11 +109,10 @@ def test_batched_pass_matches_oracle(gb, clusters):
 
 
 def test_batch_solve_matches_solo_solves(gb):
-    """Seven plans in one batch: five served by the batched launch (BF16 and
-    FP32 data, and 2k = 30 in two column groups), one with a 600-wide view
-    (its own CUDA-core pass on its branch) and an FDA plan (its own FP32
-    pass).  Each result equals its solo solve within 1e-6 and the oracle
-    within 1e-6."""
+    """Seven plans in one batch: six served by the batched launches (BF16
+    and FP32 data, 2k = 30 in two column groups, and a 600-wide view in the
+    4-CTA launch) and an FDA plan (its own FP32 pass on its branch).  Each
+    result equals its solo solve within 1e-6 and the oracle within 1e-6."""
     import torch
     shapes = [(9001, 200, 120, 5, "bf16"), (4097, 64, 40, 10, "bf16"), (20000, 512, 296, 12, "bf16"),
               (3001, 96, 80, 4, "f32"), (5000, 104, 88, 15, "bf16"), (7000, 600, 64, 4, "bf16")]
@@ -132,7 +133,7 @@ def test_batch_solve_matches_solo_solves(gb):
     allp = plans + [lplan]
     batch = gb.Batch(allp)
     res, report = gb.batch_solve(batch)
-    assert report["batched_plans"] == 5, report
+    assert report["batched_plans"] == 6, report
     assert report["batched_pass_ms"] > 0 and report["clusters"] >= 1, report
     for i, (val, _, _, info) in enumerate(res):
         assert info["status"] == gb.OK, (i, info)
