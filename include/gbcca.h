@@ -104,8 +104,8 @@ typedef struct {
                             iteration.                                      */
   int32_t tensor_cores;  /* 1 (default): the data pass runs on the tensor-core
                             kernels where the plan is eligible (CCA: BF16 or
-                            FP32 data, dx, dy <= 512, BF16 rows 16-byte
-                            aligned, any k; FDA: FP32 data, d <= 896); 0:
+                            FP32 data, any shape, BF16 rows 16-byte aligned;
+                            FDA: FP32 data, d <= 896); 0:
                             the CUDA-core kernels only (for comparisons)     */
   int32_t warm_iters;    /* block power iterations of the CCA warm start (the
                             exact CCA of the sketched pair, Alg. 1 step 4);
@@ -296,8 +296,9 @@ int32_t gbcca_sketch_gram_noalloc_max_d(void);
  * (cca_precondition / lda_solve's preconditioning through a previous call)
  * with opt.warm_start on, and stays owned by the caller; its data must stay
  * valid while the batch exists.  Every iteration, the data passes of the
- * plans the tensor-core pass serves (CCA, BF16 or FP32 data, dx, dy <= 512;
- * k > 12 in two column groups of Phi) run as ONE persistent launch over a schedule of (instance,
+ * plans the tensor-core pass serves (CCA, BF16 or FP32 data; k > 12 in two
+ * column groups of Phi) run as ONE persistent launch (two when some plans
+ * have a view wider than 512 columns: those run in 4-CTA clusters) over a schedule of (instance,
  * 64-row tile range) segments cut into near-equal work per 2-CTA cluster;
  * the other plans run their own passes.  Each plan's small kernels run on a
  * graph branch of their own, and each plan stops on its own rule (its
