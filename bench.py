@@ -376,8 +376,9 @@ def other_workloads(gb, steps: int = 2):
     out["lda_f32"] = {"solve_ms": ms, "iterations": float(np.mean([i["iters"] for i in infos])),
                       "rtol": RTOL, "refine": LDA_REFINE, "status": infos[-1]["status"], "pass_ms": pass_ms,
                       "pass_GBps": gbps, "pass_frac_of_hbm": gbps / hbm, "pass_algorithmic_bytes": nbytes,
-                      "kernels": "split_pass_kernel (tcgen05 + TMA over the BF16 hi/lo copy of the class-centred "
-                                 "FP32 data): Xhat^T (Xhat Phi)"}
+                      "kernels": "tc_pass_kernel in one-view 2-CTA clusters (tcgen05 + TMA over the row-interleaved "
+                                 "BF16 hi/lo copy of the class-centred FP32 data, the view's column pairs split over "
+                                 "the two CTAs): Xhat^T (Xhat Phi)"}
     plan.close()
     del X
     torch.cuda.empty_cache()

@@ -105,7 +105,7 @@ typedef struct {
   int32_t tensor_cores;  /* 1 (default): the data pass runs on the tensor-core
                             kernels where the plan is eligible (CCA: BF16 or
                             FP32 data, any shape, BF16 rows 16-byte aligned;
-                            FDA: FP32 data, d <= 896); 0:
+                            FDA: FP32 data, d <= 1024); 0:
                             the CUDA-core kernels only (for comparisons)     */
   int32_t warm_iters;    /* block power iterations of the CCA warm start (the
                             exact CCA of the sketched pair, Alg. 1 step 4);
@@ -113,7 +113,8 @@ typedef struct {
                             sketched solution to ~1e-6 in subspace angle     */
   int64_t wait_cycles;   /* bound, in GPU clock cycles, on one pipeline wait of
                             the FDA tensor-core pass for FP32 data (0 = the
-                            default 2e9, about one second).  A wait that runs
+                            default 2e9, about one second; the CCA passes
+                            always use the default).  A wait that runs
                             out stops the pass early: every CTA drains its own
                             copies and MMAs, and the call returns
                             GBCCA_ERR_TIMEOUT.  Small values exist to exercise

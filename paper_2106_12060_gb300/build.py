@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbcca.so")
-SOURCES = ["api.cu", "batch.cu", "dense.cu", "pass.cu", "pass_split.cu", "pass_tc.cu", "rcg.cu", "server.cu", "sketch.cu"]
+SOURCES = ["api.cu", "batch.cu", "dense.cu", "pass.cu", "hilo_copy.cu", "pass_tc.cu", "rcg.cu", "server.cu", "sketch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -54,8 +54,6 @@ void free_plan(Plan* p) {
                   (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->ls_f, (void*)p->ls_L})
     dfree(q);
   for (int v = 0; v < 2; ++v) dfree(p->ts_copy[v]);
-  dfree(p->ts_img);
-  dfree(p->ts_part);
   if (p->st_host != nullptr) cudaFreeHost(p->st_host);
   if (p->flag_host != nullptr) cudaFreeHost(p->flag_host);
   for (int i = 0; i < p->nev; ++i) cudaEventDestroy(p->ev[i]);
@@ -177,16 +175,18 @@ int alloc_plan(Plan* p) {
   GB_TRY(dalloc(&p->ls_L, 64 * 2 * (int64_t)kMaxK * kMaxK));
   GB_TRY(dalloc(&p->flag, 1));
   GB_CUDA(cudaMemset(p->flag, 0, sizeof(int)));
-  if (p->kind == kCCA && (p->dtype == GBCCA_BF16 || p->dtype == GBCCA_FP32) && p->opt.tensor_cores) {
-    // Phi images of both views per column group (two groups for 2k > 24;
-    // twice the K-boxes for views wider than 512), and the per-cluster
-    // partial slabs of every group
-    const int64_t img = (2 * k <= 24 ? 1 : 2) * 2 * (dmax > 512 ? 2 : 1) * 49152;
+  const bool tc_cca = p->kind == kCCA && (p->dtype == GBCCA_BF16 || p->dtype == GBCCA_FP32);
+  const bool tc_fda = p->kind == kLDA && p->dtype == GBCCA_FP32 && dmax <= 1024;
+  if ((tc_cca || tc_fda) && p->opt.tensor_cores) {
+    // Phi images per column group (two groups for 2k > 24): CCA both views'
+    // (twice the K-boxes for views wider than 512), FDA the one view's in 16
+    // K-boxes; and the per-cluster partial slabs of every group
+    const int64_t img = (2 * k <= 24 ? 1 : 2) * (tc_cca ? 2 * (dmax > 512 ? 2 : 1) : 2) * 49152;
     GB_TRY(dalloc(&p->tc_img, img));
     GB_CUDA(cudaMemset(p->tc_img, 0, img));
     GB_TRY(dalloc(&p->tc_part, (int64_t)p->sm_count * p->D * (k4 + 8)));
   }
-  GB_TRY(split_pass_alloc(*p));
+  GB_TRY(hilo_alloc(*p));
   GB_CUDA(cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking));
   GB_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
   GB_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
@@ -302,7 +302,7 @@ int finish_factor(Plan& p, int v, cudaStream_t st) {
 
 int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream_t st) {
   const bool center = p.kind == kLDA;
-  GB_TRY(split_pass_prepare(p, st));
+  GB_TRY(hilo_prepare(p, st));
   const bool srht = p.opt.sketch == GBCCA_SKETCH_SRHT;
   if (srht) {
     if (sh != nullptr && sg != nullptr) {

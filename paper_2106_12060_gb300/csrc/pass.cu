@@ -566,7 +566,6 @@ int fused_pass(Plan& p, bool low, bool gram_only, cudaStream_t st, int phi_cols,
   if (phi_cols <= 0) phi_cols = 2 * p.k;
   if (low && !gram_only && phi_cols == 2 * p.k && p.opt.tensor_cores) {
     if (p.tc_img != nullptr && tc_pass_eligible(p)) return tc_pass(p, st, done);
-    if (split_pass_ready(p)) return split_pass(p, st, done);
   }
   if (p.kev0 != nullptr) GB_CUDA(record_timing_event(p.kev0, st));
   const int rc = fused_pass_cores(p, low, gram_only, st, phi_cols, done);

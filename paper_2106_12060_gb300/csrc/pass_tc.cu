@@ -1,6 +1,10 @@
 // Tensor-core (tcgen05 + TMA) fused CCA data pass for BF16 data on sm_103a,
 // and for FP32 data streamed as a row-interleaved BF16 hi/lo copy (row 2i =
-// bf16(z_i), row 2i + 1 = bf16(z_i - bf16(z_i)); see `pair_sum`).
+// bf16(z_i), row 2i + 1 = bf16(z_i - bf16(z_i)); see `pair_sum`).  The FDA
+// pass (Sec. 5.1-5.2, Cor. 5.6: S_w Phi = Xhat^T (Xhat Phi) over the copy of
+// the class-centred rows) is the same kernel in one-view clusters (kSolo):
+// both CTAs stream the one view, each half of its 128-column pairs, and add
+// their partial products W of every tile before GEMM 2.
 //
 // One Riemannian-CG iteration of the CCA solver needs, for the block-diagonal
 // Phi = blkdiag([U, eta_U], [V, eta_V]) (Sec. 4.2 gradient, Table 1
@@ -68,7 +72,7 @@ constexpr long long kTimeout = kWaitCycles;       // cycles (~1 s)
 // Shared-memory layout and barriers for GEMM 1 with N = 2 kH1 (Phi columns as
 // bf16 hi rows 0 .. kH1 - 1 and lo rows kH1 .. 2 kH1 - 1; kH1 = 20 serves
 // 2k <= 20 and leaves room for a 10-slot ring, kH1 = 24 a 9-slot ring).
-template <int kH1, bool kQuad = false>
+template <int kH1, bool kQuad = false, bool kSolo = false>
 struct Lay {
   static constexpr int kN1 = 2 * kH1;
   static constexpr int kKBox1 = kN1 * 128;       // one K-box (64 columns) of the Phi image
@@ -76,9 +80,10 @@ struct Lay {
   // W operand of GEMM 2 (K-major, one K-box of 64 tile rows): rows
   // [W_x | W_y] of the hi parts (kH1 rows per view; rows 2k .. kH1 - 1 stay
   // zero), then the same rows of the lo parts, so that one MMA with
-  // N = kN2 reads the tile's columns once for both parts.
+  // N = kN2 reads the tile's columns once for both parts.  One view (FDA):
+  // its kH1 rows per part.
   static constexpr int kHalf = kH1;              // W rows of a view
-  static constexpr int kNW = 2 * kH1;            // rows of one part (hi or lo)
+  static constexpr int kNW = (kSolo ? 1 : 2) * kH1;  // rows of one part (hi or lo)
   static constexpr int kN2 = 2 * kNW;            // N of GEMM 2
   static constexpr int kWs = kNW * 128;          // bytes of one part
   static constexpr int kWBuf = 2 * kWs;          // hi + lo
@@ -90,9 +95,11 @@ struct Lay {
   // every 50 cycles, two streams overlap in the tensor pipe.
   static constexpr int kNAcc = (4 * kTW + kTileSlots * kN2 <= (int)kTmemCols) ? 2 : 1;
   static constexpr int kTG = 2 * kNAcc * kTW;    // first TMEM column of the G accumulators
-  // 4-CTA clusters (views wider than 512 columns, split over two CTAs each):
+  // 4-CTA clusters (views wider than 512 columns, split over two CTAs each)
+  // and one-view clusters (FDA: the view's columns split over the two CTAs):
   // two FP32 buffers that receive the other half's partial W of a tile
-  static constexpr int kXBytes = kQuad ? 2 * kH1 * kRows * 4 : 0;
+  static constexpr bool kHalves = kQuad || kSolo;  // a view's pairs over two CTAs
+  static constexpr int kXBytes = kHalves ? 2 * kH1 * kRows * 4 : 0;
   static constexpr int kStages = (kMaxSmem - kPhiBytes - 2 * kWBuf - kXBytes - 512 - 1024) / kSlot;
   static constexpr int kRingOff = kPhiBytes;
   static constexpr int kWsOff = kRingOff + kStages * kSlot;
@@ -109,6 +116,7 @@ struct Lay {
   static constexpr int kPhiFree = kGFree + 1;  // GEMM 1 done with a segment's Phi
   static constexpr int kXFull = kPhiFree + 1, kXFree = kXFull + 2;  // [2], [2]: partial-W exchange (quad)
   static constexpr int kNumBars = kXFree + 2;
+  static_assert(!(kQuad && kSolo), "one cluster shape");
   static_assert(kStages >= 2 * kTileSlots, "two resident tiles");
   static_assert(kN1 <= kTW && kD1Cols <= kTW, "W buffers in TMEM");
   static_assert(kN2 % 16 == 0 && kTG + kTileSlots * kN2 <= (int)kTmemCols, "G accumulators in TMEM");
@@ -151,7 +159,8 @@ struct Args {
   int k2;        // columns of Phi per view (2k)
   int ntiles;
   const uint8_t* phi_img;  // [view][K-box][2 kH1][128 B], pre-swizzled
-  float* partG;            // [cluster][D][4k]
+  float* partG;            // [cluster][D][4k] (one view: [cluster][d][2k])
+  int64_t slab;            // floats between the clusters' partial slabs (a multiple of 4)
   int* err;
   const int* done;
   int64_t img_view;        // bytes between the two views' Phi images
@@ -159,6 +168,8 @@ struct Args {
                            // hi and lo parts of one data row (FP32 data): W of the
                            // row is the sum of the two product rows, and both rows
                            // of GEMM 2's operand carry it
+  long long wait_limit;    // one-view clusters: cycles of one pipeline wait before the
+                           // kernel gives up (the other shapes use kWaitCycles)
   // several instances (insts != nullptr): cluster c takes the segments
   // seg_off[c] .. seg_off[c + 1] - 1 in order
   const Inst* insts;
@@ -178,11 +189,12 @@ struct SegView {
 };
 
 // The 128-column pairs of a view of P pairs that CTA half h takes: all of
-// them in a 2-CTA cluster; in a 4-CTA cluster the first ceil(P / 2) for
-// h = 0 and the rest for h = 1, at least one (a pair past the view's last
-// column reads zeros from the tensor map and the image, and drains nothing).
-__device__ __forceinline__ void half_pairs(int P, bool quad, int h, int* pb, int* np) {
-  if (!quad) {
+// them in a 2-CTA cluster of two views; in a 4-CTA cluster, or a one-view
+// cluster, the first ceil(P / 2) for h = 0 and the rest for h = 1, at least
+// one (a pair past the view's last column reads zeros from the tensor map and
+// the image, and drains nothing).
+__device__ __forceinline__ void half_pairs(int P, bool split, int h, int* pb, int* np) {
+  if (!split) {
     *pb = 0;
     *np = P;
     return;
@@ -197,19 +209,20 @@ __device__ __forceinline__ int seg_count(const Args& a, int cid, int ncl) {
   return a.seg_off[cid + 1] - a.seg_off[cid];
 }
 
+// (split: the view's pairs are split over two CTAs)
 __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tmx, const CUtensorMap* tmy, int view,
-                                            int cid, int ncl, int s, bool quad = false, int half = 0) {
+                                            int cid, int ncl, int s, bool split = false, int half = 0) {
   SegView v;
   if (a.insts == nullptr) {
     v.map = view == 0 ? tmx : tmy;
     v.phi = a.phi_img + view * a.img_view;
     v.d0 = a.d[0];
     v.d1 = a.d[1];
-    v.out = a.partG + (int64_t)cid * (v.d0 + v.d1) * (2 * a.k2);
+    v.out = a.partG + (int64_t)cid * a.slab;
     v.first = cid;
     v.stride = ncl;
     v.count = (a.ntiles - cid + ncl - 1) / ncl;
-    half_pairs(a.pairs[view], quad, half, &v.pb, &v.npairs);
+    half_pairs(a.pairs[view], split, half, &v.pb, &v.npairs);
     v.k2 = a.k2;
     v.pair_sum = a.pair_sum;
     v.skip = false;
@@ -224,7 +237,7 @@ __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tm
     v.first = sg.first;
     v.stride = 1;
     v.count = sg.count;
-    half_pairs(I->pairs[view], quad, half, &v.pb, &v.npairs);
+    half_pairs(I->pairs[view], split, half, &v.pb, &v.npairs);
     v.k2 = I->k2;
     v.pair_sum = I->pair_sum;
     v.skip = I->done != nullptr && *I->done != 0;
@@ -233,10 +246,12 @@ __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tm
   return v;
 }
 
-template <int kH1, bool kQuad = false>
+template <int kH1, bool kQuad = false, bool kSolo = false>
 __global__ void __launch_bounds__(256, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, Args a) {
-  using L = Lay<kH1, kQuad>;
+  using L = Lay<kH1, kQuad, kSolo>;
+  constexpr bool kHalves = L::kHalves;
+  constexpr int kNvs = kSolo ? 1 : 2;  // views per row of a partial slab
   constexpr int kStages = L::kStages;
   constexpr int kFull = L::kFull, kEmpty = L::kEmpty, kD1Full = L::kD1Full, kD1Free = L::kD1Free;
   constexpr int kEpiSync = L::kEpiSync, kWReady = L::kWReady, kWPeer = L::kWPeer, kWFree = L::kWFree;
@@ -257,14 +272,19 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // rank = 2 half + view: CTAs 2h and 2h + 1 form the pair that shares the
   // tile's W (views X and Y); in a 4-CTA cluster, CTAs v and v + 2 hold the
-  // two column halves of view v and add their partial W of every tile
+  // two column halves of view v and add their partial W of every tile.  A
+  // one-view cluster (FDA): rank = half, the two CTAs add their partial W.
   const uint32_t rank = cluster_ctarank();
-  const int view = (int)(rank & 1u);         // 0: X, 1: Y
-  const int half = kQuad ? (int)(rank >> 1) : 0;
+  const int view = kSolo ? 0 : (int)(rank & 1u);  // 0: X, 1: Y
+  const int half = kQuad ? (int)(rank >> 1) : (kSolo ? (int)rank : 0);
   const uint32_t peer = rank ^ 1u;
-  const uint32_t hpeer = rank ^ 2u;
+  const uint32_t hpeer = kSolo ? rank ^ 1u : rank ^ 2u;
   (void)hpeer;
   (void)xbuf;
+  // bound of one pipeline wait: the plan's for a one-view cluster, whose only
+  // remote operations are synchronous stores and arrivals (an abort leaves no
+  // copy in flight towards the peer); the default otherwise
+  const long long wl = kSolo ? a.wait_limit : kWaitCycles;
   const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
   const int nseg = seg_count(a, cid, ncl);
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
@@ -285,7 +305,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       mbar_init(bar(kD1Free + b), 128);
       mbar_init(bar(kWReady + b), 1);
       mbar_init(bar(kWPeer + b), 1);   // + the peer's bytes
-      mbar_init(bar(kWFree + b), 2);   // own and peer's end of GEMM 2
+      mbar_init(bar(kWFree + b), kSolo ? 1 : 2);  // own (and the peer's) end of GEMM 2
     }
     mbar_init(bar(kEpiSync), 128);
     mbar_init(bar(kGDone), 1);
@@ -325,13 +345,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     for (int s = 0; s < kStages; ++s) last_use[s] = -1;
     int jg = 0, ig = 0, sp = 0;
     for (int s = 0; s < nseg && ok; ++s) {
-      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
+      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kHalves, half);
       if (sv.count == 0) continue;
       // the Phi image is rewritten only after every GEMM 1 MMA of the
       // previous segment has completed (its issuers signal that once per
       // segment; the barrier of a tile could already be two phases behind
       // this thread, whose parity test would then pass too early)
-      if (sp > 0 && !(ok = mbar_wait(bar(kPhiFree), (sp - 1) & 1, abort_flag))) break;
+      if (sp > 0 && !(ok = mbar_wait(bar(kPhiFree), (sp - 1) & 1, abort_flag, wl))) break;
       // this segment's Phi image (GEMM 1's B operand), one bulk copy per K-box
       const uint32_t pb = bar(kPhiFull);
       mbar_expect_tx(pb, L::kPhiBytes);
@@ -343,7 +363,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         const int row0 = (sv.first + t * sv.stride) * kRows;
         for (int p = 0; p < sv.npairs; ++p, ++ig) {
           const int slot = ig % kStages, use = ig / kStages;
-          if (!(ok = mbar_wait(bar(kEmpty + slot), (use & 1) ^ 1, abort_flag))) break;
+          if (!(ok = mbar_wait(bar(kEmpty + slot), (use & 1) ^ 1, abort_flag, wl))) break;
           const uint32_t fb = bar(kFull + slot);
           mbar_expect_tx(fb, kSlot);
           const uint32_t dst = smem_u32(ring + slot * kSlot);
@@ -387,23 +407,23 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       const int acc_i = warp - 1;  // accumulator of this issuer
       const uint64_t bdesc0 = sdesc(smem_u32(phi_s), 16, 1024);
       for (int s = 0; s < nseg && ok; ++s) {
-        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
+        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kHalves, half);
         if (sv.count == 0) continue;
         const int npairs = sv.npairs;
         const int split = L::kNAcc == 2 ? (npairs + 1) / 2 : npairs;
         const int pb = acc_i == 0 ? 0 : split, pe = acc_i == 0 ? split : npairs;
-        if (!(ok = mbar_wait(bar(kPhiFull), sp & 1, abort_flag))) break;
+        if (!(ok = mbar_wait(bar(kPhiFull), sp & 1, abort_flag, wl))) break;
         ++sp;
         for (int t = 0; t < sv.count && ok; ++t, ++jg, ig += npairs) {
           const int b = jg & 1;
           // W buffer b was last read by the epilogue of tile jg - 2
-          if (jg >= 2 && !(ok = mbar_wait(bar(kD1Free + b), ((jg - 2) >> 1) & 1, abort_flag))) break;
+          if (jg >= 2 && !(ok = mbar_wait(bar(kD1Free + b), ((jg - 2) >> 1) & 1, abort_flag, wl))) break;
           tc_fence_after();
           const uint32_t d1 = tmem + (uint32_t)((L::kNAcc * b + acc_i) * kTW);
           for (int p = pb; p < pe; ++p) {
             const int it = ig + p;
             const int slot = it % kStages, use = it / kStages;
-            if (!(ok = mbar_wait(bar(kFull + slot), use & 1, abort_flag))) break;
+            if (!(ok = mbar_wait(bar(kFull + slot), use & 1, abort_flag, wl))) break;
             tc_fence_after();
             const uint64_t ad0 = sdesc(smem_u32(ring + slot * kSlot), 16, 1024);
             const uint64_t bd0 = bdesc0 + (uint64_t)((2 * p * L::kKBox1) >> 4);
@@ -440,7 +460,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         // release the Phi image when a later segment will load its own
         bool more = false;
         for (int s2 = s + 1; s2 < nseg && !more; ++s2)
-          more = seg_view(a, &tmx, &tmy, view, cid, ncl, s2, kQuad, half).count > 0;
+          more = seg_view(a, &tmx, &tmy, view, cid, ncl, s2, kHalves, half).count > 0;
         if (more) {
           if (pe > pb) {
             mma_commit(bar(kPhiFree));
@@ -451,19 +471,20 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       }
     } else {
       for (int s = 0; s < nseg && ok; ++s) {
-        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
+        const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kHalves, half);
         if (sv.count == 0) continue;
         const int npairs = sv.npairs;
         // the epilogue has drained the G accumulators of the previous segment
-        if (sp > 0 && !(ok = mbar_wait(bar(kGFree), (sp - 1) & 1, abort_flag))) break;
+        if (sp > 0 && !(ok = mbar_wait(bar(kGFree), (sp - 1) & 1, abort_flag, wl))) break;
         tc_fence_after();
         ++sp;
         for (int t = 0; t < sv.count && ok; ++t, ++jg, ig += npairs) {
           const int b = jg & 1;
-          // both halves of this tile's W operand: ours and the peer's
-          mbar_expect_tx(bar(kWPeer + b), 2 * L::kWHalf);
-          if (!(ok = mbar_wait(bar(kWReady + b), (jg >> 1) & 1, abort_flag))) break;
-          if (!(ok = mbar_wait(bar(kWPeer + b), (jg >> 1) & 1, abort_flag))) break;
+          // both halves of this tile's W operand: ours and the peer's (one
+          // view: ours alone)
+          if (!kSolo) mbar_expect_tx(bar(kWPeer + b), 2 * L::kWHalf);
+          if (!(ok = mbar_wait(bar(kWReady + b), (jg >> 1) & 1, abort_flag, wl))) break;
+          if (!kSolo && !(ok = mbar_wait(bar(kWPeer + b), (jg >> 1) & 1, abort_flag, wl))) break;
           tc_fence_after();
           const uint64_t wd0 = sdesc(smem_u32(ws + b * L::kWBuf), 16, 1024);
           const uint32_t acc0 = t > 0 ? 1u : 0u;
@@ -483,8 +504,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             mma_commit(bar(kEmpty + slot));
             issued += 4;
           }
-          // both CTAs learn that this CTA's GEMM 2 has consumed buffer b
-          mma_commit_mc(bar(kWFree + b), (uint16_t)(0x3u << (2 * half)));
+          // both CTAs learn that this CTA's GEMM 2 has consumed buffer b (one
+          // view: this CTA alone reads its W operand)
+          if constexpr (kSolo) {
+            mma_commit(bar(kWFree + b));
+          } else {
+            mma_commit_mc(bar(kWFree + b), (uint16_t)(0x3u << (2 * half)));
+          }
         }
         if (ok) mma_commit(bar(kGDone));  // this segment's G is complete
       }
@@ -505,13 +531,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     bool ok = true;
     int jg = 0, sp = 0;
     for (int s = 0; s < nseg && ok; ++s) {
-      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kQuad, half);
+      const SegView sv = seg_view(a, &tmx, &tmy, view, cid, ncl, s, kHalves, half);
       if (sv.count == 0) continue;
       const int npairs = sv.npairs;
       const bool two_acc = L::kNAcc == 2 && (npairs + 1) / 2 < npairs;
       for (int t = 0; t < sv.count; ++t, ++jg) {
         const int b = jg & 1;
-        if (!(ok = mbar_wait(bar(kD1Full + b), (jg >> 1) & 1, abort_flag))) break;
+        if (!(ok = mbar_wait(bar(kD1Full + b), (jg >> 1) & 1, abort_flag, wl))) break;
         tc_fence_after();
         float d1[L::kD1Cols];
 #pragma unroll
@@ -531,7 +557,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         tc_fence_before();
         mbar_arrive(bar(kD1Free + b));
         // both CTAs' GEMM 2 of tile jg - 2 must be done with both halves of buffer b
-        if (jg >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((jg - 2) >> 1) & 1, abort_flag))) break;
+        if (jg >= 2 && !(ok = mbar_wait(bar(kWFree + b), ((jg - 2) >> 1) & 1, abort_flag, wl))) break;
         uint8_t* wb = ws + b * L::kWBuf;
         {
           // W_v row rr = hi part (TMEM column c) + lo part (column kH1 + c),
@@ -542,20 +568,20 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           // operand.  Rows 2k .. kH1 - 1 of the operand hold zeros or values
           // of an earlier segment: they only reach G columns that are not
           // drained.
-          constexpr int kSplit = kH1 / 2;
+          constexpr int kLaneCols = kH1 / 2;
           const bool upper = lane >= 16;
           const int rr = 16 * q + (lane & 15);
           // in phases over all columns, so that the shuffles of different
           // columns are in flight together
-          float w[kSplit];
-          uint32_t hs[kSplit], ls[kSplit];
+          float w[kLaneCols];
+          uint32_t hs[kLaneCols], ls[kLaneCols];
 #pragma unroll
-          for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = d1[c0 + kSplit] + d1[kH1 + c0 + kSplit];
+          for (int c0 = 0; c0 < kLaneCols; ++c0) w[c0] = d1[c0 + kLaneCols] + d1[kH1 + c0 + kLaneCols];
 #pragma unroll
-          for (int c0 = 0; c0 < kSplit; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
-          float xs[kSplit];
+          for (int c0 = 0; c0 < kLaneCols; ++c0) w[c0] = __shfl_sync(0xffffffffu, w[c0], lane & 15);
+          float xs[kLaneCols];
 #pragma unroll
-          for (int c0 = 0; c0 < kSplit; ++c0) {
+          for (int c0 = 0; c0 < kLaneCols; ++c0) {
             float x = upper ? w[c0] : d1[c0] + d1[kH1 + c0];
             // FP32 data: the data row's W = hi-row product + lo-row product
             // (adjacent rows sit in adjacent lanes; a + b == b + a, so both
@@ -563,46 +589,47 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             if (sv.pair_sum) x += __shfl_xor_sync(0xffffffffu, x, 1);
             xs[c0] = x;
           }
-          if constexpr (kQuad) {
+          if constexpr (kHalves) {
             // W of the view = this half's product + the other half's: send
             // ours into the other half's buffer b (once it has read the one
             // of tile jg - 2), take theirs from ours; both CTAs add the same
             // two numbers (a + b == b + a), so they hold the same W
-            const int cb = upper ? kSplit : 0;
+            const int cb = upper ? kLaneCols : 0;
             // (the waits' verdicts are made warp-uniform: the shuffles below
             // need every lane)
             if (jg >= 2 &&
-                !(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFree + b), ((jg - 2) >> 1) & 1, abort_flag))))
+                !(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFree + b), ((jg - 2) >> 1) & 1, abort_flag, wl))))
               break;
             const uint32_t rx = map_peer(smem_u32(xbuf + b * kH1 * kRows), hpeer);
 #pragma unroll
-            for (int c0 = 0; c0 < kSplit; ++c0) {
+            for (int c0 = 0; c0 < kLaneCols; ++c0) {
               const uint32_t adr = rx + (uint32_t)(((cb + c0) * kRows + rr) * 4);
               asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(adr), "f"(xs[c0]) : "memory");
             }
             mbar_arrive_cluster(map_peer(bar(kXFull + b), hpeer));
-            if (!(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFull + b), (jg >> 1) & 1, abort_flag)))) break;
+            if (!(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFull + b), (jg >> 1) & 1, abort_flag, wl))))
+              break;
             const float* mine = xbuf + b * kH1 * kRows;
 #pragma unroll
-            for (int c0 = 0; c0 < kSplit; ++c0) xs[c0] += mine[(cb + c0) * kRows + rr];
+            for (int c0 = 0; c0 < kLaneCols; ++c0) xs[c0] += mine[(cb + c0) * kRows + rr];
             mbar_arrive_cluster(map_peer(bar(kXFree + b), hpeer));
           }
 #pragma unroll
-          for (int c0 = 0; c0 < kSplit; ++c0) {
+          for (int c0 = 0; c0 < kLaneCols; ++c0) {
             const __nv_bfloat16 hi = __float2bfloat16_rn(xs[c0]);
             const __nv_bfloat16 lo = __float2bfloat16_rn(xs[c0] - __bfloat162float(hi));
             hs[c0] = __bfloat16_as_ushort(hi);
             ls[c0] = __bfloat16_as_ushort(lo);
           }
 #pragma unroll
-          for (int c0 = 0; c0 < kSplit; ++c0) {
+          for (int c0 = 0; c0 < kLaneCols; ++c0) {
             hs[c0] |= __shfl_down_sync(0xffffffffu, hs[c0], 1) << 16;
             ls[c0] |= __shfl_down_sync(0xffffffffu, ls[c0], 1) << 16;
           }
           if ((lane & 1) == 0) {
 #pragma unroll
-            for (int c0 = 0; c0 < kSplit; ++c0) {
-              const int c = upper ? c0 + kSplit : c0;
+            for (int c0 = 0; c0 < kLaneCols; ++c0) {
+              const int c = upper ? c0 + kLaneCols : c0;
               if (c < sv.k2) {
                 const uint32_t off = swz(view * L::kHalf + c, rr);
                 *reinterpret_cast<uint32_t*>(wb + off) = hs[c0];
@@ -615,13 +642,15 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         mbar_arrive(bar(kEpiSync));
         if (threadIdx.x == 128) {
           // all rows written: push this view's rows (hi and lo) into the peer's
-          // buffer b, then release our own GEMM 2
-          if (!(ok = mbar_wait(bar(kEpiSync), jg & 1, abort_flag))) break;
-          const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
+          // buffer b (two views), then release our own GEMM 2
+          if (!(ok = mbar_wait(bar(kEpiSync), jg & 1, abort_flag, wl))) break;
+          if constexpr (!kSolo) {
+            const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t src = smem_u32(wb + h * L::kWs + view * L::kWHalf);
-            bulk_to_peer(map_peer(src, peer), src, L::kWHalf, pbar);
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t src = smem_u32(wb + h * L::kWs + view * L::kWHalf);
+              bulk_to_peer(map_peer(src, peer), src, L::kWHalf, pbar);
+            }
           }
           mbar_arrive(bar(kWReady + b));
         }
@@ -629,11 +658,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       if (!ok) break;
       // this segment's G: drain to its partial slab, then free the
       // accumulators for the next segment's GEMM 2
-      if (!(ok = mbar_wait(bar(kGDone), sp & 1, abort_flag))) break;
+      if (!(ok = mbar_wait(bar(kGDone), sp & 1, abort_flag, wl))) break;
       tc_fence_after();
       {
         const int D = sv.d0 + sv.d1;
-        const int k4 = 2 * sv.k2;
+        const int k4 = kNvs * sv.k2;  // floats per row of the slab
         const int dv = view == 0 ? sv.d0 : sv.d1;
         for (int p = 0; p < npairs; ++p) {
           float g[L::kN2];
@@ -708,13 +737,13 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
 // own rounding.
 // `stride` is the distance of the partial slabs (floats, a multiple of 4, at
 // least len); entries len .. stride - 1 of a slab are padding.  With ng > 0
-// the slabs hold one column group (rows of 2 ng: the view-x then the view-y
-// products of group columns 0 .. ng - 1), and entry (row, vv ng + c) goes to
-// G column vv k2 + col0 + c (rows of 2 k2); with ng = 0, G has the slabs'
-// layout.
+// the slabs hold one column group (rows of nvs ng: for CCA (nvs = 2) the
+// view-x then the view-y products of group columns 0 .. ng - 1), and entry
+// (row, vv ng + c) goes to G column vv k2 + col0 + c (rows of nvs k2); with
+// ng = 0, G has the slabs' layout.
 __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
                                                         int64_t stride, double* __restrict__ G, const int* done,
-                                                        const int* nparts_dev, int ng, int col0, int k2) {
+                                                        const int* nparts_dev, int ng, int col0, int k2, int nvs) {
   if (done != nullptr && *done) return;
   if (nparts_dev != nullptr) nparts = *nparts_dev;  // batched pass: the schedule's slab count
   __shared__ float4 red_s[4][64], red_c[4][64];
@@ -762,20 +791,22 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict_
       if (ng == 0) {
         G[idx] = out[i];
       } else {
-        const int64_t row = idx / (2 * ng);
-        const int col = (int)(idx - row * 2 * ng), vv = col / ng, c = col - vv * ng;
-        G[row * 2 * k2 + vv * k2 + col0 + c] = out[i];
+        const int64_t row = idx / (nvs * ng);
+        const int col = (int)(idx - row * nvs * ng), vv = col / ng, c = col - vv * ng;
+        G[row * nvs * k2 + vv * k2 + col0 + c] = out[i];
       }
     }
   }
 }
 
 // W^T W = Phi_bd^T G (4k x 4k), Phi_bd = blkdiag(Phi_x, Phi_y), in FP64: one
-// warp per entry, lanes over rows, fixed shuffle tree.
+// warp per entry, lanes over rows, fixed shuffle tree.  One view (nv = 1,
+// FDA): Phi^T G (2k x 2k).
 __global__ void tc_gram_kernel(const double* __restrict__ Phix, const double* __restrict__ Phiy, int dx, int dy,
-                               int k2, const double* __restrict__ G, double* __restrict__ Gram, const int* done) {
+                               int k2, int nv, const double* __restrict__ G, double* __restrict__ Gram,
+                               const int* done) {
   if (done != nullptr && *done) return;
-  const int k4 = 2 * k2;
+  const int k4 = nv * k2;
   const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (e >= k4 * k4) return;
   const int a = e / k4, b = e - a * k4;
@@ -807,10 +838,13 @@ int make_map(CUtensorMap* map, const void* base, int64_t n, int d, int64_t ld) {
 // 4-CTA clusters, each view's column pairs split over two CTAs), 16-byte
 // aligned rows (ld a multiple of 8) and 16-byte aligned bases; Phi columns
 // beyond 24 per view (k > 12, up to the library's k <= 20) are taken in a
-// second column group, which reads the data a second time.
+// second column group, which reads the data a second time.  FDA plans with
+// FP32 data and d <= 1024 stream the interleaved copy of their class-centred
+// rows in one-view clusters (the view's column pairs split over two CTAs).
 bool tc_pass_eligible(const Plan& p) {
+  if (p.kind == kLDA) return p.dtype == GBCCA_FP32 && 2 * p.k <= 2 * tc::kHalfMax && p.v[0].d <= 1024 && p.ts_ready;
   if (p.kind != kCCA || 2 * p.k > 2 * tc::kHalfMax || p.v[0].d > 1024 || p.v[1].d > 1024) return false;
-  if (p.dtype == GBCCA_FP32) return p.ts_ready && p.ts_interleaved;  // the plan's own aligned copy
+  if (p.dtype == GBCCA_FP32) return p.ts_ready;  // the plan's own aligned copy
   if (p.dtype != GBCCA_BF16) return false;
   for (int v = 0; v < 2; ++v) {
     if (p.v[v].ld % 8 != 0 || (reinterpret_cast<uintptr_t>(p.v[v].Z) & 15) != 0) return false;
@@ -833,16 +867,25 @@ static void tc_group(const Plan& p, int g, int* col0, int* ng) {
   *col0 = g * ng0;
   *ng = g == 0 ? ng0 : k2 - ng0;
 }
-static int tc_group_h1(int ng) { return ng <= 20 ? 20 : tc::kHalfMax; }
+// one-view plans (FDA): clusters of two CTAs that split the view's column
+// pairs, GEMM 2 with N = 2 x 24 (an M = 128 MMA needs N a multiple of 16)
+static bool tc_solo(const Plan& p) { return p.kind == kLDA; }
+static int tc_group_h1(const Plan& p, int ng) { return ng <= 20 && !tc_solo(p) ? 20 : tc::kHalfMax; }
 // views wider than 512 columns: 4-CTA clusters and images of 16 K-boxes
-bool tc_quad(const Plan& p) { return std::max(p.v[0].d, p.v[1].d) > 512; }
-static int64_t tc_img_view(const Plan& p) { return (tc_quad(p) ? 2 : 1) * (int64_t)tc::kPhiView; }
-static uint8_t* tc_group_img(const Plan& p, int g) { return p.tc_img + (int64_t)g * 2 * tc_img_view(p); }
-// partial slabs of group g: clusters (at most half the SMs) x D x 2 ng floats
+bool tc_quad(const Plan& p) { return p.kind == kCCA && std::max(p.v[0].d, p.v[1].d) > 512; }
+// bytes between the views' images of a group (one-view plans: 16 K-boxes,
+// the second CTA's pairs starting at K-box 8 at most)
+static int64_t tc_img_view(const Plan& p) { return (tc_quad(p) || tc_solo(p) ? 2 : 1) * (int64_t)tc::kPhiView; }
+static int tc_nviews(const Plan& p) { return tc_solo(p) ? 1 : 2; }
+static uint8_t* tc_group_img(const Plan& p, int g) { return p.tc_img + (int64_t)g * tc_nviews(p) * tc_img_view(p); }
+// floats of one cluster's partial slab of a group of ng columns: D x 2 ng
+// (one view: d x ng, rounded up to a multiple of 4)
+static int64_t tc_slab(const Plan& p, int ng) { return ((int64_t)p.D * tc_nviews(p) * ng + 3) / 4 * 4; }
+// partial slabs of group g: clusters (at most half the SMs) x one slab each
 static float* tc_group_part(const Plan& p, int g) {
   int col0 = 0, ng0 = 0;
   tc_group(p, 0, &col0, &ng0);
-  return p.tc_part + (int64_t)g * (p.sm_count / 2) * p.D * 2 * ng0;
+  return p.tc_part + (int64_t)g * (p.sm_count / 2) * tc_slab(p, ng0);
 }
 
 // The Phi images of a plan (both views, every column group), group g with
@@ -850,26 +893,31 @@ static float* tc_group_part(const Plan& p, int g) {
 // hi + lo point the pass evaluates.
 int tc_phi_image(Plan& p, int h1, cudaStream_t st, const int* done) {
   const int k2 = 2 * p.k;
-  const int dmax = std::max(p.v[0].d, p.v[1].d);
+  const int nv = tc_nviews(p);
+  const int d1 = nv > 1 ? p.v[1].d : 0;
+  double* Phi1 = nv > 1 ? p.v[1].Phi : p.v[0].Phi;
+  const int dmax = std::max(p.v[0].d, d1);
   for (int g = 0; g < tc_groups(p); ++g) {
     int col0 = 0, ng = 0;
     tc_group(p, g, &col0, &ng);
-    const int hg = h1 > 0 ? h1 : tc_group_h1(ng);
-    tc::phi_image_kernel<<<dim3(ceil_div(dmax * ng, 256), 2), 256, 0, st>>>(
-        p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2, col0, ng, hg, tc_group_img(p, g), tc_img_view(p), done);
+    const int hg = h1 > 0 ? h1 : tc_group_h1(p, ng);
+    tc::phi_image_kernel<<<dim3(ceil_div(dmax * ng, 256), nv), 256, 0, st>>>(
+        p.v[0].Phi, Phi1, p.v[0].d, d1, k2, col0, ng, hg, tc_group_img(p, g), tc_img_view(p), done);
     GB_CHECK_LAUNCH();
   }
   return GBCCA_OK;
 }
 
 // The streamed matrices of an eligible plan: the caller's BF16 matrices, or
-// for FP32 data the plan's row-interleaved hi/lo copy (2n rows).
+// for FP32 data the plan's row-interleaved hi/lo copy (2n rows).  One-view
+// plans stream view 0 (the second entry repeats it and is not read).
 static void tc_sources(const Plan& p, const void* src[2], int64_t ld[2], int64_t* rows) {
   const bool fp32 = p.dtype == GBCCA_FP32;
   *rows = fp32 ? 2 * p.n : p.n;
   for (int v = 0; v < 2; ++v) {
-    src[v] = fp32 ? (const void*)p.ts_copy[v] : p.v[v].Z;
-    ld[v] = fp32 ? p.ts_ld[v] : p.v[v].ld;
+    const int u = v < tc_nviews(p) ? v : 0;
+    src[v] = fp32 ? (const void*)p.ts_copy[u] : p.v[u].Z;
+    ld[v] = fp32 ? p.ts_ld[u] : p.v[u].ld;
   }
 }
 
@@ -881,13 +929,15 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   const void* src[2];
   int64_t ld[2];
   tc_sources(p, src, ld, &rows);
+  const bool solo = tc_solo(p);
+  const int nv = tc_nviews(p);
   if (p.tc_map_for[0] != src[0] || p.tc_map_for[1] != src[1]) {
     for (int v = 0; v < 2; ++v)
-      GB_TRY(make_map(reinterpret_cast<CUtensorMap*>(p.tc_map[v]), src[v], rows, p.v[v].d, ld[v]));
+      GB_TRY(make_map(reinterpret_cast<CUtensorMap*>(p.tc_map[v]), src[v], rows, p.v[v < nv ? v : 0].d, ld[v]));
     p.tc_map_for[0] = src[0];
     p.tc_map_for[1] = src[1];
   }
-  const int k2 = 2 * p.k, k4 = 4 * p.k;
+  const int k2 = 2 * p.k, k4 = nv * k2;
   GB_TRY(tc_phi_image(p, 0, st, done));
   const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(p.tc_map[0]);
   const CUtensorMap* my = reinterpret_cast<const CUtensorMap*>(p.tc_map[1]);
@@ -897,14 +947,16 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
   for (int g = 0; g < groups; ++g) {
     int col0 = 0, ng = 0;
     tc_group(p, g, &col0, &ng);
-    const int h1 = tc_group_h1(ng);  // Phi image rows per half (GEMM 1 N = 2 h1)
+    const int h1 = tc_group_h1(p, ng);  // Phi image rows per half (GEMM 1 N = 2 h1)
     tc::Args a{};
     a.n = p.n;
     for (int v = 0; v < 2; ++v) {
-      a.d[v] = p.v[v].d;
-      a.pairs[v] = ceil_div(p.v[v].d, 128);
+      a.d[v] = v < nv ? p.v[v].d : 0;
+      a.pairs[v] = ceil_div(a.d[v], 128);
     }
     a.k2 = ng;
+    a.slab = tc_slab(p, ng);
+    a.wait_limit = p.opt.wait_cycles > 0 ? p.opt.wait_cycles : tc::kWaitCycles;
     a.ntiles = ceil_div(rows, tc::kRows);
     a.pair_sum = fp32 ? 1 : 0;
     a.phi_img = tc_group_img(p, g);
@@ -914,10 +966,12 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     a.done = done;
     const bool quad = tc_quad(p);
     const int csz = quad ? 4 : 2;  // CTAs per cluster
-    auto kern = quad ? (h1 == 20 ? tc::tc_pass_kernel<20, true> : tc::tc_pass_kernel<tc::kHalfMax, true>)
-                     : (h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>);
-    const int smem = quad ? (h1 == 20 ? tc::Lay<20, true>::kSmemBytes : tc::Lay<tc::kHalfMax, true>::kSmemBytes)
-                          : (h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes);
+    auto kern = solo ? tc::tc_pass_kernel<tc::kHalfMax, false, true>
+                : quad ? (h1 == 20 ? tc::tc_pass_kernel<20, true> : tc::tc_pass_kernel<tc::kHalfMax, true>)
+                       : (h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>);
+    const int smem = solo ? tc::Lay<tc::kHalfMax, false, true>::kSmemBytes
+                     : quad ? (h1 == 20 ? tc::Lay<20, true>::kSmemBytes : tc::Lay<tc::kHalfMax, true>::kSmemBytes)
+                            : (h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes);
     GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
@@ -947,13 +1001,13 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     int col0 = 0, ng = 0;
     tc_group(p, g, &col0, &ng);
     // partial slabs, one per cluster
-    const int64_t len = (int64_t)p.D * 2 * ng;
-    tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), ncl, len, len, p.G, done, nullptr,
-                                                             groups > 1 ? ng : 0, col0, k2);
+    const int64_t len = (int64_t)p.D * nv * ng;
+    tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), ncl, len, tc_slab(p, ng), p.G,
+                                                             done, nullptr, groups > 1 ? ng : 0, col0, k2, nv);
     GB_CHECK_LAUNCH();
   }
-  tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
-                                                                  p.G, p.Gram, done);
+  tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(
+      p.v[0].Phi, nv > 1 ? p.v[1].Phi : p.v[0].Phi, p.v[0].d, nv > 1 ? p.v[1].d : 0, k2, nv, p.G, p.Gram, done);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }
@@ -1021,7 +1075,7 @@ TcBatch* tc_batch_create(Plan* const* plans, int n, cudaStream_t st, int* rc) {
     for (int g = 0; g < tc_groups(*plans[i]); ++g) {
       int col0 = 0, ng = 0;
       tc_group(*plans[i], g, &col0, &ng);
-      h1 = std::max(h1, tc_group_h1(ng));
+      h1 = std::max(h1, tc_group_h1(*plans[i], ng));
     }
     entries += tc_groups(*plans[i]);
     sm = std::max(sm, plans[i]->sm_count);
@@ -1209,11 +1263,11 @@ int tc_batch_post(const TcBatch* b, int i, Plan& p, cudaStream_t st, const int* 
     const int64_t len = (int64_t)p.D * 2 * ng;
     tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), 1, len, len, p.G, done,
                                                              b->nparts_d + b->first[i] + g, groups > 1 ? ng : 0,
-                                                             col0, k2);
+                                                             col0, k2, 2);
     GB_CHECK_LAUNCH();
   }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
-                                                                  p.G, p.Gram, done);
+                                                                  2, p.G, p.Gram, done);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -162,17 +162,12 @@ struct Plan {
   int batch_key_n = 0;
   bool batch_key_timed = false;
   long long batch_launches = 0;  // kernels in one replay (for the launch counter)
-  // tensor-core pass for FP32 data: BF16 hi/lo copies of the bound views
-  // (FDA: of the class-centred rows), hi then lo, leading dimension ts_ld;
-  // TMA descriptors [view][hi | lo]; Phi images; per-cluster partials
+  // tensor-core pass for FP32 data: row-interleaved BF16 hi/lo copies of
+  // the bound views (FDA: of the class-centred rows; rows 2i / 2i + 1 hold
+  // hi / lo of data row i), leading dimension ts_ld; ts_ready once made
   __nv_bfloat16* ts_copy[2] = {nullptr, nullptr};
   int64_t ts_ld[2] = {0, 0};
-  alignas(64) unsigned char ts_map[4][128] = {};
-  uint8_t* ts_img = nullptr;
-  float* ts_part = nullptr;
-  int ts_clusters = 0;
   bool ts_ready = false;
-  bool ts_interleaved = false;  // CCA: rows 2i / 2i + 1 hold hi / lo (streamed by the BF16 kernel)
   cudaEvent_t kev0 = nullptr;  // when set: recorded around the data kernel of the next pass
   cudaEvent_t kev1 = nullptr;  // resident 2-CTA clusters of the tensor-core pass (0: not yet queried)
 };
@@ -262,12 +257,9 @@ int tc_batch_max_clusters(const TcBatch* b);
 int tc_batch_clusters(const TcBatch* b);
 int64_t tc_batch_bytes(const TcBatch* b, const bool* active);
 
-// pass_split.cu: the tensor-core pass for FP32 data (CCA and FDA)
-bool split_pass_shape_ok(int kind, int dtype, int k, int d0, int d1);
-bool split_pass_ready(const Plan& p);
-int split_pass_alloc(Plan& p);
-int split_pass_prepare(Plan& p, cudaStream_t st);
-int split_pass(Plan& p, cudaStream_t st, const int* done);
+// hilo_copy.cu: the BF16 hi/lo copy of FP32 data for the tensor-core pass
+int hilo_alloc(Plan& p);
+int hilo_prepare(Plan& p, cudaStream_t st);
 
 // api.cu
 int lda_bind(Plan& p, const void* X, int64_t ldx, const int32_t* labels, double lambda, const int32_t* sketch_h,

@@ -47,7 +47,7 @@ def split_round(P):
 def gamma_batched(rows, d, fp32):
     """Single-plan bound with every 64-row tile of the instance in one
     cluster; FP32 data adds the representation of Z twice and the hi/lo row
-    sum (see test_gpu_split_pass)."""
+    sum (see test_gpu_fp32_pass)."""
     T = -(-rows // 64)
     g = 2.0 ** -17 + 2.0 ** -23 * (2 * (d / 16 + 2) + 2 * (4 * T + 1) + 4 + 2)  # + the halves' partial-W sum
     if fp32:

@@ -1,18 +1,20 @@
-"""GPU parity of the tensor-core (tcgen05 + TMA) passes for FP32 data, CCA
+"""GPU parity of the tensor-core (tcgen05 + TMA) pass for FP32 data, CCA
 and FDA, through the C ABI.
 
-Both stream a BF16 hi/lo copy of the data (FDA: of the class-centred rows):
-Z' = Z_hi + Z_lo with |Z - Z'| <= 2^-17 |Z| entrywise (z in [2^e, 2^(e+1)):
-|z - hi| <= 2^(e-8), and rounding that remainder to 8 bits errs by at most
-2^(e-17)), and evaluate Phi' = bf16 hi + lo of Phi (the point the solver then
-holds).  Products of BF16 operands are exact in FP32; the remaining errors
-are the representation of Z (entering both products), the bf16 hi + lo split
-of W (2^-17 |W|) and FP32 accumulation.  Each entry is checked against its
-own bound gamma * ref, ref the sum of |terms| (|Z|^T (|Z| |Phi'|); for the
-Gram (|Z||Phi'|)^T (|Z||Phi'|)).
+Both stream a row-interleaved BF16 hi/lo copy of the data (FDA: of the
+class-centred rows; 2n rows: row 2i the hi part of data row i, row 2i + 1 its
+lo part; 64-row tiles): Z' = Z_hi + Z_lo with |Z - Z'| <= 2^-17 |Z|
+entrywise (z in [2^e, 2^(e+1)): |z - hi| <= 2^(e-8), and rounding that
+remainder to 8 bits errs by at most 2^(e-17)), and evaluate Phi' = bf16 hi +
+lo of Phi (the point the solver then holds).  Products of BF16 operands are
+exact in FP32; the remaining errors are the representation of Z (entering
+both products), the bf16 hi + lo split of W (2^-17 |W|) and FP32
+accumulation.  Each entry is checked against its own bound gamma * ref, ref
+the sum of |terms| (|Z|^T (|Z| |Phi'|); for the Gram (|Z||Phi'|)^T
+(|Z||Phi'|)).
 
-CCA runs the BF16 kernel over a row-interleaved copy (2n rows: row 2i the hi
-part of data row i, row 2i + 1 its lo part; 64-row tiles):
+CCA (one view per CTA of a 2-CTA cluster; views wider than 512 columns split
+over two CTAs of a 4-CTA cluster):
   GEMM 1  d / 16 + 2 FP32 roundings along a chain (two issuers, hi and lo
           columns of Phi), plus the addition of the hi-row and lo-row
           products of the same data row;
@@ -23,15 +25,11 @@ part of data row i, row 2i + 1 its lo part; 64-row tiles):
 T = ceil(ceil(2n / 64) / clusters) with at least min(tiles, 64) clusters.  The
 Gram is Phi_bd^T G formed in FP64: the same gamma against |W|^T |W|.
 
-FDA runs its own kernel (32-row tiles, 128-column pairs, 2-CTA clusters):
-  GEMM 1  per issuer one FP32 chain of 8 MMAs per pair it owns (half of the
-          pairs each), two epilogue additions (accumulators, hi + lo columns
-          of Phi), and the sum of the two CTAs' products (one more);
-  GEMM 2  4 MMAs per tile into one accumulator (2 K steps x hi and lo rows of
-          W), T tiles per cluster;
-  reduce  as above;
-  gamma = 3 * 2^-17 + 2^-23 (2 (8 P1 + 3) + 2 (4 T + 1) + 4),
-P1 the pairs of the longer GEMM 1 chain, T = ceil(ceil(n / 32) / clusters).
+FDA (the one view's 128-column pairs split over the two CTAs of a cluster,
+which add their partial W of every tile): the same terms with the chain of
+the longer half (d_h = 128 ceil(P / 2) columns, P = ceil(d / 128)) and one
+more addition for the halves' sum:
+  gamma = 3 * 2^-17 + 2^-23 (2 (d_h / 16 + 2) + 2 + 2 + 2 (4 T + 1) + 4).
 Counting every MMA as two FP32 roundings of at most 2^-23 of the running sum.
 """
 import numpy as np
@@ -65,10 +63,11 @@ def split_round(P):
     return hi + bf16_round(P - hi)
 
 
-def gamma_split(n, p1):
-    tiles = -(-n // 32)
+def gamma_solo(n, d):
+    tiles = -(-2 * n // 64)
     T = -(-tiles // min(tiles, 64))
-    return 3 * 2.0 ** -17 + 2.0 ** -23 * (2 * (8 * p1 + 3) + 2 * (4 * T + 1) + 4)
+    dh = 128 * -(-(-(-d // 128)) // 2)
+    return 3 * 2.0 ** -17 + 2.0 ** -23 * (2 * (dh / 16 + 2) + 2 + 2 + 2 * (4 * T + 1) + 4)
 
 
 def gamma_interleaved(n, d):
@@ -105,13 +104,13 @@ def _cca(gb, P, n, dx, dy, k, seed=0):
 @pytest.mark.parametrize("n,dx,dy,k", [(3001, 192, 136, 5), (4099, 70, 45, 5), (20000, 512, 384, 10),
                                        (64, 64, 40, 1), (33, 24, 8, 3), (12345, 500, 24, 12), (7001, 136, 97, 15),
                                        (3001, 768, 136, 6)])
-def test_split_cca_pass_ragged(gb, n, dx, dy, k):
+def test_fp32_cca_pass_ragged(gb, n, dx, dy, k):
     P = cca_latent_problem(n, dx, dy, latent=6, dtype="f32", seed=n, colscale=(1.0, 1e-3))
     got, exp, refs = _cca(gb, P, n, dx, dy, k)
     _check(got, exp, refs, gamma_interleaved(n, max(dx, dy)))
 
 
-def test_split_cca_pass_full_workload(gb):
+def test_fp32_cca_pass_full_workload(gb):
     """The tall workload stored in FP32 (n = 262144, dx = dy = 512, k = 10)."""
     P = make_workload("cca_tall_f32")
     c = P["config"]
@@ -137,20 +136,22 @@ def _lda(gb, P, n, d, l, k, seed=0):
     return (np64(G), None, np64(Gram)), (eg, None, egram), (np.abs(Xhat).T @ aP, None, aP.T @ aP)
 
 
-@pytest.mark.parametrize("n,d,l,k", [(5003, 61, 6, 5), (20000, 784, 10, 9), (257, 130, 3, 2)])
-def test_split_lda_pass_ragged(gb, n, d, l, k):
+# ragged rows and columns; one pair (the second CTA then streams an empty
+# pair); 2k = 26 (two column groups); a 1024-column view
+@pytest.mark.parametrize("n,d,l,k", [(5003, 61, 6, 5), (20000, 784, 10, 9), (257, 130, 3, 2), (6001, 200, 16, 13),
+                                     (3001, 1024, 5, 4)])
+def test_fda_pass_ragged(gb, n, d, l, k):
     P = lda_problem(n, d, l, dtype="f32", seed=n)
     got, exp, refs = _lda(gb, P, n, d, l, k)
-    pp = -(-d // 128)
-    _check(got, exp, refs, gamma_split(n, -(-pp // 2)))
+    _check(got, exp, refs, gamma_solo(n, d))
 
 
-def test_split_lda_pass_full_workload(gb):
+def test_fda_pass_full_workload(gb):
     """The LDA workload (n = 100000, d = 784, 10 classes, k = 9)."""
     P = make_workload("lda_f32")
     c = P["config"]
     got, exp, refs = _lda(gb, P, c["n"], c["d"], c["l"], c["k"], seed=4)
-    _check(got, exp, refs, gamma_split(c["n"], 4))
+    _check(got, exp, refs, gamma_solo(c["n"], c["d"]))
 
 
 def test_tall_f32_solve(gb):

@@ -53,11 +53,13 @@ def test_fda_pass(gb, dt):
     minus the class-mean correction, bounded against (|X| + |M[y]|)^T |P|;
     the Gram against |P|^T |P|.  FP32: W chain over d (+ the FP32 copies of
     Phi and C), G partial sums over 128 rows and class sums over 64-row
-    tiles flushed to FP64; FP64: the same chains in FP64."""
+    tiles flushed to FP64; FP64: the same chains in FP64.  These are the
+    CUDA-core kernels (tensor_cores = 0); the tensor-core pass of FP32 FDA
+    plans has its own bound (test_gpu_fp32_pass)."""
     import torch
     n, d, l, k = 5003, 61, 6, 5
     P = lda_problem(n, d, l, dtype=dt, seed=3)
-    plan, _, _, _ = _solve(gb, P, n, d, l, k, dt, 1e-2, max_iter=2)
+    plan, _, _, _ = _solve(gb, P, n, d, l, k, dt, 1e-2, max_iter=2, tensor_cores=0)
     rng = np.random.default_rng(0)
     Phi = rng.standard_normal((d, 2 * k))
     Gx, _, Gram = gb.fused_pass(plan, torch.from_numpy(Phi).cuda())
