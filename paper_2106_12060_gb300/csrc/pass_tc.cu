@@ -45,7 +45,8 @@
 // lane 0 = GEMM 1 issuer (with 2k <= 20: for the first half of the pairs,
 // warp 2 lane 0 for the second half, into a second accumulator that the
 // epilogue adds); warp 3 lane 0 = GEMM 2 issuer; warp 2 = TMEM allocator;
-// warps 4-7 = epilogue (TMEM lane quarters 0-3).
+// warps 4-7 and 8-11 = two epilogue groups (even and odd tiles; TMEM lane
+// quarters 0-3 each), whose per-tile chains of dependent steps overlap.
 // Every mbarrier wait is bounded in time; on expiry the CTA records an error
 // code, waits (bounded) for its own copies and MMAs, frees TMEM and leaves
 // after a cluster barrier (no remote access can target an exited CTA).
@@ -81,9 +82,9 @@ struct Lay {
   // [W_x | W_y] of the hi parts (kH1 rows per view; rows 2k .. kH1 - 1 stay
   // zero), then the same rows of the lo parts, so that one MMA with
   // N = kN2 reads the tile's columns once for both parts.  One view (FDA):
-  // its kH1 rows per part.
+  // its rows padded to 24 per part (an M = 128 MMA needs N a multiple of 16).
   static constexpr int kHalf = kH1;              // W rows of a view
-  static constexpr int kNW = (kSolo ? 1 : 2) * kH1;  // rows of one part (hi or lo)
+  static constexpr int kNW = kSolo ? 24 : 2 * kH1;  // rows of one part (hi or lo)
   static constexpr int kN2 = 2 * kNW;            // N of GEMM 2
   static constexpr int kWs = kNW * 128;          // bytes of one part
   static constexpr int kWBuf = 2 * kWs;          // hi + lo
@@ -99,7 +100,8 @@ struct Lay {
   // and one-view clusters (FDA: the view's columns split over the two CTAs):
   // two FP32 buffers that receive the other half's partial W of a tile
   static constexpr bool kHalves = kQuad || kSolo;  // a view's pairs over two CTAs
-  static constexpr int kXBytes = kHalves ? 2 * kH1 * kRows * 4 : 0;
+  static constexpr int kXC = 24;                 // floats per row of an exchange buffer
+  static constexpr int kXBytes = kHalves ? 2 * kRows * kXC * 4 : 0;
   static constexpr int kStages = (kMaxSmem - kPhiBytes - 2 * kWBuf - kXBytes - 512 - 1024) / kSlot;
   static constexpr int kRingOff = kPhiBytes;
   static constexpr int kWsOff = kRingOff + kStages * kSlot;
@@ -115,7 +117,8 @@ struct Lay {
   static constexpr int kGFree = kPhiFull + 1;   // G drained (128 arrivals)
   static constexpr int kPhiFree = kGFree + 1;  // GEMM 1 done with a segment's Phi
   static constexpr int kXFull = kPhiFree + 1, kXFree = kXFull + 2;  // [2], [2]: partial-W exchange (quad)
-  static constexpr int kNumBars = kXFree + 2;
+  static constexpr int kEpiSyncB = kXFree + 2;  // the second epilogue group's kEpiSync
+  static constexpr int kNumBars = kEpiSyncB + 1;
   static_assert(!(kQuad && kSolo), "one cluster shape");
   static_assert(kStages >= 2 * kTileSlots, "two resident tiles");
   static_assert(kN1 <= kTW && kD1Cols <= kTW, "W buffers in TMEM");
@@ -246,8 +249,10 @@ __device__ __forceinline__ SegView seg_view(const Args& a, const CUtensorMap* tm
   return v;
 }
 
+constexpr int kThreads = 384;  // 4 role warps + two epilogue groups of 4 warps
+
 template <int kH1, bool kQuad = false, bool kSolo = false>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, Args a) {
   using L = Lay<kH1, kQuad, kSolo>;
   constexpr bool kHalves = L::kHalves;
@@ -256,7 +261,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   constexpr int kFull = L::kFull, kEmpty = L::kEmpty, kD1Full = L::kD1Full, kD1Free = L::kD1Free;
   constexpr int kEpiSync = L::kEpiSync, kWReady = L::kWReady, kWPeer = L::kWPeer, kWFree = L::kWFree;
   constexpr int kGDone = L::kGDone, kFinal = L::kFinal, kPhiFull = L::kPhiFull, kGFree = L::kGFree;
-  constexpr int kPhiFree = L::kPhiFree, kXFull = L::kXFull, kXFree = L::kXFree;
+  constexpr int kPhiFree = L::kPhiFree, kXFull = L::kXFull, kXFree = L::kXFree, kEpiSyncB = L::kEpiSyncB;
   constexpr int kNumBars = L::kNumBars;
   constexpr int kTG = L::kTG;
   if (a.done != nullptr && *a.done) return;  // uniform over the cluster: no remote access yet
@@ -268,7 +273,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* xbuf = reinterpret_cast<float*>(smem + L::kXOff);  // quad: [buffer][kH1 columns][64 rows]
+  float* xbuf = reinterpret_cast<float*>(smem + L::kXOff);  // [buffer][64 rows][kXC]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // rank = 2 half + view: CTAs 2h and 2h + 1 form the pair that shares the
   // tile's W (views X and Y); in a 4-CTA cluster, CTAs v and v + 2 hold the
@@ -308,12 +313,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       mbar_init(bar(kWFree + b), kSolo ? 1 : 2);  // own (and the peer's) end of GEMM 2
     }
     mbar_init(bar(kEpiSync), 128);
+    mbar_init(bar(kEpiSyncB), 128);
     mbar_init(bar(kGDone), 1);
     mbar_init(bar(kGFree), 128);
     mbar_init(bar(kPhiFree), L::kNAcc);  // one arrival per GEMM 1 issuer
     for (int b = 0; b < 2; ++b) {
-      mbar_init(bar(kXFull + b), 128);  // the other half's epilogue threads
-      mbar_init(bar(kXFree + b), 128);
+      mbar_init(bar(kXFull + b), 4);  // the other half's epilogue warps
+      mbar_init(bar(kXFree + b), 4);
     }
     mbar_init(bar(kFinal), 1);
     mbar_init(bar(kFinal + 1), 1);
@@ -525,7 +531,13 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
-    const int q = warp - 4;             // TMEM lane quarter
+    // Two groups of four warps: group g takes the tiles jg with jg % 2 == g
+    // (their W and GEMM 1 accumulator buffer g), so that the epilogues of
+    // two consecutive tiles run at once; group 0 drains G at segment ends.
+    const int grp = (warp - 4) >> 2;
+    const int q = warp & 3;             // TMEM lane quarter (a warp reaches lanes 32 (warp % 4) ..)
+    const int esync = grp == 0 ? kEpiSync : kEpiSyncB;
+    const int lead = 128 * (grp + 1);   // the group's first thread
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
     const int rg = 32 * q + lane;       // Z column of a G pair block (M = 128 layout)
     bool ok = true;
@@ -537,6 +549,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
       const bool two_acc = L::kNAcc == 2 && (npairs + 1) / 2 < npairs;
       for (int t = 0; t < sv.count; ++t, ++jg) {
         const int b = jg & 1;
+        if (b != grp) continue;
         if (!(ok = mbar_wait(bar(kD1Full + b), (jg >> 1) & 1, abort_flag, wl))) break;
         tc_fence_after();
         float d1[L::kD1Cols];
@@ -594,25 +607,46 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             // ours into the other half's buffer b (once it has read the one
             // of tile jg - 2), take theirs from ours; both CTAs add the same
             // two numbers (a + b == b + a), so they hold the same W
-            const int cb = upper ? kLaneCols : 0;
+            // Row rr of a buffer holds the lanes' column halves at floats
+            // 0 .. 11 and 12 .. 23 (three 16-byte stores each, padded with
+            // zeros when kH1 = 20).  The stores of a warp are released by one
+            // arrival from lane 0 after the warp's barrier, so a barrier
+            // phase counts the four epilogue warps.
+            static_assert(2 * ((kLaneCols + 3) / 4 * 4) <= L::kXC && kLaneCols <= 12, "exchange row");
+            const int xo = rr * L::kXC + (upper ? 12 : 0);
             // (the waits' verdicts are made warp-uniform: the shuffles below
             // need every lane)
             if (jg >= 2 &&
                 !(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFree + b), ((jg - 2) >> 1) & 1, abort_flag, wl))))
               break;
-            const uint32_t rx = map_peer(smem_u32(xbuf + b * kH1 * kRows), hpeer);
+            {
+              float v[12];
 #pragma unroll
-            for (int c0 = 0; c0 < kLaneCols; ++c0) {
-              const uint32_t adr = rx + (uint32_t)(((cb + c0) * kRows + rr) * 4);
-              asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(adr), "f"(xs[c0]) : "memory");
+              for (int c0 = 0; c0 < 12; ++c0) v[c0] = c0 < kLaneCols ? xs[c0 < kLaneCols ? c0 : 0] : 0.f;
+              const uint32_t rx = map_peer(smem_u32(xbuf + b * kRows * L::kXC + xo), hpeer);
+#pragma unroll
+              for (int u = 0; u < 3; ++u) st_cluster_v4(rx + 16 * u, v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
             }
-            mbar_arrive_cluster(map_peer(bar(kXFull + b), hpeer));
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(map_peer(bar(kXFull + b), hpeer));
             if (!(ok = __all_sync(0xffffffffu, mbar_wait_cluster(bar(kXFull + b), (jg >> 1) & 1, abort_flag, wl))))
               break;
-            const float* mine = xbuf + b * kH1 * kRows;
+            {
+              const float4* mine = reinterpret_cast<const float4*>(xbuf + b * kRows * L::kXC + xo);
+              float v[12];
 #pragma unroll
-            for (int c0 = 0; c0 < kLaneCols; ++c0) xs[c0] += mine[(cb + c0) * kRows + rr];
-            mbar_arrive_cluster(map_peer(bar(kXFree + b), hpeer));
+              for (int u = 0; u < 3; ++u) {
+                const float4 t = mine[u];
+                v[4 * u] = t.x;
+                v[4 * u + 1] = t.y;
+                v[4 * u + 2] = t.z;
+                v[4 * u + 3] = t.w;
+              }
+#pragma unroll
+              for (int c0 = 0; c0 < kLaneCols; ++c0) xs[c0] += v[c0];
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(map_peer(bar(kXFree + b), hpeer));
           }
 #pragma unroll
           for (int c0 = 0; c0 < kLaneCols; ++c0) {
@@ -639,11 +673,12 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           }
         }
         fence_proxy_async();
-        mbar_arrive(bar(kEpiSync));
-        if (threadIdx.x == 128) {
+        mbar_arrive(bar(esync));
+        if (threadIdx.x == lead) {
           // all rows written: push this view's rows (hi and lo) into the peer's
-          // buffer b (two views), then release our own GEMM 2
-          if (!(ok = mbar_wait(bar(kEpiSync), jg & 1, abort_flag, wl))) break;
+          // buffer b (two views), then release our own GEMM 2 (the group's
+          // barrier completes once per tile of the group)
+          if (!(ok = mbar_wait(bar(esync), (jg >> 1) & 1, abort_flag, wl))) break;
           if constexpr (!kSolo) {
             const uint32_t pbar = map_peer(bar(kWPeer + b), peer);
 #pragma unroll
@@ -656,13 +691,16 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         }
       }
       if (!ok) break;
-      // this segment's G: drain to its partial slab, then free the
+      // this segment's G (group 0): drain to its partial slab, then free the
       // accumulators for the next segment's GEMM 2
+      if (grp == 0) {
       if (!(ok = mbar_wait(bar(kGDone), sp & 1, abort_flag, wl))) break;
       tc_fence_after();
       {
+        // the slab is column-major (D rows, kNvs k2 columns): the 32 lanes
+        // of a warp hold 32 consecutive rows, so every store of a column is
+        // one 128-byte line
         const int D = sv.d0 + sv.d1;
-        const int k4 = kNvs * sv.k2;  // floats per row of the slab
         const int dv = view == 0 ? sv.d0 : sv.d1;
         for (int p = 0; p < npairs; ++p) {
           float g[L::kN2];
@@ -671,24 +709,26 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
           tmem_ld_wait();
           const int col = 128 * (sv.pb + p) + rg;
           if (col < dv) {
-            float* o = sv.out + (int64_t)(view * sv.d0 + col) * k4;
+            float* o = sv.out + view * sv.d0 + col;
 #pragma unroll
-            for (int c = 0; c < L::kNW; ++c) {
+            for (int c = 0; c < (kSolo ? L::kHalf : L::kNW); ++c) {
               const int vv = c / L::kHalf, cc = c - vv * L::kHalf;
-              if (cc < sv.k2) o[vv * sv.k2 + cc] = g[c] + g[L::kNW + c];  // hi + lo products
+              if (cc < sv.k2) o[(int64_t)(vv * sv.k2 + cc) * D] = g[c] + g[L::kNW + c];  // hi + lo products
             }
           }
         }
-        (void)D;
       }
       tc_fence_before();
       mbar_arrive(bar(kGFree));
+      }
       ++sp;
     }
     if (ok) {
-      // the peer's last end-of-GEMM-2 signals (tiles jg - 2 and jg - 1, not
-      // waited in the loop) must have reached us before we leave
-      for (int j = max(0, jg - 2); j < jg; ++j) mbar_wait(bar(kWFree + (j & 1)), (j >> 1) & 1, abort_flag);
+      // the peer's last end-of-GEMM-2 signal of this group's buffer (tile
+      // jg - 2 or jg - 1, not waited in the loop) must have reached us
+      // before we leave
+      for (int j = max(0, jg - 2); j < jg; ++j)
+        if ((j & 1) == grp) mbar_wait(bar(kWFree + (j & 1)), (j >> 1) & 1, abort_flag);
     }
     tc_fence_before();
   }
@@ -736,11 +776,12 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
 // combined in fixed order.  Error ~2 ulp of the sum, far below the partials'
 // own rounding.
 // `stride` is the distance of the partial slabs (floats, a multiple of 4, at
-// least len); entries len .. stride - 1 of a slab are padding.  With ng > 0
-// the slabs hold one column group (rows of nvs ng: for CCA (nvs = 2) the
-// view-x then the view-y products of group columns 0 .. ng - 1), and entry
-// (row, vv ng + c) goes to G column vv k2 + col0 + c (rows of nvs k2); with
-// ng = 0, G has the slabs' layout.
+// least len); entries len .. stride - 1 of a slab are padding.  A slab is
+// column-major with D = len / (nvs ng) rows: its columns are, for CCA
+// (nvs = 2), the view-x then the view-y products of group columns 0 .. ng - 1
+// (one view: nvs = 1), and entry (row, vv ng + c) goes to G column
+// vv k2 + col0 + c of the row-major G (rows of nvs k2).  A plan with one
+// column group passes ng = k2, col0 = 0.
 __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
                                                         int64_t stride, double* __restrict__ G, const int* done,
                                                         const int* nparts_dev, int ng, int col0, int k2, int nvs) {
@@ -785,16 +826,14 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict_
       out[2] += (double)a.z + (double)c.z;
       out[3] += (double)a.w + (double)c.w;
     }
+    const int64_t D = len / (nvs * ng);
     for (int i = 0; i < 4; ++i) {
       const int64_t idx = 4 * e4 + i;
       if (idx >= len) continue;
-      if (ng == 0) {
-        G[idx] = out[i];
-      } else {
-        const int64_t row = idx / (nvs * ng);
-        const int col = (int)(idx - row * nvs * ng), vv = col / ng, c = col - vv * ng;
-        G[row * nvs * k2 + vv * k2 + col0 + c] = out[i];
-      }
+      const int col = (int)(idx / D);
+      const int64_t row = idx - (int64_t)col * D;
+      const int vv = col / ng, c = col - vv * ng;
+      G[row * nvs * k2 + vv * k2 + col0 + c] = out[i];
     }
   }
 }
@@ -868,9 +907,9 @@ static void tc_group(const Plan& p, int g, int* col0, int* ng) {
   *ng = g == 0 ? ng0 : k2 - ng0;
 }
 // one-view plans (FDA): clusters of two CTAs that split the view's column
-// pairs, GEMM 2 with N = 2 x 24 (an M = 128 MMA needs N a multiple of 16)
+// pairs
 static bool tc_solo(const Plan& p) { return p.kind == kLDA; }
-static int tc_group_h1(const Plan& p, int ng) { return ng <= 20 && !tc_solo(p) ? 20 : tc::kHalfMax; }
+static int tc_group_h1(const Plan& p, int ng) { return ng <= 20 ? 20 : tc::kHalfMax; }
 // views wider than 512 columns: 4-CTA clusters and images of 16 K-boxes
 bool tc_quad(const Plan& p) { return p.kind == kCCA && std::max(p.v[0].d, p.v[1].d) > 512; }
 // bytes between the views' images of a group (one-view plans: 16 K-boxes,
@@ -966,10 +1005,10 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     a.done = done;
     const bool quad = tc_quad(p);
     const int csz = quad ? 4 : 2;  // CTAs per cluster
-    auto kern = solo ? tc::tc_pass_kernel<tc::kHalfMax, false, true>
+    auto kern = solo ? (h1 == 20 ? tc::tc_pass_kernel<20, false, true> : tc::tc_pass_kernel<tc::kHalfMax, false, true>)
                 : quad ? (h1 == 20 ? tc::tc_pass_kernel<20, true> : tc::tc_pass_kernel<tc::kHalfMax, true>)
                        : (h1 == 20 ? tc::tc_pass_kernel<20> : tc::tc_pass_kernel<tc::kHalfMax>);
-    const int smem = solo ? tc::Lay<tc::kHalfMax, false, true>::kSmemBytes
+    const int smem = solo ? (h1 == 20 ? tc::Lay<20, false, true>::kSmemBytes : tc::Lay<tc::kHalfMax, false, true>::kSmemBytes)
                      : quad ? (h1 == 20 ? tc::Lay<20, true>::kSmemBytes : tc::Lay<tc::kHalfMax, true>::kSmemBytes)
                             : (h1 == 20 ? tc::Lay<20>::kSmemBytes : tc::Lay<tc::kHalfMax>::kSmemBytes);
     GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -979,7 +1018,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     attr[0].val.clusterDim.x = csz;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(256, 1, 1);
+    cfg.blockDim = dim3(tc::kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
@@ -1003,7 +1042,7 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     // partial slabs, one per cluster
     const int64_t len = (int64_t)p.D * nv * ng;
     tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), ncl, len, tc_slab(p, ng), p.G,
-                                                             done, nullptr, groups > 1 ? ng : 0, col0, k2, nv);
+                                                             done, nullptr, ng, col0, k2, nv);
     GB_CHECK_LAUNCH();
   }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(
@@ -1237,7 +1276,7 @@ int tc_batch_launch(TcBatch* b, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
   attr[0].val.clusterDim.x = b->csz;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(tc::kThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
@@ -1262,8 +1301,7 @@ int tc_batch_post(const TcBatch* b, int i, Plan& p, cudaStream_t st, const int* 
     tc_group(p, g, &col0, &ng);
     const int64_t len = (int64_t)p.D * 2 * ng;
     tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), 1, len, len, p.G, done,
-                                                             b->nparts_d + b->first[i] + g, groups > 1 ? ng : 0,
-                                                             col0, k2, 2);
+                                                             b->nparts_d + b->first[i] + g, ng, col0, k2, 2);
     GB_CHECK_LAUNCH();
   }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
