@@ -49,8 +49,8 @@ LDA_REFINE = 1
 # from an ncu capture of 131072 rows of this workload (reads scaled by rows
 # to 262144, partial writes as measured).  Valid only for the kernel source
 # it was taken on (SHA-256 below); any other source reports null.
-PASS_TRAFFIC_BYTES = 268.660736e6 * 2 + 7.310848e6
-PASS_TRAFFIC_SRC_SHA256 = "de2a6a224cb1b1884a6ac2a2511519159a6dcaaebf8b72d2657195a0b84e65ce"
+PASS_TRAFFIC_BYTES = 268.583424e6 * 2 + 10.160384e6
+PASS_TRAFFIC_SRC_SHA256 = "24adee6b39f0a461ff8bd5b29faa93909f5a0ec30ccb45e86699e69de2d9320d"
 
 
 def pass_traffic():

@@ -159,7 +159,7 @@ __device__ void blk_jacobi(R* A, R* Q, R* lam, int n, double* rot) {
   __syncthreads();
 }
 
-// The same parallel Jacobi sweeps for n <= 32 by one warp: rotation pairs
+// The same parallel Jacobi sweeps for n <= 40 by one warp: rotation pairs
 // on lanes, warp-level barriers only (the block version spends most of its
 // time in block-wide barriers for matrices this small).  Called by all 32
 // lanes of one warp.
@@ -169,8 +169,9 @@ __device__ void warp_jacobi(R* A, R* Q, R* lam, int n, int max_sweeps = 20, R to
   const int lane = threadIdx.x & 31;
   // rotation tables of this warp (up to 8 warps of a CTA may run their own
   // decompositions side by side)
-  __shared__ R w_cs_all[8][16], w_sn_all[8][16];
-  __shared__ int w_p_all[8][16], w_q_all[8][16];
+  // (n <= 40: at most 20 rotations per round)
+  __shared__ R w_cs_all[8][20], w_sn_all[8][20];
+  __shared__ int w_p_all[8][20], w_q_all[8][20], w_rank_all[8][20];
   const int wslot = (threadIdx.x >> 5) & 7;
   R* w_cs = w_cs_all[wslot];
   R* w_sn = w_sn_all[wslot];
@@ -179,6 +180,7 @@ __device__ void warp_jacobi(R* A, R* Q, R* lam, int n, int max_sweeps = 20, R to
   for (int e = lane; e < n * n; e += 32) Q[e] = (e / n == e % n) ? R(1) : R(0);
   __syncwarp();
   const int m = n + (n & 1);
+  R prev_off = R(-1);
   for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
     R off = 0, dg = 0;
     for (int e = lane; e < n * n; e += 32) {
@@ -189,6 +191,10 @@ __device__ void warp_jacobi(R* A, R* Q, R* lam, int n, int max_sweeps = 20, R to
     off = warp_sum(off);
     dg = warp_sum(dg);
     if (off <= tol * dg || off == R(0)) break;
+    // cyclic Jacobi converges quadratically: a sweep that no longer halves
+    // the off-diagonal mass has reached the rounding floor of R
+    if (prev_off >= R(0) && off > R(0.5) * prev_off) break;
+    prev_off = off;
     for (int r = 0; r < m - 1; ++r) {
       if (lane < m / 2) {
         const int i = lane;
@@ -235,7 +241,33 @@ __device__ void warp_jacobi(R* A, R* Q, R* lam, int n, int max_sweeps = 20, R to
       __syncwarp();
     }
   }
-  if (lane == 0) {  // sort descending, swapping Q columns
+  // sort descending (ties keep the lower index first)
+  if (n <= 20) {
+    // lane i < n finds the position of eigenvalue i, then the lanes move
+    // the columns of Q there
+    int* w_rank = w_rank_all[wslot];
+    const R lv = lane < n ? A[lane * n + lane] : R(0);
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const R lj = __shfl_sync(0xffffffffu, lv, j);
+      if (lj > lv || (lj == lv && j < lane)) ++rank;
+    }
+    if (lane < n) w_rank[lane] = rank;
+    constexpr int kPer = (20 * 20 + 31) / 32;  // entries of Q per lane
+    R qv[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = lane + 32 * u;
+      qv[u] = e < n * n ? Q[e] : R(0);
+    }
+    __syncwarp();
+    if (lane < n) lam[rank] = lv;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int e = lane + 32 * u;
+      if (e < n * n) Q[(e / n) * n + w_rank[e % n]] = qv[u];
+    }
+  } else if (lane == 0) {  // selection sort, swapping Q columns
     for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
     for (int i = 0; i < n; ++i) {
       int b = i;
@@ -777,19 +809,30 @@ __global__ void linesearch_kernel(LSArgs a) {
   if (!last || tid >= 32) return;
   __threadfence();
   if (lane == 0) st->ls_count = 0;
-  volatile const double* fv = a.ls_f;
+  // every trial value at once from L2 (two per lane; the other CTAs' stores
+  // are visible there after their fences and atomics), then the sequential
+  // rule on warp shuffles: all lanes take the same decisions
+  static_assert(kNTrials <= 64, "two trial values per lane");
+  const double fva = lane < (int)gridDim.x ? __ldcg(&a.ls_f[lane]) : 0.0;
+  const double fvb = lane + 32 < (int)gridDim.x ? __ldcg(&a.ls_f[lane + 32]) : 0.0;
+  auto fv = [&](int e) {
+    const double x = __shfl_sync(0xffffffffu, fva, e & 31);
+    const double y = __shfl_sync(0xffffffffu, fvb, e & 31);
+    return e < 32 ? x : y;
+  };
   const double t0 = st->t0, df = st->df;
-  const double f0 = fv[0];
+  const double f0 = fv(0);
   int acc = -1, trials = 1;
   if (zero_step) {
     acc = 0;
-  } else if (fv[1] <= f0 + kC1 * t0 * df) {
+  } else if (fv(1) <= f0 + kC1 * t0 * df) {
     acc = 1;
     trials = 2;
     for (int e = 2; e <= kMaxExpand + 1; ++e) {
       const double te = ls_trial_t(e, t0);
       ++trials;
-      if (fv[e] < fv[acc] && fv[e] <= f0 + kC1 * te * df)
+      const double fe = fv(e);
+      if (fe < fv(acc) && fe <= f0 + kC1 * te * df)
         acc = e;
       else
         break;
@@ -798,7 +841,7 @@ __global__ void linesearch_kernel(LSArgs a) {
     trials = 2;
     for (int e = kMaxExpand + 2; e < (int)gridDim.x; ++e) {
       ++trials;
-      if (fv[e] <= f0 + kC1 * ls_trial_t(e, t0) * df) {
+      if (fv(e) <= f0 + kC1 * ls_trial_t(e, t0) * df) {
         acc = e;
         break;
       }
@@ -828,9 +871,10 @@ __global__ void linesearch_kernel(LSArgs a) {
       st->YW[e] = s;
     }
   }
+  const double f_acc = fv(acc);  // (all lanes: a shuffle)
   if (lane == 0) {
     st->t = t;
-    st->f = fv[acc];
+    st->f = f_acc;
     st->ls_trials = trials;
     if (!zero_step) {
       st->t_prev = t;
@@ -943,11 +987,15 @@ __device__ void blk_sum(double (&v)[NV], double* red) {
   if (lane == 0)
     for (int q = 0; q < NV; ++q) red[q * 8 + w] = v[q];
   __syncthreads();
-  for (int q = 0; q < NV; ++q) {
+  // the warps' sums added once, in warp order, by thread q (FP64 issue is
+  // scarce: all threads repeating them cost more than the rest together)
+  if (threadIdx.x < NV) {
     double t = 0;
-    for (int i = 0; i < nw; ++i) t += red[q * 8 + i];
-    v[q] = t;
+    for (int i = 0; i < nw; ++i) t += red[threadIdx.x * 8 + i];
+    red[NV * 8 + threadIdx.x] = t;
   }
+  __syncthreads();
+  for (int q = 0; q < NV; ++q) v[q] = red[NV * 8 + q];
   __syncthreads();
 }
 
@@ -1126,17 +1174,28 @@ __global__ void direction_kernel(DirArgs a) {
   if (!last) return;
   if (threadIdx.x == 0) {
     __threadfence();
-    volatile double* da = &st->dacc[0][0];
+    // every view's sums at once, from L2 (the other CTA's stores are visible
+    // there after its fence and our atomic)
+    double da[2][6];
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) da[w][q] = w < a.nviews ? __ldcg(&st->dacc[w][q]) : 0.0;
     for (int q = 0; q < 6; ++q) {
       acc[q] = 0;
-      for (int w = 0; w < a.nviews; ++w) acc[q] += da[w * 6 + q];  // view order: deterministic
+      for (int w = 0; w < a.nviews; ++w) acc[q] += da[w][q];  // view order: deterministic
     }
     st->dcount = 0;
   }
   const double gg = acc[0], g_Tg = acc[1], Te_g = acc[2], Te_Tg = acc[3], dfg = acc[4], dfTe = acc[5];
   if (threadIdx.x == 0) {
+    // the state's scalars in one batch of loads (each would otherwise wait
+    // for the stores before it)
+    const int first = st->first, it = st->iter;
+    const double t_prev = st->t_prev, df_prev = st->df_prev, f_cur = st->f, t_cur = st->t;
+    const double gtol = st->gtol, gn0_old = st->gn0;
     double beta = 0;
-    if (!st->first) {
+    if (!first) {
       double num = gg - g_Tg, den = Te_g - Te_Tg;
       beta = den != 0.0 ? fmax(0.0, num / den) : 0.0;
     }
@@ -1146,25 +1205,25 @@ __global__ void direction_kernel(DirArgs a) {
       df = -gg;
     }
     double gn = sqrt(fmax(gg, 0.0));
-    if (st->first) {
+    const double gn0 = first ? gn : gn0_old;
+    if (first) {
       st->gn0 = gn;
       st->t0 = 1.0 / gn;
     } else {
-      st->t0 = st->t_prev * st->df_prev / df;
+      st->t0 = t_prev * df_prev / df;
     }
     st->beta = beta;
     st->df = df;
     st->gn = gn;
-    const int it = st->iter;
     if (a.history != nullptr && it <= a.max_iter) {
-      a.history[3 * it + 0] = st->f;
+      a.history[3 * it + 0] = f_cur;
       a.history[3 * it + 1] = gn;
-      a.history[3 * it + 2] = st->first ? 0.0 : st->t;
+      a.history[3 * it + 2] = first ? 0.0 : t_cur;
     }
     st->first = 0;
     st->force_zero_step = 0;
     st->qsyl_valid = 1;
-    if (!(gn > st->gtol * st->gn0)) {
+    if (!(gn > gtol * gn0)) {
       st->done = 1;
       st->status = GBCCA_OK;
     } else if (it >= a.max_iter) {
