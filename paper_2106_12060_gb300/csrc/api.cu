@@ -48,7 +48,7 @@ void free_plan(Plan* p) {
       dfree(q);
   }
   for (void* q : {(void*)p->h, (void*)p->g, (void*)p->cs_tab, (void*)p->cs_off, (void*)p->perm, p->srht_T,
-                  (void*)p->G, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
+                  (void*)p->G, (void*)p->Gt, (void*)p->Gram, p->Wbuf, p->partG, p->partGram, p->partCls, (void*)p->counts,
                   (void*)p->means, (void*)p->Yhat, (void*)p->Cls, (void*)p->YPhi, (void*)p->clsPart, (void*)p->st,
                   (void*)p->phigram, (void*)p->phipart, (void*)p->phired, (void*)p->cross, (void*)p->crosspart, (void*)p->history, (void*)p->ritz_hist,
                   (void*)p->ws, (void*)p->flag, (void*)p->tc_img, (void*)p->tc_part, (void*)p->mt_part, (void*)p->dfx, (void*)p->ls_f, (void*)p->ls_L})
@@ -64,6 +64,8 @@ void free_plan(Plan* p) {
   if (p->join_ev != nullptr) cudaEventDestroy(p->join_ev);
   if (p->ritz_fork != nullptr) cudaEventDestroy(p->ritz_fork);
   if (p->ritz_join != nullptr) cudaEventDestroy(p->ritz_join);
+  if (p->pass_fork != nullptr) cudaEventDestroy(p->pass_fork);
+  if (p->pass_join != nullptr) cudaEventDestroy(p->pass_join);
   delete p;
 }
 
@@ -184,6 +186,7 @@ int alloc_plan(Plan* p) {
     const int64_t img = (2 * k <= 24 ? 1 : 2) * (tc_cca ? 2 * (dmax > 512 ? 2 : 1) : 2) * 49152;
     GB_TRY(dalloc(&p->tc_img, img));
     GB_CUDA(cudaMemset(p->tc_img, 0, img));
+    GB_TRY(dalloc(&p->Gt, (int64_t)p->D * p->NC));
     GB_TRY(dalloc(&p->tc_part, (int64_t)p->sm_count * p->D * (k4 + 8)));
   }
   GB_TRY(hilo_alloc(*p));
@@ -192,6 +195,8 @@ int alloc_plan(Plan* p) {
   GB_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
   GB_CUDA(cudaEventCreateWithFlags(&p->ritz_fork, cudaEventDisableTiming));
   GB_CUDA(cudaEventCreateWithFlags(&p->ritz_join, cudaEventDisableTiming));
+  GB_CUDA(cudaEventCreateWithFlags(&p->pass_fork, cudaEventDisableTiming));
+  GB_CUDA(cudaEventCreateWithFlags(&p->pass_join, cudaEventDisableTiming));
   if (p->opt.time_passes) {
     for (int i = 0; i < 2 * kMaxTimedBatch; ++i) {
       GB_CUDA(cudaEventCreate(&p->ev[i]));

@@ -782,9 +782,13 @@ __global__ void phi_image_kernel(double* __restrict__ Phix, double* __restrict__
 // (one view: nvs = 1), and entry (row, vv ng + c) goes to G column
 // vv k2 + col0 + c of the row-major G (rows of nvs k2).  A plan with one
 // column group passes ng = k2, col0 = 0.
+// Gt (optional) receives the same values column-major (nvs k2 rows of D):
+// the slabs' order, so these stores are coalesced and the Gram kernel reads
+// them so.
 __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict__ part, int nparts, int64_t len,
                                                         int64_t stride, double* __restrict__ G, const int* done,
-                                                        const int* nparts_dev, int ng, int col0, int k2, int nvs) {
+                                                        const int* nparts_dev, int ng, int col0, int k2, int nvs,
+                                                        double* __restrict__ Gt) {
   if (done != nullptr && *done) return;
   if (nparts_dev != nullptr) nparts = *nparts_dev;  // batched pass: the schedule's slab count
   __shared__ float4 red_s[4][64], red_c[4][64];
@@ -834,15 +838,16 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(const float* __restrict_
       const int64_t row = idx - (int64_t)col * D;
       const int vv = col / ng, c = col - vv * ng;
       G[row * nvs * k2 + vv * k2 + col0 + c] = out[i];
+      if (Gt != nullptr) Gt[(int64_t)(vv * k2 + col0 + c) * D + row] = out[i];
     }
   }
 }
 
 // W^T W = Phi_bd^T G (4k x 4k), Phi_bd = blkdiag(Phi_x, Phi_y), in FP64: one
-// warp per entry, lanes over rows, fixed shuffle tree.  One view (nv = 1,
-// FDA): Phi^T G (2k x 2k).
+// warp per entry, lanes over rows, fixed shuffle tree, G read column-major
+// (Gt: NC rows of D = dx + dy).  One view (nv = 1, FDA): Phi^T G (2k x 2k).
 __global__ void tc_gram_kernel(const double* __restrict__ Phix, const double* __restrict__ Phiy, int dx, int dy,
-                               int k2, int nv, const double* __restrict__ G, double* __restrict__ Gram,
+                               int k2, int nv, const double* __restrict__ Gt, double* __restrict__ Gram,
                                const int* done) {
   if (done != nullptr && *done) return;
   const int k4 = nv * k2;
@@ -855,7 +860,8 @@ __global__ void tc_gram_kernel(const double* __restrict__ Phix, const double* __
   const int d = v == 0 ? dx : dy;
   const int off = v == 0 ? 0 : dx;
   double s = 0;
-  for (int j = lane; j < d; j += 32) s += Phi[(int64_t)j * k2 + ca] * G[(int64_t)(off + j) * k4 + b];
+  const double* gb = Gt + (int64_t)b * (dx + dy) + off;
+  for (int j = lane; j < d; j += 32) s += Phi[(int64_t)j * k2 + ca] * gb[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) Gram[e] = s;
@@ -1036,17 +1042,22 @@ int tc_pass(Plan& p, cudaStream_t st, const int* done) {
     GB_CHECK_LAUNCH();
   }
   if (p.kev1 != nullptr) GB_CUDA(record_timing_event(p.kev1, st));
+  if (p.fork_after_pass) {
+    // work that needs only Phi may start beside the reduction
+    GB_CUDA(cudaEventRecord(p.pass_fork, st));
+    p.pass_forked = true;
+  }
   for (int g = 0; g < groups; ++g) {
     int col0 = 0, ng = 0;
     tc_group(p, g, &col0, &ng);
     // partial slabs, one per cluster
     const int64_t len = (int64_t)p.D * nv * ng;
     tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), ncl, len, tc_slab(p, ng), p.G,
-                                                             done, nullptr, ng, col0, k2, nv);
+                                                             done, nullptr, ng, col0, k2, nv, p.Gt);
     GB_CHECK_LAUNCH();
   }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(
-      p.v[0].Phi, nv > 1 ? p.v[1].Phi : p.v[0].Phi, p.v[0].d, nv > 1 ? p.v[1].d : 0, k2, nv, p.G, p.Gram, done);
+      p.v[0].Phi, nv > 1 ? p.v[1].Phi : p.v[0].Phi, p.v[0].d, nv > 1 ? p.v[1].d : 0, k2, nv, p.Gt, p.Gram, done);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }
@@ -1301,11 +1312,11 @@ int tc_batch_post(const TcBatch* b, int i, Plan& p, cudaStream_t st, const int* 
     tc_group(p, g, &col0, &ng);
     const int64_t len = (int64_t)p.D * 2 * ng;
     tc::tc_reduce_kernel<<<ceil_div(len, 256), 256, 0, st>>>(tc_group_part(p, g), 1, len, len, p.G, done,
-                                                             b->nparts_d + b->first[i] + g, ng, col0, k2, 2);
+                                                             b->nparts_d + b->first[i] + g, ng, col0, k2, 2, p.Gt);
     GB_CHECK_LAUNCH();
   }
   tc::tc_gram_kernel<<<ceil_div(k4 * k4 * 32, 256), 256, 0, st>>>(p.v[0].Phi, p.v[1].Phi, p.v[0].d, p.v[1].d, k2,
-                                                                  2, p.G, p.Gram, done);
+                                                                  2, p.Gt, p.Gram, done);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }

@@ -101,6 +101,7 @@ struct Plan {
 
   // pass buffers
   double* G = nullptr;        // D x NC
+  double* Gt = nullptr;       // NC x D: G column-major (tensor-core pass plans), for the Gram
   double* Gram = nullptr;     // NC x NC
   void* Wbuf = nullptr;       // n x NC (pass intermediate)
   void* partG = nullptr;      // chunksB x D x NC
@@ -157,6 +158,11 @@ struct Plan {
   cudaStream_t side_stream = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaEvent_t ritz_fork = nullptr, ritz_join = nullptr;  // the Ritz-check branch of an iteration
+  // an iteration's Phi Gram on a branch beside the pass reduction: the
+  // solver asks for it (fork_after_pass), the tensor-core pass records
+  // pass_fork after its data kernels (pass_forked)
+  cudaEvent_t pass_fork = nullptr, pass_join = nullptr;
+  bool fork_after_pass = false, pass_forked = false;
   cudaGraphExec_t batch_exec = nullptr;
   const void* batch_key_ptr[3] = {nullptr, nullptr, nullptr};
   int batch_key_n = 0;

@@ -1807,7 +1807,17 @@ int thin_blocks(const Plan& p) {
 int iteration_post(Plan& p, bool low, cudaStream_t st) {
   const int k = p.k, kk = k * k;
   const int* done = &p.st->done;
-  GB_TRY(phigram(p, st, done, p.phired));
+  if (p.pass_forked) {
+    // the Phi Gram (Phi is final once the pass has rounded it) on the side
+    // branch, beside the reduction and the Gram of the pass on `st`
+    GB_CUDA(cudaStreamWaitEvent(p.side_stream, p.pass_fork, 0));
+    GB_TRY(phigram(p, p.side_stream, done, p.phired));
+    GB_CUDA(cudaEventRecord(p.pass_join, p.side_stream));
+    GB_CUDA(cudaStreamWaitEvent(st, p.pass_join, 0));
+    p.pass_forked = false;
+  } else {
+    GB_TRY(phigram(p, st, done, p.phired));
+  }
   GB_TRY(yphi(p, st, 1));
   const bool ritz = p.opt.rtol > 0;
   if (ritz) {
@@ -1960,7 +1970,10 @@ namespace {
 int iteration(Plan& p, bool low, cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   p.kev0 = e0;
   p.kev1 = e1;
+  p.pass_forked = false;
+  p.fork_after_pass = true;
   const int prc = fused_pass(p, low, false, st, 0, &p.st->done);
+  p.fork_after_pass = false;
   p.kev0 = p.kev1 = nullptr;
   GB_TRY(prc);
   return iteration_post(p, low, st);
