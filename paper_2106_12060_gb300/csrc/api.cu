@@ -338,21 +338,24 @@ int precondition_common(Plan& p, const int32_t* sh, const int8_t* sg, cudaStream
       GB_TRY(gram_tn(w.SZ, w.d, w.SZ, w.d, p.s, w.d, w.d, w.R, w.lam, p.ws, p.ws_len, st));
     }
   }
-  // The views' blocked Cholesky factorizations touch only their own R (and
-  // the error flag) and are latency bound: view 1 runs on the plan's side
-  // stream, between a fork and a join event, while view 0 runs on `st`.
+  // The views' blocked Cholesky factorizations and triangular inverses touch
+  // only their own R, R^{-1}, workspace half (and the error flag) and are
+  // latency bound: view 1 runs on the plan's side stream, between a fork and
+  // a join event, while view 0 runs on `st`.
   if (p.nviews > 1) {
+    const int64_t half = p.ws_len / 2;
     GB_CUDA(cudaEventRecord(p.fork_ev, st));
     GB_CUDA(cudaStreamWaitEvent(p.side_stream, p.fork_ev, 0));
     GB_TRY(cholesky_upper(p.v[1].R, p.v[1].d, p.flag, p.side_stream));
+    GB_TRY(tri_inverse_upper(p.v[1].R, p.v[1].Rinv, p.v[1].d, p.ws + half, p.ws_len - half, p.side_stream));
     GB_TRY(cholesky_upper(p.v[0].R, p.v[0].d, p.flag, st));
+    GB_TRY(tri_inverse_upper(p.v[0].R, p.v[0].Rinv, p.v[0].d, p.ws, half, st));
     GB_CUDA(cudaEventRecord(p.join_ev, p.side_stream));
     GB_CUDA(cudaStreamWaitEvent(st, p.join_ev, 0));
   } else {
     GB_TRY(cholesky_upper(p.v[0].R, p.v[0].d, p.flag, st));
+    GB_TRY(tri_inverse_upper(p.v[0].R, p.v[0].Rinv, p.v[0].d, p.ws, p.ws_len, st));
   }
-  // the triangular inverses share the split-K workspace: one after the other
-  for (int v = 0; v < p.nviews; ++v) GB_TRY(tri_inverse_upper(p.v[v].R, p.v[v].Rinv, p.v[v].d, p.ws, p.ws_len, st));
   GB_TRY(read_flag(p, st));
   for (int v = 0; v < p.nviews; ++v) GB_TRY(finish_factor(p, v, st));
   if (p.opt.warm_start) {

@@ -552,9 +552,12 @@ __global__ void __launch_bounds__(128) chol_diag_kernel(double* A, int d, int p,
   }
 }
 
-// A[i-block, p] <- A[i-block, p] L_pp^{-T}: each thread solves one row by
-// forward substitution with L_pp.
-__global__ void chol_trsm_kernel(double* A, int d, int p) {
+// A[i-block, p] <- A[i-block, p] L_pp^{-T}: one warp per row, lane c holding
+// x_c; forward substitution in column order, each solved x_c broadcast by a
+// shuffle to the lanes that still subtract it (the same multiply-adds, in the
+// same order, as a serial substitution of the row).
+constexpr int kTrsmRows = 8;  // rows (warps) per CTA
+__global__ void __launch_bounds__(32 * kTrsmRows) chol_trsm_kernel(double* A, int d, int p) {
   __shared__ double L[kNB][kNB + 1];
   __shared__ double rinv[kNB];
   const int o = p * kNB, nb = min(kNB, d - o);
@@ -565,23 +568,17 @@ __global__ void chol_trsm_kernel(double* A, int d, int p) {
   __syncthreads();
   if (threadIdx.x < kNB) rinv[threadIdx.x] = threadIdx.x < nb ? 1.0 / L[threadIdx.x][threadIdx.x] : 1.0;
   __syncthreads();
-  const int row = o + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= d) return;
-  double x[kNB];
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) x[c] = c < nb ? A[(int64_t)row * d + o + c] : 0.0;
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) {
-    if (c < nb) {
-      double s = x[c];
-#pragma unroll
-      for (int q = 0; q < c; ++q) s -= L[c][q] * x[q];
-      x[c] = s * rinv[c];
-    }
+  const int lane = threadIdx.x & 31;
+  const int row = o + nb + blockIdx.x * kTrsmRows + (threadIdx.x >> 5);
+  if (row >= d) return;  // uniform over the warp
+  double acc = lane < nb ? A[(int64_t)row * d + o + lane] : 0.0;
+  double x = 0.0;
+  for (int c = 0; c < nb; ++c) {
+    if (lane == c) x = acc * rinv[c];
+    const double xc = __shfl_sync(0xffffffffu, x, c);
+    if (lane > c) acc -= L[lane][c] * xc;
   }
-#pragma unroll
-  for (int c = 0; c < kNB; ++c)
-    if (c < nb) A[(int64_t)row * d + o + c] = x[c];
+  if (lane < nb) A[(int64_t)row * d + o + lane] = x;
 }
 
 // trailing update A[I, J] -= A[I, p] A[J, p]^T for block pairs I >= J > p.
@@ -623,7 +620,7 @@ int cholesky_upper(double* A, int d, int* flag, cudaStream_t st) {
     GB_CHECK_LAUNCH();
     int below = d - (p + 1) * kNB;
     if (below > 0) {
-      chol_trsm_kernel<<<ceil_div(below, 64), 64, 0, st>>>(A, d, p);
+      chol_trsm_kernel<<<ceil_div(below, kTrsmRows), 32 * kTrsmRows, 0, st>>>(A, d, p);
       GB_CHECK_LAUNCH();
       int nt = nbk - p - 1;
       chol_syrk_kernel<<<dim3(nt, nt), 256, 0, st>>>(A, d, p);

@@ -2293,17 +2293,23 @@ __global__ void small_chol_kernel(const double* part, int nblk, int c, double* o
   }
 }
 
-// B (d x c) <- B Rinv (c x c upper), rows in parallel
-__global__ void apply_small_kernel(double* B, int d, int c, const double* Rinv) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d) return;
-  double row[2 * kMaxK];
-  for (int q = 0; q < c; ++q) row[q] = B[(int64_t)j * c + q];
-  for (int q = 0; q < c; ++q) {
-    double s = 0;
-    for (int r = 0; r <= q; ++r) s += row[r] * Rinv[r * c + q];
-    B[(int64_t)j * c + q] = s;
-  }
+// B (d x c) <- B Rinv (c x c upper): a CTA stages kApplyRows rows of B in
+// shared memory and each thread forms one entry (at most c multiply-adds),
+// so the FP64 work spreads over many SMs instead of one chain per row.
+constexpr int kApplyRows = 8;
+__global__ void __launch_bounds__(kApplyRows * 2 * kMaxK) apply_small_kernel(double* B, int d, int c,
+                                                                            const double* Rinv) {
+  __shared__ double rows[kApplyRows * 2 * kMaxK];
+  const int j0 = blockIdx.x * kApplyRows;
+  const int nr = min(kApplyRows, d - j0);
+  for (int e = threadIdx.x; e < nr * c; e += blockDim.x) rows[e] = B[(int64_t)j0 * c + e];
+  __syncthreads();
+  const int e = threadIdx.x;
+  if (e >= nr * c) return;
+  const int r = e / c, q = e - r * c;
+  double s = 0;
+  for (int t = 0; t <= q; ++t) s += rows[r * c + t] * Rinv[t * c + q];
+  B[(int64_t)(j0 + r) * c + q] = s;
 }
 
 // Rayleigh-Ritz of the power iteration: Bsmall = U^T (C V) (c x c), take the
@@ -2382,7 +2388,7 @@ int orth(Plan& p, double* B, int d, int c, double* part, double* small, cudaStre
   GB_CHECK_LAUNCH();
   small_chol_kernel<<<1, 256, sizeof(double) * (2 * c * c + c), st>>>(part, a.nblk, c, small, p.flag);
   GB_CHECK_LAUNCH();
-  apply_small_kernel<<<ceil_div(d, 128), 128, 0, st>>>(B, d, c, small);
+  apply_small_kernel<<<ceil_div(d, kApplyRows), kApplyRows * 2 * kMaxK, 0, st>>>(B, d, c, small);
   GB_CHECK_LAUNCH();
   return GBCCA_OK;
 }
