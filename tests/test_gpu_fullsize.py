@@ -143,7 +143,7 @@ def test_lda_workload(gb, name):
     c = P["config"]
     lam = 1e-6 * float(np.trace(OL.scatters(P["X64"], P["y"], c["l"])[1])) / c["d"]
     import bench
-    o = gb.default_options(s=c["s"], max_iter=1000, gtol=0.0, rtol=bench.RTOL, check_every=bench.CHECK_EVERY,
+    o = gb.default_options(s=c["s"], max_iter=1000, gtol=0.0, rtol=bench.RTOL, check_every=bench.LDA_CHECK_EVERY,
                            refine=bench.LDA_REFINE)
     plan = gb.lda_plan(c["n"], c["d"], c["l"], c["k"], c["dtype"], o)
     X = to_dev(P["X"], c["dtype"])
